@@ -1,0 +1,579 @@
+/*
+ * airpf_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, sequential FP64 CPU restatement of the Augmented Island
+ * Resampling Particle Filter (AIRPF) of Heine, "Augmented Island Resampling
+ * Particle Filters for Particle Markov Chain Monte Carlo" (arXiv 2312.06484),
+ * Algorithm 1, of the bootstrap particle filter (BPF) it reduces to for m = 1
+ * (Section 2), and of particle marginal Metropolis-Hastings (Section 1.2).
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may
+ * load this library.  It shares no code, header, table or constant generator
+ * with the CUDA path; the two meet only through the written random-stream
+ * specification below and the seeded inputs of the `synth` module.
+ *
+ * Random streams (counter-based, Philox4x32-10 of Salmon et al., SC'11):
+ *   key     = (seed & 0xffffffff, seed >> 32)
+ *   counter = (unit, t, iter, (chain << 8) | (kind << 5) | sub)
+ *   kind 0 INIT  : prior draw of particle unit = k*M+i, t = 0, sub = normal pair b
+ *   kind 1 STEP  : time t >= 1, unit = k*M+i, sub = normal pair b;
+ *                  word 2 of sub 0 is the internal-resampling uniform of draw i
+ *   kind 2 ISLAND: time t, unit = island j, sub = interaction stage s; word 0
+ *   kind 3 MH    : PMMH iteration `iter`, t = 0; sub 0 unit b -> proposal
+ *                  normals 2b, 2b+1; sub 1 unit 0 word 0 -> accept uniform
+ *   uniform(w)    = (w + 0.5) * 2^-32
+ *   normals(w0,w1): r = sqrt(-2 ln u(w0)), a = 2 pi u(w1); (r cos a, r sin a)
+ *   the normal of dimension d is component (d & 1) of pair b = d >> 1.
+ *
+ * Readings of the paper taken here (the paper is silent on them):
+ *   - time t = 1..T propagates x_{t-1} -> x_t (x_0 ~ prior), then weights
+ *     with y_t: Algorithm 1 with pi_0 := law(x_1);
+ *   - internal resampling is multinomial: draw j picks the first i with
+ *     C_i > u_j * C_{M-1}, C the sequential FP64 CDF (Section 3.3, eq. (22));
+ *   - an island whose particle weights are all zero keeps a_j = j;
+ *   - a stage picks, for island k, the lower island of the pair
+ *     {k, k xor 2^(s-1)} iff u * (W_lo + W_hi) < W_lo, one uniform per
+ *     (t, s, k), independently over k (Section 3.3, eqs. (28)-(29));
+ *   - adaptive interaction uses the strict test ENF < tau (Algorithm 1);
+ *   - a NaN log-weight counts as -inf (weight zero).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ----------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, Section 4)             */
+/* ----------------------------------------------------------------------- */
+void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {            /* Weyl key schedule between rounds */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+enum { KIND_INIT = 0, KIND_STEP = 1, KIND_ISLAND = 2, KIND_MH = 3 };
+enum { MODEL_AR1 = 0, MODEL_SV = 1, MODEL_NGM = 2, MODEL_LGSSM = 3, MODEL_TOY = 4 };
+enum { MODE_NEVER = 0, MODE_ALWAYS = 1, MODE_ADAPTIVE = 2 };
+enum { TIE_NONE = 0, TIE_RESAMPLE = 1, TIE_ISLAND = 2, TIE_ENF = 3 };
+
+#define TIE_REL 1e-12
+
+typedef struct {
+    uint64_t seed;
+    uint32_t chain;
+    uint32_t iter;
+} stream_id;
+
+static void draw(const stream_id* s, uint32_t unit, uint32_t t, uint32_t kind,
+                 uint32_t sub, uint32_t out[4])
+{
+    uint32_t ctr[4] = { unit, t, s->iter, (s->chain << 8) | (kind << 5) | sub };
+    uint32_t key[2] = { (uint32_t)(s->seed & 0xffffffffu), (uint32_t)(s->seed >> 32) };
+    oracle_philox(ctr, key, out);
+}
+
+static double unif(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+
+static void normal_pair(uint32_t w0, uint32_t w1, double* n0, double* n1)
+{
+    double rad = sqrt(-2.0 * log(unif(w0)));
+    double ang = 2.0 * M_PI * unif(w1);
+    *n0 = rad * cos(ang);
+    *n1 = rad * sin(ang);
+}
+
+/* fills z[0..n-1] with the normals of (kind, unit, t); returns word 2 of
+ * sub-block 0 and word 0 of sub-block 0 through w2/w0 when non-NULL */
+static void normals(const stream_id* s, uint32_t kind, uint32_t unit, uint32_t t,
+                    int n, double* z, uint32_t* w0, uint32_t* w2)
+{
+    int pairs = n > 0 ? (n + 1) / 2 : 1;
+    for (int b = 0; b < pairs; ++b) {
+        uint32_t w[4];
+        draw(s, unit, t, kind, (uint32_t)b, w);
+        if (b == 0) {
+            if (w0) *w0 = w[0];
+            if (w2) *w2 = w[2];
+        }
+        if (n > 0) {
+            double a, c;
+            normal_pair(w[0], w[1], &a, &c);
+            if (2 * b < n) z[2 * b] = a;
+            if (2 * b + 1 < n) z[2 * b + 1] = c;
+        }
+    }
+}
+
+/* ----------------------------------------------------------------------- */
+/* State-space models (Section 1.2, eq. (1)); parameter layout in synth/.  */
+/* ----------------------------------------------------------------------- */
+typedef struct {
+    int model, dx, dy;
+    const double* th;   /* model parameters */
+    const double* md;   /* LGSSM: A (dx*dx row-major) then C (dy*dx) */
+} model_t;
+
+int oracle_model_valid(int model, int dx, const double* th)
+{
+    switch (model) {
+    case MODEL_AR1: return th[1] > 0 && th[2] > 0 && th[3] > 0;
+    case MODEL_SV:  return fabs(th[1]) < 1.0 && th[2] > 0;
+    case MODEL_NGM: return th[0] > 0 && th[1] > 0 && th[2] > 0;
+    case MODEL_TOY: return th[0] > 0 && th[0] < 1 && th[1] > 0 && th[1] < 1;
+    case MODEL_LGSSM: return isfinite(th[dx]) && isfinite(th[dx + 1]);
+    }
+    return 0;
+}
+
+static void prior_sample(const model_t* md, const stream_id* s, uint32_t unit, double* x)
+{
+    double z[64];
+    uint32_t w0;
+    int nz = md->model == MODEL_TOY ? 0 : md->dx;
+    normals(s, KIND_INIT, unit, 0, nz, z, &w0, NULL);
+    const double* th = md->th;
+    switch (md->model) {
+    case MODEL_AR1: x[0] = th[3] * z[0]; break;
+    case MODEL_SV:  x[0] = th[0] + th[2] / sqrt(1.0 - th[1] * th[1]) * z[0]; break;
+    case MODEL_NGM: x[0] = sqrt(th[2]) * z[0]; break;
+    case MODEL_TOY: x[0] = unif(w0) < 0.5 ? 0.0 : 1.0; break;
+    case MODEL_LGSSM:
+        for (int d = 0; d < md->dx; ++d) x[d] = z[d];
+        break;
+    }
+}
+
+/* x_t ~ K_t(x_{t-1}, .); returns the internal-resampling word of this unit */
+static uint32_t transition(const model_t* md, const stream_id* s, uint32_t unit,
+                           uint32_t t, const double* xp, double* x)
+{
+    double z[64];
+    uint32_t w0, w2;
+    int nz = md->model == MODEL_TOY ? 0 : md->dx;
+    normals(s, KIND_STEP, unit, t, nz, z, &w0, &w2);
+    const double* th = md->th;
+    switch (md->model) {
+    case MODEL_AR1: x[0] = th[0] * xp[0] + th[1] * z[0]; break;
+    case MODEL_SV:  x[0] = th[0] + th[1] * (xp[0] - th[0]) + th[2] * z[0]; break;
+    case MODEL_NGM: {
+        double v = xp[0];
+        x[0] = 0.5 * v + 25.0 * v / (1.0 + v * v) + 8.0 * cos(1.2 * (double)t) + sqrt(th[0]) * z[0];
+        break;
+    }
+    case MODEL_TOY:
+        x[0] = unif(w0) < 1.0 - th[0] ? 1.0 - xp[0] : xp[0];
+        break;
+    case MODEL_LGSSM: {
+        int dx = md->dx;
+        const double* A = md->md;
+        double sq = sqrt(exp(th[dx]));
+        for (int r = 0; r < dx; ++r) {
+            double acc = 0.0;
+            for (int c = 0; c < dx; ++c) {
+                double a = (r == c) ? th[r] : A[r * dx + c];
+                acc += a * xp[c];
+            }
+            x[r] = acc + sq * z[r];
+        }
+        break;
+    }
+    }
+    return w2;
+}
+
+static double log_g(const model_t* md, const double* y, const double* x)
+{
+    const double* th = md->th;
+    const double half_log_2pi = 0.5 * log(2.0 * M_PI);
+    double l = -INFINITY;
+    switch (md->model) {
+    case MODEL_AR1: {
+        double e = (y[0] - x[0]) / th[2];
+        l = -half_log_2pi - log(th[2]) - 0.5 * e * e;
+        break;
+    }
+    case MODEL_SV:
+        l = -half_log_2pi - 0.5 * x[0] - 0.5 * y[0] * y[0] * exp(-x[0]);
+        break;
+    case MODEL_NGM: {
+        double e = y[0] - x[0] * x[0] / 20.0;
+        l = -0.5 * log(2.0 * M_PI * th[1]) - e * e / (2.0 * th[1]);
+        break;
+    }
+    case MODEL_TOY:
+        l = (y[0] == x[0]) ? log(th[1]) : log(1.0 - th[1]);
+        break;
+    case MODEL_LGSSM: {
+        int dx = md->dx, dy = md->dy;
+        const double* C = md->md + dx * dx;
+        double r = exp(th[dx + 1]);
+        double ss = 0.0;
+        for (int o = 0; o < dy; ++o) {
+            double e = y[o];
+            for (int c = 0; c < dx; ++c) e -= C[o * dx + c] * x[c];
+            ss += e * e;
+        }
+        l = -0.5 * dy * log(2.0 * M_PI * r) - ss / (2.0 * r);
+        break;
+    }
+    }
+    if (!(l > -INFINITY)) l = -INFINITY;   /* NaN counts as weight zero */
+    return l;
+}
+
+/* exported single-particle model calls (pinned in the tests) */
+double oracle_model_logg(int model, int dx, int dy, const double* th, const double* mdat,
+                         const double* y, const double* x)
+{
+    model_t md = { model, dx, dy, th, mdat };
+    return log_g(&md, y, x);
+}
+
+void oracle_model_prior(int model, int dx, int dy, const double* th, const double* mdat,
+                        uint64_t seed, uint32_t chain, uint32_t iter, uint32_t unit, double* x)
+{
+    model_t md = { model, dx, dy, th, mdat };
+    stream_id s = { seed, chain, iter };
+    prior_sample(&md, &s, unit, x);
+}
+
+void oracle_model_step(int model, int dx, int dy, const double* th, const double* mdat,
+                       uint64_t seed, uint32_t chain, uint32_t iter, uint32_t unit, uint32_t t,
+                       const double* xp, double* x)
+{
+    model_t md = { model, dx, dy, th, mdat };
+    stream_id s = { seed, chain, iter };
+    transition(&md, &s, unit, t, xp, x);
+}
+
+/* ----------------------------------------------------------------------- */
+/* helpers                                                                  */
+/* ----------------------------------------------------------------------- */
+static double log_sum_exp(const double* v, int n)
+{
+    double mx = -INFINITY;
+    for (int i = 0; i < n; ++i) if (v[i] > mx) mx = v[i];
+    if (mx == -INFINITY) return -INFINITY;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += exp(v[i] - mx);
+    return mx + log(s);
+}
+
+/* effective number of filters (Algorithm 1): (m^-1 sum W)^2 / (m^-1 sum W^2),
+ * from log-weights; 0 when every weight is zero */
+static double enf_of(const double* lw, int m)
+{
+    double mx = -INFINITY;
+    for (int k = 0; k < m; ++k) if (lw[k] > mx) mx = lw[k];
+    if (mx == -INFINITY) return 0.0;
+    double s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double w = exp(lw[k] - mx);
+        s1 += w;
+        s2 += w * w;
+    }
+    return (s1 / m) * (s1 / m) / (s2 / m);
+}
+
+/* Multinomial internal resampling of one island (Algorithm 1, internal
+ * resample): draw j takes the first i with C_i > u_j * C_{M-1}.  Returns 1 if
+ * some draw fell within TIE_REL * C_{M-1} of a CDF boundary. */
+static int resample_island(const double* l, int M, const uint32_t* wres,
+                           double* cdf, int32_t* a)
+{
+    double mx = -INFINITY;
+    for (int i = 0; i < M; ++i) if (l[i] > mx) mx = l[i];
+    if (mx == -INFINITY) {                 /* all weights zero */
+        for (int j = 0; j < M; ++j) a[j] = j;
+        return 0;
+    }
+    double acc = 0.0;
+    for (int i = 0; i < M; ++i) {
+        acc += exp(l[i] - mx);
+        cdf[i] = acc;
+    }
+    double total = cdf[M - 1];
+    int tie = 0;
+    for (int j = 0; j < M; ++j) {
+        double target = unif(wres[j]) * total;
+        int i = 0;
+        while (i < M - 1 && !(cdf[i] > target)) ++i;
+        a[j] = i;
+        double tol = TIE_REL * total;
+        if (fabs(cdf[i] - target) < tol) tie = 1;
+        if (i > 0 && fabs(cdf[i - 1] - target) < tol) tie = 1;
+    }
+    return tie;
+}
+
+static int ilog2(int m)
+{
+    int s = 0;
+    while ((1 << s) < m) ++s;
+    return s;
+}
+
+/* ----------------------------------------------------------------------- */
+/* AIRPF, Algorithm 1, one stage at a time.                                 */
+/* ----------------------------------------------------------------------- */
+typedef struct {
+    double* logz;        /* [1] log Z^N_T = log (m^-1 sum_k W^k) */
+    double* logz_trace;  /* [T] log Z^N_t after step t, or NULL */
+    int32_t* anc;        /* [T*N] parent (among the time-t particles) of the
+                            particle k*M+i held after step t, or NULL */
+    int32_t* src;        /* [T*m] island whose block island k holds after step t */
+    double* enf;         /* [T*(S+1)] ENF_{t,0..S}, or NULL */
+    int32_t* sstar;      /* [T] first non-interacting stage (S+1 if all interact) */
+    double* xfinal;      /* [N*dx] particles after step T (before mutation), or NULL */
+    int32_t* tie;        /* [2] first flagged tie: time t (0 = none) and kind */
+} airpf_out;
+
+int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, double tau,
+                 uint64_t seed, uint32_t chain, uint32_t iter,
+                 const double* theta, const double* mdat, const double* y,
+                 double* logz, double* logz_trace, int32_t* anc, int32_t* src,
+                 double* enf, int32_t* sstar, double* xfinal, int32_t* tie)
+{
+    if (m < 1 || (m & (m - 1)) || M < 1 || T < 1 || dx < 1 || dx > 64 || dy < 1) return 1;
+    if (!(tau > 0.0 && tau <= 1.0)) return 1;
+    const int N = m * M, S = ilog2(m);
+    model_t md = { model, dx, dy, theta, mdat };
+    stream_id st = { seed, chain, iter };
+
+    double* xa = malloc(sizeof(double) * N * dx);   /* parents of this step */
+    double* x = malloc(sizeof(double) * N * dx);    /* propagated particles */
+    double* xr = malloc(sizeof(double) * N * dx);   /* internally resampled */
+    double* l = malloc(sizeof(double) * N);
+    double* cdf = malloc(sizeof(double) * N);
+    uint32_t* wres = malloc(sizeof(uint32_t) * N);
+    int32_t* a = malloc(sizeof(int32_t) * N);
+    double* lw = malloc(sizeof(double) * m);        /* log W^k */
+    double* lw2 = malloc(sizeof(double) * m);
+    int* idx = malloc(sizeof(int) * m);
+    int* idx2 = malloc(sizeof(int) * m);
+    int* tie_isl = calloc((size_t)m, sizeof(int));
+    if (tie) { tie[0] = 0; tie[1] = TIE_NONE; }
+
+    /* initialisation: W^k_{0,0} = 1, particles from the prior */
+    for (int g = 0; g < N; ++g) prior_sample(&md, &st, (uint32_t)g, xa + (size_t)g * dx);
+    for (int k = 0; k < m; ++k) lw[k] = 0.0;
+
+    for (int t = 1; t <= T; ++t) {
+        const double* yt = y + (size_t)(t - 1) * dy;
+        int tie_now = TIE_NONE;
+        /* ENF_{t,0} (diagnostic, Algorithm 1) */
+        if (enf) enf[(size_t)(t - 1) * (S + 1)] = enf_of(lw, m);
+
+        /* mutation of every island's block through K_t, then weighting */
+        #pragma omp parallel for schedule(static)
+        for (int k = 0; k < m; ++k) {
+            for (int i = 0; i < M; ++i) {
+                int g = k * M + i;
+                wres[g] = transition(&md, &st, (uint32_t)g, (uint32_t)t, xa + (size_t)g * dx,
+                                     x + (size_t)g * dx);
+                l[g] = log_g(&md, yt, x + (size_t)g * dx);
+            }
+            /* W^k_{t,1} = W^k_{t,0} * M^-1 sum_i g_t(xi^{k,i}) */
+            lw[k] += log_sum_exp(l + (size_t)k * M, M) - log((double)M);
+            /* internal resampling within island k */
+            tie_isl[k] = resample_island(l + (size_t)k * M, M, wres + (size_t)k * M,
+                                         cdf + (size_t)k * M, a + (size_t)k * M);
+            for (int j = 0; j < M; ++j)
+                memcpy(xr + ((size_t)k * M + j) * dx, x + ((size_t)k * M + a[k * M + j]) * dx,
+                       sizeof(double) * dx);
+        }
+        for (int k = 0; k < m; ++k) if (tie_isl[k]) tie_now = TIE_RESAMPLE;
+
+        /* interaction stages s = 1..S (butterfly matrices A_s) */
+        for (int k = 0; k < m; ++k) idx[k] = k;
+        int first_quiet = S + 1;
+        for (int s = 1; s <= S; ++s) {
+            double e = enf_of(lw, m);
+            if (enf) enf[(size_t)(t - 1) * (S + 1) + s] = e;
+            int interact = (mode == MODE_ALWAYS) || (mode == MODE_ADAPTIVE && e < tau);
+            if (mode == MODE_ADAPTIVE && fabs(e - tau) < TIE_REL * tau && tie_now == TIE_NONE)
+                tie_now = TIE_ENF;
+            if (!interact) {
+                if (first_quiet == S + 1) first_quiet = s;
+                continue;            /* alpha_s = I: weights and blocks unchanged */
+            }
+            int b = 1 << (s - 1);
+            for (int k = 0; k < m; ++k) {
+                int lo = k & ~b, hi = k | b;
+                double ref = lw[lo] > lw[hi] ? lw[lo] : lw[hi];
+                double wlo = 0.0, whi = 0.0;
+                if (ref > -INFINITY) {
+                    wlo = exp(lw[lo] - ref);
+                    whi = exp(lw[hi] - ref);
+                }
+                uint32_t w[4];
+                draw(&st, (uint32_t)k, (uint32_t)t, KIND_ISLAND, (uint32_t)s, w);
+                double lhs = unif(w[0]) * (wlo + whi);
+                int pick = (lhs < wlo) ? lo : hi;
+                if (fabs(lhs - wlo) < TIE_REL * (wlo + whi) && tie_now == TIE_NONE)
+                    tie_now = TIE_ISLAND;
+                idx2[k] = idx[pick];
+                /* W^k_{t,s+1} = sum_l alpha_s^{kl} W^l_{t,s} = (W_lo + W_hi)/2 */
+                lw2[k] = (ref > -INFINITY) ? ref + log(0.5 * (wlo + whi)) : -INFINITY;
+            }
+            memcpy(idx, idx2, sizeof(int) * m);
+            memcpy(lw, lw2, sizeof(double) * m);
+        }
+
+        /* island k now holds the internally resampled block of island idx[k] */
+        for (int k = 0; k < m; ++k) {
+            memcpy(xa + (size_t)k * M * dx, xr + (size_t)idx[k] * M * dx, sizeof(double) * M * dx);
+            if (anc)
+                for (int i = 0; i < M; ++i)
+                    anc[(size_t)(t - 1) * N + k * M + i] = idx[k] * M + a[idx[k] * M + i];
+            if (src) src[(size_t)(t - 1) * m + k] = idx[k];
+        }
+        if (sstar) sstar[t - 1] = first_quiet;
+        if (logz_trace) logz_trace[t - 1] = log_sum_exp(lw, m) - log((double)m);
+        if (tie && tie[0] == 0 && tie_now != TIE_NONE) { tie[0] = t; tie[1] = tie_now; }
+    }
+    *logz = log_sum_exp(lw, m) - log((double)m);
+    if (xfinal) memcpy(xfinal, xa, sizeof(double) * N * dx);
+
+    free(xa); free(x); free(xr); free(l); free(cdf); free(wres); free(a);
+    free(lw); free(lw2); free(idx); free(idx2); free(tie_isl);
+    return 0;
+}
+
+/* ----------------------------------------------------------------------- */
+/* Bootstrap particle filter (Gordon et al.), the m = 1 case of Section 2.  */
+/* Written separately from oracle_airpf.  `unit0` offsets the particle      */
+/* stream so that island k of an AIRPF run is reproduced with unit0 = k*M.  */
+/* ----------------------------------------------------------------------- */
+int oracle_bpf(int model, int dx, int dy, int M, int T, uint64_t seed, uint32_t chain,
+               uint32_t iter, uint32_t unit0, const double* theta, const double* mdat,
+               const double* y, double* logz, int32_t* anc, int32_t* tie)
+{
+    if (M < 1 || T < 1 || dx < 1 || dx > 64) return 1;
+    model_t md = { model, dx, dy, theta, mdat };
+    stream_id st = { seed, chain, iter };
+    double* xp = malloc(sizeof(double) * M * dx);
+    double* x = malloc(sizeof(double) * M * dx);
+    double* l = malloc(sizeof(double) * M);
+    double* cdf = malloc(sizeof(double) * M);
+    uint32_t* wres = malloc(sizeof(uint32_t) * M);
+    int32_t* a = malloc(sizeof(int32_t) * M);
+    double lz = 0.0;
+    if (tie) { tie[0] = 0; tie[1] = TIE_NONE; }
+    for (int i = 0; i < M; ++i) prior_sample(&md, &st, unit0 + (uint32_t)i, xp + (size_t)i * dx);
+    for (int t = 1; t <= T; ++t) {
+        for (int i = 0; i < M; ++i) {
+            wres[i] = transition(&md, &st, unit0 + (uint32_t)i, (uint32_t)t, xp + (size_t)i * dx,
+                                 x + (size_t)i * dx);
+            l[i] = log_g(&md, y + (size_t)(t - 1) * dy, x + (size_t)i * dx);
+        }
+        lz += log_sum_exp(l, M) - log((double)M);
+        int tf = resample_island(l, M, wres, cdf, a);
+        if (tie && tie[0] == 0 && tf) { tie[0] = t; tie[1] = TIE_RESAMPLE; }
+        for (int j = 0; j < M; ++j) {
+            memcpy(xp + (size_t)j * dx, x + (size_t)a[j] * dx, sizeof(double) * dx);
+            if (anc) anc[(size_t)(t - 1) * M + j] = a[j];
+        }
+    }
+    *logz = lz;
+    free(xp); free(x); free(l); free(cdf); free(wres); free(a);
+    return 0;
+}
+
+/* ----------------------------------------------------------------------- */
+/* Particle marginal Metropolis-Hastings (Andrieu et al. 2010; Section 1.2 */
+/* and Theorem 1's remark): random-walk proposal on the components with     */
+/* step > 0, independent uniform priors on [lo, hi], AIRPF estimate of Z.   */
+/* The initial estimate uses iter = 0xffffffff; iteration j uses iter = j.  */
+/* state[0] holds log Z of the current theta; pass state[0] = NaN to start. */
+/* ----------------------------------------------------------------------- */
+int oracle_pmmh(int model, int dx, int dy, int m, int M, int T, int mode, double tau,
+                uint64_t seed, uint32_t chain, const double* mdat, const double* y,
+                int d_theta, const double* step, const double* lo, const double* hi,
+                double* theta /* [d_theta], in/out */, double* state_logz /* in/out */,
+                uint32_t iter0, int iters, double* theta_out, double* logz_out, int32_t* n_accept)
+{
+    double prop[64];
+    if (d_theta < 1 || d_theta > 64) return 1;
+    int acc = 0;
+    if (isnan(*state_logz)) {
+        double lz;
+        int rc = oracle_airpf(model, dx, dy, m, M, T, mode, tau, seed, chain, 0xffffffffu,
+                              theta, mdat, y, &lz, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+        if (rc) return rc;
+        *state_logz = lz;
+    }
+    for (int j = 0; j < iters; ++j) {
+        uint32_t it = iter0 + (uint32_t)j;
+        stream_id st = { seed, chain, it };
+        double z[64];
+        /* proposal normals: kind MH, sub 0, unit = pair index b, t = 0 */
+        for (int b = 0; b < (d_theta + 1) / 2; ++b) {
+            uint32_t w[4];
+            draw(&st, (uint32_t)b, 0, KIND_MH, 0, w);
+            double a, c;
+            normal_pair(w[0], w[1], &a, &c);
+            z[2 * b] = a;
+            if (2 * b + 1 < d_theta) z[2 * b + 1] = c;
+        }
+        int inside = 1;
+        for (int d = 0; d < d_theta; ++d) {
+            prop[d] = theta[d] + step[d] * z[d];
+            if (step[d] > 0.0 && !(prop[d] >= lo[d] && prop[d] <= hi[d])) inside = 0;
+        }
+        if (inside && !oracle_model_valid(model, dx, prop)) inside = 0;
+        if (inside) {
+            double lz;
+            int rc = oracle_airpf(model, dx, dy, m, M, T, mode, tau, seed, chain, it,
+                                  prop, mdat, y, &lz, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+            if (rc) return rc;
+            uint32_t w[4];
+            draw(&st, 0, 0, KIND_MH, 1, w);
+            /* uniform priors cancel inside the box */
+            if (log(unif(w[0])) < lz - *state_logz) {
+                memcpy(theta, prop, sizeof(double) * d_theta);
+                *state_logz = lz;
+                ++acc;
+            }
+        }
+        if (theta_out) memcpy(theta_out + (size_t)j * d_theta, theta, sizeof(double) * d_theta);
+        if (logz_out) logz_out[j] = *state_logz;
+    }
+    if (n_accept) *n_accept = acc;
+    return 0;
+}
+
+/* ----------------------------------------------------------------------- */
+/* R independent runs (chains chain0 .. chain0+R-1), log Z of each.         */
+/* ----------------------------------------------------------------------- */
+int oracle_airpf_batch(int model, int dx, int dy, int m, int M, int T, int mode, double tau,
+                       uint64_t seed, uint32_t chain0, uint32_t iter, int R,
+                       const double* theta, const double* mdat, const double* y, double* logz)
+{
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 4) reduction(|:bad)
+    for (int r = 0; r < R; ++r) {
+        int rc = oracle_airpf(model, dx, dy, m, M, T, mode, tau, seed, chain0 + (uint32_t)r, iter,
+                              theta, mdat, y, logz + r, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+        bad |= rc;
+    }
+    return bad;
+}
