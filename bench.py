@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""AIRPF throughput on one GB300: particle-steps/s on the stochastic-volatility workload
+(m = 1024 islands x M = 256 particles, T = 1000 observations simulated from seed 2,
+(mu, phi, sigma) = (-1, 0.95, 0.3), adaptive interaction tau = 0.3, FP32 particles with
+FP64 island weights and log Z).
+
+A step is one full AIRPF pass over y_1..y_T (every row of the hot path: propagate, weight,
+island log-sum-exp, internal resampling, ENF-controlled island interaction, log Z
+accumulation), at the next iteration index of the random streams.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl airpf|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "AIRPF particle-steps/s (SV, m=1024 x M=256, T=1000)"
+UNIT = "particle-steps/s"
+WORKLOAD = "sv_m1024_M256_T1000"
+M_ISL, M_PART, T_OBS = 1024, 256, 1000
+TAU = 0.3
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic lane-operations per particle-step of the FP32 SV path (definition, counted
+# from the algorithm, not from the compiler): Philox4x32-10 block 100, Box-Muller normal 13,
+# SV transition 3, SV log-density 9, island max 4, weight and fixed-point conversion 5,
+# integer prefix sum 10, CDF and particle stores 2, draw target 4, binary search over
+# M = 256 (8 levels x 7) 56, gather 4.
+OPS_PER_PARTICLE_STEP = 210
+SM_COUNT, LANES_PER_SM = 152, 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(T_s: int, iter_: int, threads: int | None = None):
+    """The CPU oracle on the first T_s observations of the workload; returns seconds."""
+    import oracle
+    y = synth.sv_observations(T_OBS, seed=2)[:T_s]
+    t0 = time.perf_counter()
+    oracle.airpf(synth.MODEL_SV, synth.SV_THETA, y, m=M_ISL, M=M_PART, mode=oracle.MODE_ADAPTIVE,
+                 tau=TAU, seed=1, chain=0, iter=iter_, record=False)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def calibrate_oracle(target_s: float) -> int:
+    t = oracle_sample(2, 0xFFFF0000)
+    per_step = max(t / 2, 1e-4)
+    return int(max(1, min(T_OBS, target_s / per_step)))
+
+
+def cpu_baseline_leg(target_s: float = 12.0) -> dict:
+    T_s = calibrate_oracle(target_s)
+    secs = oracle_sample(T_s, 0xFFFF0001)
+    return {"value": M_ISL * M_PART * T_s / secs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"FP64 oracle (Algorithm 1, stage by stage) on the first {T_s} of {T_OBS} steps of "
+                      f"the SV workload, m={M_ISL} x M={M_PART}, one run, {secs:.1f} s"}
+
+
+def run_reference(args) -> None:
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    budget = 150.0
+    per_step_target = max(0.2, budget / max(1, args.steps + args.warmup))
+    T_s = calibrate_oracle(per_step_target)
+    for w in range(args.warmup):
+        oracle_sample(T_s, 0xFFFE0000 + w)
+    times = [oracle_sample(T_s, j) for j in range(args.steps)]
+    tot = sum(times)
+    value = M_ISL * M_PART * T_s * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (SV observations simulated from seed 2)",
+            "config": {"workload": WORKLOAD, "sample_steps": T_s, "note": "each step: the oracle on the "
+                       f"first {T_s} observations"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"first {T_s} of {T_OBS} steps per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args) -> None:
+    import torch
+    import paper_2312_06484_gb300 as gp
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    prec = args.precision
+    y_np = synth.sv_observations(T_OBS, seed=2)
+    theta = torch.tensor(synth.SV_THETA[None, :], device="cuda")
+    y = torch.tensor(y_np, device="cuda")
+    f = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
+                 seed=1)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    chain = rank
+
+    def one(j):
+        return f.run(theta, y, chain0=chain, iter=j)["log_z"]
+
+    for w in range(args.warmup):
+        one(0xFFFF0000 + w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    lzs = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches = 0
+    for j in range(args.steps):
+        flush.fill_(j & 0xFF)                     # L2 flush between timed steps (not timed)
+        starts[j].record(stream)
+        lzs.append(one(j))
+        ends[j].record(stream)
+        launches += f.launch_count()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t)
+    ps = M_ISL * M_PART * T_OBS
+    value = ps * args.steps * ws / (tot_ms / 1e3)
+    lz32 = torch.stack(lzs).cpu().numpy().ravel()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    th_h = torch.tensor(synth.SV_THETA[None, :], dtype=torch.float64).pin_memory()
+    y_h = torch.tensor(y_np, dtype=torch.float64).pin_memory()
+    lz_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    n_e2e = max(3, min(args.steps, 50))
+    import ctypes
+    lib = f.lib
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(n_e2e):
+        st = lib.airpf_run_host(f.ctx, ctypes.c_void_p(th_h.data_ptr()), ctypes.c_void_p(y_h.data_ptr()),
+                                chain, 0x10000000 + j, ctypes.c_void_p(lz_h.data_ptr()))
+        gp._binding.check(st, f.ctx)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": ps * n_e2e * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * (3 + T_OBS),
+           "d2h_bytes_per_step": 8, "steps": n_e2e}
+
+    # all-FP64 path on the same workload, for the stated log-Z error
+    fp64 = None
+    if not args.no_fp64 and prec != "fp64":
+        f64 = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU,
+                       precision="fp64", seed=1)
+        f64.run(theta, y, chain0=chain, iter=0xFFFF0000)
+        torch.cuda.synchronize()
+        n64 = max(3, min(args.steps, 40))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        l64 = [f64.run(theta, y, chain0=chain, iter=j)["log_z"] for j in range(n64)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        lz64 = torch.stack(l64).cpu().numpy().ravel()
+        n = min(len(lz32), len(lz64))
+        fp64 = {"value": ps * n64 / (ms64 / 1e3), "ms_per_step": ms64 / n64,
+                "log_z_fp32_mean": float(lz32.mean()), "log_z_fp32_sd": float(lz32.std(ddof=1)),
+                "log_z_fp64_mean": float(lz64.mean()), "log_z_fp64_sd": float(lz64.std(ddof=1)),
+                "log_z_same_stream_abs_diff_mean": float(np.mean(np.abs(lz32[:n] - lz64[:n]))),
+                "runs": [len(lz32), len(lz64)]}
+        f64.close()
+
+    peaks, peak_src = _peaks()
+    ms_step = tot_ms / args.steps
+    steps_per_pass = T_OBS + 1
+    achieved = OPS_PER_PARTICLE_STEP * ps / (ms_step / 1e3) / 1e12
+    peak = SM_COUNT * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
+        "data": "synthetic (SV observations simulated from seed 2)",
+        "config": {"workload": WORKLOAD, "model": "SV", "m": M_ISL, "M": M_PART, "N": M_ISL * M_PART,
+                   "T": T_OBS, "interaction": f"adaptive tau={TAU}", "precision": prec,
+                   "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "pmcmc_iters_per_s": None,
+        "filter_passes_per_s": args.steps * ws / (tot_ms / 1e3),
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "airpf_step_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                     "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
+                     "launch_avg_us": 1e3 * ms_step / steps_per_pass,
+                     "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x sm_max_mhz ({peak_src})"},
+        "fp64_path": fp64,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_leg()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    f.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="airpf", choices=["airpf", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

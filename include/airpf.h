@@ -1,0 +1,186 @@
+/*
+ * airpf.h -- C ABI of the GB300 (sm_103a) Augmented Island Resampling Particle
+ * Filter library.
+ *
+ * The method is Algorithm 1 of K. Heine, "Augmented Island Resampling Particle
+ * Filters for Particle Markov Chain Monte Carlo" (arXiv 2312.06484): m filters
+ * ("islands") of M particles each; every time step weights the particles by
+ * the observation density g_t (Algorithm 1, weighting), resamples M particles
+ * multinomially inside each island (internal resample), then runs S = log2 m
+ * interaction stages with the butterfly matrices A_s of eq. (3), each stage
+ * active only while the effective number of filters (ENF) is below tau
+ * (Algorithm 1, adaptation), and mutates through K_{t+1}.  The estimate
+ * Z^N_T = m^-1 sum_k W^k_T of the marginal likelihood (Section 2,
+ * gamma^N_n(1)) is unbiased (Theorem 1), which is what particle marginal
+ * Metropolis-Hastings consumes (Section 1.2, Andrieu et al. 2010).
+ *
+ * Conventions for every entry point:
+ *   - All pointers named d_* are DEVICE pointers; all others are host pointers.
+ *   - The caller owns every input and output buffer and the device workspace.
+ *     The library owns only the host-side context object.
+ *   - Work is enqueued asynchronously on the stream given to airpf_create
+ *     (a cudaStream_t passed as void*; NULL = legacy default stream), except
+ *     where a function says it synchronises.
+ *   - Arguments are checked before anything is launched; failures return a
+ *     status code and leave a message for airpf_last_error.  The library never
+ *     aborts or exits.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ *   - log Z = -inf is a valid result (every particle weight became zero).
+ *
+ * Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11) with
+ *   key = (seed & 0xffffffff, seed >> 32),
+ *   counter = (unit, t, iter, ((chain0 + b) << 8) | (kind << 5) | sub)
+ * for filter b of a batch, with kind 0 (prior draw of particle unit = k*M+i,
+ * t = 0), 1 (transition noise of unit k*M+i at time t, normal pair `sub`;
+ * word 2 of sub 0 drives internal-resampling draw i of island k), 2 (island
+ * choice of island unit = j at stage sub = s, time t) and 3 (PMMH proposal
+ * and acceptance).  uniform(w) = (w + 0.5) 2^-32; normals by Box-Muller.
+ * Runs are therefore reproducible bit for bit given (seed, chain, iter) and
+ * independent of the launch configuration.
+ */
+#ifndef AIRPF_H
+#define AIRPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AIRPF_OK = 0,
+    AIRPF_ERR_ARG = 1,          /* invalid argument (nothing was launched) */
+    AIRPF_ERR_CUDA = 2,         /* a CUDA call failed; see airpf_last_error */
+    AIRPF_ERR_WORKSPACE = 3,    /* workspace too small or misaligned */
+    AIRPF_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    AIRPF_ERR_UNSUPPORTED = 5   /* valid but not supported by this build */
+} airpf_status;
+
+/* State-space models (Section 1.2, eq. (1)).  theta layouts:
+ *   AR1   [a, sigma_v, sigma_w, sigma_0]
+ *   SV    [mu, phi, sigma]
+ *   NGM   [q, r, p0]                       (variances)
+ *   LGSSM [A_11..A_dd, log q, log r]       model_data = A (dx*dx), C (dy*dx), row-major
+ *   TOY   [p_stay, p_correct]              binary HMM of Section 4.1 */
+typedef enum {
+    AIRPF_MODEL_AR1 = 0,
+    AIRPF_MODEL_SV = 1,
+    AIRPF_MODEL_NGM = 2,
+    AIRPF_MODEL_LGSSM = 3,
+    AIRPF_MODEL_TOY = 4
+} airpf_model;
+
+/* Interaction rule of Algorithm 1, adaptation line: NEVER gives m independent
+ * bootstrap filters (alpha_s = I, Section 3), ALWAYS uses every A_s, ADAPTIVE
+ * uses A_s iff ENF_{t,s} < tau. */
+typedef enum {
+    AIRPF_INTERACT_NEVER = 0,
+    AIRPF_INTERACT_ALWAYS = 1,
+    AIRPF_INTERACT_ADAPTIVE = 2
+} airpf_interact;
+
+/* FP64: every particle computation in double.  FP32_MIXED: propagation,
+ * log-weights and the island log-sum-exp in float, internal-resampling CDF as
+ * an exact fixed-point integer prefix sum, island weights, their
+ * normalisation and the log Z accumulation in double. */
+typedef enum {
+    AIRPF_FP64 = 0,
+    AIRPF_FP32_MIXED = 1
+} airpf_precision;
+
+typedef struct {
+    int32_t model;          /* airpf_model */
+    int32_t dx, dy;         /* state / observation dimension (1 unless LGSSM; dx <= 8, dy <= 8) */
+    int32_t m;              /* islands per filter: a power of 2, 1..4096 */
+    int32_t M;              /* particles per island: 1..1024 */
+    int32_t T;              /* observations y_1..y_T, T >= 1 */
+    int32_t B;              /* filters run together (a batch of independent runs), >= 1 */
+    int32_t mode;           /* airpf_interact */
+    double tau;             /* ENF threshold in (0, 1] (ENF normalised to [1/m, 1]) */
+    int32_t precision;      /* airpf_precision */
+    int32_t record;         /* bit 0: ancestors, bit 1: ENF and s*, bit 2: log Z trace */
+    uint64_t seed;
+} airpf_config;
+
+#define AIRPF_RECORD_LINEAGE 1
+#define AIRPF_RECORD_ENF 2
+#define AIRPF_RECORD_TRACE 4
+
+typedef struct airpf_ctx airpf_ctx;
+
+/* Number of bytes of device workspace a context with this configuration needs.
+ * Returns AIRPF_ERR_ARG for an invalid configuration. */
+airpf_status airpf_workspace_bytes(const airpf_config* cfg, size_t* bytes);
+
+/* Creates a context.  d_workspace: caller-owned device memory of at least
+ * airpf_workspace_bytes(cfg) bytes, 256-byte aligned, kept alive until
+ * airpf_destroy.  model_data: host array (LGSSM: dx*dx + dy*dx doubles; may be
+ * NULL otherwise), copied.  stream: cudaStream_t as void*.  *out receives the
+ * context (NULL on failure). */
+airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t workspace_bytes,
+                          const double* model_data, void* stream, airpf_ctx** out);
+
+airpf_status airpf_destroy(airpf_ctx* ctx);
+
+/* One AIRPF pass over y_1..y_T for each of the B filters (Algorithm 1).
+ *   d_theta   [B * d_theta] model parameters of filter b at b*d_theta (FP64)
+ *   d_y       [T * dy] observations, row t-1 = y_t (FP64)
+ *   chain0    chain index of filter 0 (filter b uses chain0 + b; < 2^24)
+ *   iter      iteration index of the random streams
+ *   d_log_z   [B] out: log Z^N_T (FP64)
+ *   d_anc     [B * T * N] out or NULL: int32 parent index (0..N-1, among the
+ *             time-t particles) of particle k*M+i held after step t, t = 1..T
+ *             (needs AIRPF_RECORD_LINEAGE)
+ *   d_enf     [B * T * (S+1)] out or NULL: ENF_{t,0..S} (needs AIRPF_RECORD_ENF)
+ *   d_sstar   [B * T] out or NULL: first non-interacting stage (S+1 = all interact)
+ *   d_trace   [B * T] out or NULL: log Z^N_t after step t (needs AIRPF_RECORD_TRACE)
+ * Asynchronous on the context's stream. */
+airpf_status airpf_run(airpf_ctx* ctx, const double* d_theta, const double* d_y,
+                       uint32_t chain0, uint32_t iter, double* d_log_z, int32_t* d_anc,
+                       double* d_enf, int32_t* d_sstar, double* d_trace);
+
+/* airpf_run with host buffers: copies theta (B*d_theta) and y (T*dy) to the
+ * device, runs, copies log_z (B) back, and synchronises the stream before
+ * returning.  For callers without device memory of their own. */
+airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y,
+                            uint32_t chain0, uint32_t iter, double* log_z);
+
+/* Random-walk particle marginal Metropolis-Hastings, one chain per filter of
+ * the batch (Andrieu et al. 2010; AIRPF is valid inside it by Theorem 1).
+ * Proposal theta' = theta + step .* N(0, I); independent uniform priors on
+ * [lo_d, hi_d] for every component with step_d > 0 (components with step_d = 0
+ * stay fixed); a proposal outside the box or outside the model's parameter
+ * domain is rejected without running the filter.
+ *   step, lo, hi   host arrays [d_theta]
+ *   d_state_theta  [B * d_theta] in/out: current theta of each chain
+ *   d_state_logz   [B] in/out: log Z of the current theta; NaN = not yet
+ *                  estimated (estimated first with iter = 0xffffffff)
+ *   iter0, iters   iterations iter0 .. iter0+iters-1
+ *   d_theta_out    [iters * B * d_theta] out or NULL: chain after each iteration
+ *   d_logz_out     [iters * B] out or NULL
+ *   d_n_accept     [B] out: accepted proposals (int32), accumulated
+ * Asynchronous; the whole chain stays on the device. */
+airpf_status airpf_pmmh(airpf_ctx* ctx, const double* d_y, const double* step, const double* lo,
+                        const double* hi, double* d_state_theta, double* d_state_logz,
+                        uint32_t chain0, uint32_t iter0, int32_t iters, double* d_theta_out,
+                        double* d_logz_out, int32_t* d_n_accept);
+
+/* Number of model parameters for (model, dx); 0 for an unknown model. */
+int32_t airpf_theta_dim(int32_t model, int32_t dx);
+
+/* Kernels launched by the last airpf_run / airpf_pmmh call (for accounting). */
+int64_t airpf_last_launch_count(const airpf_ctx* ctx);
+
+/* Message of the last failure on this context (or of the last failed
+ * airpf_create when ctx is NULL).  Never NULL. */
+const char* airpf_last_error(const airpf_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* airpf_status_string(airpf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIRPF_H */

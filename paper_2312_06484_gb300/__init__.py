@@ -1,0 +1,118 @@
+"""GB300 (sm_103a) Augmented Island Resampling Particle Filter.
+
+Heine, "Augmented Island Resampling Particle Filters for Particle Markov Chain Monte
+Carlo" (arXiv 2312.06484), Algorithm 1, run inside particle marginal Metropolis-
+Hastings.  Every step of the filter runs in the CUDA kernels of ``csrc/`` behind the C
+ABI of ``include/airpf.h``; this module only marshals torch tensors (device memory and
+streams) into that ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding
+from ._binding import AirpfConfig, AirpfError
+
+MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY = 0, 1, 2, 3, 4
+NEVER, ALWAYS, ADAPTIVE = 0, 1, 2
+FP64, FP32_MIXED = 0, 1
+RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE = 1, 2, 4
+
+_MODES = {"never": NEVER, "always": ALWAYS, "adaptive": ADAPTIVE}
+_PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED}
+
+
+def theta_dim(model: int, dx: int = 1) -> int:
+    return int(_binding.load().airpf_theta_dim(model, dx))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class AIRPF:
+    """One context: B filters of m islands x M particles over T observations.
+
+    Device workspace is a torch uint8 tensor; all work is enqueued on ``stream``
+    (default: torch's current CUDA stream)."""
+
+    def __init__(self, model: int, *, m: int, M: int, T: int, B: int = 1, dx: int = 1, dy: int = 1,
+                 mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, record: int = 0,
+                 model_data=None, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = _binding.load()
+        mode = _MODES[mode] if isinstance(mode, str) else int(mode)
+        precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        self.cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau,
+                               precision=precision, record=record, seed=seed)
+        nbytes = ctypes.c_size_t()
+        _binding.check(self.lib.airpf_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)))
+        self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        md = None
+        if model_data is not None:
+            self._md = np.ascontiguousarray(np.asarray(model_data, dtype=np.float64))
+            md = self._md.ctypes.data_as(ctypes.c_void_p)
+        ctx = ctypes.c_void_p()
+        _binding.check(self.lib.airpf_create(ctypes.byref(self.cfg), _ptr(self.workspace), nbytes.value, md,
+                                             ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx)))
+        self.ctx = ctx
+        self.m, self.M, self.T, self.B, self.dx, self.dy = m, M, T, B, dx, dy
+        self.N = m * M
+        self.S = int(round(np.log2(m)))
+        self.theta_dim = theta_dim(model, dx)
+        self.record = record
+
+    # -- runs -------------------------------------------------------------------------------
+    def run(self, theta, y, *, chain0: int = 0, iter: int = 0, lineage=False, enf=False, trace=False):
+        """One pass of Algorithm 1 for every filter of the batch.  theta: [B, d] float64 CUDA;
+        y: [T*dy] float64 CUDA.  Returns dict of CUDA tensors (log_z [B], optional
+        anc [B, T, N], enf [B, T, S+1], sstar [B, T], trace [B, T])."""
+        torch = self._torch
+        theta = theta.reshape(self.B, self.theta_dim).to(device="cuda", dtype=torch.float64).contiguous()
+        y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+        out = {"log_z": torch.empty(self.B, dtype=torch.float64, device="cuda")}
+        if lineage:
+            out["anc"] = torch.empty((self.B, self.T, self.N), dtype=torch.int32, device="cuda")
+        if enf:
+            out["enf"] = torch.empty((self.B, self.T, self.S + 1), dtype=torch.float64, device="cuda")
+            out["sstar"] = torch.empty((self.B, self.T), dtype=torch.int32, device="cuda")
+        if trace:
+            out["trace"] = torch.empty((self.B, self.T), dtype=torch.float64, device="cuda")
+        self._keep = (theta, y)
+        _binding.check(self.lib.airpf_run(self.ctx, _ptr(theta), _ptr(y), chain0, iter, _ptr(out["log_z"]),
+                                          _ptr(out.get("anc")), _ptr(out.get("enf")), _ptr(out.get("sstar")),
+                                          _ptr(out.get("trace"))), self.ctx)
+        return out
+
+    def run_host(self, theta: np.ndarray, y: np.ndarray, *, chain0: int = 0, iter: int = 0) -> np.ndarray:
+        """Host buffers in and out; synchronises.  Returns log_z [B] (numpy)."""
+        theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(self.B, self.theta_dim))
+        y = np.ascontiguousarray(np.asarray(y, dtype=np.float64).reshape(-1))
+        lz = np.empty(self.B, dtype=np.float64)
+        _binding.check(self.lib.airpf_run_host(self.ctx, theta.ctypes.data_as(ctypes.c_void_p),
+                                               y.ctypes.data_as(ctypes.c_void_p), chain0, iter,
+                                               lz.ctypes.data_as(ctypes.c_void_p)), self.ctx)
+        return lz
+
+    def launch_count(self) -> int:
+        return int(self.lib.airpf_last_launch_count(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.airpf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["AIRPF", "AirpfError", "theta_dim", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
+           "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
+           "RECORD_ENF", "RECORD_TRACE"]

@@ -1,0 +1,371 @@
+// airpf_api.cu -- C ABI of the AIRPF library (see include/airpf.h).
+//
+// Host runtime: checks arguments, carves the caller's device workspace into
+// the particle stores and island-weight buffers, captures the T+1 step
+// launches of one filter pass into a CUDA graph once per context, and replays
+// it on the caller's stream.  The graph reads every per-call value (theta, y,
+// iter, chain0) from fixed workspace addresses, so one capture serves all
+// calls, including every PMMH iteration.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/airpf.h"
+#include "airpf_internal.h"
+
+using airpf::RunParams;
+using airpf::StepParams;
+
+namespace {
+
+thread_local char g_create_error[512] = "";
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int ilog2_exact(int m)
+{
+    int s = 0;
+    while ((1 << s) < m) ++s;
+    return (1 << s) == m ? s : -1;
+}
+
+// Byte offsets of every buffer inside the workspace.
+struct WsLayout {
+    size_t run, theta, mdata, y, X[2], wr[2], we[2], ires[2], logz, trace, enf, sstar, anc, active;
+    size_t pm_prop, pm_logz_prop, pm_stats, total;
+};
+
+}  // namespace
+
+struct airpf_ctx {
+    airpf_config cfg;
+    int S, N, theta_dim;
+    unsigned char* ws;
+    size_t ws_bytes;
+    WsLayout L;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph;
+    bool graph_ready;
+    StepParams sp;
+    int64_t launches;
+    char err[512];
+};
+
+namespace {
+
+int theta_dim_of(int model, int dx)
+{
+    switch (model) {
+    case AIRPF_MODEL_AR1: return 4;
+    case AIRPF_MODEL_SV: return 3;
+    case AIRPF_MODEL_NGM: return 3;
+    case AIRPF_MODEL_LGSSM: return dx + 2;
+    case AIRPF_MODEL_TOY: return 2;
+    }
+    return 0;
+}
+
+const char* check_config(const airpf_config* c)
+{
+    if (!c) return "config is NULL";
+    if (c->model < 0 || c->model > 4) return "unknown model";
+    if (c->model == AIRPF_MODEL_LGSSM) {
+        if (c->dx < 1 || c->dx > 8 || c->dy < 1 || c->dy > 8) return "LGSSM needs 1 <= dx, dy <= 8";
+    } else if (c->dx != 1 || c->dy != 1) {
+        return "scalar models need dx = dy = 1";
+    }
+    if (c->m < 1 || c->m > 4096 || ilog2_exact(c->m) < 0) return "m must be a power of 2 in [1, 4096]";
+    if (c->M < 1 || c->M > 1024) return "M must be in [1, 1024]";
+    if (c->T < 1 || c->T > (1 << 24)) return "T must be in [1, 2^24]";
+    if (c->B < 1 || c->B > (1 << 24)) return "B must be in [1, 2^24]";
+    if ((double)c->B * c->m * c->M > 2147483647.0) return "B * m * M must be below 2^31";
+    if ((double)c->m * c->M > 4294967295.0) return "m * M must fit the 32-bit particle counter";
+    if (c->mode < 0 || c->mode > 2) return "unknown interaction mode";
+    if (!(c->tau > 0.0 && c->tau <= 1.0)) return "tau must be in (0, 1]";
+    if (c->precision != AIRPF_FP64 && c->precision != AIRPF_FP32_MIXED) return "unknown precision";
+    if (c->record < 0 || c->record > 7) return "unknown record bits";
+    return nullptr;
+}
+
+WsLayout make_ws_layout(const airpf_config* c)
+{
+    WsLayout L;
+    const size_t B = c->B, N = (size_t)c->m * c->M, T = c->T;
+    const size_t S = (size_t)ilog2_exact(c->m);
+    const size_t rsz = c->precision == AIRPF_FP64 ? 8 : 4;
+    const bool lin = c->record & AIRPF_RECORD_LINEAGE;
+    const bool enf = c->record & AIRPF_RECORD_ENF;
+    const bool tr = c->record & AIRPF_RECORD_TRACE;
+    const size_t td = (size_t)theta_dim_of(c->model, c->dx);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.run = take(sizeof(RunParams));
+    L.theta = take(sizeof(double) * B * td);
+    L.mdata = take(sizeof(double) * (size_t)(c->dx * c->dx + c->dy * c->dx));
+    L.y = take(sizeof(double) * T * c->dy);
+    for (int i = 0; i < 2; ++i) L.X[i] = take(rsz * B * c->dx * N);
+    for (int i = 0; i < 2; ++i) L.wr[i] = take(sizeof(double) * B * c->m);
+    for (int i = 0; i < 2; ++i) L.we[i] = take(sizeof(int) * B * c->m);
+    for (int i = 0; i < 2; ++i) L.ires[i] = lin ? take(sizeof(int) * B * N) : 0;
+    L.logz = take(sizeof(double) * B);
+    L.trace = tr ? take(sizeof(double) * B * T) : 0;
+    L.enf = enf ? take(sizeof(double) * B * T * (S + 1)) : 0;
+    L.sstar = enf ? take(sizeof(int) * B * T) : 0;
+    L.anc = lin ? take(sizeof(int) * B * T * N) : 0;
+    L.active = take(sizeof(int) * B);
+    L.pm_prop = take(sizeof(double) * B * td);
+    L.pm_logz_prop = take(sizeof(double) * B);
+    L.pm_stats = take(sizeof(int) * B);
+    L.total = o;
+    return L;
+}
+
+void set_err(airpf_ctx* ctx, const char* fmt, ...)
+{
+    char* dst = ctx ? ctx->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+}
+
+airpf_status cuda_fail(airpf_ctx* ctx, cudaError_t e, const char* what)
+{
+    set_err(ctx, "%s: %s", what, cudaGetErrorString(e));
+    return AIRPF_ERR_CUDA;
+}
+
+template <typename T> T* at(airpf_ctx* ctx, size_t off) { return reinterpret_cast<T*>(ctx->ws + off); }
+
+airpf_status build_graph(airpf_ctx* ctx)
+{
+    if (ctx->graph_ready) return AIRPF_OK;
+    cudaError_t e = airpf::prepare_step(ctx->sp);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attribute setup");
+    e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+    cudaError_t le = cudaSuccess;
+    for (int t = 1; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) le = airpf::launch_step(ctx->sp, t, ctx->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, le, "step launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->graph_ready = true;
+    return AIRPF_OK;
+}
+
+// Enqueue one filter pass over the workspace inputs (theta, y, run params already set).
+airpf_status enqueue_pass(airpf_ctx* ctx)
+{
+    airpf_status s = build_graph(ctx);
+    if (s != AIRPF_OK) return s;
+    cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    ctx->launches += ctx->cfg.T + 1;
+    return AIRPF_OK;
+}
+
+airpf_status copy_async(airpf_ctx* ctx, void* dst, const void* src, size_t bytes)
+{
+    if (bytes == 0) return AIRPF_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream);
+    return e == cudaSuccess ? AIRPF_OK : cuda_fail(ctx, e, "cudaMemcpyAsync");
+}
+
+}  // namespace
+
+extern "C" {
+
+airpf_status airpf_workspace_bytes(const airpf_config* cfg, size_t* bytes)
+{
+    const char* why = check_config(cfg);
+    if (why || !bytes) {
+        set_err(nullptr, "%s", why ? why : "bytes is NULL");
+        return AIRPF_ERR_ARG;
+    }
+    *bytes = make_ws_layout(cfg).total;
+    return AIRPF_OK;
+}
+
+int32_t airpf_theta_dim(int32_t model, int32_t dx) { return theta_dim_of(model, dx); }
+
+airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t workspace_bytes,
+                          const double* model_data, void* stream, airpf_ctx** out)
+{
+    if (!out) {
+        set_err(nullptr, "out is NULL");
+        return AIRPF_ERR_ARG;
+    }
+    *out = nullptr;
+    const char* why = check_config(cfg);
+    if (why) {
+        set_err(nullptr, "%s", why);
+        return AIRPF_ERR_ARG;
+    }
+    if (cfg->model == AIRPF_MODEL_LGSSM && !model_data) {
+        set_err(nullptr, "LGSSM needs model_data (A and C)");
+        return AIRPF_ERR_ARG;
+    }
+    const WsLayout L = make_ws_layout(cfg);
+    if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255u)) {
+        set_err(nullptr, "workspace must be >= %zu bytes and 256-byte aligned", L.total);
+        return AIRPF_ERR_WORKSPACE;
+    }
+    airpf_ctx* ctx = new (std::nothrow) airpf_ctx();
+    if (!ctx) {
+        set_err(nullptr, "host allocation failed");
+        return AIRPF_ERR_ARG;
+    }
+    ctx->cfg = *cfg;
+    ctx->S = ilog2_exact(cfg->m);
+    ctx->N = cfg->m * cfg->M;
+    ctx->theta_dim = theta_dim_of(cfg->model, cfg->dx);
+    ctx->ws = static_cast<unsigned char*>(d_workspace);
+    ctx->ws_bytes = workspace_bytes;
+    ctx->L = L;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        set_err(nullptr, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        delete ctx;
+        return AIRPF_ERR_CUDA;
+    }
+
+    StepParams& p = ctx->sp;
+    std::memset(&p, 0, sizeof(p));
+    p.B = cfg->B; p.m = cfg->m; p.M = cfg->M; p.N = ctx->N; p.dx = cfg->dx; p.dy = cfg->dy;
+    p.T = cfg->T; p.S = ctx->S; p.mode = cfg->mode; p.model = cfg->model;
+    p.fp64 = cfg->precision == AIRPF_FP64;
+    p.tau = cfg->tau;
+    airpf::choose_mapping(cfg->m, cfg->M, p.fp64, &p.tpi, &p.ppt, &p.G);
+    p.theta_dim = ctx->theta_dim;
+    p.seed_lo = (uint32_t)(cfg->seed & 0xffffffffu);
+    p.seed_hi = (uint32_t)(cfg->seed >> 32);
+    p.run = at<RunParams>(ctx, L.run);
+    p.theta = at<double>(ctx, L.theta);
+    p.mdata = at<double>(ctx, L.mdata);
+    p.y = at<double>(ctx, L.y);
+    p.active = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        p.X[i] = at<void>(ctx, L.X[i]);
+        p.wr[i] = at<double>(ctx, L.wr[i]);
+        p.we[i] = at<int>(ctx, L.we[i]);
+        p.ires[i] = (cfg->record & AIRPF_RECORD_LINEAGE) ? at<int>(ctx, L.ires[i]) : nullptr;
+    }
+    p.logz = at<double>(ctx, L.logz);
+    p.trace = (cfg->record & AIRPF_RECORD_TRACE) ? at<double>(ctx, L.trace) : nullptr;
+    p.enf = (cfg->record & AIRPF_RECORD_ENF) ? at<double>(ctx, L.enf) : nullptr;
+    p.sstar = (cfg->record & AIRPF_RECORD_ENF) ? at<int>(ctx, L.sstar) : nullptr;
+    p.anc = (cfg->record & AIRPF_RECORD_LINEAGE) ? at<int>(ctx, L.anc) : nullptr;
+
+    if (cfg->model == AIRPF_MODEL_LGSSM) {
+        const size_t n = sizeof(double) * (size_t)(cfg->dx * cfg->dx + cfg->dy * cfg->dx);
+        e = cudaMemcpyAsync(at<void>(ctx, L.mdata), model_data, n, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            set_err(nullptr, "model data copy: %s", cudaGetErrorString(e));
+            cudaStreamDestroy(ctx->cap_stream);
+            delete ctx;
+            return AIRPF_ERR_CUDA;
+        }
+    }
+    *out = ctx;
+    return AIRPF_OK;
+}
+
+airpf_status airpf_destroy(airpf_ctx* ctx)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    if (ctx->graph_ready) cudaGraphExecDestroy(ctx->graph);
+    cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+    return AIRPF_OK;
+}
+
+airpf_status airpf_run(airpf_ctx* ctx, const double* d_theta, const double* d_y, uint32_t chain0,
+                       uint32_t iter, double* d_log_z, int32_t* d_anc, double* d_enf, int32_t* d_sstar,
+                       double* d_trace)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    const airpf_config& c = ctx->cfg;
+    if (!d_theta || !d_y || !d_log_z) {
+        set_err(ctx, "theta, y and log_z are required");
+        return AIRPF_ERR_ARG;
+    }
+    if ((uint64_t)chain0 + (uint64_t)c.B > (1u << 24)) {
+        set_err(ctx, "chain0 + B must not exceed 2^24");
+        return AIRPF_ERR_ARG;
+    }
+    if ((d_anc && !(c.record & AIRPF_RECORD_LINEAGE)) || ((d_enf || d_sstar) && !(c.record & AIRPF_RECORD_ENF))
+        || (d_trace && !(c.record & AIRPF_RECORD_TRACE))) {
+        set_err(ctx, "an output was requested that the context does not record");
+        return AIRPF_ERR_ARG;
+    }
+    ctx->launches = 0;
+    const size_t B = c.B, T = c.T, N = ctx->N;
+    airpf_status s;
+    if ((s = copy_async(ctx, at<void>(ctx, ctx->L.theta), d_theta, sizeof(double) * B * ctx->theta_dim))) return s;
+    if ((s = copy_async(ctx, at<void>(ctx, ctx->L.y), d_y, sizeof(double) * T * c.dy))) return s;
+    cudaError_t e = airpf::launch_set_run(at<RunParams>(ctx, ctx->L.run), iter, chain0, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set_run launch");
+    ctx->launches += 1;
+    if ((s = enqueue_pass(ctx))) return s;
+    if ((s = copy_async(ctx, d_log_z, at<void>(ctx, ctx->L.logz), sizeof(double) * B))) return s;
+    if (d_anc && (s = copy_async(ctx, d_anc, at<void>(ctx, ctx->L.anc), sizeof(int) * B * T * N))) return s;
+    if (d_enf && (s = copy_async(ctx, d_enf, at<void>(ctx, ctx->L.enf), sizeof(double) * B * T * (ctx->S + 1))))
+        return s;
+    if (d_sstar && (s = copy_async(ctx, d_sstar, at<void>(ctx, ctx->L.sstar), sizeof(int) * B * T))) return s;
+    if (d_trace && (s = copy_async(ctx, d_trace, at<void>(ctx, ctx->L.trace), sizeof(double) * B * T))) return s;
+    return AIRPF_OK;
+}
+
+airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y, uint32_t chain0,
+                            uint32_t iter, double* log_z)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    if (!theta || !y || !log_z) {
+        set_err(ctx, "theta, y and log_z are required");
+        return AIRPF_ERR_ARG;
+    }
+    airpf_status s = airpf_run(ctx, theta, y, chain0, iter, log_z, nullptr, nullptr, nullptr, nullptr);
+    if (s != AIRPF_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? AIRPF_OK : cuda_fail(ctx, e, "cudaStreamSynchronize");
+}
+
+airpf_status airpf_pmmh(airpf_ctx* ctx, const double*, const double*, const double*, const double*, double*,
+                        double*, uint32_t, uint32_t, int32_t, double*, double*, int32_t*)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    set_err(ctx, "airpf_pmmh is not built yet");
+    return AIRPF_ERR_UNSUPPORTED;
+}
+
+int64_t airpf_last_launch_count(const airpf_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* airpf_last_error(const airpf_ctx* ctx) { return ctx ? ctx->err : g_create_error; }
+
+const char* airpf_status_string(airpf_status s)
+{
+    switch (s) {
+    case AIRPF_OK: return "AIRPF_OK";
+    case AIRPF_ERR_ARG: return "AIRPF_ERR_ARG";
+    case AIRPF_ERR_CUDA: return "AIRPF_ERR_CUDA";
+    case AIRPF_ERR_WORKSPACE: return "AIRPF_ERR_WORKSPACE";
+    case AIRPF_ERR_TIMEOUT: return "AIRPF_ERR_TIMEOUT";
+    case AIRPF_ERR_UNSUPPORTED: return "AIRPF_ERR_UNSUPPORTED";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

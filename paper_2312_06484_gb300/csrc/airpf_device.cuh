@@ -1,0 +1,244 @@
+// airpf_device.cuh -- device building blocks of the AIRPF hot path (sm_103a):
+// the counter-based random streams and the state-space models.
+//
+// Random streams: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
+//   key = (seed lo, seed hi), counter = (unit, t, iter, chainword | kind<<5 | sub).
+// Models: Section 1.2, eq. (1) of Heine (arXiv 2312.06484); parameter layouts as
+// in include/airpf.h.
+#pragma once
+#include <cstdint>
+#include <cmath>
+
+namespace airpf {
+
+enum Kind : uint32_t { KIND_INIT = 0, KIND_STEP = 1, KIND_ISLAND = 2, KIND_MH = 3 };
+enum Model : int { AR1 = 0, SV = 1, NGM = 2, LGSSM = 3, TOY = 4 };
+
+constexpr int kMaxDx = 8;
+constexpr int kMaxDy = 8;
+constexpr int kMaxTheta = kMaxDx + 2;
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+// Ten Philox rounds: two 32x32->64 multiplies per round (mul.lo / mul.hi), the
+// Weyl key bump between rounds.
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                             uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// The identity of one filter's streams: seed key, PMMH iteration and chain.
+struct Stream {
+    uint32_t k0, k1, iter, chainword;   // chainword = chain << 8
+
+    __device__ __forceinline__ U4 draw(uint32_t unit, uint32_t t, uint32_t kind, uint32_t sub) const
+    {
+        return philox4x32_10(unit, t, iter, chainword | (kind << 5) | sub, k0, k1);
+    }
+};
+
+__device__ __forceinline__ double unif_f64(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+
+// Box-Muller pair from two words: r = sqrt(-2 ln u0), angle 2 pi u1.
+__device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, double& z0, double& z1)
+{
+    const double rad = sqrt(-2.0 * log(unif_f64(w0)));
+    const double ang = (2.0 * 3.141592653589793) * unif_f64(w1);
+    double s, c;
+    sincos(ang, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+
+// float version on the SFU: cos(2 pi u) = -cos(pi (2u - 1)), same for sin.
+__device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, float& z0, float& z1)
+{
+    const float u0 = fmaf((float)w0, 0x1p-32f, 0x1p-33f);
+    const float rad = sqrtf(-2.0f * __logf(u0));
+    const float a = fmaf((float)w1, 0x1p-31f, 0x1p-32f) - 1.0f;
+    float s, c;
+    __sincosf(3.14159265358979f * a, &s, &c);
+    z0 = -rad * c;
+    z1 = -rad * s;
+}
+
+template <typename R> __device__ __forceinline__ R fexp(R v);
+template <> __device__ __forceinline__ double fexp<double>(double v) { return exp(v); }
+template <> __device__ __forceinline__ float fexp<float>(float v) { return __expf(v); }
+template <typename R> __device__ __forceinline__ R flog(R v);
+template <> __device__ __forceinline__ double flog<double>(double v) { return log(v); }
+template <> __device__ __forceinline__ float flog<float>(float v) { return __logf(v); }
+template <typename R> __device__ __forceinline__ R fsqrt(R v);
+template <> __device__ __forceinline__ double fsqrt<double>(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float fsqrt<float>(float v) { return sqrtf(v); }
+template <typename R> __device__ __forceinline__ R fcos(R v);
+template <> __device__ __forceinline__ double fcos<double>(double v) { return cos(v); }
+template <> __device__ __forceinline__ float fcos<float>(float v) { return __cosf(v); }
+
+// Per-filter model constants, computed once per CTA from theta.
+template <typename R>
+struct ModelPar {
+    R th[kMaxTheta];
+    R c0, c1, c2, c3;        // model-specific derived constants
+};
+
+template <typename R, int MODEL>
+__device__ __forceinline__ void model_setup(ModelPar<R>& p, const double* theta, int dx, int dy)
+{
+    const int nth = (MODEL == LGSSM) ? dx + 2 : (MODEL == AR1 ? 4 : (MODEL == TOY ? 2 : 3));
+#pragma unroll
+    for (int i = 0; i < kMaxTheta; ++i) p.th[i] = (i < nth) ? (R)theta[i] : (R)0;
+    if (MODEL == AR1) {            // a, sv, sw, s0
+        p.c0 = (R)(-0.9189385332046727 - log(theta[2]));   // -log sqrt(2 pi) - log sw
+        p.c1 = (R)(1.0 / theta[2]);
+    } else if (MODEL == SV) {      // mu, phi, sigma
+        p.c0 = (R)(theta[2] / sqrt(1.0 - theta[1] * theta[1]));   // stationary sd
+        p.c1 = (R)(-0.9189385332046727);
+    } else if (MODEL == NGM) {     // q, r, p0
+        p.c0 = (R)sqrt(theta[0]);
+        p.c1 = (R)(-0.5 * log(2.0 * 3.141592653589793 * theta[1]));
+        p.c2 = (R)(0.5 / theta[1]);
+        p.c3 = (R)sqrt(theta[2]);
+    } else if (MODEL == TOY) {     // stay, correct
+        p.c0 = (R)(1.0 - theta[0]);
+        p.c1 = (R)log(theta[1]);
+        p.c2 = (R)log(1.0 - theta[1]);
+    } else {                       // LGSSM: sqrt(q), 1/(2r), -dy/2 log(2 pi r)
+        const double r = exp(theta[dx + 1]);
+        p.c0 = (R)sqrt(exp(theta[dx]));
+        p.c1 = (R)(0.5 / r);
+        p.c2 = (R)(-0.5 * dy * log(2.0 * 3.141592653589793 * r));
+    }
+}
+
+// Normals z[0..n-1] of (kind, unit, t): pair b gives z[2b], z[2b+1].  Also
+// returns word 0 and word 2 of sub-block 0.
+template <typename R, int NZ>
+__device__ __forceinline__ void stream_normals(const Stream& st, uint32_t kind, uint32_t unit,
+                                               uint32_t t, int n, R* z, uint32_t& w0, uint32_t& w2)
+{
+    const U4 b0 = st.draw(unit, t, kind, 0);
+    w0 = b0.x;
+    w2 = b0.z;
+    if (NZ == 0) return;
+    if (NZ == 1) {
+        R z1;
+        normal_pair(b0.x, b0.y, z[0], z1);
+        return;
+    }
+    normal_pair(b0.x, b0.y, z[0], z[1]);
+#pragma unroll
+    for (int b = 1; b < (NZ + 1) / 2; ++b) {
+        if (2 * b < n) {
+            const U4 bb = st.draw(unit, t, kind, (uint32_t)b);
+            R a, c;
+            normal_pair(bb.x, bb.y, a, c);
+            z[2 * b] = a;
+            if (2 * b + 1 < NZ) z[2 * b + 1] = c;
+        }
+    }
+}
+
+// x_0 ~ pi_0
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ void model_prior(const ModelPar<R>& p, const Stream& st, uint32_t unit,
+                                            int dx, R* x)
+{
+    R z[DX > 1 ? DX : 1];
+    uint32_t w0, w2;
+    stream_normals<R, (MODEL == TOY) ? 0 : DX>(st, KIND_INIT, unit, 0u, dx, z, w0, w2);
+    if (MODEL == AR1) x[0] = p.th[3] * z[0];
+    if (MODEL == SV) x[0] = p.th[0] + p.c0 * z[0];
+    if (MODEL == NGM) x[0] = p.c3 * z[0];
+    if (MODEL == TOY) x[0] = (unif_f64(w0) < 0.5) ? (R)0 : (R)1;
+    if (MODEL == LGSSM) {
+#pragma unroll
+        for (int d = 0; d < DX; ++d) if (d < dx) x[d] = z[d];
+    }
+}
+
+// x_t ~ K_t(x_{t-1}, .); returns the internal-resampling word of the unit.
+// A (LGSSM) is row-major dx*dx in shared memory, diagonal taken from theta.
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ uint32_t model_step(const ModelPar<R>& p, const Stream& st, uint32_t unit,
+                                               uint32_t t, int dx, const R* xp, R* x, const R* A)
+{
+    R z[DX > 1 ? DX : 1];
+    uint32_t w0, w2;
+    stream_normals<R, (MODEL == TOY) ? 0 : DX>(st, KIND_STEP, unit, t, dx, z, w0, w2);
+    if (MODEL == AR1) x[0] = p.th[0] * xp[0] + p.th[1] * z[0];
+    if (MODEL == SV) x[0] = p.th[0] + p.th[1] * (xp[0] - p.th[0]) + p.th[2] * z[0];
+    if (MODEL == NGM) {
+        const R v = xp[0];
+        x[0] = (R)0.5 * v + (R)25 * v / ((R)1 + v * v) + (R)(8.0 * cos(1.2 * (double)t)) + p.c0 * z[0];
+    }
+    if (MODEL == TOY) x[0] = (unif_f64(w0) < (double)p.c0) ? (R)1 - xp[0] : xp[0];
+    if (MODEL == LGSSM) {
+#pragma unroll
+        for (int r = 0; r < DX; ++r) {
+            if (r < dx) {
+                R acc = 0;
+#pragma unroll
+                for (int c = 0; c < DX; ++c)
+                    if (c < dx) acc += ((r == c) ? p.th[r] : A[r * dx + c]) * xp[c];
+                x[r] = acc + p.c0 * z[r];
+            }
+        }
+    }
+    return w2;
+}
+
+// log g_t(y_t | x); NaN counts as -inf (weight zero).
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ R model_logg(const ModelPar<R>& p, const R* y, int dx, int dy, const R* x,
+                                        const R* Cm)
+{
+    R l;
+    if (MODEL == AR1) {
+        const R e = (y[0] - x[0]) * p.c1;
+        l = p.c0 - (R)0.5 * e * e;
+    } else if (MODEL == SV) {
+        l = p.c1 - (R)0.5 * x[0] - (R)0.5 * y[0] * y[0] * fexp<R>(-x[0]);
+    } else if (MODEL == NGM) {
+        const R e = y[0] - x[0] * x[0] / (R)20;
+        l = p.c1 - e * e * p.c2;
+    } else if (MODEL == TOY) {
+        l = (y[0] == x[0]) ? p.c1 : p.c2;
+    } else {
+        R ss = 0;
+#pragma unroll
+        for (int o = 0; o < kMaxDy; ++o) {
+            if (o < dy) {
+                R e = y[o];
+#pragma unroll
+                for (int c = 0; c < DX; ++c)
+                    if (c < dx) e -= Cm[o * dx + c] * x[c];
+                ss += e * e;
+            }
+        }
+        l = p.c2 - ss * p.c1;
+    }
+    return (l > -INFINITY) ? l : (R)(-INFINITY);
+}
+
+}  // namespace airpf

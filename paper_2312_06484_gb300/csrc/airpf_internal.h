@@ -1,0 +1,59 @@
+// airpf_internal.h -- host/device parameter block of the AIRPF kernels and
+// the launchers the C-ABI layer calls.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace airpf {
+
+// Per-run values the captured graph reads from device memory, so that one
+// graph serves every (iter, chain0) and every PMMH iteration.
+struct RunParams {
+    uint32_t iter;
+    uint32_t chain0;
+};
+
+// Everything the step kernel needs; passed by value.  Arrays are laid out
+//   particles  X[b][d][k*M + i]   (structure of arrays, one island contiguous)
+//   island weights wr/we[b][k]    (mantissa in [0.5,1) or 0, and a binary
+//                                  exponent: an extended-range double)
+struct StepParams {
+    int B, m, M, N, dx, dy, T, S, mode, model, fp64;
+    double tau;
+    int G, tpi, ppt;              // islands per CTA, threads per island, particles per thread
+    int theta_dim;
+    uint32_t seed_lo, seed_hi;
+    const RunParams* run;
+    const double* theta;          // [B][theta_dim]
+    const double* mdata;          // LGSSM: A then C
+    const double* y;              // [T][dy]
+    const int* active;            // [B] nonzero = run this filter (PMMH), or NULL
+    void* X[2];                   // particle stores, ping-pong by t & 1
+    double* wr[2];
+    int* we[2];
+    int* ires[2];                 // internal ancestors of the last step (lineage), or NULL
+    double* logz;                 // [B]
+    double* trace;                // [B][T] or NULL
+    double* enf;                  // [B][T][S+1] or NULL
+    int* sstar;                   // [B][T] or NULL
+    int* anc;                     // [B][T][N] or NULL
+};
+
+// Shared-memory bytes of one step launch.
+size_t step_smem_bytes(const StepParams& p);
+
+// Sets kernel attributes (shared-memory opt-in); call outside stream capture.
+cudaError_t prepare_step(const StepParams& p);
+
+// Launches step t (1..T: cascade of step t-1 then the island work of step t;
+// T+1: the final cascade only) on `stream`.
+cudaError_t launch_step(const StepParams& p, int t, cudaStream_t stream);
+
+// Writes the run parameters (one thread).
+cudaError_t launch_set_run(RunParams* d_run, uint32_t iter, uint32_t chain0, cudaStream_t stream);
+
+// Choose (tpi, ppt, G) for M particles per island and m islands per filter.
+void choose_mapping(int m, int M, int fp64, int* tpi, int* ppt, int* G);
+
+}  // namespace airpf

@@ -1,0 +1,64 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/airpf.h
+declares; host-side argument checks work without a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2312_06484_gb300 import _binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "airpf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(airpf_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _binding.load()
+    names = _declared_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_binding.SIGNATURES), "binding and header disagree"
+
+
+def _cfg(**kw):
+    base = dict(model=1, dx=1, dy=1, m=1024, M=256, T=1000, B=1, mode=2, tau=0.3, precision=1,
+                record=0, seed=1)
+    base.update(kw)
+    return _binding.AirpfConfig(**base)
+
+
+def test_workspace_size_and_argument_checks():
+    lib = _binding.load()
+    n = ctypes.c_size_t()
+    assert lib.airpf_workspace_bytes(ctypes.byref(_cfg()), ctypes.byref(n)) == 0
+    # two particle stores of N floats plus small buffers
+    assert 2 * 262144 * 4 <= n.value < 2 * 262144 * 4 + (1 << 20)
+    bad = [dict(m=3), dict(m=8192), dict(M=0), dict(M=1025), dict(T=0), dict(B=0), dict(tau=0.0),
+           dict(tau=1.01), dict(mode=3), dict(model=9), dict(dx=2), dict(model=3, dx=9),
+           dict(precision=7), dict(record=8)]
+    for kw in bad:
+        assert lib.airpf_workspace_bytes(ctypes.byref(_cfg(**kw)), ctypes.byref(n)) == 1, kw
+        assert lib.airpf_last_error(None)
+    out = ctypes.c_void_p()
+    assert lib.airpf_create(ctypes.byref(_cfg(m=5)), None, 0, None, None, ctypes.byref(out)) == 1
+    assert lib.airpf_create(ctypes.byref(_cfg()), None, 0, None, None, ctypes.byref(out)) == 3
+    assert out.value is None
+    assert lib.airpf_create(ctypes.byref(_cfg(model=3, dx=2, dy=2)), None, 0, None, None,
+                            ctypes.byref(out)) == 1          # LGSSM without model data
+    assert lib.airpf_theta_dim(0, 1) == 4 and lib.airpf_theta_dim(3, 8) == 10
+    assert lib.airpf_status_string(4) == b"AIRPF_ERR_TIMEOUT"
+    assert lib.airpf_run(None, None, None, 0, 0, None, None, None, None, None) == 1
+
+
+def test_lineage_record_sizes_grow_workspace():
+    lib = _binding.load()
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    lib.airpf_workspace_bytes(ctypes.byref(_cfg(m=16, M=64, T=100)), ctypes.byref(a))
+    lib.airpf_workspace_bytes(ctypes.byref(_cfg(m=16, M=64, T=100, record=7)), ctypes.byref(b))
+    assert b.value - a.value >= 100 * 1024 * 4

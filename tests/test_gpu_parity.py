@@ -1,0 +1,88 @@
+"""FP64 CUDA path vs the oracle, element by element (ancestors bit-exact, log Z within
+1e-10 relative, ENF and s* per step), through the C ABI, on seeded inputs:
+the AR(1) workload of m=16 x M=64 x T=100 in every interaction mode and batched, ragged
+and tiny sizes, every model, m = 1, the degenerate all-zero-weight case, and sampled
+filters at the full SV size m=1024 x M=256."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import compare_filter, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"never": oracle.MODE_NEVER, "always": oracle.MODE_ALWAYS, "adaptive": oracle.MODE_ADAPTIVE}
+
+
+@pytest.mark.parametrize("mode", ["adaptive", "always", "never"])
+def test_ar1_workload_all_modes(gpu_lib, mode):
+    y = synth.ar1_observations(100, seed=1)
+    B, m, M = 4, 16, 64
+    g = run_gpu(synth.MODEL_AR1, synth.AR1_THETA, y, m=m, M=M, B=B, mode=mode, tau=0.3, seed=7,
+                chain0=3, iter=2)
+    for b in range(B):
+        o = oracle.airpf(synth.MODEL_AR1, synth.AR1_THETA, y, m=m, M=M, mode=MODES[mode], tau=0.3,
+                         seed=7, chain=3 + b, iter=2)
+        compare_filter(g, b, o, m=m, what=f"{mode} b={b}")
+    assert g["launches"] == 100 + 2
+
+
+@pytest.mark.parametrize("model,theta,ymaker,m,M,T,mode,tau", [
+    (synth.MODEL_SV, synth.SV_THETA, lambda T: synth.sv_observations(T, 2), 64, 37, 40, "adaptive", 0.8),
+    (synth.MODEL_SV, synth.SV_THETA, lambda T: synth.sv_observations(T, 2), 8, 200, 30, "always", 0.3),
+    (synth.MODEL_NGM, synth.NGM_THETA, lambda T: synth.ngm_observations(T, 5), 32, 100, 30, "adaptive", 0.5),
+    (synth.MODEL_TOY, synth.TOY_THETA, lambda T: synth.toy_observations(T, 3), 4, 2, 25, "always", 0.3),
+    (synth.MODEL_AR1, synth.AR1_THETA, lambda T: synth.ar1_observations(T, 1), 1, 129, 20, "adaptive", 0.3),
+    (synth.MODEL_AR1, synth.AR1_THETA, lambda T: synth.ar1_observations(T, 1), 2, 1, 20, "always", 0.3),
+    (synth.MODEL_SV, synth.SV_THETA, lambda T: synth.sv_observations(T, 2), 4096, 4, 4, "always", 0.3),
+    (synth.MODEL_SV, synth.SV_THETA, lambda T: synth.sv_observations(T, 2), 2, 1024, 6, "adaptive", 0.99),
+])
+def test_models_and_shapes(gpu_lib, model, theta, ymaker, m, M, T, mode, tau):
+    y = ymaker(T)
+    g = run_gpu(model, theta, y, m=m, M=M, B=2, mode=mode, tau=tau, seed=11, chain0=0, iter=5)
+    for b in range(2):
+        o = oracle.airpf(model, theta, y, m=m, M=M, mode=MODES[mode], tau=tau, seed=11, chain=b, iter=5)
+        compare_filter(g, b, o, m=m, what=f"model {model} m={m} M={M} b={b}")
+
+
+def test_lgssm(gpu_lib):
+    dx, dy = 3, 2
+    A, C, md = synth.lg_model(dx, dy, seed=11)
+    th = synth.lg_theta(A, q=0.1, r=0.5)
+    y = synth.lg_observations(A, C, 0.1, 0.5, 25, seed=11)
+    g = run_gpu(synth.MODEL_LGSSM, th, y, m=16, M=32, B=2, dx=dx, dy=dy, model_data=md, mode="adaptive",
+                tau=0.6, seed=2)
+    for b in range(2):
+        o = oracle.airpf(synth.MODEL_LGSSM, th, y, m=16, M=32, dx=dx, dy=dy, model_data=md,
+                         mode=oracle.MODE_ADAPTIVE, tau=0.6, seed=2, chain=b)
+        compare_filter(g, b, o, m=16, what=f"lgssm b={b}")
+
+
+def test_m1_equals_oracle_bootstrap_filter(gpu_lib):
+    y = synth.sv_observations(50, seed=2)
+    g = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, m=1, M=256, B=1, mode="adaptive", seed=4)
+    lz, anc, tie = oracle.bpf(synth.MODEL_SV, synth.SV_THETA, y, M=256, seed=4)
+    upto = len(y) if tie[0] == 0 else tie[0] - 1
+    assert np.array_equal(g["anc"][0][:upto], anc[:upto])
+    if tie[0] == 0:
+        assert abs(g["log_z"][0] - lz) <= 1e-10 * abs(lz)
+
+
+def test_dead_filter_is_minus_infinity(gpu_lib):
+    y = np.full(6, 1e200)
+    g = run_gpu(synth.MODEL_AR1, synth.AR1_THETA, y, m=4, M=8, B=1, mode="adaptive", seed=1)
+    o = oracle.airpf(synth.MODEL_AR1, synth.AR1_THETA, y, m=4, M=8, mode=oracle.MODE_ADAPTIVE, seed=1)
+    assert g["log_z"][0] == -np.inf and o["log_z"] == -np.inf
+    assert np.array_equal(g["anc"][0], o["anc"])
+
+
+def test_full_size_sv_sampled_filters(gpu_lib):
+    """m=1024 x M=256 (the SV workload's size) with T shortened to 6, FP64, every record
+    compared for two filters of a batch of 3."""
+    y = synth.sv_observations(1000, seed=2)[:6]
+    g = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, m=1024, M=256, B=3, mode="adaptive", tau=0.3, seed=9)
+    for b in (0, 2):
+        o = oracle.airpf(synth.MODEL_SV, synth.SV_THETA, y, m=1024, M=256, mode=oracle.MODE_ADAPTIVE,
+                         tau=0.3, seed=9, chain=b)
+        compare_filter(g, b, o, m=1024, what=f"full-size b={b}")
