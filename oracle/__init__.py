@@ -52,6 +52,7 @@ def lib():
                                            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                            ctypes.c_uint32, _D, _D]
         _lib.oracle_model_valid.argtypes = [ctypes.c_int, ctypes.c_int, _D]
+        _lib.oracle_set_tie_rel.argtypes = [ctypes.c_double]
         _lib.oracle_airpf_batch.argtypes = [ctypes.c_int] * 6 + [ctypes.c_int, ctypes.c_double,
                                             ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.c_int, _D, _D, _D, _D]
@@ -84,9 +85,12 @@ def _model_data(model_data):
 
 
 def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, seed=0, chain=0,
-          iter=0, model_data=None, record=True):
+          iter=0, model_data=None, record=True, tie_rel=1e-12):
     """Literal Algorithm 1 (FP64).  Returns a dict with log_z and, if record,
-    logz_trace[T], anc[T, N], src[T, m], enf[T, S+1], sstar[T], xfinal[N, dx], tie."""
+    logz_trace[T], anc[T, N], src[T, m], enf[T, S+1], sstar[T], xfinal[N, dx], tie.
+    tie_rel: relative width of the band around a threshold in which a draw, an island
+    choice or an ENF test is flagged as a tie (a diagnostic; the arithmetic is unchanged)."""
+    lib().oracle_set_tie_rel(tie_rel)
     y = _f64(y)
     T = len(y) // dy
     S = int(round(math.log2(m)))
@@ -103,6 +107,7 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
                             _dp(th), _dp(md), _dp(y), _dp(lz), _dp(out.get("logz_trace")),
                             _ip(out.get("anc")), _ip(out.get("src")), _dp(out.get("enf")),
                             _ip(out.get("sstar")), _dp(out.get("xfinal")), _ip(tie))
+    lib().oracle_set_tie_rel(1e-12)
     if rc:
         raise ValueError("oracle_airpf rejected its arguments")
     out["log_z"] = float(lz[0])

@@ -74,7 +74,11 @@ enum { MODEL_AR1 = 0, MODEL_SV = 1, MODEL_NGM = 2, MODEL_LGSSM = 3, MODEL_TOY = 
 enum { MODE_NEVER = 0, MODE_ALWAYS = 1, MODE_ADAPTIVE = 2 };
 enum { TIE_NONE = 0, TIE_RESAMPLE = 1, TIE_ISLAND = 2, TIE_ENF = 3 };
 
-#define TIE_REL 1e-12
+/* relative width of the tie band; 1e-12 for FP64 comparisons, set wider to
+ * compare a float implementation draw by draw */
+static double TIE_REL = 1e-12;
+
+void oracle_set_tie_rel(double v) { TIE_REL = v > 0 ? v : 1e-12; }
 
 typedef struct {
     uint64_t seed;

@@ -247,7 +247,13 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.T = cfg->T; p.S = ctx->S; p.mode = cfg->mode; p.model = cfg->model;
     p.fp64 = cfg->precision == AIRPF_FP64;
     p.tau = cfg->tau;
-    airpf::choose_mapping(cfg->m, cfg->M, p.fp64, &p.tpi, &p.ppt, &p.G);
+    {
+        // tuning overrides of the island-to-thread mapping (particles per thread, islands per CTA)
+        const char* e_ppt = getenv("AIRPF_PPT");
+        const char* e_g = getenv("AIRPF_ISLANDS_PER_CTA");
+        airpf::choose_mapping(cfg->m, cfg->M, p.fp64, e_ppt ? atoi(e_ppt) : 0, e_g ? atoi(e_g) : 0, &p.tpi,
+                              &p.ppt, &p.G);
+    }
     p.theta_dim = ctx->theta_dim;
     p.seed_lo = (uint32_t)(cfg->seed & 0xffffffffu);
     p.seed_hi = (uint32_t)(cfg->seed >> 32);

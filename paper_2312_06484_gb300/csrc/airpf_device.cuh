@@ -100,6 +100,7 @@ template <typename R>
 struct ModelPar {
     R th[kMaxTheta];
     R c0, c1, c2, c3;        // model-specific derived constants
+    R drift;                 // per-step constant (NGM: 8 cos(1.2 t))
 };
 
 template <typename R, int MODEL>
@@ -129,6 +130,14 @@ __device__ __forceinline__ void model_setup(ModelPar<R>& p, const double* theta,
         p.c1 = (R)(0.5 / r);
         p.c2 = (R)(-0.5 * dy * log(2.0 * 3.141592653589793 * r));
     }
+    p.drift = (R)0;
+}
+
+// per-step constants of the transition at time t
+template <typename R, int MODEL>
+__device__ __forceinline__ void model_step_setup(ModelPar<R>& p, int t)
+{
+    if (MODEL == NGM) p.drift = (R)(8.0 * cos(1.2 * (double)t));
 }
 
 // Normals z[0..n-1] of (kind, unit, t): pair b gives z[2b], z[2b+1].  Also
@@ -190,7 +199,7 @@ __device__ __forceinline__ uint32_t model_step(const ModelPar<R>& p, const Strea
     if (MODEL == SV) x[0] = p.th[0] + p.th[1] * (xp[0] - p.th[0]) + p.th[2] * z[0];
     if (MODEL == NGM) {
         const R v = xp[0];
-        x[0] = (R)0.5 * v + (R)25 * v / ((R)1 + v * v) + (R)(8.0 * cos(1.2 * (double)t)) + p.c0 * z[0];
+        x[0] = (R)0.5 * v + (R)25 * v / ((R)1 + v * v) + p.drift + p.c0 * z[0];
     }
     if (MODEL == TOY) x[0] = (unif_f64(w0) < (double)p.c0) ? (R)1 - xp[0] : xp[0];
     if (MODEL == LGSSM) {

@@ -53,7 +53,8 @@ cudaError_t launch_step(const StepParams& p, int t, cudaStream_t stream);
 // Writes the run parameters (one thread).
 cudaError_t launch_set_run(RunParams* d_run, uint32_t iter, uint32_t chain0, cudaStream_t stream);
 
-// Choose (tpi, ppt, G) for M particles per island and m islands per filter.
-void choose_mapping(int m, int M, int fp64, int* tpi, int* ppt, int* G);
+// Choose (tpi, ppt, G) for M particles per island and m islands per filter;
+// want_ppt / want_g of 0 take the defaults.
+void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, int* ppt, int* G);
 
 }  // namespace airpf

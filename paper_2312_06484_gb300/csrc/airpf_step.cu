@@ -78,7 +78,8 @@ __host__ __device__ inline Layout make_layout(const StepParams& p)
     L.small = align16(treeb > islandb ? treeb : islandb);
     const size_t smallb = align16(sizeof(double) * (size_t)p.G) + align16(2 * sizeof(int) * (size_t)p.G)
                           + align16(sizeof(double) * 16)
-                          + align16(rsz * (size_t)(p.dx * p.dx + p.dy * p.dx + kMaxDy));
+                          + align16(rsz * (size_t)(p.dx * p.dx + p.dy * p.dx + kMaxDy))
+                          + align16(sizeof(ModelPar<double>));
     L.total = L.small + smallb;
     return L;
 }
@@ -117,6 +118,29 @@ struct XW {
     double r;
     int e;
 };
+
+// v = r 2^e with r in [0.5, 1), by exponent-field manipulation (v > 0 normal);
+// falls back to frexp for subnormal inputs.
+__device__ __forceinline__ XW xw_from_bits(double v, int e_add)
+{
+    XW w;
+    if (!(v > 0.0)) {
+        w.r = 0.0;
+        w.e = 0;
+        return w;
+    }
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) {
+        int e2;
+        w.r = frexp(v, &e2);
+        w.e = e2 + e_add;
+        return w;
+    }
+    w.r = __longlong_as_double((b & ~(0x7ffLL << 52)) | (1022LL << 52));
+    w.e = ex - 1022 + e_add;
+    return w;
+}
 
 __device__ __forceinline__ XW xw_from(double v, int e_add)
 {
@@ -186,37 +210,43 @@ __device__ void cascade(const StepParams& p, int c, int tp, int k0, const Stream
         }
     }
     __syncthreads();
-    // 4. ENF per stage, s*, log-likelihood increment
-    if (tid == 0) {
+    // 4. s*: stage s interacts iff ENF_s < tau, i.e. Tot^2 2^(s-1) < tau m Q_{s-1};
+    //    tested for all stages at once by the first warp (no division)
+    if (tid < 32) {
         const double tot = tree[tree_off(m, S)];
-        double enf_s[kMaxStages + 1];
-        for (int s = 1; s <= S; ++s)
-            enf_s[s] = (tot > 0.0) ? tot * tot * ldexp(1.0, s - 1) / ((double)m * Q[s - 1]) : 0.0;
-        int ss;
-        if (p.mode == 0) {
-            ss = 1;
-        } else if (p.mode == 1) {
-            ss = S + 1;
-        } else {
-            ss = S + 1;
-            for (int s = 1; s <= S; ++s)
-                if (!(enf_s[s] < p.tau)) { ss = s; break; }
+        bool quiet = false;
+        if (tid < S) {
+            const int s = tid + 1;
+            quiet = (tot > 0.0) && !(tot * tot * ldexp(1.0, s - 1) < p.tau * (double)m * Q[s - 1]);
         }
-        iscal[1] = ss;
-        scal[0] = tot;
-        if (designated) {
-            const double L = (tot > 0.0) ? log(tot) - log((double)m) + (double)emax * 0.6931471805599453
-                                         : -INFINITY;
-            const double lz = p.logz[c] + L;
-            p.logz[c] = lz;
-            if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
-            if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ss;
-            if (p.enf) {
-                double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (S + 1);
-                for (int s = 1; s <= S; ++s) e[s] = enf_s[s <= ss ? s : ss];
-                if (tp < p.T) {
-                    const double nxt = (tot > 0.0) ? (ss <= S ? enf_s[ss] : 1.0) : 0.0;
-                    p.enf[((size_t)c * p.T + tp) * (S + 1)] = nxt;
+        const unsigned qm = __ballot_sync(0xffffffffu, quiet);
+        if (tid == 0) {
+            int ss;
+            if (p.mode == 0) ss = 1;
+            else if (p.mode == 1) ss = S + 1;
+            else ss = qm ? (__ffs(qm)) : S + 1;       // first quiet stage
+            iscal[1] = ss;
+            scal[0] = tot;
+            if (designated) {
+                const double L = (tot > 0.0) ? log(tot) - log((double)m) + (double)emax * 0.6931471805599453
+                                             : -INFINITY;
+                const double lz = p.logz[c] + L;
+                p.logz[c] = lz;
+                if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
+                if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ss;
+                if (p.enf) {
+                    double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (S + 1);
+                    double last = 1.0;
+                    for (int s = 1; s <= S; ++s) {
+                        const int sr = s <= ss ? s : ss;
+                        const double v = (tot > 0.0) ? tot * tot * ldexp(1.0, sr - 1) / ((double)m * Q[sr - 1]) : 0.0;
+                        e[s] = v;
+                        if (s == ss) last = v;
+                    }
+                    if (tp < p.T) {
+                        const double nxt = (tot > 0.0) ? (ss <= S ? last : 1.0) : 0.0;
+                        p.enf[((size_t)c * p.T + tp) * (S + 1)] = nxt;
+                    }
                 }
             }
         }
@@ -244,6 +274,143 @@ __device__ void cascade(const StepParams& p, int c, int tp, int k0, const Stream
             const double hi = tree[tree_off(m, l) + (pi | 1)];
             const double u = unif_f64(st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x);
             j = (u * (lo + hi) < lo) ? (j & ~b) : (j | b);
+        }
+        own_src[g] = j;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Cascade of step tp in the FP32-mixed path: the same steps as cascade(), with
+// the island weights turned into 64-bit fixed-point leaves relative to the
+// largest island (50 fractional bits for the largest weight), so that the block
+// sums are exact integers, identical in every CTA and cheap; the ENF test uses
+// float, the island choice u (W_lo + W_hi) < W_lo is decided exactly in 128-bit
+// integers, and log Z and the normalisation use the exact total in double.
+// ---------------------------------------------------------------------------
+__device__ void cascade_fx(const StepParams& p, int c, int tp, int k0, const Stream& st, double* tree_d,
+                           double* scal, double* own_wr, int* own_we, int* own_src, bool designated)
+{
+    using u64 = unsigned long long;
+    const int m = p.m, S = p.S, tid = threadIdx.x, nthr = blockDim.x;
+    const double* wr = p.wr[tp & 1] + (size_t)c * m;
+    const int* we = p.we[tp & 1] + (size_t)c * m;
+    u64* tree = reinterpret_cast<u64*>(tree_d);
+    float* Q = reinterpret_cast<float*>(tree_d + 2 * m);          // [kMaxStages]
+    int* iscal = reinterpret_cast<int*>(tree_d + 2 * m + kMaxStages);
+
+    int emax = INT_MIN;
+    for (int k = tid; k < m; k += nthr) {
+        if (wr[k] > 0.0 && we[k] > emax) emax = we[k];
+    }
+    emax = warp_max(emax);
+    if (tid == 0) iscal[0] = INT_MIN;
+    __syncthreads();
+    if ((tid & 31) == 0) atomicMax(&iscal[0], emax);
+    __syncthreads();
+    emax = iscal[0];
+    const bool dead = (emax == INT_MIN);
+
+    // leaves: r in [0.5,1) has a 53-bit significand; shift it to the common scale
+    for (int k = tid; k < m; k += nthr) {
+        const double r = wr[k];
+        u64 leaf = 0;
+        if (!dead && r > 0.0) {
+            const int sh = emax - we[k] + 3;
+            const u64 mant = ((u64)__double_as_longlong(r) & ((1ull << 52) - 1)) | (1ull << 52);
+            leaf = (sh < 64) ? (mant >> sh) : 0ull;
+        }
+        tree[k] = leaf;
+    }
+    __syncthreads();
+    for (int l = 1; l <= S; ++l) {
+        const int n = m >> l;
+        u64* dst = tree + tree_off(m, l);
+        const u64* src = tree + tree_off(m, l - 1);
+        for (int b = tid; b < n; b += nthr) dst[b] = src[2 * b] + src[2 * b + 1];
+        __syncthreads();
+    }
+    {
+        const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+        for (int l = warp; l < S; l += nw) {
+            const int n = m >> l;
+            const u64* v = tree + tree_off(m, l);
+            float acc = 0.0f;
+            for (int b = lane; b < n; b += 32) {
+                const float x = __ull2float_rn(v[b]) * 0x1p-62f;
+                acc = fmaf(x, x, acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) Q[l] = acc;
+        }
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const u64 tot = tree[tree_off(m, S)];
+        const float totf = __ull2float_rn(tot) * 0x1p-62f;
+        bool quiet = false;
+        if (tid < S) {
+            const int s = tid + 1;
+            quiet = (tot > 0) && !(totf * totf * ldexpf(1.0f, s - 1) < (float)p.tau * (float)m * Q[s - 1]);
+        }
+        const unsigned qm = __ballot_sync(0xffffffffu, quiet);
+        if (tid == 0) {
+            int ss;
+            if (p.mode == 0) ss = 1;
+            else if (p.mode == 1) ss = S + 1;
+            else ss = qm ? __ffs(qm) : S + 1;
+            iscal[1] = ss;
+            scal[0] = (double)tot;
+            if (designated) {
+                // sum_k W'_k = tot 2^(emax - 50)
+                const double L = (tot > 0) ? log((double)tot) - log((double)m) + (double)(emax - 50) * 0.6931471805599453
+                                           : -INFINITY;
+                const double lz = p.logz[c] + L;
+                p.logz[c] = lz;
+                if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
+                if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ss;
+                if (p.enf) {
+                    double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (S + 1);
+                    double last = 1.0;
+                    for (int s = 1; s <= S; ++s) {
+                        const int sr = s <= ss ? s : ss;
+                        const double v = (tot > 0) ? (double)totf * totf * ldexp(1.0, sr - 1) / ((double)m * Q[sr - 1]) : 0.0;
+                        e[s] = v;
+                        if (s == ss) last = v;
+                    }
+                    if (tp < p.T) p.enf[((size_t)c * p.T + tp) * (S + 1)] = (tot > 0) ? (ss <= S ? last : 1.0) : 0.0;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int ss = iscal[1];
+    const double totd = scal[0];
+    const int lvl = ss - 1;
+    for (int g = tid; g < p.G; g += nthr) {
+        const int k = k0 + g;
+        if (dead) {
+            own_wr[g] = 0.0;
+            own_we[g] = 0;
+        } else {
+            const double bsum = (double)tree[tree_off(m, lvl) + (k >> lvl)];
+            const XW w = xw_from_bits(bsum * (double)m / (totd * ldexp(1.0, lvl)), 0);
+            own_wr[g] = w.r;
+            own_we[g] = w.e;
+        }
+        int j = k;
+        for (int s = lvl; s >= 1; --s) {
+            const int l = s - 1, b = 1 << l, pi = j >> l;
+            const u64 lo = tree[tree_off(m, l) + (pi & ~1)];
+            const u64 hi = tree[tree_off(m, l) + (pi | 1)];
+            const u64 w2 = 2ull * (u64)st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x + 1ull;
+            // (2w+1)(lo+hi) < 2^33 lo, in 128 bits
+            const u64 sum = lo + hi;
+            const u64 p_lo = w2 * sum, p_hi = __umul64hi(w2, sum);
+            const u64 r_lo = lo << 33, r_hi = lo >> 31;
+            const bool pick_lo = (p_hi < r_hi) || (p_hi == r_hi && p_lo < r_lo);
+            j = pick_lo ? (j & ~b) : (j | b);
         }
         own_src[g] = j;
     }
@@ -289,7 +456,8 @@ __global__ void __launch_bounds__(kMaxThreads) airpf_step_kernel(StepParams p, i
         }
         __syncthreads();
     } else {
-        cascade(p, c, t - 1, k0, st, tree, scal, own_wr, own_we, own_src, designated);
+        if constexpr (sizeof(R) == 8) cascade(p, c, t - 1, k0, st, tree, scal, own_wr, own_we, own_src, designated);
+        else cascade_fx(p, c, t - 1, k0, st, tree, scal, own_wr, own_we, own_src, designated);
     }
 
     // ---- lineage of step t-1: parent of particle (k, i) among time-(t-1) particles ----
@@ -311,8 +479,12 @@ __global__ void __launch_bounds__(kMaxThreads) airpf_step_kernel(StepParams p, i
     double* mxr_all = reinterpret_cast<double*>(smem + L.island + L.mxr);
     const int nwi = (p.tpi + 31) >> 5;
 
-    ModelPar<R> mp;
-    model_setup<R, MODEL>(mp, p.theta + (size_t)c * p.theta_dim, dx, p.dy);
+    ModelPar<R>* mps = reinterpret_cast<ModelPar<R>*>(
+        reinterpret_cast<unsigned char*>(mshared) + align16(sizeof(R) * (size_t)(dx * dx + p.dy * dx + kMaxDy)));
+    if (tid == 0) {
+        model_setup<R, MODEL>(*mps, p.theta + (size_t)c * p.theta_dim, dx, p.dy);
+        model_step_setup<R, MODEL>(*mps, t);
+    }
     R* Am = mshared;
     R* Cm = mshared + dx * dx;
     R* yv = Cm + p.dy * dx;
@@ -321,6 +493,7 @@ __global__ void __launch_bounds__(kMaxThreads) airpf_step_kernel(StepParams p, i
     }
     for (int q = tid; q < p.dy; q += blockDim.x) yv[q] = (R)p.y[(size_t)(t - 1) * p.dy + q];
     __syncthreads();     // also orders the cascade's smem reads before the island work reuses it
+    const ModelPar<R> mp = *mps;
 
     const int g = tid / p.tpi, li = tid - g * p.tpi;
     const int lane = tid & 31, wi = li >> 5;   // warp index within the island
@@ -415,30 +588,36 @@ __global__ void __launch_bounds__(kMaxThreads) airpf_step_kernel(StepParams p, i
     __syncthreads();
     const Cdf total = cdf[M - 1];
 
-    // multinomial draws: ancestor of draw j = first i with C_i > u_j C_{M-1}
+    // multinomial draws: ancestor of draw j = first i with C_i > u_j C_{M-1}.
+    // Fixed-depth branchless lower bound, the thread's draws advanced together.
     int* ires_out = (p.ires[t & 1] != nullptr) ? p.ires[t & 1] + (size_t)c * N + (size_t)k * M : nullptr;
+    Cdf target[kPptMax];
+    int base[kPptMax];
+#pragma unroll
+    for (int r = 0; r < kPptMax; ++r) {
+        base[r] = 0;
+        if constexpr (sizeof(R) == 8) {
+            target[r] = unif_f64(wres[r]) * total;
+        } else {
+            const unsigned long long hi = total >> 32;
+            const uint32_t lo = (uint32_t)(total & 0xffffffffull);
+            target[r] = (unsigned long long)wres[r] * hi + (unsigned long long)__umulhi(wres[r], lo);
+        }
+    }
+    for (int n = M; n > 1;) {
+        const int half = n >> 1;
+#pragma unroll
+        for (int r = 0; r < kPptMax; ++r) {
+            const Cdf v = cdf[base[r] + half - 1];
+            base[r] = (v > target[r]) ? base[r] : base[r] + half;
+        }
+        n -= half;
+    }
 #pragma unroll
     for (int r = 0; r < kPptMax; ++r) {
         const int j = li * p.ppt + r;
         if (r < p.ppt && j < M) {
-            int a = j;
-            if (alive) {
-                Cdf target;
-                if constexpr (sizeof(R) == 8) {
-                    target = unif_f64(wres[r]) * total;
-                } else {
-                    const unsigned long long hi = total >> 32;
-                    const uint32_t lo = (uint32_t)(total & 0xffffffffull);
-                    target = (unsigned long long)wres[r] * hi + (unsigned long long)__umulhi(wres[r], lo);
-                }
-                int lo_i = 0, hi_i = M - 1;
-                while (lo_i < hi_i) {
-                    const int mid = (lo_i + hi_i) >> 1;
-                    if (cdf[mid] > target) hi_i = mid;
-                    else lo_i = mid + 1;
-                }
-                a = lo_i;
-            }
+            const int a = alive ? base[r] : j;
 #pragma unroll
             for (int d = 0; d < DX; ++d)
                 if (d < dx) Xc[((size_t)c * dx + d) * N + (size_t)k * M + j] = xs[(size_t)d * M + a];
@@ -451,16 +630,23 @@ __global__ void __launch_bounds__(kMaxThreads) airpf_step_kernel(StepParams p, i
         XW w{0.0, 0};
         const double wr0 = own_wr[g];
         if (alive && wr0 > 0.0) {
-            double ssum;
-            if constexpr (sizeof(R) == 8) ssum = (double)total;
-            else ssum = (double)total * 0x1p-31;
-            double mxd = (double)mx;
-            mxd = fmin(fmax(mxd, -1.0e7), 1.0e7);
-            const double n = floor(mxd * 1.4426950408889634);
-            // two-constant reduction of mxd - n ln 2 (Cody and Waite, 1980)
-            double f = fma(-n, 0.6931471805599453, mxd);
-            f = fma(-n, 2.3190468138462996e-17, f);
-            w = xw_from(exp(f) * (ssum / (double)M) * wr0, own_we[g] + (int)n);
+            if constexpr (sizeof(R) == 8) {
+                double mxd = fmin(fmax((double)mx, -1.0e7), 1.0e7);
+                const double n = floor(mxd * 1.4426950408889634);
+                // two-constant reduction of mxd - n ln 2 (Cody and Waite, 1980)
+                double f = fma(-n, 0.6931471805599453, mxd);
+                f = fma(-n, 2.3190468138462996e-17, f);
+                w = xw_from_bits(exp(f) * ((double)total / (double)M) * wr0, own_we[g] + (int)n);
+            } else {
+                // float log-weights: exp of the reduced argument in float, the
+                // product and the exponent bookkeeping in double / integers
+                const float mxf = fminf(fmaxf((float)mx, -1.0e7f), 1.0e7f);
+                const float n = floorf(mxf * 1.44269504f);
+                float f = fmaf(-n, 0.693145752f, mxf);
+                f = fmaf(-n, 1.42860677e-06f, f);
+                const double ef = (double)__expf(f);
+                w = xw_from_bits(ef * ((double)total * (0x1p-31 / (double)M)) * wr0, own_we[g] + (int)n);
+            }
         }
         p.wr[t & 1][(size_t)c * p.m + k] = w.r;
         p.we[t & 1][(size_t)c * p.m + k] = w.e;
@@ -476,14 +662,20 @@ __global__ void set_run_kernel(RunParams* r, uint32_t iter, uint32_t chain0)
 // ---------------------------------------------------------------------------
 size_t step_smem_bytes(const StepParams& p) { return make_layout(p).total; }
 
-void choose_mapping(int m, int M, int fp64, int* tpi, int* ppt, int* G)
+void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, int* ppt, int* G)
 {
     (void)fp64;
+    // particles per thread: requested (1, 2 or 4) or 4; threads per island a
+    // multiple of 32 covering M; islands per CTA up to 256 threads (or requested)
+    int pp = (want_ppt == 1 || want_ppt == 2 || want_ppt == 4) ? want_ppt : kPptMax;
     int t = 32;
-    while (t * kPptMax < M && t < kMaxThreads) t *= 2;
+    while (t * pp < M && t < kMaxThreads) t *= 2;
+    if (t * pp < M) pp = (M + t - 1) / t;
     *tpi = t;
     *ppt = (M + t - 1) / t;
     int g = kMaxThreads / t;
+    if (want_g > 0 && want_g < g) g = want_g;
+    while (g > 1 && (g & (g - 1))) --g;      // a power of 2 dividing m
     if (g > m) g = m;
     *G = g < 1 ? 1 : g;
 }
