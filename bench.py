@@ -178,7 +178,9 @@ def run_gpu(args) -> None:
     theta = torch.tensor(synth.SV_THETA[None, :], device="cuda")
     y = torch.tensor(y_np, device="cuda")
     f = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
-                 seed=1)
+                 seed=1, launch=args.launch)
+    launch_name = {1: "steps (CUDA graph)", 2: "persistent, CTA per filter",
+                   3: "persistent cooperative grid"}[f.launch_mode]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     chain = rank
@@ -204,7 +206,7 @@ def run_gpu(args) -> None:
         lzs.append(one(j))
         ends[j].record(stream)
         launches += f.launch_count()
-    torch.cuda.synchronize()
+    f.sync()
     clk = clocks.stop()
     if dist:
         dist.barrier()
@@ -240,7 +242,7 @@ def run_gpu(args) -> None:
     fp64 = None
     if not args.no_fp64 and prec != "fp64":
         f64 = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU,
-                       precision="fp64", seed=1)
+                       precision="fp64", seed=1, launch=args.launch)
         f64.run(theta, y, chain0=chain, iter=0xFFFF0000)
         torch.cuda.synchronize()
         n64 = max(3, min(args.steps, 40))
@@ -261,7 +263,7 @@ def run_gpu(args) -> None:
 
     peaks, peak_src = _peaks()
     ms_step = tot_ms / args.steps
-    steps_per_pass = T_OBS + 1
+    steps_per_pass = T_OBS + 1      # time steps a pass executes (one launch each, or one loop trip)
     achieved = OPS_PER_PARTICLE_STEP * ps / (ms_step / 1e3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     line = {
@@ -272,7 +274,7 @@ def run_gpu(args) -> None:
         "config": {"workload": WORKLOAD, "model": "SV", "m": M_ISL, "M": M_PART, "N": M_ISL * M_PART,
                    "T": T_OBS, "interaction": f"adaptive tau={TAU}", "precision": prec,
                    "l2": "flushed between timed steps (256 MiB write, outside the step events)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "launch": launch_name},
         "pmcmc_iters_per_s": None,
         "filter_passes_per_s": args.steps * ws / (tot_ms / 1e3),
         "clocks": clk,
@@ -303,6 +305,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--launch", default="auto", choices=["auto", "steps", "grid"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -82,12 +82,27 @@ typedef enum {
 
 /* FP64: every particle computation in double.  FP32_MIXED: propagation,
  * log-weights and the island log-sum-exp in float, internal-resampling CDF as
- * an exact fixed-point integer prefix sum, island weights, their
- * normalisation and the log Z accumulation in double. */
+ * an exact fixed-point integer prefix sum; island weights (unnormalised, as
+ * in Algorithm 1, with an integer binary exponent for range), their sums
+ * (exact fixed point) and log Z in double. */
 typedef enum {
     AIRPF_FP64 = 0,
     AIRPF_FP32_MIXED = 1
 } airpf_precision;
+
+/* How a pass over y_1..y_T is launched.  AUTO picks PERSISTENT_CTA when a
+ * whole filter fits one CTA (m * threads-per-island <= 512), else
+ * PERSISTENT_GRID when every CTA of the pass can be resident at once, else
+ * STEPS.  STEPS: one launch per time step, replayed from a CUDA graph.
+ * PERSISTENT_CTA: one launch for all steps, one CTA per filter.
+ * PERSISTENT_GRID: one cooperative launch for all steps, a bounded grid
+ * barrier (1 s) between steps; a timed-out wait is reported by airpf_sync. */
+typedef enum {
+    AIRPF_LAUNCH_AUTO = 0,
+    AIRPF_LAUNCH_STEPS = 1,
+    AIRPF_LAUNCH_PERSISTENT_CTA = 2,
+    AIRPF_LAUNCH_PERSISTENT_GRID = 3
+} airpf_launch;
 
 typedef struct {
     int32_t model;          /* airpf_model */
@@ -101,6 +116,8 @@ typedef struct {
     int32_t precision;      /* airpf_precision */
     int32_t record;         /* bit 0: ancestors, bit 1: ENF and s*, bit 2: log Z trace */
     uint64_t seed;
+    int32_t launch;         /* airpf_launch (a requested mode that cannot run: AIRPF_ERR_UNSUPPORTED) */
+    int32_t reserved;       /* must be 0 */
 } airpf_config;
 
 #define AIRPF_RECORD_LINEAGE 1
@@ -165,6 +182,22 @@ airpf_status airpf_pmmh(airpf_ctx* ctx, const double* d_y, const double* step, c
                         const double* hi, double* d_state_theta, double* d_state_logz,
                         uint32_t chain0, uint32_t iter0, int32_t iters, double* d_theta_out,
                         double* d_logz_out, int32_t* d_n_accept);
+
+/* Waits for the context's stream and reports device-side failures of the
+ * work enqueued so far: AIRPF_ERR_TIMEOUT if a bounded grid-barrier wait ran
+ * out (the results of that pass are invalid; the context stays usable),
+ * AIRPF_ERR_CUDA for a CUDA error. */
+airpf_status airpf_sync(airpf_ctx* ctx);
+
+/* The airpf_launch mode the context resolved to (never AUTO). */
+int32_t airpf_launch_mode(const airpf_ctx* ctx);
+
+/* Fault injection for tests of the failure path, no counterpart in the paper.
+ * what = 1: in the next PERSISTENT_GRID pass, CTA 0 leaves before the first
+ * grid barrier, so the other CTAs' bounded wait runs out after about a second
+ * and airpf_sync returns AIRPF_ERR_TIMEOUT.  what = 0 clears it.  Returns
+ * AIRPF_ERR_UNSUPPORTED for other launch modes. */
+airpf_status airpf_debug_inject(airpf_ctx* ctx, int32_t what);
 
 /* Number of model parameters for (model, dx); 0 for an unknown model. */
 int32_t airpf_theta_dim(int32_t model, int32_t dx);

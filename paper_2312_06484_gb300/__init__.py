@@ -19,9 +19,12 @@ MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY = 0, 1, 2, 3, 4
 NEVER, ALWAYS, ADAPTIVE = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
 RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE = 1, 2, 4
+LAUNCH_AUTO, LAUNCH_STEPS, LAUNCH_PERSISTENT_CTA, LAUNCH_PERSISTENT_GRID = 0, 1, 2, 3
 
 _MODES = {"never": NEVER, "always": ALWAYS, "adaptive": ADAPTIVE}
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED}
+_LAUNCH = {"auto": LAUNCH_AUTO, "steps": LAUNCH_STEPS, "cta": LAUNCH_PERSISTENT_CTA,
+           "grid": LAUNCH_PERSISTENT_GRID}
 
 
 def theta_dim(model: int, dx: int = 1) -> int:
@@ -40,14 +43,15 @@ class AIRPF:
 
     def __init__(self, model: int, *, m: int, M: int, T: int, B: int = 1, dx: int = 1, dy: int = 1,
                  mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, record: int = 0,
-                 model_data=None, stream=None):
+                 model_data=None, stream=None, launch="auto"):
         import torch
         self._torch = torch
         self.lib = _binding.load()
         mode = _MODES[mode] if isinstance(mode, str) else int(mode)
         precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        launch = _LAUNCH[launch] if isinstance(launch, str) else int(launch)
         self.cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau,
-                               precision=precision, record=record, seed=seed)
+                               precision=precision, record=record, seed=seed, launch=launch, reserved=0)
         nbytes = ctypes.c_size_t()
         _binding.check(self.lib.airpf_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)))
         self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
@@ -101,6 +105,18 @@ class AIRPF:
     def launch_count(self) -> int:
         return int(self.lib.airpf_last_launch_count(self.ctx))
 
+    @property
+    def launch_mode(self) -> int:
+        return int(self.lib.airpf_launch_mode(self.ctx))
+
+    def sync(self):
+        """Wait for the stream; raises AirpfError (AIRPF_ERR_TIMEOUT) if a bounded device wait ran out."""
+        _binding.check(self.lib.airpf_sync(self.ctx), self.ctx)
+
+    def inject(self, what: int):
+        """Test hook of the failure path (see airpf_debug_inject)."""
+        _binding.check(self.lib.airpf_debug_inject(self.ctx, what), self.ctx)
+
     def close(self):
         if getattr(self, "ctx", None):
             self.lib.airpf_destroy(self.ctx)
@@ -115,4 +131,5 @@ class AIRPF:
 
 __all__ = ["AIRPF", "AirpfError", "theta_dim", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
            "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
-           "RECORD_ENF", "RECORD_TRACE"]
+           "RECORD_ENF", "RECORD_TRACE", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
+           "LAUNCH_PERSISTENT_GRID"]

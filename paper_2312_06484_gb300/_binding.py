@@ -21,7 +21,7 @@ class AirpfConfig(ctypes.Structure):
     _fields_ = [("model", c_int32), ("dx", c_int32), ("dy", c_int32), ("m", c_int32),
                 ("M", c_int32), ("T", c_int32), ("B", c_int32), ("mode", c_int32),
                 ("tau", c_double), ("precision", c_int32), ("record", c_int32),
-                ("seed", c_uint64)]
+                ("seed", c_uint64), ("launch", c_int32), ("reserved", c_int32)]
 
 
 # every symbol include/airpf.h declares, with (restype, argtypes)
@@ -35,6 +35,9 @@ SIGNATURES = {
     "airpf_run_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint32, c_void_p]),
     "airpf_pmmh": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                              c_uint32, c_uint32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "airpf_sync": (c_int32, [c_void_p]),
+    "airpf_launch_mode": (c_int32, [c_void_p]),
+    "airpf_debug_inject": (c_int32, [c_void_p, c_int32]),
     "airpf_theta_dim": (c_int32, [c_int32, c_int32]),
     "airpf_last_launch_count": (c_int64, [c_void_p]),
     "airpf_last_error": (ctypes.c_char_p, [c_void_p]),

@@ -34,7 +34,7 @@ int ilog2_exact(int m)
 
 // Byte offsets of every buffer inside the workspace.
 struct WsLayout {
-    size_t run, theta, mdata, y, X[2], wr[2], we[2], ires[2], logz, trace, enf, sstar, anc, active;
+    size_t run, theta, mdata, y, X[2], wr[2], we[2], ires[2], logz, trace, enf, sstar, anc, active, mpar, drift, bar;
     size_t pm_prop, pm_logz_prop, pm_stats, total;
 };
 
@@ -50,6 +50,7 @@ struct airpf_ctx {
     cudaStream_t cap_stream;
     cudaGraphExec_t graph;
     bool graph_ready;
+    int launch;               // resolved airpf_launch
     StepParams sp;
     int64_t launches;
     char err[512];
@@ -88,6 +89,8 @@ const char* check_config(const airpf_config* c)
     if (!(c->tau > 0.0 && c->tau <= 1.0)) return "tau must be in (0, 1]";
     if (c->precision != AIRPF_FP64 && c->precision != AIRPF_FP32_MIXED) return "unknown precision";
     if (c->record < 0 || c->record > 7) return "unknown record bits";
+    if (c->launch < 0 || c->launch > 3) return "unknown launch mode";
+    if (c->reserved != 0) return "reserved must be 0";
     return nullptr;
 }
 
@@ -117,6 +120,9 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.sstar = enf ? take(sizeof(int) * B * T) : 0;
     L.anc = lin ? take(sizeof(int) * B * T * N) : 0;
     L.active = take(sizeof(int) * B);
+    L.mpar = take(airpf::model_par_bytes() * B);
+    L.drift = take(sizeof(double) * T);
+    L.bar = take(sizeof(unsigned) * 4);
     L.pm_prop = take(sizeof(double) * B * td);
     L.pm_logz_prop = take(sizeof(double) * B);
     L.pm_stats = take(sizeof(int) * B);
@@ -149,7 +155,7 @@ airpf_status build_graph(airpf_ctx* ctx)
     e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
     cudaError_t le = cudaSuccess;
-    for (int t = 1; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) le = airpf::launch_step(ctx->sp, t, ctx->cap_stream);
+    for (int t = 0; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) le = airpf::launch_step(ctx->sp, t, ctx->cap_stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -167,11 +173,20 @@ airpf_status build_graph(airpf_ctx* ctx)
 // Enqueue one filter pass over the workspace inputs (theta, y, run params already set).
 airpf_status enqueue_pass(airpf_ctx* ctx)
 {
+    if (ctx->launch != AIRPF_LAUNCH_STEPS) {
+        cudaError_t e = airpf::launch_step(ctx->sp, 0, ctx->stream);      // prologue
+        if (e == cudaSuccess)
+            e = airpf::launch_persistent(ctx->sp, ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "persistent launch");
+        ctx->launches += 2;
+        ctx->sp.inject_stall = 0;
+        return AIRPF_OK;
+    }
     airpf_status s = build_graph(ctx);
     if (s != AIRPF_OK) return s;
     cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-    ctx->launches += ctx->cfg.T + 1;
+    ctx->launches += ctx->cfg.T + 2;
     return AIRPF_OK;
 }
 
@@ -247,12 +262,35 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.T = cfg->T; p.S = ctx->S; p.mode = cfg->mode; p.model = cfg->model;
     p.fp64 = cfg->precision == AIRPF_FP64;
     p.tau = cfg->tau;
+    p.inv_M = 1.0 / (double)cfg->M;
     {
         // tuning overrides of the island-to-thread mapping (particles per thread, islands per CTA)
         const char* e_ppt = getenv("AIRPF_PPT");
         const char* e_g = getenv("AIRPF_ISLANDS_PER_CTA");
-        airpf::choose_mapping(cfg->m, cfg->M, p.fp64, e_ppt ? atoi(e_ppt) : 0, e_g ? atoi(e_g) : 0, &p.tpi,
-                              &p.ppt, &p.G);
+        const int want_ppt = e_ppt ? atoi(e_ppt) : 0;
+        int want_g = e_g ? atoi(e_g) : 0;
+        int mode = cfg->launch;
+        if (mode == AIRPF_LAUNCH_AUTO || mode == AIRPF_LAUNCH_PERSISTENT_CTA) {
+            airpf::choose_mapping(cfg->m, cfg->M, p.fp64, want_ppt, cfg->m, &p.tpi, &p.ppt, &p.G);
+            if (p.G == cfg->m && p.G * p.tpi <= airpf::max_cta_threads()) {
+                mode = AIRPF_LAUNCH_PERSISTENT_CTA;
+            } else if (mode == AIRPF_LAUNCH_PERSISTENT_CTA) {
+                set_err(nullptr, "a filter of m=%d islands x M=%d does not fit one CTA", cfg->m, cfg->M);
+                cudaStreamDestroy(ctx->cap_stream);
+                delete ctx;
+                return AIRPF_ERR_UNSUPPORTED;
+            } else {
+                mode = AIRPF_LAUNCH_AUTO;
+            }
+        }
+        if (mode != AIRPF_LAUNCH_PERSISTENT_CTA) {
+            airpf::choose_mapping(cfg->m, cfg->M, p.fp64, want_ppt, want_g, &p.tpi, &p.ppt, &p.G);
+            if (p.G == cfg->m && cfg->m > 1 && p.G * p.tpi > 256) {
+                want_g = cfg->m / 2;
+                airpf::choose_mapping(cfg->m, cfg->M, p.fp64, want_ppt, want_g, &p.tpi, &p.ppt, &p.G);
+            }
+        }
+        ctx->launch = mode;
     }
     p.theta_dim = ctx->theta_dim;
     p.seed_lo = (uint32_t)(cfg->seed & 0xffffffffu);
@@ -262,6 +300,42 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.mdata = at<double>(ctx, L.mdata);
     p.y = at<double>(ctx, L.y);
     p.active = nullptr;
+    p.mpar = at<void>(ctx, L.mpar);
+    p.drift = at<void>(ctx, L.drift);
+    p.bar = at<unsigned>(ctx, L.bar);
+    p.err = at<unsigned>(ctx, L.bar) + 2;
+    p.inject_stall = 0;
+    if (ctx->launch == AIRPF_LAUNCH_AUTO || ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
+        e = airpf::prepare_step(p);
+        const bool fits = (e == cudaSuccess) && airpf::persistent_grid_fits(p);
+        if (fits) {
+            ctx->launch = AIRPF_LAUNCH_PERSISTENT_GRID;
+        } else if (ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
+            set_err(nullptr, "the grid of %d CTAs cannot be resident at once", p.B * (p.m / p.G));
+            cudaStreamDestroy(ctx->cap_stream);
+            delete ctx;
+            return AIRPF_ERR_UNSUPPORTED;
+        } else {
+            ctx->launch = AIRPF_LAUNCH_STEPS;
+        }
+    }
+    e = airpf::prepare_step(p);
+    if (e != cudaSuccess) {
+        set_err(nullptr, "kernel attribute setup: %s", cudaGetErrorString(e));
+        cudaStreamDestroy(ctx->cap_stream);
+        delete ctx;
+        return AIRPF_ERR_CUDA;
+    }
+    {
+        unsigned zero[4] = {0, 0, 0, 0};
+        e = cudaMemcpy(p.bar, zero, sizeof(zero), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            set_err(nullptr, "workspace init: %s", cudaGetErrorString(e));
+            cudaStreamDestroy(ctx->cap_stream);
+            delete ctx;
+            return AIRPF_ERR_CUDA;
+        }
+    }
     for (int i = 0; i < 2; ++i) {
         p.X[i] = at<void>(ctx, L.X[i]);
         p.wr[i] = at<double>(ctx, L.wr[i]);
@@ -345,8 +419,34 @@ airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y
     }
     airpf_status s = airpf_run(ctx, theta, y, chain0, iter, log_z, nullptr, nullptr, nullptr, nullptr);
     if (s != AIRPF_OK) return s;
+    return airpf_sync(ctx);
+}
+
+airpf_status airpf_sync(airpf_ctx* ctx)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    unsigned flag = 0;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    return e == cudaSuccess ? AIRPF_OK : cuda_fail(ctx, e, "cudaStreamSynchronize");
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, ctx->sp.err, sizeof(flag), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "airpf_sync");
+    if (flag) {
+        set_err(ctx, "a grid-barrier wait timed out; the pass's results are invalid");
+        return AIRPF_ERR_TIMEOUT;
+    }
+    return AIRPF_OK;
+}
+
+int32_t airpf_launch_mode(const airpf_ctx* ctx) { return ctx ? ctx->launch : 0; }
+
+airpf_status airpf_debug_inject(airpf_ctx* ctx, int32_t what)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    if (ctx->launch != AIRPF_LAUNCH_PERSISTENT_GRID) {
+        set_err(ctx, "fault injection needs the grid-persistent launch");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    ctx->sp.inject_stall = what == 1 ? 1 : 0;
+    return AIRPF_OK;
 }
 
 airpf_status airpf_pmmh(airpf_ctx* ctx, const double*, const double*, const double*, const double*, double*,

@@ -21,6 +21,7 @@ struct RunParams {
 struct StepParams {
     int B, m, M, N, dx, dy, T, S, mode, model, fp64;
     double tau;
+    double inv_M;                 // 1 / M
     int G, tpi, ppt;              // islands per CTA, threads per island, particles per thread
     int theta_dim;
     uint32_t seed_lo, seed_hi;
@@ -29,6 +30,11 @@ struct StepParams {
     const double* mdata;          // LGSSM: A then C
     const double* y;              // [T][dy]
     const int* active;            // [B] nonzero = run this filter (PMMH), or NULL
+    void* mpar;                   // [B] model constants (written by the prologue)
+    void* drift;                  // [T] per-step transition constant (NGM)
+    unsigned* bar;                // [2] grid barrier: arrivals, generation
+    unsigned* err;                // [1] nonzero after a timed-out wait
+    int inject_stall;             // test hook (grid-persistent launch only)
     void* X[2];                   // particle stores, ping-pong by t & 1
     double* wr[2];
     int* we[2];
@@ -43,12 +49,26 @@ struct StepParams {
 // Shared-memory bytes of one step launch.
 size_t step_smem_bytes(const StepParams& p);
 
+// Bytes of one filter's model constants.
+size_t model_par_bytes();
+
 // Sets kernel attributes (shared-memory opt-in); call outside stream capture.
 cudaError_t prepare_step(const StepParams& p);
 
-// Launches step t (1..T: cascade of step t-1 then the island work of step t;
-// T+1: the final cascade only) on `stream`.
+// Launches step t on `stream`: t = 0 the prologue (model constants), 1..T the
+// cascade of step t-1 then the island work of step t, T+1 the final cascade.
 cudaError_t launch_step(const StepParams& p, int t, cudaStream_t stream);
+
+// One launch running all T+1 steps: grid = cooperative launch over several
+// CTAs per filter, otherwise one CTA per filter.  The prologue (t = 0 launch)
+// must precede it.
+cudaError_t launch_persistent(const StepParams& p, bool grid, cudaStream_t stream);
+
+// Whether every CTA of the grid-persistent launch can be resident at once.
+bool persistent_grid_fits(const StepParams& p);
+
+// Largest CTA of the one-CTA-per-filter launch.
+int max_cta_threads();
 
 // Writes the run parameters (one thread).
 cudaError_t launch_set_run(RunParams* d_run, uint32_t iter, uint32_t chain0, cudaStream_t stream);

@@ -28,7 +28,7 @@ def test_library_exports_every_declared_symbol():
 
 def _cfg(**kw):
     base = dict(model=1, dx=1, dy=1, m=1024, M=256, T=1000, B=1, mode=2, tau=0.3, precision=1,
-                record=0, seed=1)
+                record=0, seed=1, launch=0, reserved=0)
     base.update(kw)
     return _binding.AirpfConfig(**base)
 
@@ -41,7 +41,7 @@ def test_workspace_size_and_argument_checks():
     assert 2 * 262144 * 4 <= n.value < 2 * 262144 * 4 + (1 << 20)
     bad = [dict(m=3), dict(m=8192), dict(M=0), dict(M=1025), dict(T=0), dict(B=0), dict(tau=0.0),
            dict(tau=1.01), dict(mode=3), dict(model=9), dict(dx=2), dict(model=3, dx=9),
-           dict(precision=7), dict(record=8)]
+           dict(precision=7), dict(record=8), dict(launch=4), dict(reserved=1)]
     for kw in bad:
         assert lib.airpf_workspace_bytes(ctypes.byref(_cfg(**kw)), ctypes.byref(n)) == 1, kw
         assert lib.airpf_last_error(None)

@@ -15,17 +15,21 @@ pytestmark = pytest.mark.gpu
 MODES = {"never": oracle.MODE_NEVER, "always": oracle.MODE_ALWAYS, "adaptive": oracle.MODE_ADAPTIVE}
 
 
+@pytest.mark.parametrize("launch", ["steps", "cta"])
 @pytest.mark.parametrize("mode", ["adaptive", "always", "never"])
-def test_ar1_workload_all_modes(gpu_lib, mode):
+def test_ar1_workload_all_modes(gpu_lib, mode, launch):
     y = synth.ar1_observations(100, seed=1)
     B, m, M = 4, 16, 64
     g = run_gpu(synth.MODEL_AR1, synth.AR1_THETA, y, m=m, M=M, B=B, mode=mode, tau=0.3, seed=7,
-                chain0=3, iter=2)
+                chain0=3, iter=2, launch=launch)
     for b in range(B):
         o = oracle.airpf(synth.MODEL_AR1, synth.AR1_THETA, y, m=m, M=M, mode=MODES[mode], tau=0.3,
                          seed=7, chain=3 + b, iter=2)
-        compare_filter(g, b, o, m=m, what=f"{mode} b={b}")
-    assert g["launches"] == 100 + 2
+        compare_filter(g, b, o, m=m, what=f"{mode} {launch} b={b}")
+    if launch == "steps":
+        assert g["launches"] == 100 + 3      # run parameters, prologue, T + 1 steps
+    else:
+        assert g["launches"] == 3 and g["launch_mode"] == 2
 
 
 @pytest.mark.parametrize("model,theta,ymaker,m,M,T,mode,tau", [
@@ -77,12 +81,52 @@ def test_dead_filter_is_minus_infinity(gpu_lib):
     assert np.array_equal(g["anc"][0], o["anc"])
 
 
-def test_full_size_sv_sampled_filters(gpu_lib):
+@pytest.mark.parametrize("launch", ["steps", "grid"])
+def test_full_size_sv_sampled_filters(gpu_lib, launch):
     """m=1024 x M=256 (the SV workload's size) with T shortened to 6, FP64, every record
-    compared for two filters of a batch of 3."""
+    compared: two filters of a batch of 3 in the per-step launch, the single filter of the
+    bench configuration in the grid-persistent launch."""
     y = synth.sv_observations(1000, seed=2)[:6]
-    g = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, m=1024, M=256, B=3, mode="adaptive", tau=0.3, seed=9)
-    for b in (0, 2):
+    B = 3 if launch == "steps" else 1
+    g = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, m=1024, M=256, B=B, mode="adaptive", tau=0.3, seed=9,
+                launch=launch)
+    for b in ((0, 2) if B == 3 else (0,)):
         o = oracle.airpf(synth.MODEL_SV, synth.SV_THETA, y, m=1024, M=256, mode=oracle.MODE_ADAPTIVE,
                          tau=0.3, seed=9, chain=b)
-        compare_filter(g, b, o, m=1024, what=f"full-size b={b}")
+        compare_filter(g, b, o, m=1024, what=f"full-size {launch} b={b}")
+
+
+@pytest.mark.parametrize("launch", ["steps", "grid"])
+def test_adaptive_ngm_long_run(gpu_lib, launch):
+    """Adaptive interaction with frequent partial cascades (nonlinear growth model, tau=0.9),
+    m=256 x M=64 x T=60."""
+    y = synth.ngm_observations(60, seed=5)
+    g = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, m=256, M=64, B=2, mode="adaptive", tau=0.9,
+                seed=12, launch=launch)
+    for b in range(2):
+        o = oracle.airpf(synth.MODEL_NGM, synth.NGM_THETA, y, m=256, M=64, mode=oracle.MODE_ADAPTIVE,
+                         tau=0.9, seed=12, chain=b)
+        compare_filter(g, b, o, m=256, what=f"ngm {launch} b={b}")
+
+
+def test_grid_barrier_timeout_is_reported_and_context_survives(gpu_lib):
+    """A grid-persistent pass whose barrier never completes (one CTA leaves early) ends after
+    the bounded wait with AIRPF_ERR_TIMEOUT; the next pass on the same context is correct."""
+    import torch
+    import paper_2312_06484_gb300 as gp
+    y = synth.sv_observations(8, seed=2)
+    f = gp.AIRPF(synth.MODEL_SV, m=1024, M=256, T=len(y), B=1, mode="adaptive", tau=0.3, seed=9,
+                 launch="grid")
+    th = torch.tensor(synth.SV_THETA[None, :], device="cuda")
+    yy = torch.tensor(y, device="cuda")
+    f.inject(1)
+    f.run(th, yy)
+    with pytest.raises(gp.AirpfError, match="TIMEOUT"):
+        f.sync()
+    out = f.run(th, yy)
+    f.sync()
+    o = oracle.airpf(synth.MODEL_SV, synth.SV_THETA, y, m=1024, M=256, mode=oracle.MODE_ADAPTIVE, tau=0.3,
+                     seed=9, record=False)
+    if o["tie"][0] == 0:
+        assert abs(float(out["log_z"][0]) - o["log_z"]) <= 1e-10 * abs(o["log_z"])
+    f.close()
