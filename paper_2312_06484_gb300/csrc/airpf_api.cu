@@ -34,7 +34,8 @@ int ilog2_exact(int m)
 
 // Byte offsets of every buffer inside the workspace.
 struct WsLayout {
-    size_t run, theta, mdata, y, X[2], wr[2], we[2], ires[2], logz, trace, enf, sstar, anc, active, mpar, drift, bar;
+    size_t run, theta, mdata, y, X[2], pe[2], pt[2], pq[2], csum, cup, nsrc, ires[2], logz, trace, enf,
+        sstar, anc, active, mpar, drift, bar;
     size_t pm_prop, pm_logz_prop, pm_stats, total;
 };
 
@@ -111,8 +112,13 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.mdata = take(sizeof(double) * (size_t)(c->dx * c->dx + c->dy * c->dx));
     L.y = take(sizeof(double) * T * c->dy);
     for (int i = 0; i < 2; ++i) L.X[i] = take(rsz * B * c->dx * N);
-    for (int i = 0; i < 2; ++i) L.wr[i] = take(sizeof(double) * B * c->m);
-    for (int i = 0; i < 2; ++i) L.we[i] = take(sizeof(int) * B * c->m);
+    // CTA records: at most m of them (one island per CTA), each a subtree of 2G nodes
+    for (int i = 0; i < 2; ++i) L.pe[i] = take(sizeof(int) * B * c->m);
+    for (int i = 0; i < 2; ++i) L.pt[i] = take(sizeof(double) * B * 2 * c->m);
+    for (int i = 0; i < 2; ++i) L.pq[i] = take(sizeof(double) * B * c->m * 8);
+    L.csum = take(sizeof(int) * 4 * B);
+    L.cup = take(sizeof(unsigned long long) * B * c->m);
+    L.nsrc = take(sizeof(int) * B * c->m);
     for (int i = 0; i < 2; ++i) L.ires[i] = lin ? take(sizeof(int) * B * N) : 0;
     L.logz = take(sizeof(double) * B);
     L.trace = tr ? take(sizeof(double) * B * T) : 0;
@@ -155,7 +161,10 @@ airpf_status build_graph(airpf_ctx* ctx)
     e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
     cudaError_t le = cudaSuccess;
-    for (int t = 0; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) le = airpf::launch_step(ctx->sp, t, ctx->cap_stream);
+    for (int t = 0; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) {
+        le = airpf::launch_step(ctx->sp, t, ctx->cap_stream);
+        if (le == cudaSuccess && t >= 1 && t <= ctx->cfg.T) le = airpf::launch_cascade(ctx->sp, t, ctx->cap_stream);
+    }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (le != cudaSuccess) {
@@ -186,7 +195,7 @@ airpf_status enqueue_pass(airpf_ctx* ctx)
     if (s != AIRPF_OK) return s;
     cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-    ctx->launches += ctx->cfg.T + 2;
+    ctx->launches += 2 * (int64_t)ctx->cfg.T + 2;
     return AIRPF_OK;
 }
 
@@ -263,6 +272,13 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.fp64 = cfg->precision == AIRPF_FP64;
     p.tau = cfg->tau;
     p.inv_M = 1.0 / (double)cfg->M;
+    p.tau_f = (float)cfg->tau;
+    {
+        int lg = 0;
+        while ((1 << lg) < cfg->M) ++lg;
+        p.cdf_bits = 31 - lg;                   // the CDF total stays below 2^31 + 1
+        p.cdf_scale = ldexpf(1.0f, p.cdf_bits);
+    }
     {
         // tuning overrides of the island-to-thread mapping (particles per thread, islands per CTA)
         const char* e_ppt = getenv("AIRPF_PPT");
@@ -292,6 +308,8 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         }
         ctx->launch = mode;
     }
+    p.P = cfg->m / p.G;
+    p.g = ilog2_exact(p.G);
     p.theta_dim = ctx->theta_dim;
     p.seed_lo = (uint32_t)(cfg->seed & 0xffffffffu);
     p.seed_hi = (uint32_t)(cfg->seed >> 32);
@@ -338,10 +356,14 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     }
     for (int i = 0; i < 2; ++i) {
         p.X[i] = at<void>(ctx, L.X[i]);
-        p.wr[i] = at<double>(ctx, L.wr[i]);
-        p.we[i] = at<int>(ctx, L.we[i]);
+        p.pe[i] = at<int>(ctx, L.pe[i]);
+        p.pt[i] = at<void>(ctx, L.pt[i]);
+        p.pq[i] = at<void>(ctx, L.pq[i]);
         p.ires[i] = (cfg->record & AIRPF_RECORD_LINEAGE) ? at<int>(ctx, L.ires[i]) : nullptr;
     }
+    p.csum = at<int>(ctx, L.csum);
+    p.cup = at<void>(ctx, L.cup);
+    p.nsrc = at<int>(ctx, L.nsrc);
     p.logz = at<double>(ctx, L.logz);
     p.trace = (cfg->record & AIRPF_RECORD_TRACE) ? at<double>(ctx, L.trace) : nullptr;
     p.enf = (cfg->record & AIRPF_RECORD_ENF) ? at<double>(ctx, L.enf) : nullptr;

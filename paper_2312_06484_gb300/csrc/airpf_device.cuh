@@ -22,8 +22,8 @@ struct U4 {
     uint32_t x, y, z, w;
 };
 
-// Ten Philox rounds: two 32x32->64 multiplies per round (mul.lo / mul.hi), the
-// Weyl key bump between rounds.
+// Ten Philox rounds: two 32x32->64 multiplies per round (one wide multiply
+// each), the Weyl key bump between rounds.
 __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                              uint32_t k0, uint32_t k1)
 {
@@ -33,16 +33,14 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t lo0 = 0xD2511F53u * c0;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
-        const uint32_t lo1 = 0xCD9E8D57u * c2;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ k0;
-        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
         c0 = n0;
-        c1 = lo1;
+        c1 = (uint32_t)p1;
         c2 = n2;
-        c3 = lo0;
+        c3 = (uint32_t)p0;
     }
     return U4{c0, c1, c2, c3};
 }
@@ -74,7 +72,8 @@ __device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, double& z0
 __device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, float& z0, float& z1)
 {
     const float u0 = fmaf((float)w0, 0x1p-32f, 0x1p-33f);
-    const float rad = sqrtf(-2.0f * __logf(u0));
+    const float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
+    const float rad = r2 * rsqrtf(r2);
     const float a = fmaf((float)w1, 0x1p-31f, 0x1p-32f) - 1.0f;
     float s, c;
     __sincosf(3.14159265358979f * a, &s, &c);
@@ -186,15 +185,12 @@ __device__ __forceinline__ void model_prior(const ModelPar<R>& p, const Stream& 
     }
 }
 
-// x_t ~ K_t(x_{t-1}, .); returns the internal-resampling word of the unit.
-// A (LGSSM) is row-major dx*dx in shared memory, diagonal taken from theta.
+// x_t = K_t(x_{t-1}, .) given the step's normals z (and word w0 for the binary
+// model).  A (LGSSM) is row-major dx*dx in shared memory, diagonal from theta.
 template <typename R, int MODEL, int DX>
-__device__ __forceinline__ uint32_t model_step(const ModelPar<R>& p, const Stream& st, uint32_t unit,
-                                               uint32_t t, int dx, const R* xp, R* x, const R* A)
+__device__ __forceinline__ void model_transition(const ModelPar<R>& p, int dx, const R* xp, R* x, const R* A,
+                                                 const R* z, uint32_t w0)
 {
-    R z[DX > 1 ? DX : 1];
-    uint32_t w0, w2;
-    stream_normals<R, (MODEL == TOY) ? 0 : DX>(st, KIND_STEP, unit, t, dx, z, w0, w2);
     if (MODEL == AR1) x[0] = p.th[0] * xp[0] + p.th[1] * z[0];
     if (MODEL == SV) x[0] = p.th[0] + p.th[1] * (xp[0] - p.th[0]) + p.th[2] * z[0];
     if (MODEL == NGM) {
@@ -214,6 +210,26 @@ __device__ __forceinline__ uint32_t model_step(const ModelPar<R>& p, const Strea
             }
         }
     }
+}
+
+// The step's random numbers of one unit: the transition normals z, word 0
+// (binary model) and word 2 (internal-resampling draw) of sub-block 0.
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ void model_step_noise(const Stream& st, uint32_t unit, uint32_t t, int dx, R* z,
+                                                 uint32_t& w0, uint32_t& w2)
+{
+    stream_normals<R, (MODEL == TOY) ? 0 : DX>(st, KIND_STEP, unit, t, dx, z, w0, w2);
+}
+
+// x_t ~ K_t(x_{t-1}, .); returns the internal-resampling word of the unit.
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ uint32_t model_step(const ModelPar<R>& p, const Stream& st, uint32_t unit,
+                                               uint32_t t, int dx, const R* xp, R* x, const R* A)
+{
+    R z[DX > 1 ? DX : 1];
+    uint32_t w0, w2;
+    model_step_noise<R, MODEL, DX>(st, unit, t, dx, z, w0, w2);
+    model_transition<R, MODEL, DX>(p, dx, xp, x, A, z, w0);
     return w2;
 }
 

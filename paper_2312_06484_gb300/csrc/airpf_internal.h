@@ -16,12 +16,20 @@ struct RunParams {
 
 // Everything the step kernel needs; passed by value.  Arrays are laid out
 //   particles  X[b][d][k*M + i]   (structure of arrays, one island contiguous)
-//   island weights wr/we[b][k]    (mantissa in [0.5,1) or 0, and a binary
-//                                  exponent: an extended-range double)
+//   CTA records of the island weights, one per CTA j (islands j*G .. j*G+G-1):
+//     pe[b][j]          largest binary exponent of the CTA's island weights
+//     pt[b][j][2G]      the CTA's block-sum subtree, levels 0..g (g = log2 G),
+//                       relative to 2^pe (double, or 64-bit fixed point)
+//     pq[b][j][8]       per-level sums of squares of that subtree, levels 0..g-1
+//   the cascade's result for step t+1: csum[b] (s*, largest exponent), cup[b]
+//   (block sums of level s*-1 if above the CTAs), nsrc[b][k]
 struct StepParams {
     int B, m, M, N, dx, dy, T, S, mode, model, fp64;
     double tau;
     double inv_M;                 // 1 / M
+    float tau_f;                  // tau as float (FP32-mixed ENF test)
+    float cdf_scale;              // 2^cdf_bits: fixed-point scale of the FP32-mixed CDF
+    int cdf_bits;                 // 31 - ceil(log2 M)
     int G, tpi, ppt;              // islands per CTA, threads per island, particles per thread
     int theta_dim;
     uint32_t seed_lo, seed_hi;
@@ -36,8 +44,13 @@ struct StepParams {
     unsigned* err;                // [1] nonzero after a timed-out wait
     int inject_stall;             // test hook (grid-persistent launch only)
     void* X[2];                   // particle stores, ping-pong by t & 1
-    double* wr[2];
-    int* we[2];
+    int P, g;                     // CTA records per filter (m / G) and log2 G
+    int* pe[2];                   // CTA records, ping-pong by t & 1
+    void* pt[2];
+    void* pq[2];
+    int* csum;                    // [B][4] last cascade: s*, largest exponent (INT_MIN: all zero)
+    void* cup;                    // [B][P] upper-tree level s*-1 when it lies above the CTA level
+    int* nsrc;                    // [B][m] inherited block of each island (written when s* > 1)
     int* ires[2];                 // internal ancestors of the last step (lineage), or NULL
     double* logz;                 // [B]
     double* trace;                // [B][T] or NULL
@@ -56,8 +69,12 @@ size_t model_par_bytes();
 cudaError_t prepare_step(const StepParams& p);
 
 // Launches step t on `stream`: t = 0 the prologue (model constants), 1..T the
-// cascade of step t-1 then the island work of step t, T+1 the final cascade.
+// island work of step t (each CTA publishes its record), T+1 the lineage of
+// step T.
 cudaError_t launch_step(const StepParams& p, int t, cudaStream_t stream);
+
+// Launches the cascade of step t (one CTA per filter) on `stream`.
+cudaError_t launch_cascade(const StepParams& p, int t, cudaStream_t stream);
 
 // One launch running all T+1 steps: grid = cooperative launch over several
 // CTAs per filter, otherwise one CTA per filter.  The prologue (t = 0 launch)

@@ -1,0 +1,1146 @@
+// airpf_step_impl.cuh -- the AIRPF time step on sm_103a (kernel templates;
+// instantiated per precision in airpf_launch_f32.cu / airpf_launch_f64.cu).
+//
+// A pass of Algorithm 1 (Heine, arXiv 2312.06484, main loop) is a prologue
+// launch that derives every filter's model constants, then either one launch
+// per time step (replayed from a CUDA graph) or one persistent launch that
+// loops over the steps.  CTA j of a filter owns the G islands j*G .. j*G+G-1.
+//
+// Island weights W^k are kept unnormalised, as in Algorithm 1, in an extended
+// range (mantissa plus integer binary exponent).  At the end of step t each
+// CTA publishes a record of its islands' weights: the largest binary exponent
+// e_j and the binary tree of block sums over its G islands (levels 0..g,
+// g = log2 G) relative to 2^e_j, with the per-level sums of squares.  Level l
+// of the tree over all m islands holds the sums over aligned blocks of 2^l
+// islands; levels below g are inside the records, levels g..S form the upper
+// tree over the m/G record tops.
+//
+// Step t+1 then does:
+//  1. issue the loads of the records and of the CTA's own particle block (the
+//     parents when the island keeps its own block), and draw the step's
+//     random numbers (Philox, Box-Muller) while they are in flight;
+//  2. the interaction cascade of step t (Algorithm 1, stages s = 1..S): rescale
+//     the record tops by exact powers of two to the largest exponent, build the
+//     upper tree; after s-1 interacting butterfly stages (eq. (3)) every island
+//     weight is the mean of its aligned block of 2^(s-1) islands, so
+//     ENF_{t,s} = Tot^2 2^(s-1) / (m sum_b B_{s-1,b}^2) for every stage from one
+//     tree; the interacting stages form a prefix (a stage with alpha = I leaves
+//     the weights, hence the ENF, unchanged), so s* = min{s : ENF_s >= tau}
+//     (adaptation line of Algorithm 1).  Island k's new weight W^k_{t+1,0} is
+//     its block mean at level s*-1 and the block it inherits is
+//     src(k) = c_1(c_2(...c_{s*-1}(k))), where c_s(j) picks the lower island of
+//     {j, j xor 2^(s-1)} iff u_{t,s,j} (W_lo + W_hi) < W_lo.  Every CTA of the
+//     filter computes the same upper tree from the same records, so no further
+//     barrier is needed; log Z^N_t = log(m^-1 sum_k W^k) (Section 2) is read off
+//     the tree total when it is recorded;
+//  3. the island work of step t+1: mutate the inherited internally-resampled
+//     block through K_{t+1} (Algorithm 1, last stage), weight by g_{t+1},
+//     island maximum, inclusive CDF, M multinomial draws by binary search
+//     (internal resample), gather, store, and W^k_{t+1,1} = W^k_{t+1,0} M^-1 sum g;
+//  4. publish the CTA's record.
+//
+// Arithmetic.  FP64 path: particles, CDF, island weights (double mantissa),
+// block sums and sums of squares in double, so every decision agrees with an
+// FP64 reference to rounding.  FP32-mixed path: particles and log-weights in
+// float; the CDF is an exact 32-bit fixed-point prefix sum of the weights
+// quantised to 2^-(31 - ceil(log2 M)) of the island maximum; island weights are
+// 64-bit integer mantissas with an exponent, multiplied to 64 bits, and block
+// sums are 64-bit fixed point (50 fractional bits below the largest weight);
+// the ENF test uses float; the island choice is decided exactly in 128-bit
+// integers; log Z is formed in double.  The common factor 1/M of the island
+// weights is left out of the FP32-mixed weights and restored in log Z.  The
+// FP32-mixed path issues no FP64-pipe instruction per particle or island.
+#pragma once
+#include <climits>
+#include <cstdio>
+
+#include "airpf_device.cuh"
+#include "airpf_internal.h"
+
+namespace airpf {
+
+namespace {
+
+constexpr int kMaxThreads = 512;      // per-step and grid-persistent CTAs
+constexpr int kMaxCtaThreads = 512;   // a whole filter in one CTA
+constexpr int kMinCtasPerSm = 2;      // register budget: 64 per thread at 512 threads
+constexpr int kCascadeThreads = 256;  // the cascade kernel's CTA
+constexpr int kDefaultThreads = 256;  // default CTA size of the per-step launch
+constexpr unsigned long long kWaitNs = 1000000000ull;   // bounded barrier wait: 1 s
+constexpr unsigned kSpinLimit = 1u << 26;               // iteration backstop
+constexpr int kMaxStages = 16;
+constexpr int kShuffleLevels = 5;
+constexpr int kCachedChunks = 2;      // record chunks a lane keeps in registers
+constexpr int kQw = 16;               // per-warp partial slots (one per tree level)
+using u64 = unsigned long long;
+
+template <typename R> struct CdfType;
+template <> struct CdfType<double> { using T = double; };
+template <> struct CdfType<float> { using T = unsigned; };
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+// offset (in nodes) of level l of a tree over n leaves: levels stored back to back
+__host__ __device__ __forceinline__ int tree_off(int n, int l) { return 2 * n - 2 * (n >> l); }
+
+struct Layout {
+    size_t tree, island, small, total;   // byte offsets
+    size_t cdf, xs, red, mxr;            // island sub-offsets
+    size_t cdf_stride, xs_stride, red_stride;
+};
+
+// cascade region (in 8-byte slots): upper tree [2P], own record [2G], per-warp
+// partial sums [16 warps][kQw], per-level sums [kMaxStages], a few integers
+__host__ __device__ inline size_t cascade_slots(const StepParams& p)
+{
+    return 2 * (size_t)p.P + 2 * (size_t)p.G + 16 * kQw + kMaxStages + 8;
+}
+
+__host__ __device__ inline Layout make_layout(const StepParams& p)
+{
+    Layout L;
+    const size_t rsz = p.fp64 ? 8 : 4;
+    const size_t nwi = (size_t)((p.tpi + 31) / 32);           // warps per island
+    const size_t treeb = align16(sizeof(double) * cascade_slots(p));
+    L.cdf_stride = rsz * (size_t)p.M;                          // double or u32
+    L.xs_stride = align16(rsz * (size_t)p.M * p.dx);
+    L.red_stride = sizeof(double) * nwi;
+    L.cdf = 0;
+    L.xs = L.cdf + align16(L.cdf_stride * p.G);
+    L.red = L.xs + L.xs_stride * p.G;
+    L.mxr = L.red + align16(L.red_stride * p.G);
+    const size_t islandb = L.mxr + align16(L.red_stride * p.G);
+    L.tree = 0;
+    L.island = 0;                                             // overlaps the cascade region
+    L.small = align16(treeb > islandb ? treeb : islandb);
+    const size_t smallb = align16(sizeof(double) * (size_t)p.G) + align16(2 * sizeof(int) * (size_t)p.G)
+                          + align16(sizeof(double) * (size_t)p.G) + align16(sizeof(int) * (size_t)p.G)
+                          + align16(sizeof(double) * 16)
+                          + align16(rsz * (size_t)(p.dx * p.dx + p.dy * p.dx + kMaxDy));
+    L.total = L.small + smallb;
+    return L;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_max(V v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const V w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = (w > v) ? w : v;
+    }
+    return v;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_incl_scan(V v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V w = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += w;
+    }
+    return v;
+}
+
+// A thread's PPT consecutive particles as one vector access (the caller checks
+// that the first index is a multiple of PPT), read through L2.
+template <typename R, int PPT>
+__device__ __forceinline__ void load_run(const R* src, R* out)
+{
+    if constexpr (sizeof(R) == 4 && PPT == 4) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(src));
+        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else if constexpr (sizeof(R) == 4 && PPT == 2) {
+        const float2 v = __ldcg(reinterpret_cast<const float2*>(src));
+        out[0] = v.x; out[1] = v.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < PPT; q += 2) {
+            const double2 v = __ldcg(reinterpret_cast<const double2*>(src) + q / 2);
+            out[q] = v.x; out[q + 1] = v.y;
+        }
+    }
+}
+
+template <typename R, int PPT>
+__device__ __forceinline__ void store_run(R* dst, const R* in)
+{
+    if constexpr (sizeof(R) == 4 && PPT == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4(in[0], in[1], in[2], in[3]);
+    } else if constexpr (sizeof(R) == 4 && PPT == 2) {
+        *reinterpret_cast<float2*>(dst) = make_float2(in[0], in[1]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < PPT; q += 2) reinterpret_cast<double2*>(dst)[q / 2] = make_double2(in[q], in[q + 1]);
+    }
+}
+
+// float value of a 64-bit integer by its leading-one position (truncated to 24
+// bits; integer pipe only)
+__device__ __forceinline__ float u64_to_float(u64 v)
+{
+    if (v == 0ull) return 0.0f;
+    const int lz = __clzll(v);
+    const u64 n = v << lz;
+    return __uint_as_float(((unsigned)(190 - lz) << 23) | (unsigned)((n >> 40) & 0x7fffffu));
+}
+
+// Island weight as stored: 64 bits (a double in [0.5,1) on the FP64 path, an
+// integer mantissa in [2^63, 2^64) on the FP32-mixed path; 0 = weight zero)
+// and a binary exponent.
+struct XW {
+    u64 bits;
+    int e;
+};
+
+// double v = r 2^e with r in [0.5, 1), by exponent-field manipulation for
+// normal v; frexp for subnormal v.
+__device__ __forceinline__ XW xw_from_double(double v, int e_add)
+{
+    XW w;
+    const long long b = __double_as_longlong(v);
+    if (b <= 0 || b >= (0x7ffLL << 52)) {       // zero, negative, inf or NaN
+        w.bits = 0;
+        w.e = 0;
+        return w;
+    }
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) {
+        int e2;
+        w.bits = (u64)__double_as_longlong(frexp(v, &e2));
+        w.e = e2 + e_add;
+        return w;
+    }
+    w.bits = (u64)((b & ~(0x7ffLL << 52)) | (1022LL << 52));
+    w.e = ex - 1022 + e_add;
+    return w;
+}
+
+// integer v 2^e_add, normalised so that the top bit of the mantissa is set;
+// the stored value is mantissa 2^(e - 64)
+__device__ __forceinline__ XW xw_from_u64(u64 v, int e_add)
+{
+    XW w;
+    if (v == 0ull) {
+        w.bits = 0;
+        w.e = 0;
+        return w;
+    }
+    const int lz = __clzll(v);
+    w.bits = v << lz;
+    w.e = e_add + 64 - lz;
+    return w;
+}
+
+// Arithmetic of the cascade for each precision (see file comment).
+template <bool FX> struct Casc;
+template <> struct Casc<false> {
+    using V = double;
+    using Qt = double;
+    static constexpr int kFrac = 0;           // leaf = W 2^-e_ref
+    __device__ static bool positive(u64 b) { return (long long)b > 0; }
+    __device__ static V leaf(u64 b, int de) { return ldexp(__longlong_as_double((long long)b), de); }
+    __device__ static V rescale(V v, int sh) { return ldexp(v, -sh); }
+    __device__ static Qt qscale(Qt q, int sh2) { return ldexp(q, -sh2); }
+    __device__ static Qt qv(V v) { return v; }
+    __device__ static double to_d(V v) { return v; }
+    __device__ static XW weight(V bsum, int e_add) { return xw_from_double(bsum, e_add); }
+    __device__ static Qt tau(const StepParams& p) { return p.tau; }
+    __device__ static bool pick_lo(V lo, V hi, uint32_t w) { return unif_f64(w) * (lo + hi) < lo; }
+};
+template <> struct Casc<true> {
+    using V = u64;
+    using Qt = float;
+    // stored weight mantissa * 2^(e-64); leaf = mantissa >> (e_ref - e + 14) = W 2^(50 - e_ref)
+    static constexpr int kFrac = 50;
+    __device__ static bool positive(u64 b) { return b != 0ull; }
+    __device__ static V leaf(u64 b, int de)
+    {
+        const int sh = 14 - de;
+        return sh < 64 ? (b >> sh) : 0ull;
+    }
+    __device__ static V rescale(V v, int sh) { return sh < 64 ? (v >> sh) : 0ull; }
+    __device__ static Qt qscale(Qt q, int sh2) { return sh2 < 250 ? ldexpf(q, -sh2) : 0.0f; }
+    __device__ static Qt qv(V v) { return u64_to_float(v) * 0x1p-62f; }
+    __device__ static double to_d(V v) { return (double)v; }
+    __device__ static XW weight(V bsum, int e_add) { return xw_from_u64(bsum, e_add); }
+    __device__ static Qt tau(const StepParams& p) { return p.tau_f; }
+    // u (lo + hi) < lo with u = (2w+1) 2^-33, exactly: (2w+1)(lo+hi) < 2^33 lo in 128 bits
+    __device__ static bool pick_lo(V lo, V hi, uint32_t w)
+    {
+        const u64 w2 = 2ull * (u64)w + 1ull;
+        const u64 sum = lo + hi;
+        const u64 p_lo = w2 * sum, p_hi = __umul64hi(w2, sum);
+        const u64 r_lo = lo << 33, r_hi = lo >> 31;
+        return (p_hi < r_hi) || (p_hi == r_hi && p_lo < r_lo);
+    }
+};
+
+template <typename V> __device__ __forceinline__ bool pos_v(V v) { return v > (V)0; }
+
+// ---------------------------------------------------------------------------
+// Cascade of step tp for filter c (see file comment), run once per step by the
+// filter's last CTA to finish it.  Reads the CTA records of step tp, builds the
+// upper tree, decides s*, and writes what the next step needs (the summary, the
+// upper-tree level of the block means when it lies above the CTAs, the
+// inherited blocks when a stage interacted), log Z and the records of the run.
+// Every thread of the CTA calls it.
+// ---------------------------------------------------------------------------
+template <bool FX>
+__device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st, double* raw)
+{
+    using C = Casc<FX>;
+    using V = typename C::V;
+    using Qt = typename C::Qt;
+    const int m = p.m, S = p.S, P = p.P, G = p.G, g = p.g, SU = S - g;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    const int* pe = p.pe[tp & 1] + (size_t)c * P;
+    const V* pt = reinterpret_cast<const V*>(p.pt[tp & 1]) + (size_t)c * P * 2 * G;
+    const Qt* pq = reinterpret_cast<const Qt*>(p.pq[tp & 1]) + (size_t)c * P * 8;
+    V* ut = reinterpret_cast<V*>(raw);                            // upper tree [2P]
+    Qt* Qw = reinterpret_cast<Qt*>(raw + 2 * P + 2 * G);          // [nw][kQw]
+    Qt* Q = reinterpret_cast<Qt*>(raw + 2 * P + 2 * G + 16 * kQw);   // [kMaxStages]
+    int* iscal = reinterpret_cast<int*>(raw + 2 * P + 2 * G + 16 * kQw + kMaxStages);
+
+    // 1. the lane's records (read once, all fields at once) and the largest
+    //    exponent over the records with a nonzero top
+    constexpr int kRec = 2;                 // record chunks a lane keeps in registers
+    int re[kRec];
+    V rt[kRec];
+    Qt rq[kRec][4];
+    int emax = INT_MIN;
+#pragma unroll
+    for (int i = 0; i < kRec; ++i) {
+        const int j = (warp + i * nw) * 32 + lane;
+        re[i] = INT_MIN;
+        rt[i] = (V)0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) rq[i][l] = (Qt)0;
+        if (j < P) {
+            re[i] = __ldcg(&pe[j]);
+            rt[i] = __ldcg(&pt[(size_t)j * 2 * G + tree_off(G, g)]);
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+                if (l < g) rq[i][l] = __ldcg(&pq[(size_t)j * 8 + l]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kRec; ++i)
+        if (pos_v(rt[i]) && re[i] > emax) emax = re[i];
+    for (int j = (warp + kRec * nw) * 32 + lane; j < P; j += 32 * nw) {
+        const int e = __ldcg(&pe[j]);
+        if (pos_v(__ldcg(&pt[(size_t)j * 2 * G + tree_off(G, g)])) && e > emax) emax = e;
+    }
+    emax = warp_max(emax);
+    if (tid == 0) iscal[0] = INT_MIN;
+    __syncthreads();
+    if (lane == 0) atomicMax(&iscal[0], emax);
+    __syncthreads();
+    emax = iscal[0];
+    const bool dead = (emax == INT_MIN);
+
+    // 2. upper leaves (record tops rescaled to 2^emax), the lower upper-tree
+    //    levels by warp shuffles, and every level's partial sum of squares
+    const int L5 = SU < kShuffleLevels ? SU : kShuffleLevels;
+    Qt qlow[4];                        // global levels 0..g-1 (from the records)
+    Qt qu[kShuffleLevels + 1];         // global levels g..g+L5 (upper tree)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) qlow[l] = (Qt)0;
+#pragma unroll
+    for (int u = 0; u <= kShuffleLevels; ++u) qu[u] = (Qt)0;
+    int ci = 0;
+    for (int ch = warp; ch * 32 < P; ch += nw, ++ci) {
+        const int j = ch * 32 + lane;
+        V v = (V)0;
+        if (j < P) {
+            int e = INT_MIN;
+            V top = (V)0;
+            Qt ql[4] = {(Qt)0, (Qt)0, (Qt)0, (Qt)0};
+            if (ci < kRec) {
+#pragma unroll
+                for (int i = 0; i < kRec; ++i)
+                    if (i == ci) {
+                        e = re[i];
+                        top = rt[i];
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) ql[l] = rq[i][l];
+                    }
+            } else {
+                e = __ldcg(&pe[j]);
+                top = __ldcg(&pt[(size_t)j * 2 * G + tree_off(G, g)]);
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    if (l < g) ql[l] = __ldcg(&pq[(size_t)j * 8 + l]);
+            }
+            if (!dead && pos_v(top)) {
+                const int sh = emax - e;
+                v = C::rescale(top, sh);
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    if (l < g) qlow[l] += C::qscale(ql[l], 2 * sh);
+            }
+            ut[j] = v;
+            const Qt q = C::qv(v);
+            qu[0] += q * q;
+        }
+#pragma unroll
+        for (int u = 1; u <= kShuffleLevels; ++u) {
+            if (u <= L5) {
+                v += __shfl_down_sync(0xffffffffu, v, 1 << (u - 1));
+                if ((lane & ((1 << u) - 1)) == 0 && (j >> u) < (P >> u)) {
+                    ut[tree_off(P, u) + (j >> u)] = v;
+                    const Qt q = C::qv(v);
+                    qu[u] += q * q;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (l < g) {
+            const Qt s = warp_sum(qlow[l]);
+            if (lane == 0) Qw[warp * kQw + l] = s;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u <= kShuffleLevels; ++u) {
+        if (u <= L5) {
+            const Qt s = warp_sum(qu[u]);
+            if (lane == 0) Qw[warp * kQw + g + u] = s;
+        }
+    }
+    __syncthreads();
+
+    // 3. one warp: remaining upper levels, per-level sums, s*, records
+    if (warp == 0) {
+        if (lane <= g + L5 && lane < kQw) {
+            Qt s = (Qt)0;
+            for (int w = 0; w < nw; ++w) s += Qw[w * kQw + lane];
+            Q[lane] = s;
+        }
+        if (SU > L5) {
+            // level L5 has n5 = P >> L5 nodes; the levels above them in
+            // registers when n5 <= 32, in shared memory otherwise
+            const int n5 = P >> L5;
+            if (n5 <= 32) {
+                V v = lane < n5 ? ut[tree_off(P, L5) + lane] : (V)0;
+                Qt qs[kQw];
+#pragma unroll
+                for (int l = 0; l < kQw; ++l) qs[l] = (Qt)0;
+#pragma unroll
+                for (int du = 1; du <= 5; ++du) {
+                    const int u = L5 + du;
+                    if (u <= SU) {
+                        v += __shfl_down_sync(0xffffffffu, v, 1 << (du - 1));
+                        if ((lane & ((1 << du) - 1)) == 0 && (lane >> du) < (P >> u)) {
+                            ut[tree_off(P, u) + (lane >> du)] = v;
+                            const Qt q = C::qv(v);
+#pragma unroll
+                            for (int l = 0; l < kQw; ++l)
+                                if (l == du) qs[l] += q * q;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int du = 1; du <= 5; ++du) {
+                    if (L5 + du <= SU) {
+                        const Qt sq = warp_sum(qs[du]);
+                        if (lane == 0) Q[g + L5 + du] = sq;
+                    }
+                }
+            } else {
+                for (int u = L5 + 1; u <= SU; ++u) {
+                    __syncwarp();
+                    const int n = P >> u;
+                    Qt acc = (Qt)0;
+                    for (int b = lane; b < n; b += 32) {
+                        const V v = ut[tree_off(P, u - 1) + 2 * b] + ut[tree_off(P, u - 1) + 2 * b + 1];
+                        ut[tree_off(P, u) + b] = v;
+                        const Qt q = C::qv(v);
+                        acc += q * q;
+                    }
+                    acc = warp_sum(acc);
+                    if (lane == 0) Q[g + u] = acc;
+                }
+            }
+        }
+        __syncwarp();
+        const V tot = ut[tree_off(P, SU)];
+        const Qt tq = C::qv(tot);
+        bool quiet = false;
+        if (lane < S) {
+            const int s = lane + 1;
+            // stage s interacts iff ENF_s < tau, i.e. Tot^2 2^(s-1) < tau m Q_{s-1}
+            quiet = pos_v(tot) && !(tq * tq * (Qt)(1u << (s - 1)) < C::tau(p) * (Qt)m * Q[s - 1]);
+        }
+        const unsigned qm = __ballot_sync(0xffffffffu, quiet);
+        if (lane == 0) {
+            int ss;
+            if (p.mode == 0) ss = 1;
+            else if (p.mode == 1) ss = S + 1;
+            else ss = qm ? __ffs(qm) : S + 1;              // first quiet stage
+            iscal[1] = ss;
+            if (p.trace || tp == p.T) {
+                // log Z^N_tp = log(m^-1 sum_k W^k), sum_k W^k = Tot 2^(emax - kFrac);
+                // the FP32-mixed weights leave out M^-tp
+                double lz = pos_v(tot)
+                    ? log(C::to_d(tot)) - log((double)m) + (double)(emax - C::kFrac) * 0.6931471805599453
+                    : -INFINITY;
+                if (FX) lz -= (double)tp * log((double)p.M);
+                if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
+                if (tp == p.T) p.logz[c] = lz;
+            }
+            if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ss;
+            if (p.enf) {
+                double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (S + 1);
+                double last = 1.0;
+                for (int s = 1; s <= S; ++s) {
+                    const int sr = s <= ss ? s : ss;
+                    const double v = pos_v(tot)
+                        ? (double)tq * (double)tq * ldexp(1.0, sr - 1) / ((double)m * (double)Q[sr - 1]) : 0.0;
+                    e[s] = v;
+                    if (s == ss) last = v;
+                }
+                if (tp < p.T) p.enf[((size_t)c * p.T + tp) * (S + 1)] = pos_v(tot) ? (ss <= S ? last : 1.0) : 0.0;
+            }
+        }
+    }
+    __syncthreads();
+
+    // 4. for the next step: the summary (s*, largest exponent), the upper-tree
+    //    level holding the block means when they span several CTAs, and every
+    //    island's inherited block when any stage interacted
+    const int ss = iscal[1];
+    const int lvl = ss - 1;
+    if (tid == 0) {
+        p.csum[(size_t)c * 4 + 0] = ss;
+        p.csum[(size_t)c * 4 + 1] = emax;
+    }
+    if (lvl >= g) {
+        const int n = P >> (lvl - g);
+        for (int b = tid; b < n; b += nthr)
+            reinterpret_cast<V*>(p.cup)[(size_t)c * P + b] = ut[tree_off(P, lvl - g) + b];
+    }
+    if (lvl >= 1) {
+        for (int k = tid; k < m; k += nthr) {
+            int j = k;
+            for (int s = lvl; s >= 1; --s) {
+                const int l = s - 1, b = 1 << l, pi = j >> l;
+                V lo, hi;
+                if (l >= g) {
+                    lo = ut[tree_off(P, l - g) + (pi & ~1)];
+                    hi = ut[tree_off(P, l - g) + (pi | 1)];
+                } else {
+                    // both blocks lie in the record of CTA jc, in its own scale
+                    const int jc = j >> g;
+                    const int li = pi - jc * (G >> l);
+                    const int ol = tree_off(G, l);
+                    lo = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li & ~1)]);
+                    hi = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li | 1)]);
+                }
+                const uint32_t wu = st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x;
+                j = C::pick_lo(lo, hi, wu) ? (j & ~b) : (j | b);
+            }
+            p.nsrc[(size_t)c * m + k] = j;
+        }
+    }
+}
+
+// Record of the CTA's island weights after step t (see file comment); warp 0.
+template <bool FX>
+__device__ void publish_record(const StepParams& p, int c, int t, int jo, const u64* nw_bits, const int* nw_e)
+{
+    using C = Casc<FX>;
+    using V = typename C::V;
+    using Qt = typename C::Qt;
+    const int G = p.G, g = p.g, lane = threadIdx.x & 31;
+    const bool has = lane < G;
+    const u64 b = has ? nw_bits[lane] : 0ull;
+    const int e = has ? nw_e[lane] : INT_MIN;
+    const bool ok = has && C::positive(b);
+    const int ej = warp_max(ok ? e : INT_MIN);
+    V v = (ok && ej != INT_MIN) ? C::leaf(b, e - ej) : (V)0;
+    V* rec = reinterpret_cast<V*>(p.pt[t & 1]) + ((size_t)c * p.P + jo) * 2 * G;
+    Qt* pq = reinterpret_cast<Qt*>(p.pq[t & 1]) + ((size_t)c * p.P + jo) * 8;
+    Qt q[4] = {(Qt)0, (Qt)0, (Qt)0, (Qt)0};
+    if (has) {
+        rec[lane] = v;
+        const Qt x = C::qv(v);
+        q[0] = x * x;
+    }
+#pragma unroll
+    for (int l = 1; l <= kShuffleLevels; ++l) {
+        if (l <= g) {
+            v += __shfl_down_sync(0xffffffffu, v, 1 << (l - 1));
+            if ((lane & ((1 << l) - 1)) == 0 && has) {
+                rec[tree_off(G, l) + (lane >> l)] = v;
+                const Qt x = C::qv(v);
+#pragma unroll
+                for (int r = 1; r < 4; ++r)
+                    if (r == l) q[r] += x * x;
+            }
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (l < g) {
+            const Qt s = warp_sum(q[l]);
+            if (lane == 0) pq[l] = s;
+        }
+    }
+    if (lane == 0) p.pe[t & 1][(size_t)c * p.P + jo] = ej;
+}
+
+enum { OP_STEP = 0, OP_PREPARE = 1, OP_FITS = 2, OP_PERSIST_GRID = 3, OP_PERSIST_CTA = 4, OP_CASCADE = 5 };
+
+__host__ __device__ inline size_t cascade_smem_bytes(const StepParams& p) { return align16(sizeof(double) * cascade_slots(p)); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Prologue: model constants of every filter (and the NGM drift table), once
+// per pass; also clears the grid barrier and the error word.
+// ---------------------------------------------------------------------------
+template <typename R, int MODEL>
+__global__ void airpf_prologue_kernel(StepParams p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && p.bar != nullptr) {
+        p.bar[0] = 0u;
+        p.bar[1] = 0u;
+        *p.err = 0u;
+    }
+    if (i < p.B && (p.active == nullptr || p.active[i] != 0)) {
+        ModelPar<R> mp;
+        model_setup<R, MODEL>(mp, p.theta + (size_t)i * p.theta_dim, p.dx, p.dy);
+        reinterpret_cast<ModelPar<R>*>(p.mpar)[i] = mp;
+    }
+    if (MODEL == NGM && i < p.T) reinterpret_cast<R*>(p.drift)[i] = (R)(8.0 * cos(1.2 * (double)(i + 1)));
+}
+
+// ---------------------------------------------------------------------------
+// Step t for the G islands k0.. of filter c (see file comment).  Called by every
+// thread of the CTA; all barriers inside are CTA-uniform.
+// ---------------------------------------------------------------------------
+template <typename R, int MODEL, int DX, int PPT>
+__device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int k0, unsigned char* smem)
+{
+    using Cdf = typename CdfType<R>::T;
+    constexpr bool FX = sizeof(R) == 4;
+    const int tid = threadIdx.x;
+    const int N = p.N, M = p.M, dx = p.dx;
+    const int jo = k0 / p.G;
+    const Layout L = make_layout(p);
+    double* tree = reinterpret_cast<double*>(smem + L.tree);
+    u64* own_w = reinterpret_cast<u64*>(smem + L.small);
+    int* own_we = reinterpret_cast<int*>(smem + L.small + align16(sizeof(double) * p.G));
+    int* own_src = own_we + p.G;
+    u64* new_w = reinterpret_cast<u64*>(smem + L.small + align16(sizeof(double) * p.G)
+                                        + align16(2 * sizeof(int) * p.G));
+    int* new_we = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(new_w) + align16(sizeof(double) * p.G));
+    double* scal = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(new_we) + align16(sizeof(int) * p.G));
+    R* mshared = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(scal) + align16(sizeof(double) * 16));
+    const RunParams run = *p.run;
+    const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
+    const bool designated = (k0 == 0);
+
+    // ---- 1. in flight: the own islands' weight and source block (written by the
+    //      cascade of step t-1), the own particle block, and the step's noise ----
+    if (t == 1) {
+        for (int gi = tid; gi < p.G; gi += blockDim.x) {
+            // W = 1: 0.5 2^1 as a double, 2^63 2^(1-64) as an integer mantissa
+            own_w[gi] = FX ? (1ull << 63) : (u64)__double_as_longlong(0.5);
+            own_we[gi] = 1;
+            own_src[gi] = k0 + gi;
+        }
+        if (designated && tid == 0 && p.enf) p.enf[(size_t)c * p.T * (p.S + 1)] = 1.0;
+    } else {
+        // the cascade's summary of step t-1, this CTA's record of step t-1 and
+        // (used only if some stage interacted) the inherited blocks
+        int* csum_sh = reinterpret_cast<int*>(scal) + 4;
+        u64* rec_sh = reinterpret_cast<u64*>(tree);
+        if (tid < 2) csum_sh[tid] = __ldcg(&p.csum[(size_t)c * 4 + tid]);
+        if (tid == 2) csum_sh[2] = __ldcg(&p.pe[(t - 1) & 1][(size_t)c * p.P + jo]);
+        if (tid < 2 * p.G - 1)
+            rec_sh[tid] = __ldcg(&reinterpret_cast<const u64*>(p.pt[(t - 1) & 1])[((size_t)c * p.P + jo) * 2 * p.G + tid]);
+        for (int gi = tid; gi < p.G; gi += blockDim.x) own_src[gi] = __ldcg(&p.nsrc[(size_t)c * p.m + k0 + gi]);
+        __syncthreads();
+        const int ss = csum_sh[0], emax = csum_sh[1], ej = csum_sh[2];
+        const int lvl = ss - 1;
+        for (int gi = tid; gi < p.G; gi += blockDim.x) {
+            XW w{0ull, 0};
+            if (emax != INT_MIN) {
+                if (lvl < p.g) {
+                    if (ej != INT_MIN)
+                        w = Casc<FX>::weight(reinterpret_cast<const typename Casc<FX>::V*>(rec_sh)[tree_off(p.G, lvl) + (gi >> lvl)],
+                                             ej - Casc<FX>::kFrac - lvl);
+                } else {
+                    const typename Casc<FX>::V b =
+                        __ldcg(&reinterpret_cast<const typename Casc<FX>::V*>(p.cup)[(size_t)c * p.P + ((k0 + gi) >> lvl)]);
+                    w = Casc<FX>::weight(b, emax - Casc<FX>::kFrac - lvl);
+                }
+            }
+            own_w[gi] = w.bits;
+            own_we[gi] = w.e;
+            if (ss == 1) own_src[gi] = k0 + gi;
+        }
+    }
+
+    const int g = tid / p.tpi, li = tid - g * p.tpi;
+    const int lane = tid & 31, wi = li >> 5;   // warp index within the island
+    const int k = k0 + g;
+    const R* Xp = reinterpret_cast<const R*>(p.X[(t - 1) & 1]);
+    const bool vec = (M % PPT) == 0;       // a thread's particles are one aligned vector
+    R xp[PPT][DX];
+    R z[PPT][DX > 1 ? DX : 1];
+    uint32_t w0[PPT], wres[PPT];
+    ModelPar<R> mp;
+    if (t <= p.T) {
+        mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+        if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
+        if (t >= 2) {
+            if (vec && li * PPT < M) {
+#pragma unroll
+                for (int d = 0; d < DX; ++d) {
+                    if (d < dx) {
+                        R v[PPT];
+                        load_run<R, PPT>(&Xp[((size_t)c * dx + d) * N + (size_t)k * M + li * PPT], v);
+#pragma unroll
+                        for (int r = 0; r < PPT; ++r) xp[r][d] = v[r];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    const int i = li * PPT + r;
+                    if (i < M) {
+#pragma unroll
+                        for (int d = 0; d < DX; ++d)
+                            if (d < dx) xp[r][d] = __ldcg(&Xp[((size_t)c * dx + d) * N + (size_t)k * M + i]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int i = li * PPT + r;
+            w0[r] = 0;
+            wres[r] = 0;
+            if (i < M) {
+                const uint32_t unit = (uint32_t)(k * M + i);
+                if (t == 1) model_prior<R, MODEL, DX>(mp, st, unit, dx, xp[r]);
+                model_step_noise<R, MODEL, DX>(st, unit, (uint32_t)t, dx, z[r], w0[r], wres[r]);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- lineage of step t-1: parent of particle (k, i) among time-(t-1) particles ----
+    if (p.anc != nullptr && t >= 2) {
+        const int* ires = p.ires[(t - 1) & 1] + (size_t)c * N;
+        int* anc = p.anc + ((size_t)c * p.T + (t - 2)) * N;
+        for (int q = tid; q < p.G * M; q += blockDim.x) {
+            const int gq = q / M, i = q - gq * M;
+            const int par = own_src[gq];
+            anc[(k0 + gq) * M + i] = par * M + __ldcg(&ires[par * M + i]);
+        }
+    }
+    if (t == p.T + 1) return;
+
+    // ---- 3. island work of step t ----
+    Cdf* cdf_all = reinterpret_cast<Cdf*>(smem + L.island + L.cdf);
+    R* xs_all = reinterpret_cast<R*>(smem + L.island + L.xs);
+    Cdf* red_all = reinterpret_cast<Cdf*>(smem + L.island + L.red);
+    R* mxr_all = reinterpret_cast<R*>(smem + L.island + L.mxr);
+    const int nwi = (p.tpi + 31) >> 5;
+
+    R* Am = mshared;
+    R* Cm = mshared + dx * dx;
+    R* yv = Cm + p.dy * dx;
+    if (MODEL == LGSSM) {
+        for (int q = tid; q < dx * dx + p.dy * dx; q += blockDim.x) mshared[q] = (R)p.mdata[q];
+    }
+    for (int q = tid; q < p.dy; q += blockDim.x) yv[q] = (R)p.y[(size_t)(t - 1) * p.dy + q];
+    __syncthreads();     // also orders the cascade's smem reads before the island work reuses it
+
+    const int par = own_src[g];
+    Cdf* cdf = cdf_all + (size_t)g * M;
+    R* xs = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(xs_all) + L.xs_stride * g);
+    Cdf* red = red_all + (size_t)g * (L.red_stride / sizeof(Cdf));
+    R* mxr = mxr_all + (size_t)g * (L.red_stride / sizeof(R));
+    R* Xc = reinterpret_cast<R*>(p.X[t & 1]);
+
+    R xv[PPT][DX];
+    R lv[PPT];
+    if (t >= 2 && par != k && vec && li * PPT < M) {   // the island inherits another island's block
+#pragma unroll
+        for (int d = 0; d < DX; ++d) {
+            if (d < dx) {
+                R v[PPT];
+                load_run<R, PPT>(&Xp[((size_t)c * dx + d) * N + (size_t)par * M + li * PPT], v);
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) xp[r][d] = v[r];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        lv[r] = (R)(-INFINITY);
+        const int i = li * PPT + r;
+        if (i < M) {
+            if (t >= 2 && par != k && !vec) {
+#pragma unroll
+                for (int d = 0; d < DX; ++d)
+                    if (d < dx) xp[r][d] = __ldcg(&Xp[((size_t)c * dx + d) * N + (size_t)par * M + i]);
+            }
+            model_transition<R, MODEL, DX>(mp, dx, xp[r], xv[r], Am, z[r], w0[r]);
+            lv[r] = model_logg<R, MODEL, DX>(mp, yv, dx, p.dy, xv[r], Cm);
+        }
+    }
+
+    // island maximum of the log-weights
+    R mx = lv[0];
+#pragma unroll
+    for (int r = 1; r < PPT; ++r) mx = (lv[r] > mx) ? lv[r] : mx;
+    mx = warp_max(mx);
+    if (nwi > 1) {
+        if (lane == 0) mxr[wi] = mx;
+        __syncthreads();
+        R v = mxr[0];
+        for (int w = 1; w < nwi; ++w) v = (mxr[w] > v) ? mxr[w] : v;
+        mx = v;
+    }
+    const bool alive = (mx > (R)(-INFINITY));
+
+    // weights and the thread-local inclusive prefix
+    Cdf part[PPT];
+    Cdf run_sum = 0;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        Cdf w = 0;
+        if (alive && lv[r] > (R)(-INFINITY)) {
+            if constexpr (!FX) w = exp(lv[r] - mx);
+            else w = __float2uint_rn(__expf(lv[r] - mx) * p.cdf_scale);
+        }
+        run_sum += w;
+        part[r] = run_sum;
+    }
+    // island-wide exclusive offset of this thread
+    Cdf incl = warp_incl_scan(run_sum, lane);
+    Cdf excl = incl - run_sum;
+    if (nwi > 1) {
+        if (lane == 31) red[wi] = incl;
+        __syncthreads();
+        Cdf off = 0;
+        for (int w = 0; w < wi; ++w) off += red[w];
+        excl += off;
+    }
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int i = li * PPT + r;
+        if (i < M) {
+            cdf[i] = excl + part[r];
+#pragma unroll
+            for (int d = 0; d < DX; ++d)
+                if (d < dx) xs[(size_t)d * M + i] = xv[r][d];
+        }
+    }
+    if (nwi > 1) __syncthreads();       // an island of one warp needs only the warp
+    else __syncwarp();
+    const Cdf total = cdf[M - 1];
+
+    // multinomial draws: ancestor of draw j = first i with C_i > u_j C_{M-1}.
+    // Fixed-depth branchless lower bound, the thread's draws advanced together.
+    int* ires_out = (p.ires[t & 1] != nullptr) ? p.ires[t & 1] + (size_t)c * N + (size_t)k * M : nullptr;
+    Cdf target[PPT];
+    int base[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        base[r] = 0;
+        if constexpr (!FX) target[r] = unif_f64(wres[r]) * total;
+        else target[r] = __umulhi(wres[r], total);       // floor(w total / 2^32) < total
+    }
+    for (int n = M; n > 1;) {
+        const int half = n >> 1;
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const Cdf v = cdf[base[r] + half - 1];
+            base[r] = (v > target[r]) ? base[r] : base[r] + half;
+        }
+        n -= half;
+    }
+    if (vec) {
+        if (li * PPT < M) {
+#pragma unroll
+            for (int d = 0; d < DX; ++d) {
+                if (d < dx) {
+                    R v[PPT];
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) v[r] = xs[(size_t)d * M + (alive ? base[r] : li * PPT + r)];
+                    store_run<R, PPT>(&Xc[((size_t)c * dx + d) * N + (size_t)k * M + li * PPT], v);
+                }
+            }
+            if (ires_out) {
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) ires_out[li * PPT + r] = alive ? base[r] : li * PPT + r;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int j = li * PPT + r;
+            if (j < M) {
+                const int a = alive ? base[r] : j;
+#pragma unroll
+                for (int d = 0; d < DX; ++d)
+                    if (d < dx) Xc[((size_t)c * dx + d) * N + (size_t)k * M + j] = xs[(size_t)d * M + a];
+                if (ires_out) ires_out[j] = a;
+            }
+        }
+    }
+
+    // island weight W^k_{t,1} = W^k_{t,0} exp(max) (sum_i w_i) / M, extended range
+    if (li == 0) {
+        XW w{0ull, 0};
+        const u64 wb0 = own_w[g];
+        if (alive && wb0 != 0ull) {
+            if constexpr (!FX) {
+                double mxd = fmin(fmax((double)mx, -1.0e7), 1.0e7);
+                const double n = floor(mxd * 1.4426950408889634);
+                // two-constant reduction of mxd - n ln 2 (Cody and Waite, 1980)
+                double f = fma(-n, 0.6931471805599453, mxd);
+                f = fma(-n, 2.3190468138462996e-17, f);
+                w = xw_from_double(exp(f) * ((double)total * p.inv_M) * __longlong_as_double((long long)wb0),
+                                   own_we[g] + (int)n);
+            } else {
+                // exp(max) = 2^n e^f in float; the mantissa products in 64-bit integers:
+                // W' = wm 2^(e-64) * ef24 2^(efe-23) * total 2^-cdf_bits * 2^n   (1/M left out)
+                const float mxf = fminf(fmaxf(mx, -1.0e7f), 1.0e7f);
+                const float n = floorf(mxf * 1.44269504f);
+                float f = fmaf(-n, 0.693145752f, mxf);
+                f = fmaf(-n, 1.42860677e-06f, f);
+                const unsigned efb = __float_as_uint(__expf(f));
+                const unsigned ef24 = (efb & 0x7fffffu) | 0x800000u;
+                const int efe = (int)((efb >> 23) & 0xff) - 127;    // 0, or +-1 at the ends of [0, ln 2)
+                const u64 p1 = __umul64hi(wb0, (u64)ef24 << 40);     // = wm ef24 2^-24
+                const int l1 = __clzll(p1);
+                const u64 q1 = p1 << l1;
+                const int e1 = own_we[g] + 1 - l1 + efe;
+                const int lt = __clzll((u64)total);
+                const u64 p2 = __umul64hi(q1, (u64)total << lt);     // = q1 total 2^(lt-64)
+                const int l2 = __clzll(p2);
+                w.bits = p2 << l2;
+                w.e = e1 + 64 - lt - l2 + (int)n - p.cdf_bits;
+            }
+        }
+        new_w[g] = w.bits;
+        new_we[g] = w.e;
+    }
+    __syncthreads();
+
+    // ---- 4. the CTA's record of step t (the cascade reads it) ----
+    if (tid < 32) publish_record<FX>(p, c, t, jo, new_w, new_we);
+}
+
+// ---------------------------------------------------------------------------
+// Grid barrier of the cooperative persistent kernel (generation counter).  The
+// wait is bounded: after 1 s (or kSpinLimit polls) the CTA sets the error word
+// and every CTA leaves the time loop at its next barrier.  bar[0] counts
+// arrivals, bar[1] is the generation; both and *err are zeroed by the prologue.
+// ---------------------------------------------------------------------------
+static __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+static __device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    return v;
+}
+
+static __device__ bool grid_barrier(unsigned* bar, unsigned* err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g0 = ld_acquire_gpu(bar + 1);
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned it = 0;
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_gpu(bar + 1) == g0) {
+                ++it;
+                if (it > kSpinLimit || ((it & 255u) == 0u && global_ns() - t0 > kWaitNs)) {
+                    atomicExch(err, 1u);
+                    ok = 0;
+                    break;
+                }
+                if (it > 64u) __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ld_acquire_gpu(err) != 0u) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename R, int MODEL, int DX, int PPT>
+__global__ void __launch_bounds__(kMaxThreads, kMinCtasPerSm) airpf_step_kernel(StepParams p, int t)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cpf = p.m / p.G;                 // CTAs per filter
+    const int c = blockIdx.x / cpf;
+    const int k0 = (blockIdx.x - c * cpf) * p.G;
+    if (p.active != nullptr && p.active[c] == 0) return;   // uniform over the CTA
+    step_body<R, MODEL, DX, PPT>(p, t, c, k0, smem);
+}
+
+// The cascade of step t: one CTA per filter.
+template <typename R>
+__global__ void __launch_bounds__(kCascadeThreads) airpf_cascade_kernel(StepParams p, int t)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int c = blockIdx.x;
+    if (p.active != nullptr && p.active[c] == 0) return;
+    const RunParams run = *p.run;
+    const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
+    cascade_all<sizeof(R) == 4>(p, c, t, st, reinterpret_cast<double*>(smem));
+}
+
+// All T+1 steps in one launch.  GRID: the filter spans several co-resident CTAs
+// (cooperative launch); a step's records are published before a grid barrier,
+// the filter's first CTA runs the cascade, and a second barrier releases the
+// next step.  Otherwise one CTA holds a whole filter and runs its cascade
+// itself between block barriers.
+template <typename R, int MODEL, int DX, int PPT, bool GRID>
+__global__ void __launch_bounds__(GRID ? kMaxThreads : kMaxCtaThreads, kMinCtasPerSm) airpf_persistent_kernel(StepParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int cpf = p.m / p.G;
+    const int c = blockIdx.x / cpf;
+    const int k0 = (blockIdx.x - c * cpf) * p.G;
+    const bool act = (p.active == nullptr || p.active[c] != 0);
+    if (!GRID && !act) return;
+    // fault-injection hook: CTA 0 leaves before the first barrier, so the other
+    // CTAs' bounded wait runs out (tests the timeout path)
+    if (GRID && p.inject_stall && blockIdx.x == 0) return;
+    const RunParams run = *p.run;
+    const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
+    for (int t = 1; t <= p.T + 1; ++t) {
+        if (act) step_body<R, MODEL, DX, PPT>(p, t, c, k0, smem);
+        if (t > p.T) break;
+        if (GRID) {
+            if (!grid_barrier(p.bar, p.err)) return;
+            if (act && k0 == 0) cascade_all<sizeof(R) == 4>(p, c, t, st, reinterpret_cast<double*>(smem));
+            if (!grid_barrier(p.bar, p.err)) return;
+        } else {
+            __syncthreads();
+            cascade_all<sizeof(R) == 4>(p, c, t, st, reinterpret_cast<double*>(smem));
+            __syncthreads();
+        }
+    }
+}
+
+template <typename R, int MODEL, int DX, int PPT>
+static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
+{
+    const size_t smem = step_smem_bytes(p);
+    const int block = p.G * p.tpi;
+    const int grid = p.B * (p.m / p.G);
+    const int want = smem > 48 * 1024 ? (int)smem : 48 * 1024;
+    if (op == OP_PREPARE) {
+        // opt in to more than 48 KB of dynamic shared memory (outside any capture)
+        cudaError_t e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        const size_t cs = cascade_smem_bytes(p);
+        if (e == cudaSuccess && cs > 48 * 1024)
+            e = cudaFuncSetAttribute(airpf_cascade_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
+        return e;
+    }
+    if (op == OP_FITS) {
+        // can every CTA of the grid-persistent kernel be resident at once?
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
+                                                              block, smem);
+        *fits = (e == cudaSuccess && block <= kMaxThreads && (long long)per_sm * sms >= grid) ? 1 : 0;
+        return e;
+    }
+    if (op == OP_PERSIST_GRID) {
+        StepParams q = p;
+        void* args[] = {&q};
+        return cudaLaunchCooperativeKernel((const void*)airpf_persistent_kernel<R, MODEL, DX, PPT, true>, dim3(grid),
+                                           dim3(block), args, smem, stream);
+    }
+    if (op == OP_PERSIST_CTA) {
+        airpf_persistent_kernel<R, MODEL, DX, PPT, false><<<grid, block, smem, stream>>>(p);
+        return cudaGetLastError();
+    }
+    if (op == OP_CASCADE) {
+        const size_t cs = cascade_smem_bytes(p);
+        airpf_cascade_kernel<R><<<p.B, kCascadeThreads, cs, stream>>>(p, t);
+        return cudaGetLastError();
+    }
+    if (t == 0) {
+        const int n = p.B > p.T ? p.B : p.T;
+        airpf_prologue_kernel<R, MODEL><<<(n + 127) / 128, 128, 0, stream>>>(p);
+        return cudaGetLastError();
+    }
+    airpf_step_kernel<R, MODEL, DX, PPT><<<grid, block, smem, stream>>>(p, t);
+    return cudaGetLastError();
+}
+
+// dispatch over model and particles per thread for one precision
+template <typename R>
+static cudaError_t dispatch_typed(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
+{
+    if (p.ppt == 2) {
+        switch (p.model) {
+        case AR1: return launch_typed<R, AR1, 1, 2>(p, t, stream, op, fits);
+        case SV: return launch_typed<R, SV, 1, 2>(p, t, stream, op, fits);
+        case NGM: return launch_typed<R, NGM, 1, 2>(p, t, stream, op, fits);
+        case TOY: return launch_typed<R, TOY, 1, 2>(p, t, stream, op, fits);
+        case LGSSM: return launch_typed<R, LGSSM, kMaxDx, 2>(p, t, stream, op, fits);
+        }
+    } else if (p.ppt == 4) {
+        switch (p.model) {
+        case AR1: return launch_typed<R, AR1, 1, 4>(p, t, stream, op, fits);
+        case SV: return launch_typed<R, SV, 1, 4>(p, t, stream, op, fits);
+        case NGM: return launch_typed<R, NGM, 1, 4>(p, t, stream, op, fits);
+        case TOY: return launch_typed<R, TOY, 1, 4>(p, t, stream, op, fits);
+        case LGSSM: return launch_typed<R, LGSSM, kMaxDx, 4>(p, t, stream, op, fits);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace airpf
