@@ -168,16 +168,25 @@ airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y
  * Proposal theta' = theta + step .* N(0, I); independent uniform priors on
  * [lo_d, hi_d] for every component with step_d > 0 (components with step_d = 0
  * stay fixed); a proposal outside the box or outside the model's parameter
- * domain is rejected without running the filter.
+ * domain is rejected without running its filter (its CTAs skip the pass).
+ * Iteration j draws its proposal and acceptance uniform from kind-3 streams
+ * with iter = iter0 + j (see the random-number convention above) and runs the
+ * filter with that iter; u < exp(log Z' - log Z) accepts.
+ *   d_y            [T * dy] observations (FP64)
  *   step, lo, hi   host arrays [d_theta]
  *   d_state_theta  [B * d_theta] in/out: current theta of each chain
  *   d_state_logz   [B] in/out: log Z of the current theta; NaN = not yet
  *                  estimated (estimated first with iter = 0xffffffff)
- *   iter0, iters   iterations iter0 .. iter0+iters-1
- *   d_theta_out    [iters * B * d_theta] out or NULL: chain after each iteration
+ *   chain0         chain of filter 0 (filter b is chain chain0 + b)
+ *   iter0, iters   iterations iter0 .. iter0+iters-1 (iter0 + iters < 2^32 - 1);
+ *                  a chain resumes by calling again with the next iter0
+ *   d_theta_out    [iters * B * d_theta] out or NULL: chain state after
+ *                  iteration j at row j*B + b
  *   d_logz_out     [iters * B] out or NULL
- *   d_n_accept     [B] out: accepted proposals (int32), accumulated
- * Asynchronous; the whole chain stays on the device. */
+ *   d_n_accept     [B] in/out: accepted proposals (int32), added to
+ * Asynchronous on the context's stream; the whole chain stays on the device.
+ * Per iteration, and once more for the initial estimate, it enqueues two
+ * one-thread-per-chain kernels around one filter pass. */
 airpf_status airpf_pmmh(airpf_ctx* ctx, const double* d_y, const double* step, const double* lo,
                         const double* hi, double* d_state_theta, double* d_state_logz,
                         uint32_t chain0, uint32_t iter0, int32_t iters, double* d_theta_out,

@@ -102,6 +102,32 @@ class AIRPF:
                                                lz.ctypes.data_as(ctypes.c_void_p)), self.ctx)
         return lz
 
+    def pmmh(self, y, state_theta, state_logz, *, step, lo, hi, iters: int, chain0: int = 0,
+             iter0: int = 0, n_accept=None, record: bool = True):
+        """Random-walk PMMH, one chain per filter, entirely on the device (airpf_pmmh).
+        state_theta [B, d] and state_logz [B] are float64 CUDA tensors updated in place
+        (NaN log Z: estimated first).  step/lo/hi: length-d sequences.  Returns dict with
+        n_accept [B] (int32, accumulated into ``n_accept`` if given) and, with record,
+        theta [iters, B, d] and log_z [iters, B]."""
+        torch = self._torch
+        d = self.theta_dim
+        assert state_theta.dtype == torch.float64 and state_theta.is_cuda and state_theta.is_contiguous()
+        assert state_logz.dtype == torch.float64 and state_logz.is_cuda and state_logz.numel() == self.B
+        y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+        arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(d)) for v in (step, lo, hi)]
+        if n_accept is None:
+            n_accept = torch.zeros(self.B, dtype=torch.int32, device="cuda")
+        out = {"n_accept": n_accept}
+        if record:
+            out["theta"] = torch.empty((iters, self.B, d), dtype=torch.float64, device="cuda")
+            out["log_z"] = torch.empty((iters, self.B), dtype=torch.float64, device="cuda")
+        self._keep = (y, arrs)
+        _binding.check(self.lib.airpf_pmmh(self.ctx, _ptr(y), *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                           _ptr(state_theta), _ptr(state_logz), chain0, iter0, iters,
+                                           _ptr(out.get("theta")), _ptr(out.get("log_z")), _ptr(n_accept)),
+                       self.ctx)
+        return out
+
     def launch_count(self) -> int:
         return int(self.lib.airpf_last_launch_count(self.ctx))
 

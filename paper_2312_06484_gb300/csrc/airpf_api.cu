@@ -51,8 +51,11 @@ struct airpf_ctx {
     cudaStream_t cap_stream;
     cudaGraphExec_t graph;
     bool graph_ready;
+    cudaGraphExec_t graph_pm;   // the same pass with per-filter active flags (PMMH)
+    bool graph_pm_ready;
     int launch;               // resolved airpf_launch
     StepParams sp;
+    StepParams sp_pm;
     int64_t launches;
     char err[512];
 };
@@ -153,17 +156,17 @@ airpf_status cuda_fail(airpf_ctx* ctx, cudaError_t e, const char* what)
 
 template <typename T> T* at(airpf_ctx* ctx, size_t off) { return reinterpret_cast<T*>(ctx->ws + off); }
 
-airpf_status build_graph(airpf_ctx* ctx)
+airpf_status build_graph(airpf_ctx* ctx, const StepParams& p, cudaGraphExec_t* graph, bool* ready)
 {
-    if (ctx->graph_ready) return AIRPF_OK;
-    cudaError_t e = airpf::prepare_step(ctx->sp);
+    if (*ready) return AIRPF_OK;
+    cudaError_t e = airpf::prepare_step(p);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attribute setup");
     e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
     cudaError_t le = cudaSuccess;
     for (int t = 0; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) {
-        le = airpf::launch_step(ctx->sp, t, ctx->cap_stream);
-        if (le == cudaSuccess && t >= 1 && t <= ctx->cfg.T) le = airpf::launch_cascade(ctx->sp, t, ctx->cap_stream);
+        le = airpf::launch_step(p, t, ctx->cap_stream);
+        if (le == cudaSuccess && t >= 1 && t <= ctx->cfg.T) le = airpf::launch_cascade(p, t, ctx->cap_stream);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &g);
@@ -172,28 +175,31 @@ airpf_status build_graph(airpf_ctx* ctx)
         return cuda_fail(ctx, le, "step launch during capture");
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    e = cudaGraphInstantiate(graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-    ctx->graph_ready = true;
+    *ready = true;
     return AIRPF_OK;
 }
 
-// Enqueue one filter pass over the workspace inputs (theta, y, run params already set).
-airpf_status enqueue_pass(airpf_ctx* ctx)
+// Enqueue one filter pass over the workspace inputs (theta, y, run params
+// already set); pm selects the parameter block with per-filter active flags.
+airpf_status enqueue_pass(airpf_ctx* ctx, bool pm = false)
 {
+    StepParams& p = pm ? ctx->sp_pm : ctx->sp;
     if (ctx->launch != AIRPF_LAUNCH_STEPS) {
-        cudaError_t e = airpf::launch_step(ctx->sp, 0, ctx->stream);      // prologue
+        cudaError_t e = airpf::launch_step(p, 0, ctx->stream);      // prologue
         if (e == cudaSuccess)
-            e = airpf::launch_persistent(ctx->sp, ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID, ctx->stream);
+            e = airpf::launch_persistent(p, ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "persistent launch");
         ctx->launches += 2;
-        ctx->sp.inject_stall = 0;
+        p.inject_stall = 0;
         return AIRPF_OK;
     }
-    airpf_status s = build_graph(ctx);
+    airpf_status s = pm ? build_graph(ctx, p, &ctx->graph_pm, &ctx->graph_pm_ready)
+                        : build_graph(ctx, p, &ctx->graph, &ctx->graph_ready);
     if (s != AIRPF_OK) return s;
-    cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+    cudaError_t e = cudaGraphLaunch(pm ? ctx->graph_pm : ctx->graph, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
     ctx->launches += 2 * (int64_t)ctx->cfg.T + 2;
     return AIRPF_OK;
@@ -369,6 +375,8 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.enf = (cfg->record & AIRPF_RECORD_ENF) ? at<double>(ctx, L.enf) : nullptr;
     p.sstar = (cfg->record & AIRPF_RECORD_ENF) ? at<int>(ctx, L.sstar) : nullptr;
     p.anc = (cfg->record & AIRPF_RECORD_LINEAGE) ? at<int>(ctx, L.anc) : nullptr;
+    ctx->sp_pm = p;
+    ctx->sp_pm.active = at<int>(ctx, L.active);
 
     if (cfg->model == AIRPF_MODEL_LGSSM) {
         const size_t n = sizeof(double) * (size_t)(cfg->dx * cfg->dx + cfg->dy * cfg->dx);
@@ -389,6 +397,7 @@ airpf_status airpf_destroy(airpf_ctx* ctx)
 {
     if (!ctx) return AIRPF_ERR_ARG;
     if (ctx->graph_ready) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->graph_pm_ready) cudaGraphExecDestroy(ctx->graph_pm);
     cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return AIRPF_OK;
@@ -471,12 +480,74 @@ airpf_status airpf_debug_inject(airpf_ctx* ctx, int32_t what)
     return AIRPF_OK;
 }
 
-airpf_status airpf_pmmh(airpf_ctx* ctx, const double*, const double*, const double*, const double*, double*,
-                        double*, uint32_t, uint32_t, int32_t, double*, double*, int32_t*)
+airpf_status airpf_pmmh(airpf_ctx* ctx, const double* d_y, const double* step, const double* lo,
+                        const double* hi, double* d_state_theta, double* d_state_logz, uint32_t chain0,
+                        uint32_t iter0, int32_t iters, double* d_theta_out, double* d_logz_out,
+                        int32_t* d_n_accept)
 {
     if (!ctx) return AIRPF_ERR_ARG;
-    set_err(ctx, "airpf_pmmh is not built yet");
-    return AIRPF_ERR_UNSUPPORTED;
+    const airpf_config& c = ctx->cfg;
+    if (!d_y || !step || !lo || !hi || !d_state_theta || !d_state_logz || !d_n_accept) {
+        set_err(ctx, "y, step, lo, hi, state_theta, state_logz and n_accept are required");
+        return AIRPF_ERR_ARG;
+    }
+    if (iters < 0) {
+        set_err(ctx, "iters must be >= 0");
+        return AIRPF_ERR_ARG;
+    }
+    if ((uint64_t)chain0 + (uint64_t)c.B > (1u << 24)) {
+        set_err(ctx, "chain0 + B must not exceed 2^24");
+        return AIRPF_ERR_ARG;
+    }
+    if ((uint64_t)iter0 + (uint64_t)iters > 0xffffffffull) {
+        set_err(ctx, "iter0 + iters must stay below 2^32 - 1 (reserved for the initial estimate)");
+        return AIRPF_ERR_ARG;
+    }
+    const int td = ctx->theta_dim;
+    airpf::PmmhParams q;
+    std::memset(&q, 0, sizeof(q));
+    q.B = c.B;
+    q.theta_dim = td;
+    q.model = c.model;
+    q.dx = c.dx;
+    q.seed_lo = (uint32_t)(c.seed & 0xffffffffu);
+    q.seed_hi = (uint32_t)(c.seed >> 32);
+    q.chain0 = chain0;
+    for (int d = 0; d < td; ++d) {
+        if (!(step[d] >= 0.0) || (step[d] > 0.0 && !(lo[d] <= hi[d]))) {
+            set_err(ctx, "component %d: step must be >= 0 and lo <= hi", d);
+            return AIRPF_ERR_ARG;
+        }
+        q.step[d] = step[d];
+        q.lo[d] = lo[d];
+        q.hi[d] = hi[d];
+    }
+    q.run = at<RunParams>(ctx, ctx->L.run);
+    q.theta = at<double>(ctx, ctx->L.theta);
+    q.logz = at<double>(ctx, ctx->L.logz);
+    q.active = at<int>(ctx, ctx->L.active);
+    q.state_theta = d_state_theta;
+    q.state_logz = d_state_logz;
+    q.n_accept = d_n_accept;
+    q.theta_out = d_theta_out;
+    q.logz_out = d_logz_out;
+
+    ctx->launches = 0;
+    airpf_status s;
+    if ((s = copy_async(ctx, at<void>(ctx, ctx->L.y), d_y, sizeof(double) * (size_t)c.T * c.dy))) return s;
+    // the initial estimate of the chains whose log Z is NaN (a pass with no
+    // active filter when there is none), then one pass per iteration
+    for (int64_t j = -1; j < iters; ++j) {
+        const int initial = j < 0;
+        const uint32_t it = initial ? 0xffffffffu : iter0 + (uint32_t)j;
+        cudaError_t e = airpf::launch_pmmh_propose(q, it, initial, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "PMMH proposal launch");
+        if ((s = enqueue_pass(ctx, true))) return s;
+        e = airpf::launch_pmmh_accept(q, it, initial ? 0 : (int)j, initial, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "PMMH acceptance launch");
+        ctx->launches += 2;
+    }
+    return AIRPF_OK;
 }
 
 int64_t airpf_last_launch_count(const airpf_ctx* ctx) { return ctx ? ctx->launches : 0; }

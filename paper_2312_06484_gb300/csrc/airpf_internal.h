@@ -90,6 +90,27 @@ int max_cta_threads();
 // Writes the run parameters (one thread).
 cudaError_t launch_set_run(RunParams* d_run, uint32_t iter, uint32_t chain0, cudaStream_t stream);
 
+// Parameter block of the PMMH kernels (airpf_pmmh.cu); passed by value.
+struct PmmhParams {
+    int B, theta_dim, model, dx;
+    uint32_t seed_lo, seed_hi, chain0;
+    double step[16], lo[16], hi[16];     // random-walk scales and the prior box
+    RunParams* run;                      // the pass's (iter, chain0)
+    double* theta;                       // [B][theta_dim] the pass's parameters
+    const double* logz;                  // [B] the pass's log Z
+    int* active;                         // [B] which filters the pass runs
+    double* state_theta;                 // [B][theta_dim] chain state
+    double* state_logz;                  // [B]
+    int* n_accept;                       // [B]
+    double* theta_out;                   // [iters][B][theta_dim] or NULL
+    double* logz_out;                    // [iters][B] or NULL
+};
+
+// PMMH set-up of one pass (proposal, or the initial estimate of NaN log Z)
+// and its conclusion (accept/reject, outputs of iteration j).
+cudaError_t launch_pmmh_propose(const PmmhParams& q, uint32_t iter, int initial, cudaStream_t stream);
+cudaError_t launch_pmmh_accept(const PmmhParams& q, uint32_t iter, int j, int initial, cudaStream_t stream);
+
 // Choose (tpi, ppt, G) for M particles per island and m islands per filter;
 // want_ppt / want_g of 0 take the defaults.
 void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, int* ppt, int* G);
