@@ -91,9 +91,9 @@ typedef enum {
 } airpf_precision;
 
 /* How a pass over y_1..y_T is launched.  AUTO picks PERSISTENT_CTA when a
- * whole filter fits one CTA (m * threads-per-island <= 512), else
- * PERSISTENT_GRID when every CTA of the pass can be resident at once, else
- * STEPS.  STEPS: one launch per time step, replayed from a CUDA graph.
+ * whole filter fits one CTA (m * threads-per-island <= 512), else STEPS.
+ * STEPS: two launches per time step (the island-step kernel, then the
+ * cascade kernel with one CTA per filter), replayed from a CUDA graph.
  * PERSISTENT_CTA: one launch for all steps, one CTA per filter.
  * PERSISTENT_GRID: one cooperative launch for all steps, a bounded grid
  * barrier (1 s) between steps; a timed-out wait is reported by airpf_sync. */
@@ -114,7 +114,7 @@ typedef struct {
     int32_t mode;           /* airpf_interact */
     double tau;             /* ENF threshold in (0, 1] (ENF normalised to [1/m, 1]) */
     int32_t precision;      /* airpf_precision */
-    int32_t record;         /* bit 0: ancestors, bit 1: ENF and s*, bit 2: log Z trace */
+    int32_t record;         /* bit 0: ancestors, bit 1: ENF and s*, bit 2: log Z trace, bit 3: kernel timing */
     uint64_t seed;
     int32_t launch;         /* airpf_launch (a requested mode that cannot run: AIRPF_ERR_UNSUPPORTED) */
     int32_t reserved;       /* must be 0 */
@@ -123,6 +123,7 @@ typedef struct {
 #define AIRPF_RECORD_LINEAGE 1
 #define AIRPF_RECORD_ENF 2
 #define AIRPF_RECORD_TRACE 4
+#define AIRPF_RECORD_TIMING 8   /* STEPS launch only: CUDA events around each kernel (airpf_kernel_times) */
 
 typedef struct airpf_ctx airpf_ctx;
 
@@ -197,6 +198,14 @@ airpf_status airpf_pmmh(airpf_ctx* ctx, const double* d_y, const double* step, c
  * out (the results of that pass are invalid; the context stays usable),
  * AIRPF_ERR_CUDA for a CUDA error. */
 airpf_status airpf_sync(airpf_ctx* ctx);
+
+/* Measurement aid, no counterpart in the paper.  For a context created with
+ * AIRPF_RECORD_TIMING (which puts CUDA event-record nodes before and after each
+ * kernel of steps 1..T into the pass's graph): waits for the stream and
+ * returns the summed durations, in milliseconds, of the T island-step kernels
+ * and of the T cascade kernels of the last airpf_run.  AIRPF_ERR_UNSUPPORTED
+ * for a context without the flag. */
+airpf_status airpf_kernel_times(airpf_ctx* ctx, double* step_ms, double* cascade_ms);
 
 /* The airpf_launch mode the context resolved to (never AUTO). */
 int32_t airpf_launch_mode(const airpf_ctx* ctx);

@@ -18,7 +18,7 @@ from ._binding import AirpfConfig, AirpfError
 MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY = 0, 1, 2, 3, 4
 NEVER, ALWAYS, ADAPTIVE = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
-RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE = 1, 2, 4
+RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE, RECORD_TIMING = 1, 2, 4, 8
 LAUNCH_AUTO, LAUNCH_STEPS, LAUNCH_PERSISTENT_CTA, LAUNCH_PERSISTENT_GRID = 0, 1, 2, 3
 
 _MODES = {"never": NEVER, "always": ALWAYS, "adaptive": ADAPTIVE}
@@ -128,6 +128,12 @@ class AIRPF:
                        self.ctx)
         return out
 
+    def kernel_times(self):
+        """(island-step kernels ms, cascade kernels ms) of the last run; needs RECORD_TIMING."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _binding.check(self.lib.airpf_kernel_times(self.ctx, ctypes.byref(a), ctypes.byref(b)), self.ctx)
+        return a.value, b.value
+
     def launch_count(self) -> int:
         return int(self.lib.airpf_last_launch_count(self.ctx))
 
@@ -157,5 +163,5 @@ class AIRPF:
 
 __all__ = ["AIRPF", "AirpfError", "theta_dim", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
            "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
-           "RECORD_ENF", "RECORD_TRACE", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
+           "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
            "LAUNCH_PERSISTENT_GRID"]

@@ -56,6 +56,8 @@ struct airpf_ctx {
     int launch;               // resolved airpf_launch
     StepParams sp;
     StepParams sp_pm;
+    cudaEvent_t* ev;          // AIRPF_RECORD_TIMING: 4 events per step (island kernel, cascade kernel)
+    int n_ev;
     int64_t launches;
     char err[512];
 };
@@ -92,7 +94,7 @@ const char* check_config(const airpf_config* c)
     if (c->mode < 0 || c->mode > 2) return "unknown interaction mode";
     if (!(c->tau > 0.0 && c->tau <= 1.0)) return "tau must be in (0, 1]";
     if (c->precision != AIRPF_FP64 && c->precision != AIRPF_FP32_MIXED) return "unknown precision";
-    if (c->record < 0 || c->record > 7) return "unknown record bits";
+    if (c->record < 0 || c->record > 15) return "unknown record bits";
     if (c->launch < 0 || c->launch > 3) return "unknown launch mode";
     if (c->reserved != 0) return "reserved must be 0";
     return nullptr;
@@ -164,9 +166,19 @@ airpf_status build_graph(airpf_ctx* ctx, const StepParams& p, cudaGraphExec_t* g
     e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
     cudaError_t le = cudaSuccess;
+    // timing: event-record nodes around each kernel of steps 1..T (plain graph only)
+    const bool timed = ctx->ev && graph == &ctx->graph;
+    auto mark = [&](int t, int which) {
+        if (timed && le == cudaSuccess && t >= 1 && t <= ctx->cfg.T)
+            le = cudaEventRecordWithFlags(ctx->ev[4 * (t - 1) + which], ctx->cap_stream, cudaEventRecordExternal);
+    };
     for (int t = 0; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) {
-        le = airpf::launch_step(p, t, ctx->cap_stream);
+        mark(t, 0);
+        if (le == cudaSuccess) le = airpf::launch_step(p, t, ctx->cap_stream);
+        mark(t, 1);
+        mark(t, 2);
         if (le == cudaSuccess && t >= 1 && t <= ctx->cfg.T) le = airpf::launch_cascade(p, t, ctx->cap_stream);
+        mark(t, 3);
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &g);
@@ -329,7 +341,11 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.bar = at<unsigned>(ctx, L.bar);
     p.err = at<unsigned>(ctx, L.bar) + 2;
     p.inject_stall = 0;
-    if (ctx->launch == AIRPF_LAUNCH_AUTO || ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
+    // AUTO takes per-step launches for filters that span several CTAs: on GB300 a
+    // kernel boundary (about 1 us in a graph) costs less than the device-scope
+    // release/acquire pair of a grid barrier (about 3 us)
+    if (ctx->launch == AIRPF_LAUNCH_AUTO) ctx->launch = AIRPF_LAUNCH_STEPS;
+    if (ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
         e = airpf::prepare_step(p);
         const bool fits = (e == cudaSuccess) && airpf::persistent_grid_fits(p);
         if (fits) {
@@ -389,6 +405,27 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
             return AIRPF_ERR_CUDA;
         }
     }
+    if (cfg->record & AIRPF_RECORD_TIMING) {
+        if (ctx->launch != AIRPF_LAUNCH_STEPS || cfg->T > (1 << 16)) {
+            set_err(nullptr, "AIRPF_RECORD_TIMING needs the STEPS launch and T <= 65536");
+            cudaStreamDestroy(ctx->cap_stream);
+            delete ctx;
+            return AIRPF_ERR_UNSUPPORTED;
+        }
+        ctx->n_ev = 4 * cfg->T;
+        ctx->ev = new (std::nothrow) cudaEvent_t[ctx->n_ev];
+        int made = 0;
+        e = ctx->ev ? cudaSuccess : cudaErrorMemoryAllocation;
+        for (; made < ctx->n_ev && e == cudaSuccess; ++made) e = cudaEventCreate(&ctx->ev[made]);
+        if (e != cudaSuccess) {
+            set_err(nullptr, "timing events: %s", cudaGetErrorString(e));
+            for (int i = 0; i + 1 < made; ++i) cudaEventDestroy(ctx->ev[i]);
+            delete[] ctx->ev;
+            cudaStreamDestroy(ctx->cap_stream);
+            delete ctx;
+            return AIRPF_ERR_CUDA;
+        }
+    }
     *out = ctx;
     return AIRPF_OK;
 }
@@ -398,6 +435,10 @@ airpf_status airpf_destroy(airpf_ctx* ctx)
     if (!ctx) return AIRPF_ERR_ARG;
     if (ctx->graph_ready) cudaGraphExecDestroy(ctx->graph);
     if (ctx->graph_pm_ready) cudaGraphExecDestroy(ctx->graph_pm);
+    if (ctx->ev) {
+        for (int i = 0; i < ctx->n_ev; ++i) cudaEventDestroy(ctx->ev[i]);
+        delete[] ctx->ev;
+    }
     cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return AIRPF_OK;
@@ -464,6 +505,29 @@ airpf_status airpf_sync(airpf_ctx* ctx)
         set_err(ctx, "a grid-barrier wait timed out; the pass's results are invalid");
         return AIRPF_ERR_TIMEOUT;
     }
+    return AIRPF_OK;
+}
+
+airpf_status airpf_kernel_times(airpf_ctx* ctx, double* step_ms, double* cascade_ms)
+{
+    if (!ctx || !step_ms || !cascade_ms) return AIRPF_ERR_ARG;
+    if (!ctx->ev) {
+        set_err(ctx, "the context was created without AIRPF_RECORD_TIMING");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "airpf_kernel_times");
+    double a = 0.0, b = 0.0;
+    for (int t = 0; t < ctx->cfg.T; ++t) {
+        float x = 0.f, y = 0.f;
+        e = cudaEventElapsedTime(&x, ctx->ev[4 * t], ctx->ev[4 * t + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&y, ctx->ev[4 * t + 2], ctx->ev[4 * t + 3]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventElapsedTime");
+        a += x;
+        b += y;
+    }
+    *step_ms = a;
+    *cascade_ms = b;
     return AIRPF_OK;
 }
 
