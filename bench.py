@@ -170,8 +170,9 @@ def run_reference(args) -> None:
 def run_gpu(args) -> None:
     import torch
     import paper_2312_06484_gb300 as gp
+    from paper_2312_06484_gb300 import replicas
 
-    ws, rank, local = _dist()
+    ws, rank, local = replicas.world()
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -188,7 +189,7 @@ def run_gpu(args) -> None:
                    3: "persistent cooperative grid"}[f.launch_mode]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    chain = rank
+    chain = replicas.chain_base(rank)      # one independent chain per rank
 
     def one(j):
         return f.run(theta, y, chain0=chain, iter=j)["log_z"]
@@ -218,12 +219,9 @@ def run_gpu(args) -> None:
     torch.cuda.synchronize()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t)
+    tot_ms = replicas.max_over_ranks(tot_ms, device="cuda")   # the slowest rank's time
     ps = M_ISL * M_PART * T_OBS
-    value = ps * args.steps * ws / (tot_ms / 1e3)
+    value = replicas.job_rate(ps * args.steps, tot_ms / 1e3, ws)
     lz32 = torch.stack(lzs).cpu().numpy().ravel()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region

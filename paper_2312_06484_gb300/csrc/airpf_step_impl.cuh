@@ -2,9 +2,14 @@
 // instantiated per precision in airpf_launch_f32.cu / airpf_launch_f64.cu).
 //
 // A pass of Algorithm 1 (Heine, arXiv 2312.06484, main loop) is a prologue
-// launch that derives every filter's model constants, then either one launch
-// per time step (replayed from a CUDA graph) or one persistent launch that
-// loops over the steps.  CTA j of a filter owns the G islands j*G .. j*G+G-1.
+// launch that derives every filter's model constants, then, for t = 1..T, an
+// island-step launch (every CTA of every filter) followed by a cascade launch
+// (one CTA per filter), and a last island-step launch for t = T+1 that only
+// records the lineage of step T -- replayed from a CUDA graph.  Where a filter
+// fits one CTA, one persistent launch runs all steps instead (the CTA runs the
+// cascade itself between block barriers); the cooperative-grid launch runs the
+// cascade in the filter's first CTA between two bounded grid barriers.
+// CTA j of a filter owns the G islands j*G .. j*G+G-1.
 //
 // Island weights W^k are kept unnormalised, as in Algorithm 1, in an extended
 // range (mantissa plus integer binary exponent).  At the end of step t each
@@ -15,29 +20,32 @@
 // islands; levels below g are inside the records, levels g..S form the upper
 // tree over the m/G record tops.
 //
-// Step t+1 then does:
-//  1. issue the loads of the records and of the CTA's own particle block (the
-//     parents when the island keeps its own block), and draw the step's
-//     random numbers (Philox, Box-Muller) while they are in flight;
-//  2. the interaction cascade of step t (Algorithm 1, stages s = 1..S): rescale
-//     the record tops by exact powers of two to the largest exponent, build the
-//     upper tree; after s-1 interacting butterfly stages (eq. (3)) every island
-//     weight is the mean of its aligned block of 2^(s-1) islands, so
-//     ENF_{t,s} = Tot^2 2^(s-1) / (m sum_b B_{s-1,b}^2) for every stage from one
-//     tree; the interacting stages form a prefix (a stage with alpha = I leaves
-//     the weights, hence the ENF, unchanged), so s* = min{s : ENF_s >= tau}
-//     (adaptation line of Algorithm 1).  Island k's new weight W^k_{t+1,0} is
-//     its block mean at level s*-1 and the block it inherits is
-//     src(k) = c_1(c_2(...c_{s*-1}(k))), where c_s(j) picks the lower island of
-//     {j, j xor 2^(s-1)} iff u_{t,s,j} (W_lo + W_hi) < W_lo.  Every CTA of the
-//     filter computes the same upper tree from the same records, so no further
-//     barrier is needed; log Z^N_t = log(m^-1 sum_k W^k) (Section 2) is read off
-//     the tree total when it is recorded;
-//  3. the island work of step t+1: mutate the inherited internally-resampled
-//     block through K_{t+1} (Algorithm 1, last stage), weight by g_{t+1},
-//     island maximum, inclusive CDF, M multinomial draws by binary search
-//     (internal resample), gather, store, and W^k_{t+1,1} = W^k_{t+1,0} M^-1 sum g;
-//  4. publish the CTA's record.
+// Cascade kernel of step t (Algorithm 1, interaction stages s = 1..S): read
+// each record once, rescale the record tops by exact powers of two to the
+// largest exponent, build the upper tree by warp shuffles.  After s-1
+// interacting butterfly stages (eq. (3)) every island weight is the mean of
+// its aligned block of 2^(s-1) islands, so
+//   ENF_{t,s} = Tot^2 2^(s-1) / (m sum_b B_{s-1,b}^2)
+// for every stage from one tree; the interacting stages form a prefix (a stage
+// with alpha = I leaves the weights, hence the ENF, unchanged), so
+// s* = min{s : ENF_s >= tau} (adaptation line of Algorithm 1).  Island k's new
+// weight W^k_{t+1,0} is its block mean at level s*-1 and the block it inherits
+// is src(k) = c_1(c_2(...c_{s*-1}(k))), where c_s(j) picks the lower island of
+// {j, j xor 2^(s-1)} iff u_{t,s,j} (W_lo + W_hi) < W_lo.  The kernel writes the
+// summary (s*, largest exponent), the upper-tree level s*-1 when it lies above
+// the CTA level, src(k) when s* > 1, and log Z^N_t = log(m^-1 sum_k W^k)
+// (Section 2) from the tree total when it is recorded.
+//
+// Island-step kernel of step t+1, per CTA:
+//  1. load the summary, the CTA's own record and (s* > 1) the inherited
+//     blocks; issue the loads of the CTA's own particle block (the parents
+//     when the island keeps its block) and draw the step's random numbers
+//     (Philox, Box-Muller) while they are in flight;
+//  2. mutate the inherited internally-resampled block through K_{t+1}
+//     (Algorithm 1, last stage), weight by g_{t+1}, island maximum, inclusive
+//     CDF, M multinomial draws by binary search (internal resample), gather,
+//     store, and W^k_{t+1,1} = W^k_{t+1,0} M^-1 sum g;
+//  3. publish the CTA's record.
 //
 // Arithmetic.  FP64 path: particles, CDF, island weights (double mantissa),
 // block sums and sums of squares in double, so every decision agrees with an
@@ -288,12 +296,13 @@ template <> struct Casc<true> {
 template <typename V> __device__ __forceinline__ bool pos_v(V v) { return v > (V)0; }
 
 // ---------------------------------------------------------------------------
-// Cascade of step tp for filter c (see file comment), run once per step by the
-// filter's last CTA to finish it.  Reads the CTA records of step tp, builds the
-// upper tree, decides s*, and writes what the next step needs (the summary, the
-// upper-tree level of the block means when it lies above the CTAs, the
-// inherited blocks when a stage interacted), log Z and the records of the run.
-// Every thread of the CTA calls it.
+// Cascade of step tp for filter c (see file comment), run by one CTA: the
+// cascade kernel's, or the persistent kernel's that holds the filter (or its
+// first CTA).  Reads the CTA records of step tp, builds the upper tree, decides
+// s*, and writes what the next step needs (the summary, the upper-tree level of
+// the block means when it lies above the CTAs, the inherited blocks when a
+// stage interacted), log Z and the records of the run.  Every thread of the
+// CTA calls it.
 // ---------------------------------------------------------------------------
 template <bool FX>
 __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st, double* raw)
@@ -313,7 +322,7 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
 
     // 1. the lane's records (read once, all fields at once) and the largest
     //    exponent over the records with a nonzero top
-    constexpr int kRec = 2;                 // record chunks a lane keeps in registers
+    constexpr int kRec = kCachedChunks;
     int re[kRec];
     V rt[kRec];
     Qt rq[kRec][4];
