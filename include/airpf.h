@@ -164,6 +164,40 @@ airpf_status airpf_run(airpf_ctx* ctx, const double* d_theta, const double* d_y,
 airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y,
                             uint32_t chain0, uint32_t iter, double* log_z);
 
+/* Size of the device scratch of airpf_run_static: a fixed device array inside
+ * the library, which CUDA allocates when the library's module loads on a device. */
+#define AIRPF_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* One AIRPF pass, as airpf_run, with no context, no workspace and no device
+ * allocation of any kind.  No counterpart in the paper: it is for callers that
+ * cannot allocate device memory where they need a likelihood estimate -- there
+ * cudaMalloc/cudaFree would stall other work (cudaFree waits for the whole
+ * device) or break the caller's own rule (a serving loop with a fixed memory
+ * budget, a pool allocator that owns all device memory, a callback that must
+ * not block) -- and that have no spare device buffer to lend as workspace.
+ * The pass runs on a static scratch of AIRPF_STATIC_SCRATCH_BYTES per device;
+ * nothing in it needs to start at zero (each pass writes every word it reads).
+ *   cfg           as for airpf_create; record must be 0; launch AUTO, STEPS or
+ *                 PERSISTENT_CTA (PERSISTENT_GRID: AIRPF_ERR_UNSUPPORTED)
+ *   d_theta       [B * d_theta] device, read in place
+ *   d_y           [T * dy] device, read in place
+ *   d_model_data  LGSSM: device array A (dx*dx) then C (dy*dx); else NULL
+ *   chain0, iter  as for airpf_run
+ *   d_log_z       [B] out (device)
+ *   stream        cudaStream_t as void*
+ * A configuration whose scratch would exceed AIRPF_STATIC_SCRATCH_BYTES returns
+ * AIRPF_ERR_WORKSPACE before any work (airpf_last_error(NULL) states both
+ * sizes); give it a context with its own workspace instead.  The first call on
+ * each device does a one-time set-up (it looks up the scratch address, which
+ * also loads the library's module onto that device); make it before any stream
+ * capture.  Calls that overlap in time on one device (different streams, or
+ * host threads without ordering between them) share the scratch and race:
+ * order them on one stream or with events.  Asynchronous on `stream`; failures
+ * leave their message for airpf_last_error(NULL). */
+airpf_status airpf_run_static(const airpf_config* cfg, const double* d_theta, const double* d_y,
+                              const double* d_model_data, uint32_t chain0, uint32_t iter,
+                              double* d_log_z, void* stream);
+
 /* Random-walk particle marginal Metropolis-Hastings, one chain per filter of
  * the batch (Andrieu et al. 2010; AIRPF is valid inside it by Theorem 1).
  * Proposal theta' = theta + step .* N(0, I); independent uniform priors on

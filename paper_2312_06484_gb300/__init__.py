@@ -161,7 +161,29 @@ class AIRPF:
             pass
 
 
-__all__ = ["AIRPF", "AirpfError", "theta_dim", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
+def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: int = 1, dy: int = 1,
+               mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, chain0: int = 0,
+               iter: int = 0, model_data=None, launch="auto", stream=None):
+    """One pass through airpf_run_static: no context and no device allocation (the library's
+    static scratch serves as workspace).  theta [B, d], y [T*dy], log_z [B] (out) and the
+    optional model_data are float64 CUDA tensors, used in place."""
+    import torch
+    lib = _binding.load()
+    mode = _MODES[mode] if isinstance(mode, str) else int(mode)
+    precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    launch = _LAUNCH[launch] if isinstance(launch, str) else int(launch)
+    T = y.numel() // dy
+    cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau, precision=precision,
+                      record=0, seed=seed, launch=launch, reserved=0)
+    for t in (theta, y, log_z) + ((model_data,) if model_data is not None else ()):
+        assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    _binding.check(lib.airpf_run_static(ctypes.byref(cfg), _ptr(theta), _ptr(y), _ptr(model_data), chain0, iter,
+                                        _ptr(log_z), ctypes.c_void_p(stream.cuda_stream)))
+    return log_z
+
+
+__all__ = ["AIRPF", "AirpfError", "theta_dim", "run_static", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
            "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
            "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
            "LAUNCH_PERSISTENT_GRID"]

@@ -35,6 +35,8 @@ SIGNATURES = {
     "airpf_run_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint32, c_void_p]),
     "airpf_pmmh": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                              c_uint32, c_uint32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "airpf_run_static": (c_int32, [ctypes.POINTER(AirpfConfig), c_void_p, c_void_p, c_void_p, c_uint32,
+                                   c_uint32, c_void_p, c_void_p]),
     "airpf_sync": (c_int32, [c_void_p]),
     "airpf_launch_mode": (c_int32, [c_void_p]),
     "airpf_kernel_times": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),

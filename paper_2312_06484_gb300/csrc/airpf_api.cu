@@ -226,6 +226,16 @@ airpf_status copy_async(airpf_ctx* ctx, void* dst, const void* src, size_t bytes
 
 }  // namespace
 
+namespace airpf {
+void set_create_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_error, sizeof(g_create_error), fmt, ap);
+    va_end(ap);
+}
+}  // namespace airpf
+
 extern "C" {
 
 airpf_status airpf_workspace_bytes(const airpf_config* cfg, size_t* bytes)

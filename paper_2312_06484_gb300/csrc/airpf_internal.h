@@ -111,6 +111,9 @@ struct PmmhParams {
 cudaError_t launch_pmmh_propose(const PmmhParams& q, uint32_t iter, int initial, cudaStream_t stream);
 cudaError_t launch_pmmh_accept(const PmmhParams& q, uint32_t iter, int j, int initial, cudaStream_t stream);
 
+// Message for airpf_last_error(NULL) (calls without a context), printf-style.
+void set_create_error(const char* fmt, ...);
+
 // Choose (tpi, ppt, G) for M particles per island and m islands per filter;
 // want_ppt / want_g of 0 take the defaults.
 void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, int* ppt, int* G);
