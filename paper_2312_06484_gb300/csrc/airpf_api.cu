@@ -166,18 +166,21 @@ airpf_status build_graph(airpf_ctx* ctx, const StepParams& p, cudaGraphExec_t* g
     e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
     cudaError_t le = cudaSuccess;
-    // timing: event-record nodes around each kernel of steps 1..T (plain graph only)
+    // timing: event-record nodes around each kernel of steps 1..T (plain graph
+    // only), with plain stream-order edges between the kernels
     const bool timed = ctx->ev && graph == &ctx->graph;
+    StepParams q = p;
+    if (timed) q.pdl = 0;
     auto mark = [&](int t, int which) {
         if (timed && le == cudaSuccess && t >= 1 && t <= ctx->cfg.T)
             le = cudaEventRecordWithFlags(ctx->ev[4 * (t - 1) + which], ctx->cap_stream, cudaEventRecordExternal);
     };
     for (int t = 0; t <= ctx->cfg.T + 1 && le == cudaSuccess; ++t) {
         mark(t, 0);
-        if (le == cudaSuccess) le = airpf::launch_step(p, t, ctx->cap_stream);
+        if (le == cudaSuccess) le = airpf::launch_step(q, t, ctx->cap_stream);
         mark(t, 1);
         mark(t, 2);
-        if (le == cudaSuccess && t >= 1 && t <= ctx->cfg.T) le = airpf::launch_cascade(p, t, ctx->cap_stream);
+        if (le == cudaSuccess && t >= 1 && t <= ctx->cfg.T) le = airpf::launch_cascade(q, t, ctx->cap_stream);
         mark(t, 3);
     }
     cudaGraph_t g = nullptr;
@@ -355,6 +358,12 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     // kernel boundary (about 1 us in a graph) costs less than the device-scope
     // release/acquire pair of a grid barrier (about 3 us)
     if (ctx->launch == AIRPF_LAUNCH_AUTO) ctx->launch = AIRPF_LAUNCH_STEPS;
+    {
+        // per-step launches overlap each kernel's start with the previous one
+        // (programmatic dependent launch); AIRPF_PDL=0 turns it off
+        const char* e_pdl = getenv("AIRPF_PDL");
+        p.pdl = (ctx->launch == AIRPF_LAUNCH_STEPS && !(e_pdl && atoi(e_pdl) == 0)) ? 1 : 0;
+    }
     if (ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
         e = airpf::prepare_step(p);
         const bool fits = (e == cudaSuccess) && airpf::persistent_grid_fits(p);

@@ -73,7 +73,7 @@ constexpr int kMaxThreads = 512;      // per-step and grid-persistent CTAs
 constexpr int kMaxCtaThreads = 512;   // a whole filter in one CTA
 constexpr int kMinCtasPerSm = 2;      // register budget: 64 per thread at 512 threads
 constexpr int kCascadeThreads = 256;  // the cascade kernel's CTA
-constexpr int kDefaultThreads = 256;  // default CTA size of the per-step launch
+constexpr int kDefaultThreads = 512;  // default CTA size of the per-step launch (measured best with PDL)
 constexpr unsigned long long kWaitNs = 1000000000ull;   // bounded barrier wait: 1 s
 constexpr unsigned kSpinLimit = 1u << 26;               // iteration backstop
 constexpr int kMaxStages = 16;
@@ -158,6 +158,12 @@ __device__ __forceinline__ V warp_incl_scan(V v, int lane)
     }
     return v;
 }
+
+// Programmatic dependent launch: wait until the previous kernel of the stream
+// has completed and its memory is visible (returns at once for a kernel
+// launched without the attribute), and let the next kernel start launching.
+__device__ __forceinline__ void dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // A thread's PPT consecutive particles as one vector access (the caller checks
 // that the first index is a multiple of PPT), read through L2.
@@ -641,7 +647,8 @@ __global__ void airpf_prologue_kernel(StepParams p)
 // thread of the CTA; all barriers inside are CTA-uniform.
 // ---------------------------------------------------------------------------
 template <typename R, int MODEL, int DX, int PPT>
-__device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int k0, unsigned char* smem)
+__device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int k0, unsigned char* smem,
+                                          bool dep = false)
 {
     using Cdf = typename CdfType<R>::T;
     constexpr bool FX = sizeof(R) == 4;
@@ -662,8 +669,64 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
     const bool designated = (k0 == 0);
 
-    // ---- 1. in flight: the own islands' weight and source block (written by the
-    //      cascade of step t-1), the own particle block, and the step's noise ----
+    // ---- 1. before any dependency: the step's noise (and at t = 1 the prior
+    //      draw), from the run parameters and model constants only, which the
+    //      kernels of this pass never write ----
+    const int g = tid / p.tpi, li = tid - g * p.tpi;
+    const int lane = tid & 31, wi = li >> 5;   // warp index within the island
+    const int k = k0 + g;
+    const R* Xp = reinterpret_cast<const R*>(p.X[(t - 1) & 1]);
+    const bool vec = (M % PPT) == 0;       // a thread's particles are one aligned vector
+    R xp[PPT][DX];
+    R z[PPT][DX > 1 ? DX : 1];
+    uint32_t w0[PPT], wres[PPT];
+    ModelPar<R> mp;
+    if (t <= p.T) {
+        mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+        if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int i = li * PPT + r;
+            w0[r] = 0;
+            wres[r] = 0;
+            if (i < M) {
+                const uint32_t unit = (uint32_t)(k * M + i);
+                if (t == 1) model_prior<R, MODEL, DX>(mp, st, unit, dx, xp[r]);
+                model_step_noise<R, MODEL, DX>(st, unit, (uint32_t)t, dx, z[r], w0[r], wres[r]);
+            }
+        }
+    }
+
+    // ---- 2. everything below reads what earlier kernels of the pass wrote ----
+    if (dep) {
+        dependency_wait();
+        allow_dependents();
+    }
+    if (t >= 2 && t <= p.T) {           // the own block (the parents when the island keeps it)
+        if (vec && li * PPT < M) {
+#pragma unroll
+            for (int d = 0; d < DX; ++d) {
+                if (d < dx) {
+                    R v[PPT];
+                    load_run<R, PPT>(&Xp[((size_t)c * dx + d) * N + (size_t)k * M + li * PPT], v);
+#pragma unroll
+                    for (int r = 0; r < PPT; ++r) xp[r][d] = v[r];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < PPT; ++r) {
+                const int i = li * PPT + r;
+                if (i < M) {
+#pragma unroll
+                    for (int d = 0; d < DX; ++d)
+                        if (d < dx) xp[r][d] = __ldcg(&Xp[((size_t)c * dx + d) * N + (size_t)k * M + i]);
+                }
+            }
+        }
+    }
+
+    // the own islands' weight and source block (written by the cascade of step t-1)
     if (t == 1) {
         for (int gi = tid; gi < p.G; gi += blockDim.x) {
             // W = 1: 0.5 2^1 as a double, 2^63 2^(1-64) as an integer mantissa
@@ -704,53 +767,6 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
     }
 
-    const int g = tid / p.tpi, li = tid - g * p.tpi;
-    const int lane = tid & 31, wi = li >> 5;   // warp index within the island
-    const int k = k0 + g;
-    const R* Xp = reinterpret_cast<const R*>(p.X[(t - 1) & 1]);
-    const bool vec = (M % PPT) == 0;       // a thread's particles are one aligned vector
-    R xp[PPT][DX];
-    R z[PPT][DX > 1 ? DX : 1];
-    uint32_t w0[PPT], wres[PPT];
-    ModelPar<R> mp;
-    if (t <= p.T) {
-        mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
-        if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
-        if (t >= 2) {
-            if (vec && li * PPT < M) {
-#pragma unroll
-                for (int d = 0; d < DX; ++d) {
-                    if (d < dx) {
-                        R v[PPT];
-                        load_run<R, PPT>(&Xp[((size_t)c * dx + d) * N + (size_t)k * M + li * PPT], v);
-#pragma unroll
-                        for (int r = 0; r < PPT; ++r) xp[r][d] = v[r];
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < PPT; ++r) {
-                    const int i = li * PPT + r;
-                    if (i < M) {
-#pragma unroll
-                        for (int d = 0; d < DX; ++d)
-                            if (d < dx) xp[r][d] = __ldcg(&Xp[((size_t)c * dx + d) * N + (size_t)k * M + i]);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-            const int i = li * PPT + r;
-            w0[r] = 0;
-            wres[r] = 0;
-            if (i < M) {
-                const uint32_t unit = (uint32_t)(k * M + i);
-                if (t == 1) model_prior<R, MODEL, DX>(mp, st, unit, dx, xp[r]);
-                model_step_noise<R, MODEL, DX>(st, unit, (uint32_t)t, dx, z[r], w0[r], wres[r]);
-            }
-        }
-    }
     __syncthreads();
 
     // ---- lineage of step t-1: parent of particle (k, i) among time-(t-1) particles ----
@@ -1022,7 +1038,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinCtasPerSm) airpf_step_kernel(
     const int c = blockIdx.x / cpf;
     const int k0 = (blockIdx.x - c * cpf) * p.G;
     if (p.active != nullptr && p.active[c] == 0) return;   // uniform over the CTA
-    step_body<R, MODEL, DX, PPT>(p, t, c, k0, smem);
+    step_body<R, MODEL, DX, PPT>(p, t, c, k0, smem, p.pdl != 0);
 }
 
 // The cascade of step t: one CTA per filter.
@@ -1032,6 +1048,10 @@ __global__ void __launch_bounds__(kCascadeThreads) airpf_cascade_kernel(StepPara
     extern __shared__ __align__(16) unsigned char smem[];
     const int c = blockIdx.x;
     if (p.active != nullptr && p.active[c] == 0) return;
+    if (p.pdl) {                  // the records are the island-step kernel's output
+        dependency_wait();
+        allow_dependents();
+    }
     const RunParams run = *p.run;
     const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
     cascade_all<sizeof(R) == 4>(p, c, t, st, reinterpret_cast<double*>(smem));
@@ -1069,6 +1089,26 @@ __global__ void __launch_bounds__(GRID ? kMaxThreads : kMaxCtaThreads, kMinCtasP
             __syncthreads();
         }
     }
+}
+
+// Launch with the programmatic-stream-serialization attribute: the kernel may
+// begin while the previous kernel of the stream finishes, and waits for it with
+// griddepcontrol.wait before touching that kernel's output.
+template <typename K>
+static cudaError_t launch_dependent(K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                                    const StepParams& p, int t)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, p, t);
 }
 
 template <typename R, int MODEL, int DX, int PPT>
@@ -1116,6 +1156,7 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     }
     if (op == OP_CASCADE) {
         const size_t cs = cascade_smem_bytes(p);
+        if (p.pdl) return launch_dependent(airpf_cascade_kernel<R>, dim3(p.B), dim3(kCascadeThreads), cs, stream, p, t);
         airpf_cascade_kernel<R><<<p.B, kCascadeThreads, cs, stream>>>(p, t);
         return cudaGetLastError();
     }
@@ -1124,6 +1165,10 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         airpf_prologue_kernel<R, MODEL><<<(n + 127) / 128, 128, 0, stream>>>(p);
         return cudaGetLastError();
     }
+    // step 1 follows the prologue in plain stream order; later steps may start
+    // launching while the previous cascade runs (programmatic dependent launch)
+    if (p.pdl && t >= 2)
+        return launch_dependent(airpf_step_kernel<R, MODEL, DX, PPT>, dim3(grid), dim3(block), smem, stream, p, t);
     airpf_step_kernel<R, MODEL, DX, PPT><<<grid, block, smem, stream>>>(p, t);
     return cudaGetLastError();
 }
