@@ -92,8 +92,12 @@ typedef enum {
 
 /* How a pass over y_1..y_T is launched.  AUTO picks PERSISTENT_CTA when a
  * whole filter fits one CTA (m * threads-per-island <= 512), else STEPS.
- * STEPS: two launches per time step (the island-step kernel, then the
- * cascade kernel with one CTA per filter), replayed from a CUDA graph.
+ * STEPS: one launch per time step, replayed from a CUDA graph; each CTA
+ * first runs the interaction cascade of the previous step from the per-CTA
+ * summaries of the island weights, then its islands' step.  (Environment
+ * AIRPF_FUSED=0 instead runs the cascade as a second kernel per step, one CTA
+ * per filter.)  Consecutive kernels overlap their start with programmatic
+ * dependent launch.
  * PERSISTENT_CTA: one launch for all steps, one CTA per filter.
  * PERSISTENT_GRID: one cooperative launch for all steps, a bounded grid
  * barrier (1 s) between steps; a timed-out wait is reported by airpf_sync. */
@@ -237,7 +241,8 @@ airpf_status airpf_sync(airpf_ctx* ctx);
  * AIRPF_RECORD_TIMING (which puts CUDA event-record nodes before and after each
  * kernel of steps 1..T into the pass's graph): waits for the stream and
  * returns the summed durations, in milliseconds, of the T island-step kernels
- * and of the T cascade kernels of the last airpf_run.  AIRPF_ERR_UNSUPPORTED
+ * and of the T cascade kernels (0 when every CTA runs the cascade itself) of
+ * the last airpf_run.  AIRPF_ERR_UNSUPPORTED
  * for a context without the flag. */
 airpf_status airpf_kernel_times(airpf_ctx* ctx, double* step_ms, double* cascade_ms);
 

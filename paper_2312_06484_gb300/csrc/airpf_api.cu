@@ -180,7 +180,8 @@ airpf_status build_graph(airpf_ctx* ctx, const StepParams& p, cudaGraphExec_t* g
         if (le == cudaSuccess) le = airpf::launch_step(q, t, ctx->cap_stream);
         mark(t, 1);
         mark(t, 2);
-        if (le == cudaSuccess && t >= 1 && t <= ctx->cfg.T) le = airpf::launch_cascade(q, t, ctx->cap_stream);
+        if (le == cudaSuccess && !q.fused && t >= 1 && t <= ctx->cfg.T)
+            le = airpf::launch_cascade(q, t, ctx->cap_stream);
         mark(t, 3);
     }
     cudaGraph_t g = nullptr;
@@ -216,7 +217,7 @@ airpf_status enqueue_pass(airpf_ctx* ctx, bool pm = false)
     if (s != AIRPF_OK) return s;
     cudaError_t e = cudaGraphLaunch(pm ? ctx->graph_pm : ctx->graph, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-    ctx->launches += 2 * (int64_t)ctx->cfg.T + 2;
+    ctx->launches += (p.fused ? 1 : 2) * (int64_t)ctx->cfg.T + 2;
     return AIRPF_OK;
 }
 
@@ -363,6 +364,11 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         // (programmatic dependent launch); AIRPF_PDL=0 turns it off
         const char* e_pdl = getenv("AIRPF_PDL");
         p.pdl = (ctx->launch == AIRPF_LAUNCH_STEPS && !(e_pdl && atoi(e_pdl) == 0)) ? 1 : 0;
+        // fused steps: every CTA runs the previous step's cascade itself from the
+        // CTA records, so a step is one kernel; AIRPF_FUSED=0 selects the
+        // island-step + cascade kernel pair instead
+        const char* e_fused = getenv("AIRPF_FUSED");
+        p.fused = (ctx->launch == AIRPF_LAUNCH_STEPS && !(e_fused && atoi(e_fused) == 0)) ? 1 : 0;
     }
     if (ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
         e = airpf::prepare_step(p);

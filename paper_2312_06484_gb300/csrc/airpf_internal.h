@@ -44,6 +44,7 @@ struct StepParams {
     unsigned* err;                // [1] nonzero after a timed-out wait
     int inject_stall;             // test hook (grid-persistent launch only)
     int pdl;                      // per-step launches: programmatic dependent launch
+    int fused;                    // per-step launches: each CTA runs the previous step's cascade itself
     void* X[2];                   // particle stores, ping-pong by t & 1
     int P, g;                     // CTA records per filter (m / G) and log2 G
     int* pe[2];                   // CTA records, ping-pong by t & 1

@@ -73,7 +73,7 @@ constexpr int kMaxThreads = 512;      // per-step and grid-persistent CTAs
 constexpr int kMaxCtaThreads = 512;   // a whole filter in one CTA
 constexpr int kMinCtasPerSm = 2;      // register budget: 64 per thread at 512 threads
 constexpr int kCascadeThreads = 256;  // the cascade kernel's CTA
-constexpr int kDefaultThreads = 512;  // default CTA size of the per-step launch (measured best with PDL)
+constexpr int kDefaultThreads = 256;  // default CTA size of the per-step launch (measured best, fused steps)
 constexpr unsigned long long kWaitNs = 1000000000ull;   // bounded barrier wait: 1 s
 constexpr unsigned kSpinLimit = 1u << 26;               // iteration backstop
 constexpr int kMaxStages = 16;
@@ -101,7 +101,7 @@ struct Layout {
 // partial sums [16 warps][kQw], per-level sums [kMaxStages], a few integers
 __host__ __device__ inline size_t cascade_slots(const StepParams& p)
 {
-    return 2 * (size_t)p.P + 2 * (size_t)p.G + 16 * kQw + kMaxStages + 8;
+    return 2 * (size_t)p.P + 2 * (size_t)p.G + 16 * kQw + kMaxStages + 8 + 3 * 16;
 }
 
 __host__ __device__ inline Layout make_layout(const StepParams& p)
@@ -310,8 +310,55 @@ template <typename V> __device__ __forceinline__ bool pos_v(V v) { return v > (V
 // stage interacted), log Z and the records of the run.  Every thread of the
 // CTA calls it.
 // ---------------------------------------------------------------------------
+// The run's records of step tp (one thread): log Z^N_tp when traced or at
+// tp = T, s*, and ENF_{tp,1..S} (stages from s* on repeat ENF_{s*}) with
+// ENF_{tp+1,0}.  Q[l] = sum over level-l blocks of the squared block sums,
+// filled at least up to level s*-1.
 template <bool FX>
-__device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st, double* raw)
+__device__ void cascade_records(const StepParams& p, int c, int tp, int ss, typename Casc<FX>::V tot, int emax,
+                                const typename Casc<FX>::Qt* Q)
+{
+    using C = Casc<FX>;
+    const int m = p.m, S = p.S;
+    const auto tq = C::qv(tot);
+    if (p.trace || tp == p.T) {
+        // log Z^N_tp = log(m^-1 sum_k W^k), sum_k W^k = Tot 2^(emax - kFrac);
+        // the FP32-mixed weights leave out M^-tp
+        double lz = pos_v(tot)
+            ? log(C::to_d(tot)) - log((double)m) + (double)(emax - C::kFrac) * 0.6931471805599453
+            : -INFINITY;
+        if (FX) lz -= (double)tp * log((double)p.M);
+        if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
+        if (tp == p.T) p.logz[c] = lz;
+    }
+    if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ss;
+    if (p.enf) {
+        double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (S + 1);
+        double last = 1.0;
+        for (int s = 1; s <= S; ++s) {
+            const int sr = s <= ss ? s : ss;
+            const double v = pos_v(tot)
+                ? (double)tq * (double)tq * ldexp(1.0, sr - 1) / ((double)m * (double)Q[sr - 1]) : 0.0;
+            e[s] = v;
+            if (s == ss) last = v;
+        }
+        if (tp < p.T) p.enf[((size_t)c * p.T + tp) * (S + 1)] = pos_v(tot) ? (ss <= S ? last : 1.0) : 0.0;
+    }
+}
+
+// Where the cascade's result goes: to global memory for the next step's CTAs
+// (the summary, cup, nsrc), or, when a CTA runs the cascade itself before its
+// island work (fused step), straight into that CTA's own island slots.
+struct CascadeOwn {
+    int k0;            // first island of the CTA
+    u64* w;            // [G] weight mantissas
+    int* we;           // [G] weight exponents
+    int* src;          // [G] inherited blocks
+};
+
+template <bool FX>
+__device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st, double* raw,
+                            const CascadeOwn* own = nullptr, bool records = true)
 {
     using C = Casc<FX>;
     using V = typename C::V;
@@ -325,6 +372,10 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     Qt* Qw = reinterpret_cast<Qt*>(raw + 2 * P + 2 * G);          // [nw][kQw]
     Qt* Q = reinterpret_cast<Qt*>(raw + 2 * P + 2 * G + 16 * kQw);   // [kMaxStages]
     int* iscal = reinterpret_cast<int*>(raw + 2 * P + 2 * G + 16 * kQw + kMaxStages);
+    double* wpart = raw + 2 * P + 2 * G + 16 * kQw + kMaxStages + 8;     // [3][16] per-warp partials
+    int* w_emax = reinterpret_cast<int*>(wpart);
+    V* w_tot = reinterpret_cast<V*>(wpart + 16);
+    Qt* w_q0 = reinterpret_cast<Qt*>(wpart + 32);
 
     // 1. the lane's records (read once, all fields at once) and the largest
     //    exponent over the records with a nonzero top
@@ -356,12 +407,100 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
         if (pos_v(__ldcg(&pt[(size_t)j * 2 * G + tree_off(G, g)])) && e > emax) emax = e;
     }
     emax = warp_max(emax);
-    if (tid == 0) iscal[0] = INT_MIN;
+    if (lane == 0) w_emax[warp] = emax;
     __syncthreads();
-    if (lane == 0) atomicMax(&iscal[0], emax);
-    __syncthreads();
-    emax = iscal[0];
+    emax = INT_MIN;
+    for (int w = 0; w < nw; ++w) emax = max(emax, w_emax[w]);
     const bool dead = (emax == INT_MIN);
+
+    // 1b. fast path.  Stage 1 needs only Tot = sum_k W^k and Q_0 = sum_k (W^k)^2
+    //     (ENF_1 = Tot^2 / (m Q_0)); when it does not interact (always under
+    //     NEVER, and on most ADAPTIVE steps) s* = 1, every island keeps its own
+    //     weight and block, and the tree of block sums is not needed.
+    if (p.mode != 1) {
+        V tpart = (V)0;
+        Qt qpart = (Qt)0;
+        for (int i = 0, j = warp * 32 + lane; j < P; ++i, j += 32 * nw) {
+            int e;
+            V top;
+            Qt q0r = (Qt)0;
+            if (i < kRec) {
+                e = INT_MIN;
+                top = (V)0;
+#pragma unroll
+                for (int r = 0; r < kRec; ++r)
+                    if (r == i) {
+                        e = re[r];
+                        top = rt[r];
+                        q0r = rq[r][0];
+                    }
+            } else {
+                e = __ldcg(&pe[j]);
+                top = __ldcg(&pt[(size_t)j * 2 * G + tree_off(G, g)]);
+                if (g >= 1) q0r = __ldcg(&pq[(size_t)j * 8]);
+            }
+            if (!dead && pos_v(top)) {
+                const int sh = emax - e;
+                const V v = C::rescale(top, sh);
+                tpart += v;
+                if (g >= 1) {
+                    qpart += C::qscale(q0r, 2 * sh);
+                } else {
+                    const Qt q = C::qv(v);
+                    qpart += q * q;
+                }
+            }
+        }
+        tpart = warp_sum(tpart);
+        qpart = warp_sum(qpart);
+        if (lane == 0) {
+            w_tot[warp] = tpart;
+            w_q0[warp] = qpart;
+        }
+        __syncthreads();
+        V tot = (V)0;
+        Qt q0 = (Qt)0;
+        for (int w = 0; w < nw; ++w) {
+            tot += w_tot[w];
+            q0 += w_q0[w];
+        }
+        const Qt tq = C::qv(tot);
+        const bool quiet1 = p.mode == 0 || (pos_v(tot) && !(tq * tq < C::tau(p) * (Qt)m * q0));
+        if (quiet1) {
+            if (tid == 0 && records) {
+                Q[0] = q0;
+                cascade_records<FX>(p, c, tp, 1, tot, emax, Q);
+            }
+            if (own != nullptr) {
+                const int jo = own->k0 >> g;
+                const int ej = __ldcg(&pe[jo]);
+                for (int gi = tid; gi < G; gi += nthr) {
+                    XW w{0ull, 0};
+                    if (!dead && ej != INT_MIN) {
+                        const V leaf = __ldcg(&pt[(size_t)jo * 2 * G + gi]);
+                        w = g >= 1 ? C::weight(leaf, ej - C::kFrac) : C::weight(C::rescale(leaf, emax - ej), emax - C::kFrac);
+                    }
+                    own->w[gi] = w.bits;
+                    own->we[gi] = w.e;
+                    own->src[gi] = own->k0 + gi;
+                }
+                return;
+            }
+            if (tid == 0) {
+                p.csum[(size_t)c * 4 + 0] = 1;
+                p.csum[(size_t)c * 4 + 1] = emax;
+            }
+            if (g == 0) {     // level 0 lies above the CTAs: the rescaled record tops
+                for (int j = tid; j < P; j += nthr) {
+                    const int e = __ldcg(&pe[j]);
+                    const V top = __ldcg(&pt[(size_t)j * 2 * G]);
+                    reinterpret_cast<V*>(p.cup)[(size_t)c * P + j] =
+                        (!dead && pos_v(top)) ? C::rescale(top, emax - e) : (V)0;
+                }
+            }
+            return;
+        }
+    }
 
     // 2. upper leaves (record tops rescaled to 2^emax), the lower upper-tree
     //    levels by warp shuffles, and every level's partial sum of squares
@@ -504,29 +643,7 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
             else if (p.mode == 1) ss = S + 1;
             else ss = qm ? __ffs(qm) : S + 1;              // first quiet stage
             iscal[1] = ss;
-            if (p.trace || tp == p.T) {
-                // log Z^N_tp = log(m^-1 sum_k W^k), sum_k W^k = Tot 2^(emax - kFrac);
-                // the FP32-mixed weights leave out M^-tp
-                double lz = pos_v(tot)
-                    ? log(C::to_d(tot)) - log((double)m) + (double)(emax - C::kFrac) * 0.6931471805599453
-                    : -INFINITY;
-                if (FX) lz -= (double)tp * log((double)p.M);
-                if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
-                if (tp == p.T) p.logz[c] = lz;
-            }
-            if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ss;
-            if (p.enf) {
-                double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (S + 1);
-                double last = 1.0;
-                for (int s = 1; s <= S; ++s) {
-                    const int sr = s <= ss ? s : ss;
-                    const double v = pos_v(tot)
-                        ? (double)tq * (double)tq * ldexp(1.0, sr - 1) / ((double)m * (double)Q[sr - 1]) : 0.0;
-                    e[s] = v;
-                    if (s == ss) last = v;
-                }
-                if (tp < p.T) p.enf[((size_t)c * p.T + tp) * (S + 1)] = pos_v(tot) ? (ss <= S ? last : 1.0) : 0.0;
-            }
+            if (records) cascade_records<FX>(p, c, tp, ss, tot, emax, Q);
         }
     }
     __syncthreads();
@@ -536,6 +653,45 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     //    island's inherited block when any stage interacted
     const int ss = iscal[1];
     const int lvl = ss - 1;
+    if (own != nullptr) {
+        // this CTA's islands k0 .. k0+G-1: block mean at level s*-1 and the walk
+        const int jo = own->k0 >> g;
+        for (int gi = tid; gi < G; gi += nthr) {
+            const int k = own->k0 + gi;
+            XW w{0ull, 0};
+            if (!dead) {
+                if (lvl < g) {
+                    const int ej = __ldcg(&pe[jo]);
+                    if (ej != INT_MIN)
+                        w = C::weight(__ldcg(&pt[(size_t)jo * 2 * G + tree_off(G, lvl) + (gi >> lvl)]),
+                                      ej - C::kFrac - lvl);
+                } else {
+                    w = C::weight(ut[tree_off(P, lvl - g) + (k >> lvl)], emax - C::kFrac - lvl);
+                }
+            }
+            own->w[gi] = w.bits;
+            own->we[gi] = w.e;
+            int j = k;
+            for (int s = lvl; s >= 1; --s) {
+                const int l = s - 1, b = 1 << l, pi = j >> l;
+                V lo, hi;
+                if (l >= g) {
+                    lo = ut[tree_off(P, l - g) + (pi & ~1)];
+                    hi = ut[tree_off(P, l - g) + (pi | 1)];
+                } else {
+                    const int jc = j >> g;
+                    const int li = pi - jc * (G >> l);
+                    const int ol = tree_off(G, l);
+                    lo = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li & ~1)]);
+                    hi = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li | 1)]);
+                }
+                const uint32_t wu = st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x;
+                j = C::pick_lo(lo, hi, wu) ? (j & ~b) : (j | b);
+            }
+            own->src[gi] = j;
+        }
+        return;
+    }
     if (tid == 0) {
         p.csum[(size_t)c * 4 + 0] = ss;
         p.csum[(size_t)c * 4 + 1] = emax;
@@ -735,6 +891,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             own_src[gi] = k0 + gi;
         }
         if (designated && tid == 0 && p.enf) p.enf[(size_t)c * p.T * (p.S + 1)] = 1.0;
+    } else if (p.fused) {
+        // this CTA runs the cascade of step t-1 itself, from every CTA record of
+        // the filter (the first CTA also writes log Z and the run's records)
+        const CascadeOwn own{k0, own_w, own_we, own_src};
+        cascade_all<FX>(p, c, t - 1, st, tree, &own, designated);
     } else {
         // the cascade's summary of step t-1, this CTA's record of step t-1 and
         // (used only if some stage interacted) the inherited blocks
