@@ -27,7 +27,9 @@ def test_ar1_workload_all_modes(gpu_lib, mode, launch):
                          seed=7, chain=3 + b, iter=2)
         compare_filter(g, b, o, m=m, what=f"{mode} {launch} b={b}")
     if launch == "steps":
-        assert g["launches"] == 2 * 100 + 3  # run parameters, prologue, T steps, T cascades, lineage
+        # run parameters, prologue, T island steps, the lineage step, and T cascade kernels
+        # unless every CTA runs the cascade itself (fused steps)
+        assert g["launches"] in (2 * 100 + 3, 100 + 3)
     else:
         assert g["launches"] == 3 and g["launch_mode"] == 2
 
