@@ -183,10 +183,12 @@ def run_gpu(args) -> None:
     y_np = synth.sv_observations(T_OBS, seed=2)
     theta = torch.tensor(synth.SV_THETA[None, :], device="cuda")
     y = torch.tensor(y_np, device="cuda")
+    tile = dict(ppt=args.ppt, islands_per_cta=args.islands_per_cta)
     f = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
-                 seed=1, launch=args.launch)
-    launch_name = {1: "steps (CUDA graph)", 2: "persistent, CTA per filter",
-                   3: "persistent cooperative grid"}[f.launch_mode]
+                 seed=1, launch=args.launch, **tile)
+    launch_name = {1: "one kernel per step (CUDA graph, programmatic dependent launch)",
+                   2: "persistent, CTA per filter", 3: "persistent cooperative grid",
+                   4: "island-step + cascade kernel per step (CUDA graph)"}[f.launch_mode]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     chain = replicas.chain_base(rank)      # one independent chain per rank
@@ -267,7 +269,8 @@ def run_gpu(args) -> None:
     # per-kernel durations, live: the same workload through a graph with CUDA event-record
     # nodes around each kernel (island-step kernel, cascade kernel), on the same stream
     ft = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
-                  seed=1, launch="steps", record=gp.RECORD_TIMING)
+                  seed=1, launch=f.launch_mode if f.launch_mode in (1, 4) else "steps", record=gp.RECORD_TIMING,
+                  **tile)
     ft.run(theta, y, chain0=chain, iter=0xFFFE0000)
     ft.sync()
     n_k = max(3, min(args.steps, 10))
@@ -354,7 +357,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--launch", default="auto", choices=["auto", "steps", "grid"])
+    ap.add_argument("--launch", default="auto", choices=["auto", "steps", "split", "grid"])
+    ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0: automatic)")
+    ap.add_argument("--islands-per-cta", type=int, default=0, help="islands per CTA (0: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -94,10 +94,11 @@ typedef enum {
  * whole filter fits one CTA (m * threads-per-island <= 512), else STEPS.
  * STEPS: one launch per time step, replayed from a CUDA graph; each CTA
  * first runs the interaction cascade of the previous step from the per-CTA
- * summaries of the island weights, then its islands' step.  (Environment
- * AIRPF_FUSED=0 instead runs the cascade as a second kernel per step, one CTA
- * per filter.)  Consecutive kernels overlap their start with programmatic
- * dependent launch.
+ * summaries of the island weights, then its islands' step.  STEPS_SPLIT: the
+ * cascade runs as a second kernel per step with one CTA per filter (AUTO
+ * takes it when a filter spans more than 512 CTAs, where every CTA reading
+ * every summary would cost more).  Consecutive per-step kernels overlap their
+ * start with programmatic dependent launch.
  * PERSISTENT_CTA: one launch for all steps, one CTA per filter.
  * PERSISTENT_GRID: one cooperative launch for all steps, a bounded grid
  * barrier (1 s) between steps; a timed-out wait is reported by airpf_sync. */
@@ -105,7 +106,8 @@ typedef enum {
     AIRPF_LAUNCH_AUTO = 0,
     AIRPF_LAUNCH_STEPS = 1,
     AIRPF_LAUNCH_PERSISTENT_CTA = 2,
-    AIRPF_LAUNCH_PERSISTENT_GRID = 3
+    AIRPF_LAUNCH_PERSISTENT_GRID = 3,
+    AIRPF_LAUNCH_STEPS_SPLIT = 4
 } airpf_launch;
 
 typedef struct {
@@ -122,6 +124,8 @@ typedef struct {
     uint64_t seed;
     int32_t launch;         /* airpf_launch (a requested mode that cannot run: AIRPF_ERR_UNSUPPORTED) */
     int32_t reserved;       /* must be 0 */
+    int32_t ppt;            /* particles per thread: 2 or 4, 0 = automatic */
+    int32_t islands_per_cta;/* islands per CTA: a power of 2, 0 = automatic (capped at 512 threads) */
 } airpf_config;
 
 #define AIRPF_RECORD_LINEAGE 1
@@ -230,6 +234,50 @@ airpf_status airpf_pmmh(airpf_ctx* ctx, const double* d_y, const double* step, c
                         const double* hi, double* d_state_theta, double* d_state_logz,
                         uint32_t chain0, uint32_t iter0, int32_t iters, double* d_theta_out,
                         double* d_logz_out, int32_t* d_n_accept);
+
+/* ---- Batches of uneven size and the tiling autotuner ----
+ * Chains whose (m, M) differ run as a group: one context per size class (its
+ * chains are the filters of that context's batch, each with its own theta),
+ * each context created on a stream of its own.  The group forks every member
+ * stream from `stream` with an event, enqueues each member's work on its own
+ * stream, and joins them back, so the classes' kernels run side by side and
+ * the caller sees one asynchronous operation on `stream`.  The contexts stay
+ * owned by the caller and must outlive the group. */
+typedef struct airpf_group airpf_group;
+
+airpf_status airpf_group_create(airpf_ctx* const* ctxs, int32_t n, void* stream, airpf_group** out);
+airpf_status airpf_group_destroy(airpf_group* g);
+
+/* airpf_run for every member i with d_theta[i], chain0[i], d_log_z[i] and the
+ * shared observations d_y (record outputs are not taken here). */
+airpf_status airpf_group_run(airpf_group* g, const double* const* d_theta, const double* d_y,
+                             const uint32_t* chain0, uint32_t iter, double* const* d_log_z);
+
+/* airpf_pmmh for every member i (state, chain0, outputs and acceptance
+ * counters per member; d_theta_out and d_logz_out may be NULL, as may their
+ * entries), same proposal and prior for all. */
+airpf_status airpf_group_pmmh(airpf_group* g, const double* d_y, const double* step, const double* lo,
+                              const double* hi, double* const* d_state_theta, double* const* d_state_logz,
+                              const uint32_t* chain0, uint32_t iter0, int32_t iters,
+                              double* const* d_theta_out, double* const* d_logz_out,
+                              int32_t* const* d_n_accept);
+
+/* airpf_sync of every member, then waits for `stream`. */
+airpf_status airpf_group_sync(airpf_group* g);
+
+/* Tiling autotuner (no counterpart in the paper).  Times `passes` passes of
+ * each candidate tiling of cfg -- particles per thread {2, 4} x islands per
+ * CTA {1, 2, 4, 8, 16} (up to 512 threads) x {STEPS, STEPS_SPLIT}, plus
+ * PERSISTENT_CTA when a filter fits one CTA; candidates with the same actual
+ * mapping are timed once -- after one warm-up pass each, with CUDA events on
+ * `stream`, and returns in *best the configuration of the fastest (cfg with
+ * launch, ppt and islands_per_cta set) and its milliseconds per pass.
+ * d_workspace must hold airpf_workspace_bytes(cfg) rounded up to 256, plus
+ * 8*B bytes (the timed passes' log Z).  Synchronises.  The tiling does not
+ * change what a pass computes, only how fast. */
+airpf_status airpf_autotune(const airpf_config* cfg, void* d_workspace, size_t workspace_bytes,
+                            const double* model_data, const double* d_theta, const double* d_y,
+                            int32_t passes, void* stream, airpf_config* best, float* best_ms);
 
 /* Waits for the context's stream and reports device-side failures of the
  * work enqueued so far: AIRPF_ERR_TIMEOUT if a bounded grid-barrier wait ran

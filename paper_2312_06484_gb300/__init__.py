@@ -19,12 +19,12 @@ MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY = 0, 1, 2, 3, 4
 NEVER, ALWAYS, ADAPTIVE = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
 RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE, RECORD_TIMING = 1, 2, 4, 8
-LAUNCH_AUTO, LAUNCH_STEPS, LAUNCH_PERSISTENT_CTA, LAUNCH_PERSISTENT_GRID = 0, 1, 2, 3
+LAUNCH_AUTO, LAUNCH_STEPS, LAUNCH_PERSISTENT_CTA, LAUNCH_PERSISTENT_GRID, LAUNCH_STEPS_SPLIT = 0, 1, 2, 3, 4
 
 _MODES = {"never": NEVER, "always": ALWAYS, "adaptive": ADAPTIVE}
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED}
 _LAUNCH = {"auto": LAUNCH_AUTO, "steps": LAUNCH_STEPS, "cta": LAUNCH_PERSISTENT_CTA,
-           "grid": LAUNCH_PERSISTENT_GRID}
+           "grid": LAUNCH_PERSISTENT_GRID, "split": LAUNCH_STEPS_SPLIT}
 
 
 def theta_dim(model: int, dx: int = 1) -> int:
@@ -43,7 +43,7 @@ class AIRPF:
 
     def __init__(self, model: int, *, m: int, M: int, T: int, B: int = 1, dx: int = 1, dy: int = 1,
                  mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, record: int = 0,
-                 model_data=None, stream=None, launch="auto"):
+                 model_data=None, stream=None, launch="auto", ppt: int = 0, islands_per_cta: int = 0):
         import torch
         self._torch = torch
         self.lib = _binding.load()
@@ -51,7 +51,8 @@ class AIRPF:
         precision = _PREC[precision] if isinstance(precision, str) else int(precision)
         launch = _LAUNCH[launch] if isinstance(launch, str) else int(launch)
         self.cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau,
-                               precision=precision, record=record, seed=seed, launch=launch, reserved=0)
+                               precision=precision, record=record, seed=seed, launch=launch, reserved=0,
+                               ppt=ppt, islands_per_cta=islands_per_cta)
         nbytes = ctypes.c_size_t()
         _binding.check(self.lib.airpf_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)))
         self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
@@ -161,6 +162,104 @@ class AIRPF:
             pass
 
 
+class Group:
+    """Chains of uneven (m, M): one ``AIRPF`` context per size class (its chains are that
+    context's batch), run side by side through airpf_group_*.  Each member must have been
+    created on a stream of its own; the group forks them from ``stream`` (default: torch's
+    current stream) and joins them back."""
+
+    def __init__(self, members, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = _binding.load()
+        self.members = list(members)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr = (ctypes.c_void_p * len(self.members))(*[mb.ctx.value for mb in self.members])
+        g = ctypes.c_void_p()
+        _binding.check(self.lib.airpf_group_create(arr, len(self.members), ctypes.c_void_p(self.stream.cuda_stream),
+                                                   ctypes.byref(g)))
+        self.g = g
+
+    @staticmethod
+    def _ptrs(ts):
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+
+    def run(self, thetas, y, chain0s, *, iter: int = 0):
+        """thetas[i]: [B_i, d] float64 CUDA; returns the list of log Z tensors [B_i]."""
+        torch = self._torch
+        thetas = [t.to(device="cuda", dtype=torch.float64).contiguous() for t in thetas]
+        y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+        out = [torch.empty(mb.B, dtype=torch.float64, device="cuda") for mb in self.members]
+        c0 = (ctypes.c_uint32 * len(self.members))(*chain0s)
+        self._keep = (thetas, y)
+        _binding.check(self.lib.airpf_group_run(self.g, self._ptrs(thetas), _ptr(y), c0, iter, self._ptrs(out)))
+        return out
+
+    def pmmh(self, y, states_theta, states_logz, *, step, lo, hi, iters: int, chain0s, iter0: int = 0,
+             n_accepts=None, record: bool = False):
+        """airpf_pmmh for every member, one call; states are updated in place."""
+        torch = self._torch
+        n = len(self.members)
+        y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+        d = self.members[0].theta_dim
+        arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(d)) for v in (step, lo, hi)]
+        if n_accepts is None:
+            n_accepts = [torch.zeros(mb.B, dtype=torch.int32, device="cuda") for mb in self.members]
+        th_out = [torch.empty((iters, mb.B, d), dtype=torch.float64, device="cuda") for mb in self.members] \
+            if record else None
+        lz_out = [torch.empty((iters, mb.B), dtype=torch.float64, device="cuda") for mb in self.members] \
+            if record else None
+        c0 = (ctypes.c_uint32 * n)(*chain0s)
+        self._keep = (y, arrs)
+        _binding.check(self.lib.airpf_group_pmmh(
+            self.g, _ptr(y), *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs], self._ptrs(states_theta),
+            self._ptrs(states_logz), c0, iter0, iters, self._ptrs(th_out) if record else None,
+            self._ptrs(lz_out) if record else None, self._ptrs(n_accepts)))
+        return {"n_accept": n_accepts, "theta": th_out, "log_z": lz_out}
+
+    def sync(self):
+        _binding.check(self.lib.airpf_group_sync(self.g))
+
+    def close(self):
+        if getattr(self, "g", None):
+            self.lib.airpf_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(model, theta, y, *, m: int, M: int, B: int = 1, dx: int = 1, dy: int = 1, mode="adaptive",
+             tau: float = 0.3, precision="fp64", seed: int = 0, model_data=None, passes: int = 3, stream=None):
+    """airpf_autotune: the fastest tiling for this configuration.  Returns
+    ({"launch", "ppt", "islands_per_cta"}, ms per pass)."""
+    import torch
+    lib = _binding.load()
+    mode = _MODES[mode] if isinstance(mode, str) else int(mode)
+    precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+    theta = theta.to(device="cuda", dtype=torch.float64).contiguous()
+    cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=y.numel() // dy, B=B, mode=mode, tau=tau,
+                      precision=precision, record=0, seed=seed, launch=0, reserved=0)
+    need = ctypes.c_size_t()
+    _binding.check(lib.airpf_workspace_bytes(ctypes.byref(cfg), ctypes.byref(need)))
+    ws = torch.empty(((need.value + 255) // 256) * 256 + 8 * B, dtype=torch.uint8, device="cuda")
+    md = None
+    if model_data is not None:
+        md_np = np.ascontiguousarray(np.asarray(model_data, dtype=np.float64))
+        md = md_np.ctypes.data_as(ctypes.c_void_p)
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    best = AirpfConfig()
+    ms = ctypes.c_float()
+    _binding.check(lib.airpf_autotune(ctypes.byref(cfg), _ptr(ws), ws.numel(), md, _ptr(theta), _ptr(y), passes,
+                                      ctypes.c_void_p(stream.cuda_stream), ctypes.byref(best), ctypes.byref(ms)))
+    return {"launch": int(best.launch), "ppt": int(best.ppt), "islands_per_cta": int(best.islands_per_cta)}, \
+        float(ms.value)
+
+
 def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: int = 1, dy: int = 1,
                mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, chain0: int = 0,
                iter: int = 0, model_data=None, launch="auto", stream=None):
@@ -183,7 +282,7 @@ def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: i
     return log_z
 
 
-__all__ = ["AIRPF", "AirpfError", "theta_dim", "run_static", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
+__all__ = ["AIRPF", "AirpfError", "Group", "autotune", "theta_dim", "run_static", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
            "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
            "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
-           "LAUNCH_PERSISTENT_GRID"]
+           "LAUNCH_PERSISTENT_GRID", "LAUNCH_STEPS_SPLIT"]

@@ -95,8 +95,11 @@ const char* check_config(const airpf_config* c)
     if (!(c->tau > 0.0 && c->tau <= 1.0)) return "tau must be in (0, 1]";
     if (c->precision != AIRPF_FP64 && c->precision != AIRPF_FP32_MIXED) return "unknown precision";
     if (c->record < 0 || c->record > 15) return "unknown record bits";
-    if (c->launch < 0 || c->launch > 3) return "unknown launch mode";
+    if (c->launch < 0 || c->launch > 4) return "unknown launch mode";
     if (c->reserved != 0) return "reserved must be 0";
+    if (c->ppt != 0 && c->ppt != 2 && c->ppt != 4) return "ppt must be 0, 2 or 4";
+    if (c->islands_per_cta < 0 || c->islands_per_cta > 4096 || (c->islands_per_cta & (c->islands_per_cta - 1)))
+        return "islands_per_cta must be 0 or a power of 2";
     return nullptr;
 }
 
@@ -156,6 +159,8 @@ airpf_status cuda_fail(airpf_ctx* ctx, cudaError_t e, const char* what)
     return AIRPF_ERR_CUDA;
 }
 
+bool is_steps(int launch) { return launch == AIRPF_LAUNCH_STEPS || launch == AIRPF_LAUNCH_STEPS_SPLIT; }
+
 template <typename T> T* at(airpf_ctx* ctx, size_t off) { return reinterpret_cast<T*>(ctx->ws + off); }
 
 airpf_status build_graph(airpf_ctx* ctx, const StepParams& p, cudaGraphExec_t* graph, bool* ready)
@@ -203,7 +208,7 @@ airpf_status build_graph(airpf_ctx* ctx, const StepParams& p, cudaGraphExec_t* g
 airpf_status enqueue_pass(airpf_ctx* ctx, bool pm = false)
 {
     StepParams& p = pm ? ctx->sp_pm : ctx->sp;
-    if (ctx->launch != AIRPF_LAUNCH_STEPS) {
+    if (!is_steps(ctx->launch)) {
         cudaError_t e = airpf::launch_step(p, 0, ctx->stream);      // prologue
         if (e == cudaSuccess)
             e = airpf::launch_persistent(p, ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID, ctx->stream);
@@ -231,6 +236,8 @@ airpf_status copy_async(airpf_ctx* ctx, void* dst, const void* src, size_t bytes
 }  // namespace
 
 namespace airpf {
+cudaStream_t ctx_stream(const airpf_ctx* ctx) { return ctx->stream; }
+
 void set_create_error(const char* fmt, ...)
 {
     va_list ap;
@@ -312,11 +319,10 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         p.cdf_scale = ldexpf(1.0f, p.cdf_bits);
     }
     {
-        // tuning overrides of the island-to-thread mapping (particles per thread, islands per CTA)
-        const char* e_ppt = getenv("AIRPF_PPT");
-        const char* e_g = getenv("AIRPF_ISLANDS_PER_CTA");
-        const int want_ppt = e_ppt ? atoi(e_ppt) : 0;
-        int want_g = e_g ? atoi(e_g) : 0;
+        // the island-to-thread mapping: requested particles per thread and
+        // islands per CTA, or the defaults
+        const int want_ppt = cfg->ppt;
+        int want_g = cfg->islands_per_cta;
         int mode = cfg->launch;
         if (mode == AIRPF_LAUNCH_AUTO || mode == AIRPF_LAUNCH_PERSISTENT_CTA) {
             airpf::choose_mapping(cfg->m, cfg->M, p.fp64, want_ppt, cfg->m, &p.tpi, &p.ppt, &p.G);
@@ -358,18 +364,14 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     // AUTO takes per-step launches for filters that span several CTAs: on GB300 a
     // kernel boundary (about 1 us in a graph) costs less than the device-scope
     // release/acquire pair of a grid barrier (about 3 us)
-    if (ctx->launch == AIRPF_LAUNCH_AUTO) ctx->launch = AIRPF_LAUNCH_STEPS;
-    {
-        // per-step launches overlap each kernel's start with the previous one
-        // (programmatic dependent launch); AIRPF_PDL=0 turns it off
-        const char* e_pdl = getenv("AIRPF_PDL");
-        p.pdl = (ctx->launch == AIRPF_LAUNCH_STEPS && !(e_pdl && atoi(e_pdl) == 0)) ? 1 : 0;
-        // fused steps: every CTA runs the previous step's cascade itself from the
-        // CTA records, so a step is one kernel; AIRPF_FUSED=0 selects the
-        // island-step + cascade kernel pair instead
-        const char* e_fused = getenv("AIRPF_FUSED");
-        p.fused = (ctx->launch == AIRPF_LAUNCH_STEPS && !(e_fused && atoi(e_fused) == 0)) ? 1 : 0;
-    }
+    // (and every CTA runs the cascade itself unless a filter spans more than
+    // 512 CTAs, where reading all CTA records in every CTA would cost more)
+    if (ctx->launch == AIRPF_LAUNCH_AUTO)
+        ctx->launch = p.P <= 512 ? AIRPF_LAUNCH_STEPS : AIRPF_LAUNCH_STEPS_SPLIT;
+    // per-step launches overlap each kernel's start with the previous one
+    // (programmatic dependent launch); fused steps have no cascade kernel
+    p.pdl = is_steps(ctx->launch) ? 1 : 0;
+    p.fused = ctx->launch == AIRPF_LAUNCH_STEPS ? 1 : 0;
     if (ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
         e = airpf::prepare_step(p);
         const bool fits = (e == cudaSuccess) && airpf::persistent_grid_fits(p);
@@ -431,8 +433,8 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         }
     }
     if (cfg->record & AIRPF_RECORD_TIMING) {
-        if (ctx->launch != AIRPF_LAUNCH_STEPS || cfg->T > (1 << 16)) {
-            set_err(nullptr, "AIRPF_RECORD_TIMING needs the STEPS launch and T <= 65536");
+        if (!is_steps(ctx->launch) || cfg->T > (1 << 16)) {
+            set_err(nullptr, "AIRPF_RECORD_TIMING needs a per-step launch and T <= 65536");
             cudaStreamDestroy(ctx->cap_stream);
             delete ctx;
             return AIRPF_ERR_UNSUPPORTED;

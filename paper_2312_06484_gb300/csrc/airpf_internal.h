@@ -116,6 +116,13 @@ cudaError_t launch_pmmh_accept(const PmmhParams& q, uint32_t iter, int j, int in
 // Message for airpf_last_error(NULL) (calls without a context), printf-style.
 void set_create_error(const char* fmt, ...);
 
+}  // namespace airpf
+
+struct airpf_ctx;
+namespace airpf {
+// The stream a context enqueues on (for the batch runner).
+cudaStream_t ctx_stream(const airpf_ctx* ctx);
+
 // Choose (tpi, ppt, G) for M particles per island and m islands per filter;
 // want_ppt / want_g of 0 take the defaults.
 void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, int* ppt, int* G);
