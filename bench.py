@@ -167,6 +167,50 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def batched_leg(gp, torch, ws: int, n_chains: int = 256, T: int = 500, passes: int = 2) -> dict:
+    """Batched serving of proposals: 256 SV chains with their own theta and uneven sizes
+    (m in {64, 256, 1024, 4096} x M in {32, 128, 512, 1024}, uniform per chain), T = 500,
+    FP32; one context per size class with an autotuned tiling, the classes run side by
+    side as a group.  A group pass is one PMMH likelihood evaluation for every chain."""
+    ms_, Ms_ = synth.batched_sizes(n_chains, seed=8)
+    thetas, redraws = synth.batched_sv_thetas(n_chains, seed=7)
+    y = torch.tensor(synth.sv_observations(T, seed=2), device="cuda")
+    keys = sorted(set(zip(ms_.tolist(), Ms_.tolist())))
+    members, th, c0, base = [], [], [], 0
+    t0 = time.perf_counter()
+    for (m, M) in keys:
+        idx = [i for i in range(n_chains) if (ms_[i], Ms_[i]) == (m, M)]
+        tht = torch.tensor(thetas[idx], device="cuda")
+        best, _ = gp.autotune(synth.MODEL_SV, tht, y[:16], m=m, M=M, B=len(idx), precision="fp32", seed=1, passes=2)
+        members.append(gp.AIRPF(synth.MODEL_SV, m=m, M=M, T=T, B=len(idx), mode="adaptive", tau=TAU,
+                                precision="fp32", seed=1, stream=torch.cuda.Stream(), **best))
+        th.append(tht)
+        c0.append(base)
+        base += len(idx)
+    tune_s = time.perf_counter() - t0
+    grp = gp.Group(members)
+    grp.run(th, y, c0, iter=0xFFFF0000)
+    grp.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for j in range(passes):
+        grp.run(th, y, c0, iter=j)
+    e1.record()
+    grp.sync()
+    torch.cuda.synchronize()
+    ms_pass = e0.elapsed_time(e1) / passes
+    ps = float((ms_ * Ms_).sum()) * T
+    out = {"workload": f"batched_sv_{n_chains}chains_T{T}", "particles": int((ms_ * Ms_).sum()),
+           "classes": len(keys), "ms_per_pass": ms_pass,
+           "particle_steps_per_s": ps * ws / (ms_pass / 1e3),
+           "chain_iters_per_s": n_chains * ws / (ms_pass / 1e3), "passes": passes,
+           "autotune_s": tune_s, "theta_redraws": int(redraws), "precision": "fp32"}
+    grp.close()
+    for mb in members:
+        mb.close()
+    return out
+
+
 def run_gpu(args) -> None:
     import torch
     import paper_2312_06484_gb300 as gp
@@ -306,6 +350,8 @@ def run_gpu(args) -> None:
             "proposal": "random walk, steps (0.05, 0.01, 0.02) on (mu, phi, sigma), box prior "
                         "U(-5,5) x U(-1,1) x U(0,2)"}
 
+    batched = None if args.no_batched else batched_leg(gp, torch, ws)
+
     peaks, peak_src = _peaks()
     ms_step = tot_ms / args.steps
     step_us = 1e3 * ms_step / T_OBS           # one time step: island-step kernel + cascade kernel
@@ -338,6 +384,7 @@ def run_gpu(args) -> None:
                                              "holds the node-to-node latency, so compare the share"},
                      "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x sm_max_mhz ({peak_src})"},
         "fp64_path": fp64,
+        "batched": batched,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
@@ -357,6 +404,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-chains leg")
     ap.add_argument("--launch", default="auto", choices=["auto", "steps", "split", "grid"])
     ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0: automatic)")
     ap.add_argument("--islands-per-cta", type=int, default=0, help="islands per CTA (0: automatic)")

@@ -113,7 +113,7 @@ typedef enum {
 typedef struct {
     int32_t model;          /* airpf_model */
     int32_t dx, dy;         /* state / observation dimension (1 unless LGSSM; dx <= 8, dy <= 8) */
-    int32_t m;              /* islands per filter: a power of 2, 1..4096 */
+    int32_t m;              /* islands per filter: a power of 2, 1..65536 */
     int32_t M;              /* particles per island: 1..1024 */
     int32_t T;              /* observations y_1..y_T, T >= 1 */
     int32_t B;              /* filters run together (a batch of independent runs), >= 1 */

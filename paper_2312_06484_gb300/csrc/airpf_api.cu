@@ -34,7 +34,7 @@ int ilog2_exact(int m)
 
 // Byte offsets of every buffer inside the workspace.
 struct WsLayout {
-    size_t run, theta, mdata, y, X[2], pe[2], pt[2], pq[2], csum, cup, nsrc, ires[2], logz, trace, enf,
+    size_t run, theta, mdata, y, X[2], pe[2], pt[2], pq[2], csum, cup, nsrc, utg, ires[2], logz, trace, enf,
         sstar, anc, active, mpar, drift, bar;
     size_t pm_prop, pm_logz_prop, pm_stats, total;
 };
@@ -85,7 +85,7 @@ const char* check_config(const airpf_config* c)
     } else if (c->dx != 1 || c->dy != 1) {
         return "scalar models need dx = dy = 1";
     }
-    if (c->m < 1 || c->m > 4096 || ilog2_exact(c->m) < 0) return "m must be a power of 2 in [1, 4096]";
+    if (c->m < 1 || c->m > 65536 || ilog2_exact(c->m) < 0) return "m must be a power of 2 in [1, 65536]";
     if (c->M < 1 || c->M > 1024) return "M must be in [1, 1024]";
     if (c->T < 1 || c->T > (1 << 24)) return "T must be in [1, 2^24]";
     if (c->B < 1 || c->B > (1 << 24)) return "B must be in [1, 2^24]";
@@ -127,6 +127,7 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.csum = take(sizeof(int) * 4 * B);
     L.cup = take(sizeof(unsigned long long) * B * c->m);
     L.nsrc = take(sizeof(int) * B * c->m);
+    L.utg = take(sizeof(double) * B * 2 * c->m);
     for (int i = 0; i < 2; ++i) L.ires[i] = lin ? take(sizeof(int) * B * N) : 0;
     L.logz = take(sizeof(double) * B);
     L.trace = tr ? take(sizeof(double) * B * T) : 0;
@@ -372,6 +373,14 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     // (programmatic dependent launch); fused steps have no cascade kernel
     p.pdl = is_steps(ctx->launch) ? 1 : 0;
     p.fused = ctx->launch == AIRPF_LAUNCH_STEPS ? 1 : 0;
+    p.split = ctx->launch == AIRPF_LAUNCH_STEPS_SPLIT ? 1 : 0;
+    if (airpf::step_smem_bytes(p) > 227 * 1024) {
+        set_err(nullptr, "the step kernel would need %zu bytes of shared memory (m/G = %d CTA records per filter); "
+                "use AIRPF_LAUNCH_STEPS_SPLIT or more islands per CTA", airpf::step_smem_bytes(p), p.P);
+        cudaStreamDestroy(ctx->cap_stream);
+        delete ctx;
+        return AIRPF_ERR_UNSUPPORTED;
+    }
     if (ctx->launch == AIRPF_LAUNCH_PERSISTENT_GRID) {
         e = airpf::prepare_step(p);
         const bool fits = (e == cudaSuccess) && airpf::persistent_grid_fits(p);
@@ -413,6 +422,7 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.csum = at<int>(ctx, L.csum);
     p.cup = at<void>(ctx, L.cup);
     p.nsrc = at<int>(ctx, L.nsrc);
+    p.utg = at<void>(ctx, L.utg);
     p.logz = at<double>(ctx, L.logz);
     p.trace = (cfg->record & AIRPF_RECORD_TRACE) ? at<double>(ctx, L.trace) : nullptr;
     p.enf = (cfg->record & AIRPF_RECORD_ENF) ? at<double>(ctx, L.enf) : nullptr;

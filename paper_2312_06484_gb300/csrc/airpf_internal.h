@@ -45,6 +45,8 @@ struct StepParams {
     int inject_stall;             // test hook (grid-persistent launch only)
     int pdl;                      // per-step launches: programmatic dependent launch
     int fused;                    // per-step launches: each CTA runs the previous step's cascade itself
+    int split;                    // per-step launches with a cascade kernel that leaves the tree in utg
+    void* utg;                    // [B][2P] upper tree of the last cascade (split steps)
     void* X[2];                   // particle stores, ping-pong by t & 1
     int P, g;                     // CTA records per filter (m / G) and log2 G
     int* pe[2];                   // CTA records, ping-pong by t & 1

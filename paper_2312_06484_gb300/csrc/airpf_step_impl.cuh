@@ -53,7 +53,8 @@
 // float; the CDF is an exact 32-bit fixed-point prefix sum of the weights
 // quantised to 2^-(31 - ceil(log2 M)) of the island maximum; island weights are
 // 64-bit integer mantissas with an exponent, multiplied to 64 bits, and block
-// sums are 64-bit fixed point (50 fractional bits below the largest weight);
+// sums are 64-bit fixed point (63 - log2 m fractional bits below the largest
+// weight, so a sum over all m islands stays below 2^63);
 // the ENF test uses float; the island choice is decided exactly in 128-bit
 // integers; log Z is formed in double.  The common factor 1/M of the island
 // weights is left out of the FP32-mixed weights and restored in log Z.  The
@@ -101,7 +102,7 @@ struct Layout {
 // partial sums [16 warps][kQw], per-level sums [kMaxStages], a few integers
 __host__ __device__ inline size_t cascade_slots(const StepParams& p)
 {
-    return 2 * (size_t)p.P + 2 * (size_t)p.G + 16 * kQw + kMaxStages + 8 + 3 * 16;
+    return (p.split ? 0 : 2 * (size_t)p.P) + 2 * (size_t)p.G + 16 * kQw + kMaxStages + 8 + 3 * 16;
 }
 
 __host__ __device__ inline Layout make_layout(const StepParams& p)
@@ -260,9 +261,10 @@ template <bool FX> struct Casc;
 template <> struct Casc<false> {
     using V = double;
     using Qt = double;
-    static constexpr int kFrac = 0;           // leaf = W 2^-e_ref
+    // leaf = W 2^-e_ref
+    __device__ static int frac(const StepParams&) { return 0; }
     __device__ static bool positive(u64 b) { return (long long)b > 0; }
-    __device__ static V leaf(u64 b, int de) { return ldexp(__longlong_as_double((long long)b), de); }
+    __device__ static V leaf(u64 b, int de, int) { return ldexp(__longlong_as_double((long long)b), de); }
     __device__ static V rescale(V v, int sh) { return ldexp(v, -sh); }
     __device__ static Qt qscale(Qt q, int sh2) { return ldexp(q, -sh2); }
     __device__ static Qt qv(V v) { return v; }
@@ -274,12 +276,14 @@ template <> struct Casc<false> {
 template <> struct Casc<true> {
     using V = u64;
     using Qt = float;
-    // stored weight mantissa * 2^(e-64); leaf = mantissa >> (e_ref - e + 14) = W 2^(50 - e_ref)
-    static constexpr int kFrac = 50;
+    // stored weight mantissa * 2^(e-64); leaf = mantissa >> (e_ref - e + 64 - frac)
+    // = W 2^(frac - e_ref) < 2^frac.  With frac = 63 - log2 m a sum over all m
+    // islands stays below 2^63.
+    __device__ static int frac(const StepParams& p) { return 63 - p.S; }
     __device__ static bool positive(u64 b) { return b != 0ull; }
-    __device__ static V leaf(u64 b, int de)
+    __device__ static V leaf(u64 b, int de, int fr)
     {
-        const int sh = 14 - de;
+        const int sh = 64 - fr - de;
         return sh < 64 ? (b >> sh) : 0ull;
     }
     __device__ static V rescale(V v, int sh) { return sh < 64 ? (v >> sh) : 0ull; }
@@ -322,10 +326,10 @@ __device__ void cascade_records(const StepParams& p, int c, int tp, int ss, type
     const int m = p.m, S = p.S;
     const auto tq = C::qv(tot);
     if (p.trace || tp == p.T) {
-        // log Z^N_tp = log(m^-1 sum_k W^k), sum_k W^k = Tot 2^(emax - kFrac);
+        // log Z^N_tp = log(m^-1 sum_k W^k), sum_k W^k = Tot 2^(emax - frac);
         // the FP32-mixed weights leave out M^-tp
         double lz = pos_v(tot)
-            ? log(C::to_d(tot)) - log((double)m) + (double)(emax - C::kFrac) * 0.6931471805599453
+            ? log(C::to_d(tot)) - log((double)m) + (double)(emax - C::frac(p)) * 0.6931471805599453
             : -INFINITY;
         if (FX) lz -= (double)tp * log((double)p.M);
         if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
@@ -356,6 +360,63 @@ struct CascadeOwn {
     int* src;          // [G] inherited blocks
 };
 
+// A CTA's own islands after the cascade of step tp: the weight W^k_{tp+1,0}
+// (block mean at level s*-1: from the CTA's record below the CTA level, from
+// the upper tree ut above it) and the inherited block src(k), walked from
+// stage s*-1 down (stage levels below g from the records of step tp).
+template <bool FX>
+__device__ void own_outputs(const StepParams& p, int c, int tp, const Stream& st, const typename Casc<FX>::V* ut,
+                            bool ut_global, int ss, int emax, const CascadeOwn& own)
+{
+    using C = Casc<FX>;
+    using V = typename C::V;
+    const int P = p.P, G = p.G, g = p.g;
+    const int* pe = p.pe[tp & 1] + (size_t)c * P;
+    const V* pt = reinterpret_cast<const V*>(p.pt[tp & 1]) + (size_t)c * P * 2 * G;
+    const int lvl = ss - 1;
+    const bool dead = (emax == INT_MIN);
+    const int jo = own.k0 >> g;
+    auto utv = [&](int i) { return ut_global ? __ldcg(&ut[i]) : ut[i]; };
+    for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
+        const int k = own.k0 + gi;
+        XW w{0ull, 0};
+        if (!dead) {
+            const int ej = __ldcg(&pe[jo]);
+            if (lvl == 0 && g == 0) {          // the island is the CTA: its rescaled record top
+                if (ej != INT_MIN)
+                    w = C::weight(C::rescale(__ldcg(&pt[(size_t)jo * 2 * G]), emax - ej), emax - C::frac(p));
+            } else if (lvl < g) {
+                if (ej != INT_MIN)
+                    w = C::weight(__ldcg(&pt[(size_t)jo * 2 * G + tree_off(G, lvl) + (gi >> lvl)]),
+                                  ej - C::frac(p) - lvl);
+            } else {
+                w = C::weight(utv(tree_off(P, lvl - g) + (k >> lvl)), emax - C::frac(p) - lvl);
+            }
+        }
+        own.w[gi] = w.bits;
+        own.we[gi] = w.e;
+        int j = k;
+        for (int s = lvl; s >= 1; --s) {
+            const int l = s - 1, b = 1 << l, pi = j >> l;
+            V lo, hi;
+            if (l >= g) {
+                lo = utv(tree_off(P, l - g) + (pi & ~1));
+                hi = utv(tree_off(P, l - g) + (pi | 1));
+            } else {
+                // both blocks lie in the record of CTA jc, in its own scale
+                const int jc = j >> g;
+                const int li = pi - jc * (G >> l);
+                const int ol = tree_off(G, l);
+                lo = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li & ~1)]);
+                hi = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li | 1)]);
+            }
+            const uint32_t wu = st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x;
+            j = C::pick_lo(lo, hi, wu) ? (j & ~b) : (j | b);
+        }
+        own.src[gi] = j;
+    }
+}
+
 template <bool FX>
 __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st, double* raw,
                             const CascadeOwn* own = nullptr, bool records = true)
@@ -368,11 +429,14 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     const int* pe = p.pe[tp & 1] + (size_t)c * P;
     const V* pt = reinterpret_cast<const V*>(p.pt[tp & 1]) + (size_t)c * P * 2 * G;
     const Qt* pq = reinterpret_cast<const Qt*>(p.pq[tp & 1]) + (size_t)c * P * 8;
-    V* ut = reinterpret_cast<V*>(raw);                            // upper tree [2P]
-    Qt* Qw = reinterpret_cast<Qt*>(raw + 2 * P + 2 * G);          // [nw][kQw]
-    Qt* Q = reinterpret_cast<Qt*>(raw + 2 * P + 2 * G + 16 * kQw);   // [kMaxStages]
-    int* iscal = reinterpret_cast<int*>(raw + 2 * P + 2 * G + 16 * kQw + kMaxStages);
-    double* wpart = raw + 2 * P + 2 * G + 16 * kQw + kMaxStages + 8;     // [3][16] per-warp partials
+    // the upper tree [2P]: in shared memory, or (split steps) in global memory,
+    // where the next step's island kernels read it
+    const int uo = p.split ? 0 : 2 * P;
+    V* ut = p.split ? reinterpret_cast<V*>(p.utg) + (size_t)c * 2 * P : reinterpret_cast<V*>(raw);
+    Qt* Qw = reinterpret_cast<Qt*>(raw + uo + 2 * G);             // [nw][kQw]
+    Qt* Q = reinterpret_cast<Qt*>(raw + uo + 2 * G + 16 * kQw);   // [kMaxStages]
+    int* iscal = reinterpret_cast<int*>(raw + uo + 2 * G + 16 * kQw + kMaxStages);
+    double* wpart = raw + uo + 2 * G + 16 * kQw + kMaxStages + 8;     // [3][16] per-warp partials
     int* w_emax = reinterpret_cast<int*>(wpart);
     V* w_tot = reinterpret_cast<V*>(wpart + 16);
     Qt* w_q0 = reinterpret_cast<Qt*>(wpart + 32);
@@ -472,25 +536,14 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
                 cascade_records<FX>(p, c, tp, 1, tot, emax, Q);
             }
             if (own != nullptr) {
-                const int jo = own->k0 >> g;
-                const int ej = __ldcg(&pe[jo]);
-                for (int gi = tid; gi < G; gi += nthr) {
-                    XW w{0ull, 0};
-                    if (!dead && ej != INT_MIN) {
-                        const V leaf = __ldcg(&pt[(size_t)jo * 2 * G + gi]);
-                        w = g >= 1 ? C::weight(leaf, ej - C::kFrac) : C::weight(C::rescale(leaf, emax - ej), emax - C::kFrac);
-                    }
-                    own->w[gi] = w.bits;
-                    own->we[gi] = w.e;
-                    own->src[gi] = own->k0 + gi;
-                }
+                own_outputs<FX>(p, c, tp, st, ut, false, 1, emax, *own);
                 return;
             }
             if (tid == 0) {
                 p.csum[(size_t)c * 4 + 0] = 1;
                 p.csum[(size_t)c * 4 + 1] = emax;
             }
-            if (g == 0) {     // level 0 lies above the CTAs: the rescaled record tops
+            if (g == 0 && !p.split) {     // level 0 lies above the CTAs: the rescaled record tops
                 for (int j = tid; j < P; j += nthr) {
                     const int e = __ldcg(&pe[j]);
                     const V top = __ldcg(&pt[(size_t)j * 2 * G]);
@@ -654,48 +707,14 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     const int ss = iscal[1];
     const int lvl = ss - 1;
     if (own != nullptr) {
-        // this CTA's islands k0 .. k0+G-1: block mean at level s*-1 and the walk
-        const int jo = own->k0 >> g;
-        for (int gi = tid; gi < G; gi += nthr) {
-            const int k = own->k0 + gi;
-            XW w{0ull, 0};
-            if (!dead) {
-                if (lvl < g) {
-                    const int ej = __ldcg(&pe[jo]);
-                    if (ej != INT_MIN)
-                        w = C::weight(__ldcg(&pt[(size_t)jo * 2 * G + tree_off(G, lvl) + (gi >> lvl)]),
-                                      ej - C::kFrac - lvl);
-                } else {
-                    w = C::weight(ut[tree_off(P, lvl - g) + (k >> lvl)], emax - C::kFrac - lvl);
-                }
-            }
-            own->w[gi] = w.bits;
-            own->we[gi] = w.e;
-            int j = k;
-            for (int s = lvl; s >= 1; --s) {
-                const int l = s - 1, b = 1 << l, pi = j >> l;
-                V lo, hi;
-                if (l >= g) {
-                    lo = ut[tree_off(P, l - g) + (pi & ~1)];
-                    hi = ut[tree_off(P, l - g) + (pi | 1)];
-                } else {
-                    const int jc = j >> g;
-                    const int li = pi - jc * (G >> l);
-                    const int ol = tree_off(G, l);
-                    lo = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li & ~1)]);
-                    hi = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li | 1)]);
-                }
-                const uint32_t wu = st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x;
-                j = C::pick_lo(lo, hi, wu) ? (j & ~b) : (j | b);
-            }
-            own->src[gi] = j;
-        }
+        own_outputs<FX>(p, c, tp, st, ut, false, ss, emax, *own);
         return;
     }
     if (tid == 0) {
         p.csum[(size_t)c * 4 + 0] = ss;
         p.csum[(size_t)c * 4 + 1] = emax;
     }
+    if (p.split) return;          // the next step's CTAs read the tree in global memory
     if (lvl >= g) {
         const int n = P >> (lvl - g);
         for (int b = tid; b < n; b += nthr)
@@ -739,7 +758,7 @@ __device__ void publish_record(const StepParams& p, int c, int t, int jo, const 
     const int e = has ? nw_e[lane] : INT_MIN;
     const bool ok = has && C::positive(b);
     const int ej = warp_max(ok ? e : INT_MIN);
-    V v = (ok && ej != INT_MIN) ? C::leaf(b, e - ej) : (V)0;
+    V v = (ok && ej != INT_MIN) ? C::leaf(b, e - ej, C::frac(p)) : (V)0;
     V* rec = reinterpret_cast<V*>(p.pt[t & 1]) + ((size_t)c * p.P + jo) * 2 * G;
     Qt* pq = reinterpret_cast<Qt*>(p.pq[t & 1]) + ((size_t)c * p.P + jo) * 8;
     Qt q[4] = {(Qt)0, (Qt)0, (Qt)0, (Qt)0};
@@ -896,6 +915,15 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         // the filter (the first CTA also writes log Z and the run's records)
         const CascadeOwn own{k0, own_w, own_we, own_src};
         cascade_all<FX>(p, c, t - 1, st, tree, &own, designated);
+    } else if (p.split) {
+        // the cascade kernel of step t-1 left s*, the largest exponent and the
+        // upper tree; this CTA derives its islands' weights and walks
+        int* csum_sh = reinterpret_cast<int*>(scal) + 4;
+        if (tid < 2) csum_sh[tid] = __ldcg(&p.csum[(size_t)c * 4 + tid]);
+        __syncthreads();
+        const CascadeOwn own{k0, own_w, own_we, own_src};
+        own_outputs<FX>(p, c, t - 1, st, reinterpret_cast<const typename Casc<FX>::V*>(p.utg) + (size_t)c * 2 * p.P,
+                        true, csum_sh[0], csum_sh[1], own);
     } else {
         // the cascade's summary of step t-1, this CTA's record of step t-1 and
         // (used only if some stage interacted) the inherited blocks
@@ -915,11 +943,11 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
                 if (lvl < p.g) {
                     if (ej != INT_MIN)
                         w = Casc<FX>::weight(reinterpret_cast<const typename Casc<FX>::V*>(rec_sh)[tree_off(p.G, lvl) + (gi >> lvl)],
-                                             ej - Casc<FX>::kFrac - lvl);
+                                             ej - Casc<FX>::frac(p) - lvl);
                 } else {
                     const typename Casc<FX>::V b =
                         __ldcg(&reinterpret_cast<const typename Casc<FX>::V*>(p.cup)[(size_t)c * p.P + ((k0 + gi) >> lvl)]);
-                    w = Casc<FX>::weight(b, emax - Casc<FX>::kFrac - lvl);
+                    w = Casc<FX>::weight(b, emax - Casc<FX>::frac(p) - lvl);
                 }
             }
             own_w[gi] = w.bits;

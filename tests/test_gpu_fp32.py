@@ -36,3 +36,21 @@ def test_fp32_matches_oracle_draw_by_draw(gpu_lib, model, theta, y, m, M, mode, 
         assert np.array_equal(g["sstar"][b], o["sstar"]), f"filter {b}"
         assert abs(g["log_z"][b] - o["log_z"]) <= 1e-5 * abs(o["log_z"]) + 1e-4, (b, g["log_z"][b], o["log_z"])
     assert clean >= 0.75 * B, f"only {clean} tie-free filters"
+
+
+@pytest.mark.parametrize("M", [256, 512])
+def test_fp32_matches_fp64_at_m65536(M):
+    """With m = 65536 islands the FP32-mixed island-weight sums span 2^16 weights; the fixed
+    point keeps 63 - log2 m fractional bits so the sum cannot wrap.  On the same random
+    streams the FP32-mixed log Z stays within a fraction of a nat of the FP64 one."""
+    import torch
+    import paper_2312_06484_gb300 as gp
+    T = 20
+    y = torch.tensor(synth.ngm_observations(T, seed=5), device="cuda")
+    th = torch.tensor(synth.NGM_THETA[None, :], device="cuda")
+    lz = {}
+    for prec in ("fp32", "fp64"):
+        f = gp.AIRPF(synth.MODEL_NGM, m=65536, M=M, T=T, B=1, mode="adaptive", tau=0.3, precision=prec, seed=1)
+        lz[prec] = float(f.run(th, y, iter=1)["log_z"].item())
+        f.close()
+    assert np.isfinite(lz["fp64"]) and abs(lz["fp32"] - lz["fp64"]) < 0.5, lz

@@ -132,3 +132,30 @@ def test_grid_barrier_timeout_is_reported_and_context_survives(gpu_lib):
     if o["tie"][0] == 0:
         assert abs(float(out["log_z"][0]) - o["log_z"]) <= 1e-10 * abs(o["log_z"])
     f.close()
+
+
+@pytest.mark.parametrize("mode", ["adaptive", "always"])
+def test_split_steps_match_oracle(gpu_lib, mode):
+    """Split steps (island-step kernel + one-CTA cascade kernel that leaves the block-sum tree
+    in global memory; each CTA walks its own islands) against the oracle."""
+    y = synth.ngm_observations(40, seed=5)
+    m, M = 64, 32
+    g = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, m=m, M=M, B=2, mode=mode, tau=0.5, seed=4, chain0=1,
+                iter=3, launch="split")
+    assert g["launch_mode"] == 4
+    for b in range(2):
+        o = oracle.airpf(synth.MODEL_NGM, synth.NGM_THETA, y, m=m, M=M, mode=MODES[mode], tau=0.5, seed=4,
+                         chain=1 + b, iter=3)
+        compare_filter(g, b, o, m=m, what=f"split {mode} b={b}")
+
+
+def test_ngm_m65536_full_size_fp64():
+    """The large nonlinear-growth workload at full size (m = 65536 islands x M = 256,
+    N = 16.8M) on a short series, FP64, against the oracle: ancestors, s*, ENF and log Z."""
+    y = synth.ngm_observations(3, seed=5)
+    m, M = 65536, 256
+    g = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, m=m, M=M, B=1, mode="adaptive", tau=0.3, seed=1)
+    assert g["launch_mode"] == 4            # AUTO splits the step when a filter spans > 512 CTAs
+    o = oracle.airpf(synth.MODEL_NGM, synth.NGM_THETA, y, m=m, M=M, mode=oracle.MODE_ADAPTIVE, tau=0.3, seed=1)
+    upto = compare_filter(g, 0, o, m=m, what="NGM m=65536")
+    assert upto >= 1
