@@ -56,6 +56,14 @@ def lib():
         _lib.oracle_airpf_batch.argtypes = [ctypes.c_int] * 6 + [ctypes.c_int, ctypes.c_double,
                                             ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.c_int, _D, _D, _D, _D]
+        _lib.oracle_model_logf.argtypes = [ctypes.c_int] * 3 + [_D, _D, ctypes.c_uint32, _D, _D]
+        _lib.oracle_model_logf.restype = ctypes.c_double
+        _lib.oracle_model_logmu.argtypes = [ctypes.c_int] * 3 + [_D, _D, _D]
+        _lib.oracle_model_logmu.restype = ctypes.c_double
+        _lib.oracle_logz_fixed.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint64, ctypes.c_uint32,
+                                           ctypes.c_uint32, _D, _D, _D, _I, _I, _D]
+        _lib.oracle_fisher_score.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint64, ctypes.c_uint32,
+                                             ctypes.c_uint32, _D, _D, _D, _I, _I, ctypes.c_int, _D]
     return _lib
 
 
@@ -187,3 +195,61 @@ def model_step(model, theta, xp, *, unit, t, dx=1, dy=1, seed=0, chain=0, iter=0
 
 def model_valid(model, theta, dx=1) -> bool:
     return bool(lib().oracle_model_valid(model, dx, _dp(_f64(theta))))
+
+
+def model_logf(model, theta, xp, x, *, t=1, dx=1, dy=1, model_data=None) -> float:
+    """log f_t(x | xp), the transition density."""
+    return lib().oracle_model_logf(model, dx, dy, _dp(_f64(theta)), _dp(_model_data(model_data)), t,
+                                   _dp(_f64(xp)), _dp(_f64(x)))
+
+
+def model_logmu(model, theta, x, *, dx=1, dy=1, model_data=None) -> float:
+    """log pi_0(x), the prior density of x_0."""
+    return lib().oracle_model_logmu(model, dx, dy, _dp(_f64(theta)), _dp(_model_data(model_data)),
+                                    _dp(_f64(x)))
+
+
+def logz_fixed(model, theta, y, anc, sstar, *, m, M, dx=1, dy=1, seed=0, chain=0, iter=0,
+               model_data=None) -> float:
+    """log Z of a run with its random numbers, lineage anc [T, N] and s* [T] held fixed,
+    as a function of theta (FP64)."""
+    y = _f64(y)
+    T = len(y) // dy
+    anc = np.ascontiguousarray(np.asarray(anc, dtype=np.int32).reshape(T, m * M))
+    sstar = np.ascontiguousarray(np.asarray(sstar, dtype=np.int32).reshape(T))
+    out = np.zeros(1)
+    rc = lib().oracle_logz_fixed(model, dx, dy, m, M, T, seed, chain, iter, _dp(_f64(theta)),
+                                 _dp(_model_data(model_data)), _dp(y), _ip(anc), _ip(sstar), _dp(out))
+    if rc:
+        raise ValueError("oracle_logz_fixed rejected its arguments")
+    return float(out[0])
+
+
+def logz_fixed_gradient(model, theta, y, anc, sstar, *, h=1e-5, **kw) -> np.ndarray:
+    """Central differences of logz_fixed in every component of theta (step h max(1, |theta_d|))."""
+    th = _f64(theta).copy()
+    g = np.zeros(len(th))
+    for d in range(len(th)):
+        hd = h * max(1.0, abs(th[d]))
+        tp, tm = th.copy(), th.copy()
+        tp[d] += hd
+        tm[d] -= hd
+        g[d] = (logz_fixed(model, tp, y, anc, sstar, **kw) - logz_fixed(model, tm, y, anc, sstar, **kw)) / (2 * hd)
+    return g
+
+
+def fisher_score(model, theta, y, anc, sstar, *, m, M, dx=1, dy=1, seed=0, chain=0, iter=0,
+                 model_data=None) -> np.ndarray:
+    """Fisher-identity score along the lineages of a run (FP64)."""
+    y = _f64(y)
+    T = len(y) // dy
+    th = _f64(theta)
+    anc = np.ascontiguousarray(np.asarray(anc, dtype=np.int32).reshape(T, m * M))
+    sstar = np.ascontiguousarray(np.asarray(sstar, dtype=np.int32).reshape(T))
+    out = np.zeros(len(th))
+    rc = lib().oracle_fisher_score(model, dx, dy, m, M, T, seed, chain, iter, _dp(th),
+                                   _dp(_model_data(model_data)), _dp(y), _ip(anc), _ip(sstar), len(th),
+                                   _dp(out))
+    if rc:
+        raise ValueError("oracle_fisher_score rejected its arguments")
+    return out

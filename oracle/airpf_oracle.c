@@ -581,3 +581,211 @@ int oracle_airpf_batch(int model, int dx, int dy, int m, int M, int T, int mode,
     }
     return bad;
 }
+
+/* ----------------------------------------------------------------------- */
+/* Gradients of log Z (test references for the adjoint and the Fisher score)*/
+/* ----------------------------------------------------------------------- */
+
+/* log f_t(x | xp): density of the transition K_t (Section 1.2, eq. (1)). */
+static double log_f(const model_t* md, uint32_t t, const double* xp, const double* x)
+{
+    const double* th = md->th;
+    const double l2pi = log(2.0 * M_PI);
+    switch (md->model) {
+    case MODEL_AR1: {
+        double e = (x[0] - th[0] * xp[0]) / th[1];
+        return -0.5 * l2pi - log(th[1]) - 0.5 * e * e;
+    }
+    case MODEL_SV: {
+        double e = (x[0] - th[0] - th[1] * (xp[0] - th[0])) / th[2];
+        return -0.5 * l2pi - log(th[2]) - 0.5 * e * e;
+    }
+    case MODEL_NGM: {
+        double v = xp[0];
+        double mu = 0.5 * v + 25.0 * v / (1.0 + v * v) + 8.0 * cos(1.2 * (double)t);
+        double e = x[0] - mu;
+        return -0.5 * log(2.0 * M_PI * th[0]) - e * e / (2.0 * th[0]);
+    }
+    case MODEL_LGSSM: {
+        int dx = md->dx;
+        const double* A = md->md;
+        double q = exp(th[dx]), ss = 0.0;
+        for (int r = 0; r < dx; ++r) {
+            double mu = 0.0;
+            for (int c = 0; c < dx; ++c) mu += ((r == c) ? th[r] : A[r * dx + c]) * xp[c];
+            ss += (x[r] - mu) * (x[r] - mu);
+        }
+        return -0.5 * dx * log(2.0 * M_PI * q) - ss / (2.0 * q);
+    }
+    }
+    return -INFINITY;
+}
+
+/* log of the prior density pi_0(x) of x_0 */
+static double log_mu(const model_t* md, const double* x)
+{
+    const double* th = md->th;
+    const double l2pi = log(2.0 * M_PI);
+    switch (md->model) {
+    case MODEL_AR1: {
+        double e = x[0] / th[3];
+        return -0.5 * l2pi - log(th[3]) - 0.5 * e * e;
+    }
+    case MODEL_SV: {
+        double sd = th[2] / sqrt(1.0 - th[1] * th[1]), e = (x[0] - th[0]) / sd;
+        return -0.5 * l2pi - log(sd) - 0.5 * e * e;
+    }
+    case MODEL_NGM:
+        return -0.5 * log(2.0 * M_PI * th[2]) - x[0] * x[0] / (2.0 * th[2]);
+    case MODEL_LGSSM: {
+        double ss = 0.0;
+        for (int d = 0; d < md->dx; ++d) ss += x[d] * x[d];
+        return -0.5 * md->dx * l2pi - 0.5 * ss;
+    }
+    }
+    return -INFINITY;
+}
+
+double oracle_model_logf(int model, int dx, int dy, const double* th, const double* mdat, uint32_t t,
+                         const double* xp, const double* x)
+{
+    model_t md = { model, dx, dy, th, mdat };
+    return log_f(&md, t, xp, x);
+}
+
+double oracle_model_logmu(int model, int dx, int dy, const double* th, const double* mdat, const double* x)
+{
+    model_t md = { model, dx, dy, th, mdat };
+    return log_mu(&md, x);
+}
+
+/* The particles x_t (t = 0..T, time-t particles before resampling; x_0 the
+ * prior draws) and the island log-weights log W^k_{t,1} of a run whose
+ * lineage (anc, as oracle_airpf records it) and first quiet stages s*_t are
+ * given: the random numbers are the run's, the ancestors and island choices
+ * are held fixed, and the weights follow Algorithm 1 with the interacting
+ * stages 1..s*_t-1 (after them every island weight is the mean of its block
+ * of 2^(s*_t-1) islands).  xs [(T+1)*N*dx] and lw1 [T*m] may be NULL. */
+static void fixed_lineage_pass(const model_t* md, const stream_id* st, int m, int M, int T, const double* y,
+                               const int32_t* anc, const int32_t* sstar, double* xs, double* lw1,
+                               double* logz, double* l_out)
+{
+    const int N = m * M, dx = md->dx;
+    double* held = malloc(sizeof(double) * N * dx);
+    double* x = malloc(sizeof(double) * N * dx);
+    double* l = malloc(sizeof(double) * N);
+    double* lw = malloc(sizeof(double) * m);
+    double* lwn = malloc(sizeof(double) * m);
+    for (int g = 0; g < N; ++g) prior_sample(md, st, (uint32_t)g, held + (size_t)g * dx);
+    if (xs) memcpy(xs, held, sizeof(double) * N * dx);
+    for (int k = 0; k < m; ++k) lw[k] = 0.0;
+    for (int t = 1; t <= T; ++t) {
+        const double* yt = y + (size_t)(t - 1) * md->dy;
+        for (int g = 0; g < N; ++g) {
+            transition(md, st, (uint32_t)g, (uint32_t)t, held + (size_t)g * dx, x + (size_t)g * dx);
+            l[g] = log_g(md, yt, x + (size_t)g * dx);
+        }
+        if (l_out) memcpy(l_out + (size_t)(t - 1) * N, l, sizeof(double) * N);
+        if (xs) memcpy(xs + (size_t)t * N * dx, x, sizeof(double) * N * dx);
+        for (int k = 0; k < m; ++k) lw[k] += log_sum_exp(l + (size_t)k * M, M) - log((double)M);
+        if (lw1) memcpy(lw1 + (size_t)(t - 1) * m, lw, sizeof(double) * m);
+        /* block means at level s*_t - 1 */
+        int lvl = sstar[t - 1] - 1, bs = 1 << lvl;
+        for (int b = 0; b < m; b += bs) {
+            double v = log_sum_exp(lw + b, bs) - lvl * log(2.0);
+            for (int k = b; k < b + bs; ++k) lwn[k] = v;
+        }
+        memcpy(lw, lwn, sizeof(double) * m);
+        /* held particles after step t */
+        for (int g = 0; g < N; ++g)
+            memcpy(held + (size_t)g * dx, x + (size_t)anc[(size_t)(t - 1) * N + g] * dx, sizeof(double) * dx);
+    }
+    *logz = log_sum_exp(lw, m) - log((double)m);
+    free(held); free(x); free(l); free(lw); free(lwn);
+}
+
+/* log Z^N_T as a function of theta with the run's random numbers, ancestors and
+ * s* held fixed: the quantity whose gradient the adjoint pass computes. */
+int oracle_logz_fixed(int model, int dx, int dy, int m, int M, int T, uint64_t seed, uint32_t chain,
+                      uint32_t iter, const double* theta, const double* mdat, const double* y,
+                      const int32_t* anc, const int32_t* sstar, double* logz)
+{
+    if (m < 1 || (m & (m - 1)) || M < 1 || T < 1 || dx < 1 || dx > 64 || dy < 1) return 1;
+    model_t md = { model, dx, dy, theta, mdat };
+    stream_id st = { seed, chain, iter };
+    fixed_lineage_pass(&md, &st, m, M, T, y, anc, sstar, NULL, NULL, logz, NULL);
+    return 0;
+}
+
+/* Fisher-identity score along the lineages (Section 1.2 with the genealogy of
+ * the particle system as the smoother): every time-t particle q carries the
+ * final weight delta_t(q) of its descendants (delta_T = island share of the
+ * final weight times the particle's share within its island; delta_{t-1} of a
+ * parent = sum over its children), and
+ *   score = sum_t sum_q delta_t(q) grad_theta [log f_t(x_t^q | parent) + log g_t(y_t | x_t^q)]
+ *           + sum_q delta_0(q) grad_theta log pi_0(x_0^q).
+ * The theta-gradients of the densities are central differences (step
+ * h_d = 1e-6 max(1, |theta_d|)) of log_f, log_g and log_mu at fixed x. */
+int oracle_fisher_score(int model, int dx, int dy, int m, int M, int T, uint64_t seed, uint32_t chain,
+                        uint32_t iter, const double* theta, const double* mdat, const double* y,
+                        const int32_t* anc, const int32_t* sstar, int d_theta, double* score)
+{
+    if (m < 1 || (m & (m - 1)) || M < 1 || T < 1 || dx < 1 || dx > 64 || dy < 1 || d_theta < 1 ||
+        d_theta > 64)
+        return 1;
+    const int N = m * M;
+    model_t md = { model, dx, dy, theta, mdat };
+    stream_id st = { seed, chain, iter };
+    double* xs = malloc(sizeof(double) * (size_t)(T + 1) * N * dx);
+    double* lw1 = malloc(sizeof(double) * (size_t)T * m);
+    double* l = malloc(sizeof(double) * (size_t)T * N);
+    double* dl = malloc(sizeof(double) * N);
+    double* dlp = malloc(sizeof(double) * N);
+    double logz;
+    fixed_lineage_pass(&md, &st, m, M, T, y, anc, sstar, xs, lw1, &logz, l);
+    /* delta_T: island share x share within the island */
+    double lz = log_sum_exp(lw1 + (size_t)(T - 1) * m, m);
+    for (int k = 0; k < m; ++k) {
+        const double* lk = l + (size_t)(T - 1) * N + (size_t)k * M;
+        double li = log_sum_exp(lk, M);
+        for (int i = 0; i < M; ++i) {
+            double v = lw1[(size_t)(T - 1) * m + k] - lz + lk[i] - li;
+            dl[k * M + i] = (v > -INFINITY) ? exp(v) : 0.0;
+        }
+    }
+    double thp[64], thm[64];
+    for (int d = 0; d < d_theta; ++d) score[d] = 0.0;
+    for (int t = T; t >= 1; --t) {
+        const double* yt = y + (size_t)(t - 1) * dy;
+        const double* xt = xs + (size_t)t * N * dx;
+        const double* xprev = xs + (size_t)(t - 1) * N * dx;
+        for (int g = 0; g < N; ++g) {
+            if (dl[g] == 0.0) continue;
+            /* the parent of particle g of time t among the time-(t-1) particles */
+            const double* xp = (t == 1) ? xprev + (size_t)g * dx
+                                        : xprev + (size_t)anc[(size_t)(t - 2) * N + g] * dx;
+            for (int d = 0; d < d_theta; ++d) {
+                double h = 1e-6 * (fabs(theta[d]) > 1.0 ? fabs(theta[d]) : 1.0);
+                memcpy(thp, theta, sizeof(double) * d_theta);
+                memcpy(thm, theta, sizeof(double) * d_theta);
+                thp[d] += h;
+                thm[d] -= h;
+                model_t mp = { model, dx, dy, thp, mdat }, mm = { model, dx, dy, thm, mdat };
+                double fp = log_f(&mp, (uint32_t)t, xp, xt + (size_t)g * dx) + log_g(&mp, yt, xt + (size_t)g * dx);
+                double fm = log_f(&mm, (uint32_t)t, xp, xt + (size_t)g * dx) + log_g(&mm, yt, xt + (size_t)g * dx);
+                if (t == 1) {
+                    fp += log_mu(&mp, xp);
+                    fm += log_mu(&mm, xp);
+                }
+                score[d] += dl[g] * (fp - fm) / (2.0 * h);
+            }
+        }
+        if (t >= 2) {
+            for (int g = 0; g < N; ++g) dlp[g] = 0.0;
+            for (int g = 0; g < N; ++g) dlp[anc[(size_t)(t - 2) * N + g]] += dl[g];
+            memcpy(dl, dlp, sizeof(double) * N);
+        }
+    }
+    free(xs); free(lw1); free(l); free(dl); free(dlp);
+    return 0;
+}
