@@ -120,18 +120,22 @@ typedef struct {
     int32_t mode;           /* airpf_interact */
     double tau;             /* ENF threshold in (0, 1] (ENF normalised to [1/m, 1]) */
     int32_t precision;      /* airpf_precision */
-    int32_t record;         /* bit 0: ancestors, bit 1: ENF and s*, bit 2: log Z trace, bit 3: kernel timing */
+    int32_t record;         /* bit 0: ancestors, bit 1: ENF and s*, bit 2: log Z trace, bit 3: kernel timing,
+                               bit 4: gradient pass */
     uint64_t seed;
     int32_t launch;         /* airpf_launch (a requested mode that cannot run: AIRPF_ERR_UNSUPPORTED) */
     int32_t reserved;       /* must be 0 */
     int32_t ppt;            /* particles per thread: 2 or 4, 0 = automatic */
     int32_t islands_per_cta;/* islands per CTA: a power of 2, 0 = automatic (capped at 512 threads) */
+    int32_t ckpt;           /* AIRPF_RECORD_GRAD: states kept every ckpt steps, recomputed in
+                               between during the backward pass (0 = every step) */
 } airpf_config;
 
 #define AIRPF_RECORD_LINEAGE 1
 #define AIRPF_RECORD_ENF 2
 #define AIRPF_RECORD_TRACE 4
 #define AIRPF_RECORD_TIMING 8   /* STEPS launch only: CUDA events around each kernel (airpf_kernel_times) */
+#define AIRPF_RECORD_GRAD 16    /* keep what airpf_grad's backward pass needs (AR1 and LGSSM) */
 
 typedef struct airpf_ctx airpf_ctx;
 
@@ -284,6 +288,24 @@ airpf_status airpf_autotune(const airpf_config* cfg, void* d_workspace, size_t w
  * out (the results of that pass are invalid; the context stays usable),
  * AIRPF_ERR_CUDA for a CUDA error. */
 airpf_status airpf_sync(airpf_ctx* ctx);
+
+/* Gradient of log Z^N_T with respect to theta for each filter (AR1 and LGSSM;
+ * a context created with AIRPF_RECORD_GRAD).  Runs the pass (as airpf_run,
+ * writing d_log_z), then a backward pass over t = T..1 that needs the pass's
+ * lineage, s*, island log-weights and the states kept every `ckpt` steps
+ * (states in between are recomputed from the regenerated noise):
+ *   d_grad   [B * d_theta] out or NULL: the adjoint gradient of log Z with the
+ *            random numbers, ancestors, island choices and s* held fixed (the
+ *            reparameterisation gradient; biased for the gradient of log Z
+ *            itself, exact for the function a fixed lineage defines)
+ *   d_score  [B * d_theta] out or NULL: the Fisher-identity score along the
+ *            lineages, sum over particles of the final weight of their
+ *            descendants times grad_theta log [f(x_t | parent) g(y_t | x_t)]
+ *            (plus the prior's term), which estimates grad log Z consistently
+ * At least one of them.  theta layouts as for the models above.  Asynchronous
+ * on the context's stream. */
+airpf_status airpf_grad(airpf_ctx* ctx, const double* d_theta, const double* d_y, uint32_t chain0,
+                        uint32_t iter, double* d_log_z, double* d_grad, double* d_score);
 
 /* Measurement aid, no counterpart in the paper.  For a context created with
  * AIRPF_RECORD_TIMING (which puts CUDA event-record nodes before and after each

@@ -18,7 +18,7 @@ from ._binding import AirpfConfig, AirpfError
 MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY = 0, 1, 2, 3, 4
 NEVER, ALWAYS, ADAPTIVE = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
-RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE, RECORD_TIMING = 1, 2, 4, 8
+RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE, RECORD_TIMING, RECORD_GRAD = 1, 2, 4, 8, 16
 LAUNCH_AUTO, LAUNCH_STEPS, LAUNCH_PERSISTENT_CTA, LAUNCH_PERSISTENT_GRID, LAUNCH_STEPS_SPLIT = 0, 1, 2, 3, 4
 
 _MODES = {"never": NEVER, "always": ALWAYS, "adaptive": ADAPTIVE}
@@ -43,7 +43,8 @@ class AIRPF:
 
     def __init__(self, model: int, *, m: int, M: int, T: int, B: int = 1, dx: int = 1, dy: int = 1,
                  mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, record: int = 0,
-                 model_data=None, stream=None, launch="auto", ppt: int = 0, islands_per_cta: int = 0):
+                 model_data=None, stream=None, launch="auto", ppt: int = 0, islands_per_cta: int = 0,
+                 ckpt: int = 0):
         import torch
         self._torch = torch
         self.lib = _binding.load()
@@ -52,7 +53,7 @@ class AIRPF:
         launch = _LAUNCH[launch] if isinstance(launch, str) else int(launch)
         self.cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau,
                                precision=precision, record=record, seed=seed, launch=launch, reserved=0,
-                               ppt=ppt, islands_per_cta=islands_per_cta)
+                               ppt=ppt, islands_per_cta=islands_per_cta, ckpt=ckpt)
         nbytes = ctypes.c_size_t()
         _binding.check(self.lib.airpf_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)))
         self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
@@ -127,6 +128,21 @@ class AIRPF:
                                            _ptr(state_theta), _ptr(state_logz), chain0, iter0, iters,
                                            _ptr(out.get("theta")), _ptr(out.get("log_z")), _ptr(n_accept)),
                        self.ctx)
+        return out
+
+    def grad(self, theta, y, *, chain0: int = 0, iter: int = 0):
+        """airpf_grad (context created with RECORD_GRAD): returns dict of CUDA tensors log_z [B],
+        grad [B, d] (adjoint with the lineage held fixed) and score [B, d] (Fisher-identity
+        score along the lineages)."""
+        torch = self._torch
+        theta = theta.reshape(self.B, self.theta_dim).to(device="cuda", dtype=torch.float64).contiguous()
+        y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+        out = {"log_z": torch.empty(self.B, dtype=torch.float64, device="cuda"),
+               "grad": torch.empty((self.B, self.theta_dim), dtype=torch.float64, device="cuda"),
+               "score": torch.empty((self.B, self.theta_dim), dtype=torch.float64, device="cuda")}
+        self._keep = (theta, y)
+        _binding.check(self.lib.airpf_grad(self.ctx, _ptr(theta), _ptr(y), chain0, iter, _ptr(out["log_z"]),
+                                           _ptr(out["grad"]), _ptr(out["score"])), self.ctx)
         return out
 
     def kernel_times(self):
@@ -284,5 +300,5 @@ def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: i
 
 __all__ = ["AIRPF", "AirpfError", "Group", "autotune", "theta_dim", "run_static", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
            "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
-           "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
+           "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "RECORD_GRAD", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
            "LAUNCH_PERSISTENT_GRID", "LAUNCH_STEPS_SPLIT"]

@@ -22,7 +22,7 @@ class AirpfConfig(ctypes.Structure):
                 ("M", c_int32), ("T", c_int32), ("B", c_int32), ("mode", c_int32),
                 ("tau", c_double), ("precision", c_int32), ("record", c_int32),
                 ("seed", c_uint64), ("launch", c_int32), ("reserved", c_int32), ("ppt", c_int32),
-                ("islands_per_cta", c_int32)]
+                ("islands_per_cta", c_int32), ("ckpt", c_int32)]
 
 
 # every symbol include/airpf.h declares, with (restype, argtypes)
@@ -48,6 +48,7 @@ SIGNATURES = {
     "airpf_group_sync": (c_int32, [c_void_p]),
     "airpf_autotune": (c_int32, [ctypes.POINTER(AirpfConfig), c_void_p, c_size_t, c_void_p, c_void_p, c_void_p,
                                  c_int32, c_void_p, ctypes.POINTER(AirpfConfig), ctypes.POINTER(ctypes.c_float)]),
+    "airpf_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint32, c_void_p, c_void_p, c_void_p]),
     "airpf_sync": (c_int32, [c_void_p]),
     "airpf_launch_mode": (c_int32, [c_void_p]),
     "airpf_kernel_times": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libairpf.so")
-SOURCES = ["airpf_launch_f32.cu", "airpf_launch_f64.cu", "airpf_step.cu", "airpf_api.cu", "airpf_pmmh.cu", "airpf_static.cu", "airpf_group.cu"]
+SOURCES = ["airpf_launch_f32.cu", "airpf_launch_f64.cu", "airpf_step.cu", "airpf_api.cu", "airpf_pmmh.cu", "airpf_static.cu", "airpf_group.cu", "airpf_grad.cu"]
 HEADERS = ["airpf_device.cuh", "airpf_internal.h", "airpf_step_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -36,7 +36,9 @@ int ilog2_exact(int m)
 struct WsLayout {
     size_t run, theta, mdata, y, X[2], pe[2], pt[2], pq[2], csum, cup, nsrc, utg, ires[2], logz, trace, enf,
         sstar, anc, active, mpar, drift, bar;
-    size_t pm_prop, pm_logz_prop, pm_stats, total;
+    size_t pm_prop, pm_logz_prop, pm_stats;
+    size_t xck, xblk, logw, gpi[2], xh[3], dh[3], gout, sout;   // gradient pass
+    size_t total;
 };
 
 }  // namespace
@@ -53,6 +55,8 @@ struct airpf_ctx {
     bool graph_ready;
     cudaGraphExec_t graph_pm;   // the same pass with per-filter active flags (PMMH)
     bool graph_pm_ready;
+    cudaGraphExec_t graph_bwd;  // the backward pass of the gradient
+    bool graph_bwd_ready;
     int launch;               // resolved airpf_launch
     StepParams sp;
     StepParams sp_pm;
@@ -94,7 +98,8 @@ const char* check_config(const airpf_config* c)
     if (c->mode < 0 || c->mode > 2) return "unknown interaction mode";
     if (!(c->tau > 0.0 && c->tau <= 1.0)) return "tau must be in (0, 1]";
     if (c->precision != AIRPF_FP64 && c->precision != AIRPF_FP32_MIXED) return "unknown precision";
-    if (c->record < 0 || c->record > 15) return "unknown record bits";
+    if (c->record < 0 || c->record > 31) return "unknown record bits";
+    if (c->ckpt < 0 || c->ckpt > c->T) return "ckpt must be in [0, T]";
     if (c->launch < 0 || c->launch > 4) return "unknown launch mode";
     if (c->reserved != 0) return "reserved must be 0";
     if (c->ppt != 0 && c->ppt != 2 && c->ppt != 4) return "ppt must be 0, 2 or 4";
@@ -109,8 +114,9 @@ WsLayout make_ws_layout(const airpf_config* c)
     const size_t B = c->B, N = (size_t)c->m * c->M, T = c->T;
     const size_t S = (size_t)ilog2_exact(c->m);
     const size_t rsz = c->precision == AIRPF_FP64 ? 8 : 4;
-    const bool lin = c->record & AIRPF_RECORD_LINEAGE;
-    const bool enf = c->record & AIRPF_RECORD_ENF;
+    const bool grad = c->record & AIRPF_RECORD_GRAD;
+    const bool lin = (c->record & AIRPF_RECORD_LINEAGE) || grad;    // the gradient pass needs the
+    const bool enf = (c->record & AIRPF_RECORD_ENF) || grad;        // lineage and s* of the run
     const bool tr = c->record & AIRPF_RECORD_TRACE;
     const size_t td = (size_t)theta_dim_of(c->model, c->dx);
     size_t o = 0;
@@ -141,6 +147,21 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.pm_prop = take(sizeof(double) * B * td);
     L.pm_logz_prop = take(sizeof(double) * B);
     L.pm_stats = take(sizeof(int) * B);
+    L.xck = L.xblk = L.logw = L.gout = L.sout = 0;
+    for (int i = 0; i < 3; ++i) L.xh[i] = L.dh[i] = 0;
+    L.gpi[0] = L.gpi[1] = 0;
+    if (grad) {
+        const size_t K = c->ckpt > 0 ? (size_t)c->ckpt : 1;
+        const size_t nck = T / K + 1 + (T % K != 0 ? 1 : 0);
+        L.xck = take(rsz * B * nck * c->dx * N);
+        L.xblk = take(rsz * B * K * c->dx * N);
+        L.logw = take(sizeof(double) * B * T * c->m);
+        for (int i = 0; i < 2; ++i) L.gpi[i] = take(sizeof(double) * B * c->m);
+        for (int i = 0; i < 3; ++i) L.xh[i] = take(rsz * B * c->dx * N);
+        for (int i = 0; i < 3; ++i) L.dh[i] = take(sizeof(double) * B * N);
+        L.gout = take(sizeof(double) * B * td);
+        L.sout = take(sizeof(double) * B * td);
+    }
     L.total = o;
     return L;
 }
@@ -280,6 +301,10 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         set_err(nullptr, "LGSSM needs model_data (A and C)");
         return AIRPF_ERR_ARG;
     }
+    if ((cfg->record & AIRPF_RECORD_GRAD) && !airpf::grad_supported(cfg->model)) {
+        set_err(nullptr, "the gradient pass supports the AR1 and LGSSM models");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
     const WsLayout L = make_ws_layout(cfg);
     if (!d_workspace || workspace_bytes < L.total || ((uintptr_t)d_workspace & 255u)) {
         set_err(nullptr, "workspace must be >= %zu bytes and 256-byte aligned", L.total);
@@ -417,7 +442,7 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         p.pe[i] = at<int>(ctx, L.pe[i]);
         p.pt[i] = at<void>(ctx, L.pt[i]);
         p.pq[i] = at<void>(ctx, L.pq[i]);
-        p.ires[i] = (cfg->record & AIRPF_RECORD_LINEAGE) ? at<int>(ctx, L.ires[i]) : nullptr;
+        p.ires[i] = L.ires[i] ? at<int>(ctx, L.ires[i]) : nullptr;
     }
     p.csum = at<int>(ctx, L.csum);
     p.cup = at<void>(ctx, L.cup);
@@ -425,9 +450,24 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.utg = at<void>(ctx, L.utg);
     p.logz = at<double>(ctx, L.logz);
     p.trace = (cfg->record & AIRPF_RECORD_TRACE) ? at<double>(ctx, L.trace) : nullptr;
-    p.enf = (cfg->record & AIRPF_RECORD_ENF) ? at<double>(ctx, L.enf) : nullptr;
-    p.sstar = (cfg->record & AIRPF_RECORD_ENF) ? at<int>(ctx, L.sstar) : nullptr;
-    p.anc = (cfg->record & AIRPF_RECORD_LINEAGE) ? at<int>(ctx, L.anc) : nullptr;
+    p.enf = L.enf ? at<double>(ctx, L.enf) : nullptr;
+    p.sstar = L.sstar ? at<int>(ctx, L.sstar) : nullptr;
+    p.anc = L.anc ? at<int>(ctx, L.anc) : nullptr;
+    if (cfg->record & AIRPF_RECORD_GRAD) {
+        p.grad = 1;
+        p.ckpt = cfg->ckpt > 0 ? cfg->ckpt : 1;
+        p.nck = cfg->T / p.ckpt + 1 + (cfg->T % p.ckpt != 0 ? 1 : 0);
+        p.xck = at<void>(ctx, L.xck);
+        p.xblk = at<void>(ctx, L.xblk);
+        p.logw = at<double>(ctx, L.logw);
+        for (int i = 0; i < 2; ++i) p.gpi[i] = at<double>(ctx, L.gpi[i]);
+        for (int i = 0; i < 3; ++i) {
+            p.xh[i] = at<void>(ctx, L.xh[i]);
+            p.dh[i] = at<double>(ctx, L.dh[i]);
+        }
+        p.gout = at<double>(ctx, L.gout);
+        p.sout = at<double>(ctx, L.sout);
+    }
     ctx->sp_pm = p;
     ctx->sp_pm.active = at<int>(ctx, L.active);
 
@@ -472,6 +512,7 @@ airpf_status airpf_destroy(airpf_ctx* ctx)
     if (!ctx) return AIRPF_ERR_ARG;
     if (ctx->graph_ready) cudaGraphExecDestroy(ctx->graph);
     if (ctx->graph_pm_ready) cudaGraphExecDestroy(ctx->graph_pm);
+    if (ctx->graph_bwd_ready) cudaGraphExecDestroy(ctx->graph_bwd);
     if (ctx->ev) {
         for (int i = 0; i < ctx->n_ev; ++i) cudaEventDestroy(ctx->ev[i]);
         delete[] ctx->ev;
@@ -542,6 +583,51 @@ airpf_status airpf_sync(airpf_ctx* ctx)
         set_err(ctx, "a grid-barrier wait timed out; the pass's results are invalid");
         return AIRPF_ERR_TIMEOUT;
     }
+    return AIRPF_OK;
+}
+
+airpf_status airpf_grad(airpf_ctx* ctx, const double* d_theta, const double* d_y, uint32_t chain0, uint32_t iter,
+                        double* d_log_z, double* d_grad, double* d_score)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    if (!ctx->sp.grad) {
+        set_err(ctx, "the context was created without AIRPF_RECORD_GRAD");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    if (!d_grad && !d_score) {
+        set_err(ctx, "grad or score is required");
+        return AIRPF_ERR_ARG;
+    }
+    airpf_status s = airpf_run(ctx, d_theta, d_y, chain0, iter, d_log_z, nullptr, nullptr, nullptr, nullptr);
+    if (s != AIRPF_OK) return s;
+    const int64_t fwd = ctx->launches;
+    if (!ctx->graph_bwd_ready) {
+        cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+        cudaError_t le = airpf::launch_grad_backward(ctx->sp, ctx->cap_stream);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(ctx, le, "gradient launch during capture");
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ctx->graph_bwd, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        ctx->graph_bwd_ready = true;
+    }
+    cudaError_t e = cudaGraphLaunch(ctx->graph_bwd, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+    {
+        const int T = ctx->cfg.T, K = ctx->sp.ckpt;
+        int rec = 0;
+        for (int t = 1; t <= T; ++t) rec += (t % K != 0 && t != T);
+        ctx->launches = fwd + 1 + T + (T - 1) + rec;
+    }
+    const size_t n = sizeof(double) * (size_t)ctx->cfg.B * ctx->theta_dim;
+    if (d_grad && (s = copy_async(ctx, d_grad, ctx->sp.gout, n))) return s;
+    if (d_score && (s = copy_async(ctx, d_score, ctx->sp.sout, n))) return s;
     return AIRPF_OK;
 }
 

@@ -1,0 +1,400 @@
+// airpf_grad.cu -- gradient of log Z^N_T with respect to theta, after a forward
+// pass that recorded the lineage, s*, the island log-weights and checkpointed
+// states (record AIRPF_RECORD_GRAD).
+//
+// Adjoint with the lineage held fixed.  With the random numbers, the
+// ancestors, the island choices and s* fixed, log Z = log sum_k W^k_{T,1} is a
+// smooth function of theta through the particles x_t = f(parent, z_t) and the
+// observation densities.  Reverse mode gives
+//   d log Z / d l_t(k,i) = pi_t(k) w_t(k,i),
+// where w_t(k,i) is particle i's normalised weight within island k and pi_t(k)
+// the island's smoothing weight: pi_T(k) = W^k_{T,1} / sum_j W^j_{T,1}, and,
+// going back, each block of 2^(s*_{t-1} - 1) islands hands its total pi_t mass
+// to its members in proportion to W^j_{t-1,1} (the block averaging of the
+// interaction stages, eq. (3), is linear and symmetric).  Particle adjoints
+// x^_t = x^ from the children + l^ dl/dx flow to the parents through
+// (df/dparent)^T by atomic scatter-add along the lineage; theta^ collects
+// l^ dl/dtheta + x^ df/dtheta (and the prior's dependence at t = 1).
+//
+// Fisher-identity score along the lineages: every time-t particle carries the
+// final weight delta_t of its descendants (delta_T = pi_T w_T, scattered back
+// along the lineage), and score = sum_t sum_q delta_t(q) grad_theta
+// [log f(x_t^q | parent) + log g(y_t | x_t^q)] + the prior's term.
+//
+// States between checkpoints are recomputed from the previous state, the
+// lineage and the regenerated transition noise.  Particle arithmetic in the
+// pass's precision R; smoothing weights, descendant weights and the theta
+// sums in double.
+#include <climits>
+
+#include "airpf_device.cuh"
+#include "airpf_internal.h"
+
+namespace airpf {
+namespace {
+
+constexpr int kGradThreads = 128;
+
+// time-t particles [dx][N] of filter c: a checkpoint slot or the recomputed block
+template <typename R>
+__device__ __forceinline__ R* xstate(const StepParams& p, int c, int t)
+{
+    const size_t per = (size_t)p.dx * p.N;
+    int slot = -1;
+    if (t == 0) slot = 0;
+    else if (t % p.ckpt == 0) slot = t / p.ckpt;
+    else if (t == p.T) slot = p.nck - 1;
+    if (slot >= 0) return reinterpret_cast<R*>(p.xck) + ((size_t)c * p.nck + slot) * per;
+    return reinterpret_cast<R*>(p.xblk) + ((size_t)c * p.ckpt + (t % p.ckpt)) * per;
+}
+
+// index among the time-(t-1) particles of the parent of time-t particle g
+__device__ __forceinline__ int parent_of(const StepParams& p, int c, int t, int g)
+{
+    return t == 1 ? g : __ldcg(&p.anc[((size_t)c * p.T + (t - 2)) * p.N + g]);
+}
+
+template <typename R>
+__device__ void load_model_matrices(const StepParams& p, R* A, R* C)
+{
+    const int dx = p.dx, dy = p.dy;
+    for (int q = threadIdx.x; q < dx * dx + dy * dx; q += blockDim.x) {
+        const R v = (R)p.mdata[q];
+        if (q < dx * dx) A[q] = v;
+        else C[q - dx * dx] = v;
+    }
+}
+
+// x_t of the particles between checkpoints: x_t(g) = f(x_{t-1}(parent), z_t(g))
+template <typename R, int MODEL, int DX>
+__global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, int t)
+{
+    __shared__ R Am[kMaxDx * kMaxDx + kMaxDy * kMaxDx];
+    const int c = blockIdx.y;
+    if (MODEL == LGSSM) load_model_matrices<R>(p, Am, Am + p.dx * p.dx);
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= p.N) return;
+    const ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+    const RunParams run = *p.run;
+    const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
+    const int dx = p.dx, N = p.N;
+    const R* xprev = xstate<R>(p, c, t - 1);
+    R* xt = xstate<R>(p, c, t);
+    const int par = parent_of(p, c, t, g);
+    R xp[DX], x[DX], z[DX > 1 ? DX : 1];
+#pragma unroll
+    for (int d = 0; d < DX; ++d) xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
+    uint32_t w0, w2;
+    model_step_noise<R, MODEL, DX>(st, (uint32_t)g, (uint32_t)t, dx, z, w0, w2);
+    model_transition<R, MODEL, DX>(mp, dx, xp, x, Am, z, w0);
+#pragma unroll
+    for (int d = 0; d < DX; ++d)
+        if (d < dx) xt[(size_t)d * N + g] = x[d];
+}
+
+// pi_T(k) = W^k_{T,1} / sum_j W^j_{T,1}: one CTA per filter
+__global__ void __launch_bounds__(256) grad_pi_final_kernel(StepParams p)
+{
+    __shared__ double red[32];
+    const int c = blockIdx.x, m = p.m;
+    const double* lw = p.logw + ((size_t)c * p.T + (p.T - 1)) * m;
+    double mx = -INFINITY;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) mx = fmax(mx, lw[k]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = -INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    __syncthreads();
+    double sum = 0.0;
+    if (mx > -INFINITY)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) sum += exp(lw[k] - mx);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    double* pi = p.gpi[p.T & 1] + (size_t)c * m;
+    for (int k = threadIdx.x; k < m; k += blockDim.x)
+        pi[k] = (sum > 0.0 && lw[k] > -INFINITY) ? exp(lw[k] - mx) / sum : 0.0;
+}
+
+// pi_{t-1} from pi_t: the blocks of 2^(s*_{t-1} - 1) islands redistribute their
+// pi_t mass in proportion to W_{t-1,1}; one thread per block
+__global__ void __launch_bounds__(256) grad_pi_step_kernel(StepParams p, int t)
+{
+    const int c = blockIdx.y, m = p.m;
+    const int lvl = p.sstar[(size_t)c * p.T + (t - 2)] - 1;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (m >> lvl)) return;
+    const int j0 = b << lvl, n = 1 << lvl;
+    const double* lw = p.logw + ((size_t)c * p.T + (t - 2)) * m;
+    const double* pin = p.gpi[t & 1] + (size_t)c * m;
+    double* pout = p.gpi[(t - 1) & 1] + (size_t)c * m;
+    double mx = -INFINITY, mass = 0.0;
+    for (int j = j0; j < j0 + n; ++j) {
+        mx = fmax(mx, lw[j]);
+        mass += pin[j];
+    }
+    double sw = 0.0;
+    if (mx > -INFINITY)
+        for (int j = j0; j < j0 + n; ++j) sw += exp(lw[j] - mx);
+    for (int j = j0; j < j0 + n; ++j)
+        pout[j] = (sw > 0.0 && lw[j] > -INFINITY) ? exp(lw[j] - mx) / sw * mass : 0.0;
+}
+
+// mean of the transition from the parent, and its scale (z = (x - mean) / scale)
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, const R* xp, const R* A, R* mu,
+                                                R& s)
+{
+    if (MODEL == AR1) {
+        mu[0] = mp.th[0] * xp[0];
+        s = mp.th[1];
+    } else {
+#pragma unroll
+        for (int r = 0; r < DX; ++r) {
+            if (r < dx) {
+                R acc = 0;
+#pragma unroll
+                for (int cc = 0; cc < DX; ++cc)
+                    if (cc < dx) acc += ((r == cc) ? mp.th[r] : A[r * dx + cc]) * xp[cc];
+                mu[r] = acc;
+            }
+        }
+        s = mp.c0;                       // sqrt(q)
+    }
+}
+
+// Step t of the backward pass: one CTA per island.
+template <typename R, int MODEL, int DX>
+__global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p, int t)
+{
+    extern __shared__ __align__(16) unsigned char gsm[];
+    __shared__ R Am[kMaxDx * kMaxDx + kMaxDy * kMaxDx];
+    __shared__ R yv[kMaxDy];
+    __shared__ double red[2 * kMaxTheta][kGradThreads / 32];
+    __shared__ R rmx[kGradThreads / 32];
+    __shared__ double rsum[kGradThreads / 32];
+    R* lsm = reinterpret_cast<R*>(gsm);                  // [M] log-weights of the island
+    const int c = blockIdx.y, k = blockIdx.x;
+    const int M = p.M, N = p.N, dx = p.dx, dy = p.dy, td = p.theta_dim;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (MODEL == LGSSM) load_model_matrices<R>(p, Am, Am + dx * dx);
+    for (int o = tid; o < dy; o += blockDim.x) yv[o] = (R)p.y[(size_t)(t - 1) * dy + o];
+    __syncthreads();
+    const R* Cm = Am + dx * dx;
+    const ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+    const R* xt = xstate<R>(p, c, t);
+    const R* xprev = xstate<R>(p, c, t - 1);
+    const size_t xo = (size_t)c * dx * N;
+    const R* xh_in = reinterpret_cast<const R*>(p.xh[t % 3]) + xo;
+    R* xh_out = reinterpret_cast<R*>(p.xh[(t + 2) % 3]) + xo;
+    R* xh_zero = reinterpret_cast<R*>(p.xh[(t + 1) % 3]) + xo;
+    const double* dh_in = p.dh[t % 3] + (size_t)c * N;
+    double* dh_out = p.dh[(t + 2) % 3] + (size_t)c * N;
+    double* dh_zero = p.dh[(t + 1) % 3] + (size_t)c * N;
+    const double pik = p.gpi[t & 1][(size_t)c * p.m + k];
+
+    // island softmax of the log-weights
+    R mx = (R)(-INFINITY);
+    for (int i = tid; i < M; i += blockDim.x) {
+        const int g = k * M + i;
+        R x[DX];
+#pragma unroll
+        for (int d = 0; d < DX; ++d) x[d] = (d < dx) ? xt[(size_t)d * N + g] : (R)0;
+        const R l = model_logg<R, MODEL, DX>(mp, yv, dx, dy, x, Cm);
+        lsm[i] = l;
+        mx = l > mx ? l : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const R v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    if (lane == 0) rmx[warp] = mx;
+    __syncthreads();
+    mx = rmx[0];
+    for (int w = 1; w < nw; ++w) mx = rmx[w] > mx ? rmx[w] : mx;
+    double sum = 0.0;
+    if (mx > (R)(-INFINITY))
+        for (int i = tid; i < M; i += blockDim.x) sum += (double)exp(lsm[i] - mx);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) rsum[warp] = sum;
+    __syncthreads();
+    sum = 0.0;
+    for (int w = 0; w < nw; ++w) sum += rsum[w];
+
+    double ga[kMaxTheta], gs[kMaxTheta];
+#pragma unroll
+    for (int d = 0; d < kMaxTheta; ++d) {
+        ga[d] = 0.0;
+        gs[d] = 0.0;
+    }
+    for (int i = tid; i < M; i += blockDim.x) {
+        const int g = k * M + i;
+        const double wi = (sum > 0.0 && lsm[i] > (R)(-INFINITY)) ? (double)exp(lsm[i] - mx) / sum : 0.0;
+        const double lhat = pik * wi;                              // d log Z / d l_t(k,i)
+        const double delta = (t == p.T) ? lhat : dh_in[g];         // descendant weight
+        const int par = parent_of(p, c, t, g);
+        R x[DX], xp[DX], mu[DX];
+        R s;
+#pragma unroll
+        for (int d = 0; d < DX; ++d) {
+            x[d] = (d < dx) ? xt[(size_t)d * N + g] : (R)0;
+            xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
+        }
+        transition_mean<R, MODEL, DX>(mp, dx, xp, Am, mu, s);
+        double xhat[DX], v[DX];
+#pragma unroll
+        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? (double)xh_in[(size_t)d * N + g] : 0.0;
+        if (MODEL == AR1) {
+            const double a = mp.th[0], sv = mp.th[1], sw = mp.th[2], s0 = mp.th[3];
+            const double e = (double)yv[0] - (double)x[0];
+            const double zz = ((double)x[0] - (double)mu[0]) / sv;
+            const double dsw = -1.0 / sw + e * e / (sw * sw * sw);
+            xhat[0] += lhat * e / (sw * sw);
+            ga[0] += xhat[0] * (double)xp[0];
+            ga[1] += xhat[0] * zz;
+            ga[2] += lhat * dsw;
+            v[0] = a * xhat[0];
+            gs[0] += delta * zz * (double)xp[0] / sv;
+            gs[1] += delta * (zz * zz - 1.0) / sv;
+            gs[2] += delta * dsw;
+            if (t == 1) {                          // x_0 = sigma_0 z_0
+                const double x0 = (double)xp[0];
+                ga[3] += v[0] * x0 / s0;
+                gs[3] += delta * (x0 * x0 / (s0 * s0) - 1.0) / s0;
+            }
+        } else {
+            const double r = 0.5 / (double)mp.c1;  // c1 = 1/(2r)
+            double ee[kMaxDy], ss = 0.0;
+#pragma unroll
+            for (int o = 0; o < kMaxDy; ++o) {
+                ee[o] = 0.0;
+                if (o < dy) {
+                    double e = (double)yv[o];
+#pragma unroll
+                    for (int cc = 0; cc < DX; ++cc)
+                        if (cc < dx) e -= (double)Cm[o * dx + cc] * (double)x[cc];
+                    ee[o] = e;
+                    ss += e * e;
+                }
+            }
+            const double dlr = -0.5 * dy + ss / (2.0 * r);
+            double zn = 0.0, qsum = 0.0;
+#pragma unroll
+            for (int d = 0; d < DX; ++d) {
+                if (d < dx) {
+                    double dl = 0.0;
+#pragma unroll
+                    for (int o = 0; o < kMaxDy; ++o)
+                        if (o < dy) dl += (double)Cm[o * dx + d] * ee[o];
+                    xhat[d] += lhat * dl / r;
+                    const double zd = ((double)x[d] - (double)mu[d]) / (double)s;
+                    ga[d] += xhat[d] * (double)xp[d];               // A_dd
+                    qsum += xhat[d] * 0.5 * (double)s * zd;          // log q
+                    gs[d] += delta * zd * (double)xp[d] / (double)s;
+                    zn += zd * zd;
+                }
+            }
+            ga[dx] += qsum;
+            ga[dx + 1] += lhat * dlr;
+            gs[dx] += delta * 0.5 * (zn - (double)dx);
+            gs[dx + 1] += delta * dlr;
+#pragma unroll
+            for (int cc = 0; cc < DX; ++cc) {
+                v[cc] = 0.0;
+                if (cc < dx) {
+#pragma unroll
+                    for (int rr = 0; rr < DX; ++rr)
+                        if (rr < dx) v[cc] += (double)((rr == cc) ? mp.th[rr] : Am[rr * dx + cc]) * xhat[rr];
+                }
+            }
+        }
+        if (t >= 2) {                      // to the parent, along the lineage
+#pragma unroll
+            for (int d = 0; d < DX; ++d)
+                if (d < dx) atomicAdd(&xh_out[(size_t)d * N + par], (R)v[d]);
+            atomicAdd(&dh_out[par], delta);
+        }
+#pragma unroll
+        for (int d = 0; d < DX; ++d)
+            if (d < dx) xh_zero[(size_t)d * N + g] = (R)0;
+        dh_zero[g] = 0.0;
+    }
+    // the CTA's theta sums
+#pragma unroll
+    for (int d = 0; d < kMaxTheta; ++d) {
+        if (d < td) {
+            double a = ga[d], b = gs[d];
+            for (int o = 16; o > 0; o >>= 1) {
+                a += __shfl_xor_sync(0xffffffffu, a, o);
+                b += __shfl_xor_sync(0xffffffffu, b, o);
+            }
+            if (lane == 0) {
+                red[d][warp] = a;
+                red[kMaxTheta + d][warp] = b;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid < td) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            a += red[tid][w];
+            b += red[kMaxTheta + tid][w];
+        }
+        atomicAdd(&p.gout[(size_t)c * td + tid], a);
+        atomicAdd(&p.sout[(size_t)c * td + tid], b);
+    }
+}
+
+template <typename R, int MODEL, int DX>
+cudaError_t backward_typed(const StepParams& p, cudaStream_t stream)
+{
+    const size_t xbytes = (size_t)p.B * p.dx * p.N * sizeof(R);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemsetAsync(p.xh[i], 0, xbytes, stream);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        e = cudaMemsetAsync(p.dh[i], 0, sizeof(double) * (size_t)p.B * p.N, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.gout, 0, sizeof(double) * (size_t)p.B * p.theta_dim, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.sout, 0, sizeof(double) * (size_t)p.B * p.theta_dim, stream);
+    if (e != cudaSuccess) return e;
+    grad_pi_final_kernel<<<p.B, 256, 0, stream>>>(p);
+    const size_t smem = sizeof(R) * (size_t)p.M;
+    const dim3 pgrid((p.N + 255) / 256, p.B), igrid(p.m, p.B), bgrid((p.m + 255) / 256, p.B);
+    const int K = p.ckpt;
+    const int nb = (p.T + K - 1) / K;
+    for (int b = nb - 1; b >= 0 && e == cudaSuccess; --b) {
+        const int lo = b * K + 1, hi = (b + 1) * K < p.T ? (b + 1) * K : p.T;
+        for (int t = lo; t <= hi; ++t)
+            if (t % K != 0 && t != p.T) grad_recompute_kernel<R, MODEL, DX><<<pgrid, 256, 0, stream>>>(p, t);
+        for (int t = hi; t >= lo; --t) {
+            grad_island_kernel<R, MODEL, DX><<<igrid, kGradThreads, smem, stream>>>(p, t);
+            if (t >= 2) grad_pi_step_kernel<<<bgrid, 256, 0, stream>>>(p, t);
+        }
+        e = cudaGetLastError();
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+template <typename R>
+cudaError_t backward_r(const StepParams& p, cudaStream_t stream)
+{
+    if (p.model == AR1) return backward_typed<R, AR1, 1>(p, stream);
+    if (p.model == LGSSM) return backward_typed<R, LGSSM, kMaxDx>(p, stream);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+bool grad_supported(int model) { return model == AR1 || model == LGSSM; }
+
+cudaError_t launch_grad_backward(const StepParams& p, cudaStream_t stream)
+{
+    if (p.M * (p.fp64 ? 8 : 4) > 48 * 1024) return cudaErrorInvalidValue;
+    return p.fp64 ? backward_r<double>(p, stream) : backward_r<float>(p, stream);
+}
+
+}  // namespace airpf

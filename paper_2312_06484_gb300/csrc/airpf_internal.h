@@ -47,6 +47,20 @@ struct StepParams {
     int fused;                    // per-step launches: each CTA runs the previous step's cascade itself
     int split;                    // per-step launches with a cascade kernel that leaves the tree in utg
     void* utg;                    // [B][2P] upper tree of the last cascade (split steps)
+    // gradient pass (record AIRPF_RECORD_GRAD): states x_t at checkpoints
+    // (slot 0 = x_0, slot t/ckpt, and slot nck-1 = x_T when T is no multiple
+    // of ckpt), the recomputed states between checkpoints, log W^k_{t,1}, the
+    // island smoothing weights, the particle adjoints and descendant weights
+    // (three rotating buffers each), and the two results
+    int grad, ckpt, nck;
+    void* xck;                    // [B][nck][dx][N]
+    void* xblk;                   // [B][ckpt][dx][N]
+    double* logw;                 // [B][T][m]
+    double* gpi[2];               // [B][m]
+    void* xh[3];                  // [B][dx][N]
+    double* dh[3];                // [B][N]
+    double* gout;                 // [B][theta_dim] adjoint gradient
+    double* sout;                 // [B][theta_dim] Fisher score
     void* X[2];                   // particle stores, ping-pong by t & 1
     int P, g;                     // CTA records per filter (m / G) and log2 G
     int* pe[2];                   // CTA records, ping-pong by t & 1
@@ -90,6 +104,11 @@ bool persistent_grid_fits(const StepParams& p);
 
 // Largest CTA of the one-CTA-per-filter launch.
 int max_cta_threads();
+
+// The backward pass of the gradient (after a recorded forward pass), enqueued
+// on `stream`: AR1 and LGSSM only.  Zeroes its accumulators first.
+cudaError_t launch_grad_backward(const StepParams& p, cudaStream_t stream);
+bool grad_supported(int model);
 
 // Writes the run parameters (one thread).
 cudaError_t launch_set_run(RunParams* d_run, uint32_t iter, uint32_t chain0, cudaStream_t stream);

@@ -1020,6 +1020,26 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             lv[r] = model_logg<R, MODEL, DX>(mp, yv, dx, p.dy, xv[r], Cm);
         }
     }
+    if (p.grad) {
+        // states for the gradient pass: the prior draws x_0 (slot 0, at t = 1)
+        // and the time-t particles at the checkpoints (every ckpt steps, and T)
+        const int slot = (t % p.ckpt == 0) ? t / p.ckpt : (t == p.T ? p.nck - 1 : -1);
+        R* xck = reinterpret_cast<R*>(p.xck) + (size_t)c * p.nck * dx * N;
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int i = li * PPT + r;
+            if (i < M) {
+                const size_t gi = (size_t)k * M + i;
+#pragma unroll
+                for (int d = 0; d < DX; ++d) {
+                    if (d < dx) {
+                        if (t == 1) xck[(size_t)d * N + gi] = xp[r][d];
+                        if (slot >= 0) xck[((size_t)slot * dx + d) * N + gi] = xv[r][d];
+                    }
+                }
+            }
+        }
+    }
 
     // island maximum of the log-weights
     R mx = lv[0];
@@ -1158,6 +1178,13 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
         new_w[g] = w.bits;
         new_we[g] = w.e;
+        if (p.grad) {        // log W^k_{t,1} (the FP32-mixed weights leave out M^-t)
+            double lw = -INFINITY;
+            if (w.bits != 0ull)
+                lw = FX ? log((double)w.bits) + (double)(w.e - 64) * 0.6931471805599453
+                        : log(__longlong_as_double((long long)w.bits)) + (double)w.e * 0.6931471805599453;
+            p.logw[((size_t)c * p.T + (t - 1)) * p.m + k] = lw;
+        }
     }
     __syncthreads();
 
