@@ -211,6 +211,60 @@ def batched_leg(gp, torch, ws: int, n_chains: int = 256, T: int = 500, passes: i
     return out
 
 
+def grad_leg(gp, torch, ws: int, passes: int = 2) -> dict:
+    """Differentiation workload: LGSSM d_x = 8, d_y = 4 (A = 0.8 I + 0.05 G scaled to spectral
+    radius 0.95, C ~ N(0, 1/d_x), Q = 0.1 I, R = 0.5 I), T = 200, m = 2048 x M = 128, FP32;
+    one evaluation = the forward pass plus the backward pass (adjoint gradient and Fisher
+    score over the 10 parameters), states kept every 10 steps."""
+    dx, dy, T = 8, 4, 200
+    A, C, md = synth.lg_model(dx, dy, seed=4)
+    th = torch.tensor(synth.lg_theta(A, q=0.1, r=0.5)[None, :], device="cuda")
+    y = torch.tensor(synth.lg_observations(A, C, 0.1, 0.5, T, seed=4), device="cuda")
+    f = gp.AIRPF(synth.MODEL_LGSSM, m=2048, M=128, T=T, B=1, dx=dx, dy=dy, mode="adaptive", tau=TAU,
+                 precision="fp32", seed=1, record=gp.RECORD_GRAD, model_data=md, ckpt=10)
+    f.grad(th, y, iter=0xFFFF0000)
+    f.sync()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(f.stream)
+    for j in range(passes):
+        out = f.grad(th, y, iter=j)
+    e1.record(f.stream)
+    for j in range(passes):
+        f.run(th, y, iter=j)
+    e2.record(f.stream)
+    f.sync()
+    ms = e0.elapsed_time(e1) / passes
+    ms_fwd = e1.elapsed_time(e2) / passes
+    res = {"workload": "lgssm_dx8_dy4_m2048_M128_T200", "ms_per_eval": ms, "grad_evals_per_s": ws / (ms / 1e3),
+           "forward_ms": ms_fwd, "backward_over_forward": (ms - ms_fwd) / ms_fwd, "ckpt": 10,
+           "precision": "fp32", "score_norm": float(out["score"].norm()), "grad_norm": float(out["grad"].norm())}
+    f.close()
+    return res
+
+
+def ngm_leg(gp, torch, ws: int, T: int = 1000) -> dict:
+    """Large nonlinear-growth workload: m = 65536 islands, adaptive tau = 0.3, T = 1000; FP32
+    over M in {64, 128, 256, 512}, and FP64 at M = 256 (one timed pass each, after one
+    untimed pass)."""
+    y = torch.tensor(synth.ngm_observations(T, seed=5), device="cuda")
+    th = torch.tensor(synth.NGM_THETA[None, :], device="cuda")
+    out = {"workload": f"ngm_m65536_T{T}", "points": []}
+    for prec, M in [("fp32", 64), ("fp32", 128), ("fp32", 256), ("fp32", 512), ("fp64", 256)]:
+        f = gp.AIRPF(synth.MODEL_NGM, m=65536, M=M, T=T, B=1, mode="adaptive", tau=TAU, precision=prec, seed=1)
+        f.run(th, y, iter=0xFFFF0000)
+        f.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(f.stream)
+        lz = f.run(th, y, iter=1)["log_z"]
+        e1.record(f.stream)
+        f.sync()
+        ms = e0.elapsed_time(e1)
+        out["points"].append({"M": M, "precision": prec, "ms_per_pass": ms,
+                              "particle_steps_per_s": 65536 * M * T * ws / (ms / 1e3), "log_z": float(lz.item())})
+        f.close()
+    return out
+
+
 def run_gpu(args) -> None:
     import torch
     import paper_2312_06484_gb300 as gp
@@ -351,6 +405,8 @@ def run_gpu(args) -> None:
                         "U(-5,5) x U(-1,1) x U(0,2)"}
 
     batched = None if args.no_batched else batched_leg(gp, torch, ws)
+    gradient = None if args.no_grad else grad_leg(gp, torch, ws)
+    ngm = None if args.no_ngm else ngm_leg(gp, torch, ws)
 
     peaks, peak_src = _peaks()
     ms_step = tot_ms / args.steps
@@ -385,6 +441,8 @@ def run_gpu(args) -> None:
                      "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x sm_max_mhz ({peak_src})"},
         "fp64_path": fp64,
         "batched": batched,
+        "gradient": gradient,
+        "ngm_large": ngm,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
@@ -405,6 +463,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-chains leg")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient leg")
+    ap.add_argument("--no-ngm", action="store_true", help="skip the large NGM leg")
     ap.add_argument("--launch", default="auto", choices=["auto", "steps", "split", "grid"])
     ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0: automatic)")
     ap.add_argument("--islands-per-cta", type=int, default=0, help="islands per CTA (0: automatic)")
