@@ -22,9 +22,9 @@
 // [log f(x_t^q | parent) + log g(y_t | x_t^q)] + the prior's term.
 //
 // States between checkpoints are recomputed from the previous state, the
-// lineage and the regenerated transition noise.  Particle arithmetic in the
-// pass's precision R; smoothing weights, descendant weights and the theta
-// sums in double.
+// lineage and the regenerated transition noise.  Particle arithmetic and the
+// per-thread sums in the pass's precision R; smoothing weights, descendant
+// weights and the CTA and grid sums of the theta terms in double.
 #include <climits>
 
 #include "airpf_device.cuh"
@@ -225,17 +225,20 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     sum = 0.0;
     for (int w = 0; w < nw; ++w) sum += rsum[w];
 
-    double ga[kMaxTheta], gs[kMaxTheta];
+    // per-thread sums in the pass's precision (a thread holds few particles),
+    // the CTA and grid reductions in double
+    R ga[kMaxTheta], gs[kMaxTheta];
 #pragma unroll
     for (int d = 0; d < kMaxTheta; ++d) {
-        ga[d] = 0.0;
-        gs[d] = 0.0;
+        ga[d] = (R)0;
+        gs[d] = (R)0;
     }
     for (int i = tid; i < M; i += blockDim.x) {
         const int g = k * M + i;
-        const double wi = (sum > 0.0 && lsm[i] > (R)(-INFINITY)) ? (double)exp(lsm[i] - mx) / sum : 0.0;
-        const double lhat = pik * wi;                              // d log Z / d l_t(k,i)
-        const double delta = (t == p.T) ? lhat : dh_in[g];         // descendant weight
+        const R wi = (sum > 0.0 && lsm[i] > (R)(-INFINITY)) ? (R)((double)exp(lsm[i] - mx) / sum) : (R)0;
+        const R lhat = (R)pik * wi;                                  // d log Z / d l_t(k,i)
+        const double delta_d = (t == p.T) ? pik * (double)wi : dh_in[g];   // descendant weight
+        const R delta = (R)delta_d;
         const int par = parent_of(p, c, t, g);
         R x[DX], xp[DX], mu[DX];
         R s;
@@ -245,78 +248,79 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
             xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
         }
         transition_mean<R, MODEL, DX>(mp, dx, xp, Am, mu, s);
-        double xhat[DX], v[DX];
+        R xhat[DX], v[DX];
 #pragma unroll
-        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? (double)xh_in[(size_t)d * N + g] : 0.0;
+        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? xh_in[(size_t)d * N + g] : (R)0;
         if (MODEL == AR1) {
-            const double a = mp.th[0], sv = mp.th[1], sw = mp.th[2], s0 = mp.th[3];
-            const double e = (double)yv[0] - (double)x[0];
-            const double zz = ((double)x[0] - (double)mu[0]) / sv;
-            const double dsw = -1.0 / sw + e * e / (sw * sw * sw);
+            const R a = mp.th[0], sv = mp.th[1], sw = mp.th[2], s0 = mp.th[3];
+            const R e = yv[0] - x[0];
+            const R zz = (x[0] - mu[0]) / sv;
+            const R dsw = (R)(-1) / sw + e * e / (sw * sw * sw);
             xhat[0] += lhat * e / (sw * sw);
-            ga[0] += xhat[0] * (double)xp[0];
+            ga[0] += xhat[0] * xp[0];
             ga[1] += xhat[0] * zz;
             ga[2] += lhat * dsw;
             v[0] = a * xhat[0];
-            gs[0] += delta * zz * (double)xp[0] / sv;
-            gs[1] += delta * (zz * zz - 1.0) / sv;
+            gs[0] += delta * zz * xp[0] / sv;
+            gs[1] += delta * (zz * zz - (R)1) / sv;
             gs[2] += delta * dsw;
             if (t == 1) {                          // x_0 = sigma_0 z_0
-                const double x0 = (double)xp[0];
+                const R x0 = xp[0];
                 ga[3] += v[0] * x0 / s0;
-                gs[3] += delta * (x0 * x0 / (s0 * s0) - 1.0) / s0;
+                gs[3] += delta * (x0 * x0 / (s0 * s0) - (R)1) / s0;
             }
         } else {
-            const double r = 0.5 / (double)mp.c1;  // c1 = 1/(2r)
-            double ee[kMaxDy], ss = 0.0;
+            const R inv_r = (R)2 * mp.c1;          // c1 = 1/(2r)
+            R ee[kMaxDy], ss = 0;
 #pragma unroll
             for (int o = 0; o < kMaxDy; ++o) {
-                ee[o] = 0.0;
+                ee[o] = 0;
                 if (o < dy) {
-                    double e = (double)yv[o];
+                    R e = yv[o];
 #pragma unroll
                     for (int cc = 0; cc < DX; ++cc)
-                        if (cc < dx) e -= (double)Cm[o * dx + cc] * (double)x[cc];
+                        if (cc < dx) e -= Cm[o * dx + cc] * x[cc];
                     ee[o] = e;
                     ss += e * e;
                 }
             }
-            const double dlr = -0.5 * dy + ss / (2.0 * r);
-            double zn = 0.0, qsum = 0.0;
+            const R dlr = (R)(-0.5) * (R)dy + ss * mp.c1;
+            const R inv_s = (R)1 / s;
+            R zn = 0, qsum = 0;
 #pragma unroll
             for (int d = 0; d < DX; ++d) {
                 if (d < dx) {
-                    double dl = 0.0;
+                    R dl = 0;
 #pragma unroll
                     for (int o = 0; o < kMaxDy; ++o)
-                        if (o < dy) dl += (double)Cm[o * dx + d] * ee[o];
-                    xhat[d] += lhat * dl / r;
-                    const double zd = ((double)x[d] - (double)mu[d]) / (double)s;
-                    ga[d] += xhat[d] * (double)xp[d];               // A_dd
-                    qsum += xhat[d] * 0.5 * (double)s * zd;          // log q
-                    gs[d] += delta * zd * (double)xp[d] / (double)s;
+                        if (o < dy) dl += Cm[o * dx + d] * ee[o];
+                    xhat[d] += lhat * dl * inv_r;
+                    const R zd = (x[d] - mu[d]) * inv_s;
+                    ga[d] += xhat[d] * xp[d];                   // A_dd
+                    qsum += xhat[d] * (R)0.5 * s * zd;           // log q
+                    gs[d] += delta * zd * xp[d] * inv_s;
                     zn += zd * zd;
                 }
             }
             ga[dx] += qsum;
             ga[dx + 1] += lhat * dlr;
-            gs[dx] += delta * 0.5 * (zn - (double)dx);
+            gs[dx] += delta * (R)0.5 * (zn - (R)dx);
             gs[dx + 1] += delta * dlr;
 #pragma unroll
             for (int cc = 0; cc < DX; ++cc) {
-                v[cc] = 0.0;
+                v[cc] = 0;
                 if (cc < dx) {
 #pragma unroll
                     for (int rr = 0; rr < DX; ++rr)
-                        if (rr < dx) v[cc] += (double)((rr == cc) ? mp.th[rr] : Am[rr * dx + cc]) * xhat[rr];
+                        if (rr < dx) v[cc] += ((rr == cc) ? mp.th[rr] : Am[rr * dx + cc]) * xhat[rr];
                 }
             }
         }
         if (t >= 2) {                      // to the parent, along the lineage
 #pragma unroll
             for (int d = 0; d < DX; ++d)
-                if (d < dx) atomicAdd(&xh_out[(size_t)d * N + par], (R)v[d]);
-            atomicAdd(&dh_out[par], delta);
+                if (d < dx) atomicAdd(&xh_out[(size_t)d * N + par], v[d]);
+            atomicAdd(&dh_out[par], delta_d);
         }
 #pragma unroll
         for (int d = 0; d < DX; ++d)
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
 #pragma unroll
     for (int d = 0; d < kMaxTheta; ++d) {
         if (d < td) {
-            double a = ga[d], b = gs[d];
+            double a = (double)ga[d], b = (double)gs[d];
             for (int o = 16; o > 0; o >>= 1) {
                 a += __shfl_xor_sync(0xffffffffu, a, o);
                 b += __shfl_xor_sync(0xffffffffu, b, o);
