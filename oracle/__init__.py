@@ -64,6 +64,10 @@ def lib():
                                            ctypes.c_uint32, _D, _D, _D, _I, _I, _D]
         _lib.oracle_fisher_score.argtypes = [ctypes.c_int] * 6 + [ctypes.c_uint64, ctypes.c_uint32,
                                              ctypes.c_uint32, _D, _D, _D, _I, _I, ctypes.c_int, _D]
+        _lib.oracle_pmmh_langevin.argtypes = [ctypes.c_int] * 6 + [ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_uint64, ctypes.c_uint32, _D, _D, ctypes.c_int,
+                                              _D, _D, _D, _D, _D, _D, ctypes.c_uint32, ctypes.c_int,
+                                              _D, _D, _I]
     return _lib
 
 
@@ -253,3 +257,25 @@ def fisher_score(model, theta, y, anc, sstar, *, m, M, dx=1, dy=1, seed=0, chain
     if rc:
         raise ValueError("oracle_fisher_score rejected its arguments")
     return out
+
+
+def pmmh_langevin(model, theta0, y, *, m, M, step, lo, hi, iters, mode=MODE_ADAPTIVE, tau=0.3, dx=1,
+                  dy=1, seed=0, chain=0, model_data=None, iter0=0, state_logz=float("nan"), state_grad=None):
+    """PMMH with the Langevin proposal driven by the Fisher score.  Returns dict with
+    theta[iters, d], logz[iters], n_accept and the final theta, log Z and score (for resume)."""
+    y = _f64(y)
+    T = len(y) // dy
+    th = _f64(theta0).copy()
+    d = len(th)
+    md = _model_data(model_data)
+    st = np.array([state_logz], dtype=np.float64)
+    g = np.zeros(d) if state_grad is None else _f64(state_grad).copy()
+    tr = np.zeros((iters, d))
+    lz = np.zeros(iters)
+    nacc = np.zeros(1, np.int32)
+    rc = lib().oracle_pmmh_langevin(model, dx, dy, m, M, T, mode, tau, seed, chain, _dp(md), _dp(y), d,
+                                    _dp(_f64(step)), _dp(_f64(lo)), _dp(_f64(hi)), _dp(th), _dp(st), _dp(g),
+                                    iter0, iters, _dp(tr), _dp(lz), _ip(nacc))
+    if rc:
+        raise ValueError("oracle_pmmh_langevin rejected its arguments")
+    return dict(theta=tr, logz=lz, n_accept=int(nacc[0]), theta_final=th, logz_final=float(st[0]), grad_final=g)

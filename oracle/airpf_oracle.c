@@ -789,3 +789,93 @@ int oracle_fisher_score(int model, int dx, int dy, int m, int M, int T, uint64_t
     free(xs); free(lw1); free(l); free(dl); free(dlp);
     return 0;
 }
+
+/* log Z and the Fisher score of one run at theta (the run's own lineage). */
+static int logz_and_score(int model, int dx, int dy, int m, int M, int T, int mode, double tau, uint64_t seed,
+                          uint32_t chain, uint32_t iter, const double* theta, const double* mdat, const double* y,
+                          int d_theta, double* lz, double* score)
+{
+    const int N = m * M;
+    int32_t* anc = malloc(sizeof(int32_t) * (size_t)T * N);
+    int32_t* sstar = malloc(sizeof(int32_t) * (size_t)T);
+    int rc = oracle_airpf(model, dx, dy, m, M, T, mode, tau, seed, chain, iter, theta, mdat, y, lz, NULL, anc,
+                          NULL, NULL, sstar, NULL, NULL);
+    if (!rc)
+        rc = oracle_fisher_score(model, dx, dy, m, M, T, seed, chain, iter, theta, mdat, y, anc, sstar, d_theta,
+                                 score);
+    free(anc);
+    free(sstar);
+    return rc;
+}
+
+/* Particle marginal Metropolis-Hastings with a Langevin proposal driven by the
+ * Fisher score g of each likelihood estimate:
+ *   theta'_d = theta_d + h_d^2 g_d(theta) / 2 + h_d eps_d   (h_d = step[d]; h_d = 0 keeps theta_d)
+ * accepted iff log u < log Z' - log Z + log q(theta | theta') - log q(theta' | theta),
+ * q the proposal's normal density (uniform box priors cancel inside the box).
+ * Streams as oracle_pmmh (kind MH: eps from sub 0, u from sub 1 word 0); the
+ * initial estimate (state_logz NaN) uses iter 0xffffffff and also sets state_grad. */
+int oracle_pmmh_langevin(int model, int dx, int dy, int m, int M, int T, int mode, double tau, uint64_t seed,
+                         uint32_t chain, const double* mdat, const double* y, int d_theta, const double* step,
+                         const double* lo, const double* hi, double* theta, double* state_logz,
+                         double* state_grad, uint32_t iter0, int iters, double* theta_out, double* logz_out,
+                         int32_t* n_accept)
+{
+    double prop[64], gp[64], eps[64];
+    if (d_theta < 1 || d_theta > 64) return 1;
+    int acc = 0;
+    if (isnan(*state_logz)) {
+        int rc = logz_and_score(model, dx, dy, m, M, T, mode, tau, seed, chain, 0xffffffffu, theta, mdat, y,
+                                d_theta, state_logz, state_grad);
+        if (rc) return rc;
+    }
+    for (int j = 0; j < iters; ++j) {
+        uint32_t it = iter0 + (uint32_t)j;
+        stream_id st = { seed, chain, it };
+        for (int b = 0; b < (d_theta + 1) / 2; ++b) {
+            uint32_t w[4];
+            draw(&st, (uint32_t)b, 0, KIND_MH, 0, w);
+            double a, c;
+            normal_pair(w[0], w[1], &a, &c);
+            eps[2 * b] = a;
+            if (2 * b + 1 < d_theta) eps[2 * b + 1] = c;
+        }
+        int inside = 1;
+        double lqf = 0.0;
+        for (int d = 0; d < d_theta; ++d) {
+            double h = step[d];
+            prop[d] = theta[d] + 0.5 * h * h * state_grad[d] + h * eps[d];
+            if (h > 0.0) {
+                lqf -= 0.5 * eps[d] * eps[d];
+                if (!(prop[d] >= lo[d] && prop[d] <= hi[d])) inside = 0;
+            }
+        }
+        if (inside && !oracle_model_valid(model, dx, prop)) inside = 0;
+        if (inside) {
+            double lz;
+            int rc = logz_and_score(model, dx, dy, m, M, T, mode, tau, seed, chain, it, prop, mdat, y, d_theta,
+                                    &lz, gp);
+            if (rc) return rc;
+            double lqr = 0.0;
+            for (int d = 0; d < d_theta; ++d) {
+                double h = step[d];
+                if (h > 0.0) {
+                    double e = (theta[d] - prop[d] - 0.5 * h * h * gp[d]) / h;
+                    lqr -= 0.5 * e * e;
+                }
+            }
+            uint32_t w[4];
+            draw(&st, 0, 0, KIND_MH, 1, w);
+            if (log(unif(w[0])) < lz - *state_logz + lqr - lqf) {
+                memcpy(theta, prop, sizeof(double) * d_theta);
+                memcpy(state_grad, gp, sizeof(double) * d_theta);
+                *state_logz = lz;
+                ++acc;
+            }
+        }
+        if (theta_out) memcpy(theta_out + (size_t)j * d_theta, theta, sizeof(double) * d_theta);
+        if (logz_out) logz_out[j] = *state_logz;
+    }
+    if (n_accept) *n_accept = acc;
+    return 0;
+}

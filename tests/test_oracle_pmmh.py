@@ -41,3 +41,31 @@ def test_pmmh_resume_is_exact():
                      state_logz=h1["logz_final"], **kw)
     assert np.array_equal(full["theta"], np.concatenate([h1["theta"], h2["theta"]]))
     assert np.array_equal(full["logz"], np.concatenate([h1["logz"], h2["logz"]]))
+
+
+def test_langevin_pmmh_posterior_matches_quadrature():
+    """The Langevin proposal (driven by the Fisher score of each estimate) targets the same
+    posterior of the AR coefficient as quadrature of the Kalman likelihood under U(-1, 1)."""
+    y = synth.ar1_observations(100, seed=1)
+    _, _, mean, var = kalman.ar1_posterior_grid(y)
+    step = [0.06, 0, 0, 0]
+    lo, hi = [-1, 0, 0, 0], [1, 0, 0, 0]
+    r = oracle.pmmh_langevin(synth.MODEL_AR1, [0.5, 1.0, 1.0, 1.0], y, m=4, M=64, step=step, lo=lo, hi=hi,
+                             iters=1500, mode=oracle.MODE_ADAPTIVE, tau=0.3, seed=41)
+    a = r["theta"][300:, 0]
+    se = _batch_means_se(a)
+    assert abs(a.mean() - mean) < 4.5 * se + 1e-3, (a.mean(), mean, se)
+    assert 0.4 * var < a.var() < 2.5 * var
+    assert 0.1 < r["n_accept"] / 1500 < 0.99
+
+
+def test_langevin_pmmh_resume_is_exact():
+    y = synth.ar1_observations(30, seed=1)
+    kw = dict(m=4, M=16, step=[0.05, 0.05, 0, 0], lo=[-1, 0.1, 0, 0], hi=[1, 3, 0, 0],
+              mode=oracle.MODE_ALWAYS, seed=8, chain=5)
+    full = oracle.pmmh_langevin(synth.MODEL_AR1, [0.5, 1, 1, 1], y, iters=12, **kw)
+    h1 = oracle.pmmh_langevin(synth.MODEL_AR1, [0.5, 1, 1, 1], y, iters=6, **kw)
+    h2 = oracle.pmmh_langevin(synth.MODEL_AR1, h1["theta_final"], y, iters=6, iter0=6,
+                              state_logz=h1["logz_final"], state_grad=h1["grad_final"], **kw)
+    assert np.array_equal(full["theta"], np.concatenate([h1["theta"], h2["theta"]]))
+    assert np.array_equal(full["logz"], np.concatenate([h1["logz"], h2["logz"]]))
