@@ -235,7 +235,24 @@ def grad_leg(gp, torch, ws: int, passes: int = 2) -> dict:
     f.sync()
     ms = e0.elapsed_time(e1) / passes
     ms_fwd = e1.elapsed_time(e2) / passes
+    # Langevin-proposal PMMH on the 10 parameters (one gradient pass per iteration)
+    n_pm = 4
+    st_th, st_lz = th.clone(), torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    st_g = torch.zeros_like(th)
+    hstep = [0.002] * dx + [0.01, 0.01]
+    lo = list(synth.lg_theta(A, q=0.1, r=0.5) - 1.0)
+    hi = list(synth.lg_theta(A, q=0.1, r=0.5) + 1.0)
+    f.pmmh_langevin(y, st_th, st_lz, st_g, step=hstep, lo=lo, hi=hi, iters=1, iter0=0)
+    f.sync()
+    e3, e4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e3.record(f.stream)
+    pm = f.pmmh_langevin(y, st_th, st_lz, st_g, step=hstep, lo=lo, hi=hi, iters=n_pm, iter0=1)
+    e4.record(f.stream)
+    f.sync()
+    ms_pm = e3.elapsed_time(e4) / n_pm
     res = {"workload": "lgssm_dx8_dy4_m2048_M128_T200", "ms_per_eval": ms, "grad_evals_per_s": ws / (ms / 1e3),
+           "langevin_pmmh_iters_per_s": ws / (ms_pm / 1e3), "langevin_accepted": int(pm["n_accept"].item()),
+           "langevin_iters": n_pm,
            "forward_ms": ms_fwd, "backward_over_forward": (ms - ms_fwd) / ms_fwd, "ckpt": 10,
            "precision": "fp32", "score_norm": float(out["score"].norm()), "grad_norm": float(out["grad"].norm())}
     f.close()

@@ -266,6 +266,24 @@ airpf_status airpf_group_pmmh(airpf_group* g, const double* d_y, const double* s
                               double* const* d_theta_out, double* const* d_logz_out,
                               int32_t* const* d_n_accept);
 
+/* PMMH with a Langevin proposal (the differentiation workload's sampler; the
+ * paper's PMMH with a gradient-driven proposal): for a context created with
+ * AIRPF_RECORD_GRAD, each iteration proposes
+ *   theta'_d = theta_d + step_d^2 g_d(theta) / 2 + step_d eps_d,
+ * g the Fisher-identity score of the chain's current estimate (airpf_grad),
+ * runs the gradient pass at theta', and accepts iff
+ *   log u < log Z' - log Z + log q(theta | theta') - log q(theta' | theta)
+ * (q the proposal's normal density; uniform box priors [lo, hi] cancel inside
+ * the box; a proposal outside the box or the model's domain is rejected).
+ * eps and u come from the same kind-3 stream words as airpf_pmmh.
+ *   d_state_grad  [B * d_theta] in/out: score at the current theta; set by the
+ *                 initial estimate when d_state_logz is NaN
+ * The other arguments as for airpf_pmmh.  Asynchronous. */
+airpf_status airpf_pmmh_langevin(airpf_ctx* ctx, const double* d_y, const double* step, const double* lo,
+                                 const double* hi, double* d_state_theta, double* d_state_logz,
+                                 double* d_state_grad, uint32_t chain0, uint32_t iter0, int32_t iters,
+                                 double* d_theta_out, double* d_logz_out, int32_t* d_n_accept);
+
 /* airpf_sync of every member, then waits for `stream`. */
 airpf_status airpf_group_sync(airpf_group* g);
 

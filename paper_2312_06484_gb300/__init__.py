@@ -130,6 +130,30 @@ class AIRPF:
                        self.ctx)
         return out
 
+    def pmmh_langevin(self, y, state_theta, state_logz, state_grad, *, step, lo, hi, iters: int,
+                      chain0: int = 0, iter0: int = 0, n_accept=None, record: bool = True):
+        """PMMH with the Langevin proposal (airpf_pmmh_langevin; context with RECORD_GRAD).
+        state_theta [B, d], state_logz [B] (NaN: estimated first) and state_grad [B, d] are
+        float64 CUDA tensors updated in place."""
+        torch = self._torch
+        d = self.theta_dim
+        for t in (state_theta, state_logz, state_grad):
+            assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+        y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+        arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(d)) for v in (step, lo, hi)]
+        if n_accept is None:
+            n_accept = torch.zeros(self.B, dtype=torch.int32, device="cuda")
+        out = {"n_accept": n_accept}
+        if record:
+            out["theta"] = torch.empty((iters, self.B, d), dtype=torch.float64, device="cuda")
+            out["log_z"] = torch.empty((iters, self.B), dtype=torch.float64, device="cuda")
+        self._keep = (y, arrs)
+        _binding.check(self.lib.airpf_pmmh_langevin(
+            self.ctx, _ptr(y), *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs], _ptr(state_theta),
+            _ptr(state_logz), _ptr(state_grad), chain0, iter0, iters, _ptr(out.get("theta")),
+            _ptr(out.get("log_z")), _ptr(n_accept)), self.ctx)
+        return out
+
     def grad(self, theta, y, *, chain0: int = 0, iter: int = 0):
         """airpf_grad (context created with RECORD_GRAD): returns dict of CUDA tensors log_z [B],
         grad [B, d] (adjoint with the lineage held fixed) and score [B, d] (Fisher-identity

@@ -49,6 +49,8 @@ SIGNATURES = {
     "airpf_autotune": (c_int32, [ctypes.POINTER(AirpfConfig), c_void_p, c_size_t, c_void_p, c_void_p, c_void_p,
                                  c_int32, c_void_p, ctypes.POINTER(AirpfConfig), ctypes.POINTER(ctypes.c_float)]),
     "airpf_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint32, c_void_p, c_void_p, c_void_p]),
+    "airpf_pmmh_langevin": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_uint32, c_uint32, c_int32, c_void_p, c_void_p, c_void_p]),
     "airpf_sync": (c_int32, [c_void_p]),
     "airpf_launch_mode": (c_int32, [c_void_p]),
     "airpf_kernel_times": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),

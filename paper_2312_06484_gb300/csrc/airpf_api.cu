@@ -36,7 +36,7 @@ int ilog2_exact(int m)
 struct WsLayout {
     size_t run, theta, mdata, y, X[2], pe[2], pt[2], pq[2], csum, cup, nsrc, utg, ires[2], logz, trace, enf,
         sstar, anc, active, mpar, drift, bar;
-    size_t pm_prop, pm_logz_prop, pm_stats;
+    size_t pm_prop, pm_logz_prop, pm_stats, pm_gprop, pm_lqf;
     size_t xck, xblk, logw, gpi[2], xh[3], dh[3], gout, sout;   // gradient pass
     size_t total;
 };
@@ -147,6 +147,8 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.pm_prop = take(sizeof(double) * B * td);
     L.pm_logz_prop = take(sizeof(double) * B);
     L.pm_stats = take(sizeof(int) * B);
+    L.pm_gprop = take(sizeof(double) * B * td);
+    L.pm_lqf = take(sizeof(double) * B);
     L.xck = L.xblk = L.logw = L.gout = L.sout = 0;
     for (int i = 0; i < 3; ++i) L.xh[i] = L.dh[i] = 0;
     L.gpi[0] = L.gpi[1] = 0;
@@ -734,6 +736,73 @@ airpf_status airpf_pmmh(airpf_ctx* ctx, const double* d_y, const double* step, c
         if (e != cudaSuccess) return cuda_fail(ctx, e, "PMMH acceptance launch");
         ctx->launches += 2;
     }
+    return AIRPF_OK;
+}
+
+airpf_status airpf_pmmh_langevin(airpf_ctx* ctx, const double* d_y, const double* step, const double* lo,
+                                 const double* hi, double* d_state_theta, double* d_state_logz,
+                                 double* d_state_grad, uint32_t chain0, uint32_t iter0, int32_t iters,
+                                 double* d_theta_out, double* d_logz_out, int32_t* d_n_accept)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    const airpf_config& c = ctx->cfg;
+    if (!ctx->sp.grad) {
+        set_err(ctx, "the Langevin proposal needs a context created with AIRPF_RECORD_GRAD");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    if (!d_y || !step || !lo || !hi || !d_state_theta || !d_state_logz || !d_state_grad || !d_n_accept) {
+        set_err(ctx, "y, step, lo, hi, state_theta, state_logz, state_grad and n_accept are required");
+        return AIRPF_ERR_ARG;
+    }
+    if (iters < 0 || (uint64_t)chain0 + (uint64_t)c.B > (1u << 24) ||
+        (uint64_t)iter0 + (uint64_t)iters > 0xffffffffull) {
+        set_err(ctx, "iters >= 0, chain0 + B <= 2^24 and iter0 + iters < 2^32 - 1 are required");
+        return AIRPF_ERR_ARG;
+    }
+    const int td = ctx->theta_dim;
+    airpf::PmmhParams q;
+    std::memset(&q, 0, sizeof(q));
+    q.B = c.B;
+    q.theta_dim = td;
+    q.model = c.model;
+    q.dx = c.dx;
+    q.seed_lo = (uint32_t)(c.seed & 0xffffffffu);
+    q.seed_hi = (uint32_t)(c.seed >> 32);
+    q.chain0 = chain0;
+    for (int d = 0; d < td; ++d) {
+        if (!(step[d] >= 0.0) || (step[d] > 0.0 && !(lo[d] <= hi[d]))) {
+            set_err(ctx, "component %d: step must be >= 0 and lo <= hi", d);
+            return AIRPF_ERR_ARG;
+        }
+        q.step[d] = step[d];
+        q.lo[d] = lo[d];
+        q.hi[d] = hi[d];
+    }
+    q.theta = at<double>(ctx, ctx->L.pm_prop);          // the proposals, input of each gradient pass
+    q.logz = at<double>(ctx, ctx->L.pm_logz_prop);
+    q.active = at<int>(ctx, ctx->L.active);
+    q.state_theta = d_state_theta;
+    q.state_logz = d_state_logz;
+    q.n_accept = d_n_accept;
+    q.theta_out = d_theta_out;
+    q.logz_out = d_logz_out;
+    q.state_grad = d_state_grad;
+    q.gprop = at<double>(ctx, ctx->L.pm_gprop);
+    q.lqf = at<double>(ctx, ctx->L.pm_lqf);
+    int64_t launches = 0;
+    for (int64_t j = -1; j < iters; ++j) {
+        const int initial = j < 0;
+        const uint32_t it = initial ? 0xffffffffu : iter0 + (uint32_t)j;
+        cudaError_t e = airpf::launch_lmh_propose(q, it, initial, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "Langevin proposal launch");
+        airpf_status s = airpf_grad(ctx, q.theta, d_y, chain0, it, at<double>(ctx, ctx->L.pm_logz_prop), nullptr,
+                                    at<double>(ctx, ctx->L.pm_gprop));
+        if (s != AIRPF_OK) return s;
+        launches += ctx->launches + 2;
+        e = airpf::launch_lmh_accept(q, it, initial ? 0 : (int)j, initial, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "Langevin acceptance launch");
+    }
+    ctx->launches = launches;
     return AIRPF_OK;
 }
 

@@ -127,12 +127,19 @@ struct PmmhParams {
     int* n_accept;                       // [B]
     double* theta_out;                   // [iters][B][theta_dim] or NULL
     double* logz_out;                    // [iters][B] or NULL
+    // Langevin proposal: the score at the chain state and at the proposal, and
+    // log q(proposal | state) up to its constant
+    double* state_grad;                  // [B][theta_dim]
+    const double* gprop;                 // [B][theta_dim]
+    double* lqf;                         // [B]
 };
 
 // PMMH set-up of one pass (proposal, or the initial estimate of NaN log Z)
 // and its conclusion (accept/reject, outputs of iteration j).
 cudaError_t launch_pmmh_propose(const PmmhParams& q, uint32_t iter, int initial, cudaStream_t stream);
 cudaError_t launch_pmmh_accept(const PmmhParams& q, uint32_t iter, int j, int initial, cudaStream_t stream);
+cudaError_t launch_lmh_propose(const PmmhParams& q, uint32_t iter, int initial, cudaStream_t stream);
+cudaError_t launch_lmh_accept(const PmmhParams& q, uint32_t iter, int j, int initial, cudaStream_t stream);
 
 // Message for airpf_last_error(NULL) (calls without a context), printf-style.
 void set_create_error(const char* fmt, ...);

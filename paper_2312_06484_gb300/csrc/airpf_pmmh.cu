@@ -97,6 +97,108 @@ __global__ void pmmh_accept_kernel(PmmhParams q, uint32_t iter, int j, int initi
     if (q.logz_out) q.logz_out[(size_t)j * q.B + b] = q.state_logz[b];
 }
 
+// Langevin proposal for every chain b (the score g of the current estimate
+// drives it): theta'_d = theta_d + h_d^2 g_d / 2 + h_d eps_d, h_d = step[d]
+// (h_d = 0 keeps theta_d); eps from the same stream words as the random walk.
+// log q(theta' | theta) = -|eps|^2 / 2 (over the moving components, up to its
+// constant) goes to lqf[b].  A proposal outside the prior box or the model's
+// domain is marked inactive and the pass runs on the current theta instead.
+// initial: the pass estimates log Z and the score at the current theta.
+__global__ void lmh_propose_kernel(PmmhParams q, uint32_t iter, int initial)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= q.B) return;
+    const int td = q.theta_dim;
+    const double* cur = q.state_theta + (size_t)b * td;
+    const double* g = q.state_grad + (size_t)b * td;
+    double* prop = q.theta + (size_t)b * td;
+    if (initial) {
+        for (int d = 0; d < td; ++d) prop[d] = cur[d];
+        q.active[b] = isnan(q.state_logz[b]) ? 1 : 0;
+        return;
+    }
+    const Stream st{q.seed_lo, q.seed_hi, iter, (q.chain0 + (uint32_t)b) << 8};
+    bool inside = true;
+    double lqf = 0.0;
+    for (int pq = 0; 2 * pq < td; ++pq) {
+        const U4 w = st.draw((uint32_t)pq, 0u, KIND_MH, 0u);
+        double z[2];
+        normal_pair(w.x, w.y, z[0], z[1]);
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int d = 2 * pq + h2;
+            if (d >= td) break;
+            const double h = q.step[d];
+            prop[d] = cur[d] + 0.5 * h * h * g[d] + h * z[h2];
+            if (h > 0.0) {
+                lqf -= 0.5 * z[h2] * z[h2];
+                if (!(prop[d] >= q.lo[d] && prop[d] <= q.hi[d])) inside = false;
+            }
+        }
+    }
+    if (inside && !theta_in_domain(q.model, q.dx, prop)) inside = false;
+    if (!inside)
+        for (int d = 0; d < td; ++d) prop[d] = cur[d];
+    q.active[b] = inside ? 1 : 0;
+    q.lqf[b] = lqf;
+}
+
+// After the gradient pass at the proposals: the Metropolis-Hastings decision
+// with log q(theta | theta') from the proposal's score, or (initial) the first
+// estimate and score of chains whose log Z was NaN.
+__global__ void lmh_accept_kernel(PmmhParams q, uint32_t iter, int j, int initial)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= q.B) return;
+    const int td = q.theta_dim;
+    double* cur = q.state_theta + (size_t)b * td;
+    double* g = q.state_grad + (size_t)b * td;
+    const double* gp = q.gprop + (size_t)b * td;
+    if (initial) {
+        if (q.active[b]) {
+            q.state_logz[b] = q.logz[b];
+            for (int d = 0; d < td; ++d) g[d] = gp[d];
+        }
+        return;
+    }
+    if (q.active[b]) {
+        const double* prop = q.theta + (size_t)b * td;
+        double lqr = 0.0;
+        for (int d = 0; d < td; ++d) {
+            const double h = q.step[d];
+            if (h > 0.0) {
+                const double e = (cur[d] - prop[d] - 0.5 * h * h * gp[d]) / h;
+                lqr -= 0.5 * e * e;
+            }
+        }
+        const Stream st{q.seed_lo, q.seed_hi, iter, (q.chain0 + (uint32_t)b) << 8};
+        const U4 w = st.draw(0u, 0u, KIND_MH, 1u);
+        const double lz = q.logz[b];
+        if (log(unif_f64(w.x)) < lz - q.state_logz[b] + lqr - q.lqf[b]) {
+            for (int d = 0; d < td; ++d) {
+                cur[d] = prop[d];
+                g[d] = gp[d];
+            }
+            q.state_logz[b] = lz;
+            q.n_accept[b] += 1;
+        }
+    }
+    if (q.theta_out)
+        for (int d = 0; d < td; ++d) q.theta_out[((size_t)j * q.B + b) * td + d] = cur[d];
+    if (q.logz_out) q.logz_out[(size_t)j * q.B + b] = q.state_logz[b];
+}
+
+cudaError_t launch_lmh_propose(const PmmhParams& q, uint32_t iter, int initial, cudaStream_t stream)
+{
+    lmh_propose_kernel<<<(q.B + 127) / 128, 128, 0, stream>>>(q, iter, initial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lmh_accept(const PmmhParams& q, uint32_t iter, int j, int initial, cudaStream_t stream)
+{
+    lmh_accept_kernel<<<(q.B + 127) / 128, 128, 0, stream>>>(q, iter, j, initial);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pmmh_propose(const PmmhParams& q, uint32_t iter, int initial, cudaStream_t stream)
 {
     pmmh_propose_kernel<<<(q.B + 127) / 128, 128, 0, stream>>>(q, iter, initial);

@@ -111,3 +111,55 @@ def test_pmmh_fp32_chain_is_valid():
     assert np.all(np.isfinite(g["log_z"]))
     assert np.all(np.abs(g["theta"][:, 0, 0]) <= 1.0)
     assert 0 < g["n_accept"][0] < 60
+
+
+def _gpu_langevin(theta0, y, *, iters, splits=None, **kw):
+    import torch
+    import paper_2312_06484_gb300 as gp
+    f = gp.AIRPF(synth.MODEL_AR1, m=kw["m"], M=kw["M"], T=len(y), B=1, mode=kw["mode"], tau=kw["tau"],
+                 precision="fp64", seed=kw["seed"], record=gp.RECORD_GRAD)
+    th = torch.tensor(np.asarray(theta0, np.float64)[None, :], device="cuda")
+    lz = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    g = torch.zeros_like(th)
+    yy = torch.tensor(np.asarray(y, np.float64), device="cuda")
+    acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    thetas, logzs, it0 = [], [], 0
+    for n in (splits or [iters]):
+        out = f.pmmh_langevin(yy, th, lz, g, step=kw["step"], lo=kw["lo"], hi=kw["hi"], iters=n, iter0=it0,
+                              n_accept=acc)
+        thetas.append(out["theta"])
+        logzs.append(out["log_z"])
+        it0 += n
+    f.sync()
+    res = dict(theta=torch.cat(thetas).cpu().numpy()[:, 0, :], log_z=torch.cat(logzs).cpu().numpy()[:, 0],
+               n_accept=int(acc.item()))
+    f.close()
+    return res
+
+
+LANGEVIN = dict(m=8, M=32, mode="adaptive", tau=0.5, seed=13, step=[0.08, 0.05, 0.0, 0.0],
+                lo=[-1.0, 0.1, 0.0, 0.0], hi=[1.0, 3.0, 0.0, 0.0])
+
+
+def test_langevin_pmmh_chain_matches_oracle():
+    """FP64 Langevin chain on AR(1) (a and sigma_v move): the GPU's proposals use the GPU
+    score, the oracle's its own; both agree to rounding, so the chains take the same
+    decisions."""
+    y = synth.ar1_observations(30, seed=1)
+    theta0 = [0.5, 1.0, 1.0, 1.0]
+    g = _gpu_langevin(theta0, y, iters=10, **LANGEVIN)
+    kw = dict(LANGEVIN)
+    kw["mode"] = {"never": 0, "always": 1, "adaptive": 2}[kw["mode"]]
+    o = oracle.pmmh_langevin(synth.MODEL_AR1, theta0, y, iters=10, chain=0, **kw)
+    np.testing.assert_allclose(g["theta"], o["theta"], rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(g["log_z"], o["logz"], rtol=1e-7)
+    assert g["n_accept"] == o["n_accept"]
+    assert 0 < o["n_accept"] <= 10
+
+
+def test_langevin_pmmh_resume_is_exact():
+    y = synth.ar1_observations(30, seed=1)
+    full = _gpu_langevin([0.5, 1.0, 1.0, 1.0], y, iters=8, **LANGEVIN)
+    split = _gpu_langevin([0.5, 1.0, 1.0, 1.0], y, iters=8, splits=[3, 5], **LANGEVIN)
+    assert np.array_equal(full["theta"], split["theta"]) and np.array_equal(full["log_z"], split["log_z"])
+    assert full["n_accept"] == split["n_accept"]
