@@ -821,7 +821,7 @@ __global__ void airpf_prologue_kernel(StepParams p)
 // Step t for the G islands k0.. of filter c (see file comment).  Called by every
 // thread of the CTA; all barriers inside are CTA-uniform.
 // ---------------------------------------------------------------------------
-template <typename R, int MODEL, int DX, int PPT>
+template <typename R, int MODEL, int DX, int PPT, bool REC = true>
 __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int k0, unsigned char* smem,
                                           bool dep = false)
 {
@@ -959,7 +959,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     __syncthreads();
 
     // ---- lineage of step t-1: parent of particle (k, i) among time-(t-1) particles ----
-    if (p.anc != nullptr && t >= 2) {
+    if (REC && p.anc != nullptr && t >= 2) {
         const int* ires = p.ires[(t - 1) & 1] + (size_t)c * N;
         int* anc = p.anc + ((size_t)c * p.T + (t - 2)) * N;
         for (int q = tid; q < p.G * M; q += blockDim.x) {
@@ -1020,7 +1020,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             lv[r] = model_logg<R, MODEL, DX>(mp, yv, dx, p.dy, xv[r], Cm);
         }
     }
-    if (p.grad) {
+    if (REC && p.grad) {
         // states for the gradient pass: the prior draws x_0 (slot 0, at t = 1)
         // and the time-t particles at the checkpoints (every ckpt steps, and T)
         const int slot = (t % p.ckpt == 0) ? t / p.ckpt : (t == p.T ? p.nck - 1 : -1);
@@ -1094,7 +1094,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
 
     // multinomial draws: ancestor of draw j = first i with C_i > u_j C_{M-1}.
     // Fixed-depth branchless lower bound, the thread's draws advanced together.
-    int* ires_out = (p.ires[t & 1] != nullptr) ? p.ires[t & 1] + (size_t)c * N + (size_t)k * M : nullptr;
+    int* ires_out = (REC && p.ires[t & 1] != nullptr) ? p.ires[t & 1] + (size_t)c * N + (size_t)k * M : nullptr;
     Cdf target[PPT];
     int base[PPT];
 #pragma unroll
@@ -1178,7 +1178,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
         new_w[g] = w.bits;
         new_we[g] = w.e;
-        if (p.grad) {        // log W^k_{t,1} (the FP32-mixed weights leave out M^-t)
+        if (REC && p.grad) {        // log W^k_{t,1} (the FP32-mixed weights leave out M^-t)
             double lw = -INFINITY;
             if (w.bits != 0ull)
                 lw = FX ? log((double)w.bits) + (double)(w.e - 64) * 0.6931471805599453
@@ -1246,7 +1246,9 @@ static __device__ bool grid_barrier(unsigned* bar, unsigned* err)
     return s_ok != 0;
 }
 
-template <typename R, int MODEL, int DX, int PPT>
+// REC = false: a leaner instantiation for passes that record no lineage and
+// keep nothing for the gradient (shorter instruction stream)
+template <typename R, int MODEL, int DX, int PPT, bool REC>
 __global__ void __launch_bounds__(kMaxThreads, kMinCtasPerSm) airpf_step_kernel(StepParams p, int t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1254,7 +1256,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinCtasPerSm) airpf_step_kernel(
     const int c = blockIdx.x / cpf;
     const int k0 = (blockIdx.x - c * cpf) * p.G;
     if (p.active != nullptr && p.active[c] == 0) return;   // uniform over the CTA
-    step_body<R, MODEL, DX, PPT>(p, t, c, k0, smem, p.pdl != 0);
+    step_body<R, MODEL, DX, PPT, REC>(p, t, c, k0, smem, p.pdl != 0);
 }
 
 // The cascade of step t: one CTA per filter.
@@ -1336,8 +1338,11 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     const int want = smem > 48 * 1024 ? (int)smem : 48 * 1024;
     if (op == OP_PREPARE) {
         // opt in to more than 48 KB of dynamic shared memory (outside any capture)
-        cudaError_t e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT>,
+        cudaError_t e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, true>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -1383,9 +1388,20 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     }
     // step 1 follows the prologue in plain stream order; later steps may start
     // launching while the previous cascade runs (programmatic dependent launch)
+    {
+        const bool rec = p.anc != nullptr || p.grad != 0 || p.ires[0] != nullptr;
+        if (rec) {
+            if (p.pdl && t >= 2)
+                return launch_dependent(airpf_step_kernel<R, MODEL, DX, PPT, true>, dim3(grid), dim3(block), smem,
+                                        stream, p, t);
+            airpf_step_kernel<R, MODEL, DX, PPT, true><<<grid, block, smem, stream>>>(p, t);
+            return cudaGetLastError();
+        }
+    }
     if (p.pdl && t >= 2)
-        return launch_dependent(airpf_step_kernel<R, MODEL, DX, PPT>, dim3(grid), dim3(block), smem, stream, p, t);
-    airpf_step_kernel<R, MODEL, DX, PPT><<<grid, block, smem, stream>>>(p, t);
+        return launch_dependent(airpf_step_kernel<R, MODEL, DX, PPT, false>, dim3(grid), dim3(block), smem, stream,
+                                p, t);
+    airpf_step_kernel<R, MODEL, DX, PPT, false><<<grid, block, smem, stream>>>(p, t);
     return cudaGetLastError();
 }
 
