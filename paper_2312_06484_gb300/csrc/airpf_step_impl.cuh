@@ -417,7 +417,9 @@ __device__ void own_outputs(const StepParams& p, int c, int tp, const Stream& st
     }
 }
 
-template <bool FX>
+// OWN: the result goes to the calling CTA's own islands (fused steps), so the
+// code that writes it for the next step's CTAs is compiled out
+template <bool FX, bool OWN = false>
 __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st, double* raw,
                             const CascadeOwn* own = nullptr, bool records = true)
 {
@@ -535,7 +537,7 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
                 Q[0] = q0;
                 cascade_records<FX>(p, c, tp, 1, tot, emax, Q);
             }
-            if (own != nullptr) {
+            if (OWN) {
                 own_outputs<FX>(p, c, tp, st, ut, false, 1, emax, *own);
                 return;
             }
@@ -706,7 +708,7 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     //    island's inherited block when any stage interacted
     const int ss = iscal[1];
     const int lvl = ss - 1;
-    if (own != nullptr) {
+    if (OWN) {
         own_outputs<FX>(p, c, tp, st, ut, false, ss, emax, *own);
         return;
     }
@@ -821,7 +823,9 @@ __global__ void airpf_prologue_kernel(StepParams p)
 // Step t for the G islands k0.. of filter c (see file comment).  Called by every
 // thread of the CTA; all barriers inside are CTA-uniform.
 // ---------------------------------------------------------------------------
-template <typename R, int MODEL, int DX, int PPT, bool REC = true>
+// LV: which launch the body serves, fixed at compile time for the per-step
+// kernels (1 fused steps, 2 split steps) or chosen at run time (0)
+template <typename R, int MODEL, int DX, int PPT, bool REC = true, int LV = 0>
 __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int k0, unsigned char* smem,
                                           bool dep = false)
 {
@@ -910,12 +914,12 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             own_src[gi] = k0 + gi;
         }
         if (designated && tid == 0 && p.enf) p.enf[(size_t)c * p.T * (p.S + 1)] = 1.0;
-    } else if (p.fused) {
+    } else if (LV == 1 || (LV == 0 && p.fused)) {
         // this CTA runs the cascade of step t-1 itself, from every CTA record of
         // the filter (the first CTA also writes log Z and the run's records)
         const CascadeOwn own{k0, own_w, own_we, own_src};
-        cascade_all<FX>(p, c, t - 1, st, tree, &own, designated);
-    } else if (p.split) {
+        cascade_all<FX, true>(p, c, t - 1, st, tree, &own, designated);
+    } else if (LV == 2 || (LV == 0 && p.split)) {
         // the cascade kernel of step t-1 left s*, the largest exponent and the
         // upper tree; this CTA derives its islands' weights and walks
         int* csum_sh = reinterpret_cast<int*>(scal) + 4;
@@ -1248,7 +1252,7 @@ static __device__ bool grid_barrier(unsigned* bar, unsigned* err)
 
 // REC = false: a leaner instantiation for passes that record no lineage and
 // keep nothing for the gradient (shorter instruction stream)
-template <typename R, int MODEL, int DX, int PPT, bool REC>
+template <typename R, int MODEL, int DX, int PPT, bool REC, int LV>
 __global__ void __launch_bounds__(kMaxThreads, kMinCtasPerSm) airpf_step_kernel(StepParams p, int t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1256,7 +1260,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinCtasPerSm) airpf_step_kernel(
     const int c = blockIdx.x / cpf;
     const int k0 = (blockIdx.x - c * cpf) * p.G;
     if (p.active != nullptr && p.active[c] == 0) return;   // uniform over the CTA
-    step_body<R, MODEL, DX, PPT, REC>(p, t, c, k0, smem, p.pdl != 0);
+    step_body<R, MODEL, DX, PPT, REC, LV>(p, t, c, k0, smem, p.pdl != 0);
 }
 
 // The cascade of step t: one CTA per filter.
@@ -1338,10 +1342,13 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     const int want = smem > 48 * 1024 ? (int)smem : 48 * 1024;
     if (op == OP_PREPARE) {
         // opt in to more than 48 KB of dynamic shared memory (outside any capture)
-        cudaError_t e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, true>,
+        cudaError_t e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, true, 0>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false>,
+            e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 2>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
@@ -1388,21 +1395,16 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     }
     // step 1 follows the prologue in plain stream order; later steps may start
     // launching while the previous cascade runs (programmatic dependent launch)
-    {
-        const bool rec = p.anc != nullptr || p.grad != 0 || p.ires[0] != nullptr;
-        if (rec) {
-            if (p.pdl && t >= 2)
-                return launch_dependent(airpf_step_kernel<R, MODEL, DX, PPT, true>, dim3(grid), dim3(block), smem,
-                                        stream, p, t);
-            airpf_step_kernel<R, MODEL, DX, PPT, true><<<grid, block, smem, stream>>>(p, t);
-            return cudaGetLastError();
-        }
-    }
-    if (p.pdl && t >= 2)
-        return launch_dependent(airpf_step_kernel<R, MODEL, DX, PPT, false>, dim3(grid), dim3(block), smem, stream,
-                                p, t);
-    airpf_step_kernel<R, MODEL, DX, PPT, false><<<grid, block, smem, stream>>>(p, t);
-    return cudaGetLastError();
+    // the lean instantiations (no recording, one launch form) where they apply
+    const bool rec = p.anc != nullptr || p.grad != 0 || p.ires[0] != nullptr;
+    auto go = [&](auto kernel) -> cudaError_t {
+        if (p.pdl && t >= 2) return launch_dependent(kernel, dim3(grid), dim3(block), smem, stream, p, t);
+        kernel<<<grid, block, smem, stream>>>(p, t);
+        return cudaGetLastError();
+    };
+    if (!rec && p.fused) return go(airpf_step_kernel<R, MODEL, DX, PPT, false, 1>);
+    if (!rec && p.split) return go(airpf_step_kernel<R, MODEL, DX, PPT, false, 2>);
+    return go(airpf_step_kernel<R, MODEL, DX, PPT, true, 0>);
 }
 
 // dispatch over model and particles per thread for one precision
