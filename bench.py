@@ -470,6 +470,38 @@ def run_gpu(args) -> None:
         dist.destroy_process_group()
 
 
+def run_profile_case(args) -> None:
+    """One workload for a profiler capture: the m = 65536 x M = 256 NGM pass (FP32, T = 20;
+    split steps), or the d_x = 8 gradient evaluation (T = 20).  Prints the time of the last
+    of --steps runs (a capture's timing is not a bench value)."""
+    import torch
+    import paper_2312_06484_gb300 as gp
+    T = 20
+    if args.profile_case == "ngm256":
+        f = gp.AIRPF(synth.MODEL_NGM, m=65536, M=256, T=T, B=1, mode="adaptive", tau=TAU, precision="fp32", seed=1)
+        y = torch.tensor(synth.ngm_observations(T, seed=5), device="cuda")
+        th = torch.tensor(synth.NGM_THETA[None, :], device="cuda")
+        run = lambda j: f.run(th, y, iter=j)
+    else:
+        dx, dy = 8, 4
+        A, C, md = synth.lg_model(dx, dy, seed=4)
+        th = torch.tensor(synth.lg_theta(A, q=0.1, r=0.5)[None, :], device="cuda")
+        y = torch.tensor(synth.lg_observations(A, C, 0.1, 0.5, T, seed=4), device="cuda")
+        f = gp.AIRPF(synth.MODEL_LGSSM, m=2048, M=128, T=T, B=1, dx=dx, dy=dy, mode="adaptive", tau=TAU,
+                     precision="fp32", seed=1, record=gp.RECORD_GRAD, model_data=md, ckpt=5)
+        run = lambda j: f.grad(th, y, iter=j)
+    ms = 0.0
+    for j in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(f.stream)
+        run(j)
+        e1.record(f.stream)
+        f.sync()
+        ms = e0.elapsed_time(e1)
+    print(json.dumps({"profile_case": args.profile_case, "T": T, "ms_last_run": ms}), flush=True)
+    f.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,6 +514,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-chains leg")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient leg")
     ap.add_argument("--no-ngm", action="store_true", help="skip the large NGM leg")
+    ap.add_argument("--profile-case", choices=["ngm256", "grad"], default=None,
+                    help="run one small workload for a profiler capture instead of the bench line")
     ap.add_argument("--launch", default="auto", choices=["auto", "steps", "split", "grid"])
     ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0: automatic)")
     ap.add_argument("--islands-per-cta", type=int, default=0, help="islands per CTA (0: automatic)")
@@ -490,6 +524,8 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case:
+        run_profile_case(args)
     else:
         run_gpu(args)
 

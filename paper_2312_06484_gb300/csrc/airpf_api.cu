@@ -396,6 +396,12 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     // 512 CTAs, where reading all CTA records in every CTA would cost more)
     if (ctx->launch == AIRPF_LAUNCH_AUTO)
         ctx->launch = p.P <= 512 ? AIRPF_LAUNCH_STEPS : AIRPF_LAUNCH_STEPS_SPLIT;
+    if (ctx->launch == AIRPF_LAUNCH_STEPS_SPLIT && cfg->islands_per_cta == 0) {
+        // split steps: 512-thread CTAs, so the one-CTA cascade reads half as many records
+        airpf::choose_mapping(cfg->m, cfg->M, p.fp64, cfg->ppt, 512 / p.tpi, &p.tpi, &p.ppt, &p.G);
+        p.P = cfg->m / p.G;
+        p.g = ilog2_exact(p.G);
+    }
     // per-step launches overlap each kernel's start with the previous one
     // (programmatic dependent launch); fused steps have no cascade kernel
     p.pdl = is_steps(ctx->launch) ? 1 : 0;

@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     __shared__ R yv[kMaxDy];
     __shared__ double red[2 * kMaxTheta][kGradThreads / 32];
     __shared__ R rmx[kGradThreads / 32];
-    __shared__ double rsum[kGradThreads / 32];
+    __shared__ R rsum[kGradThreads / 32];
     R* lsm = reinterpret_cast<R*>(gsm);                  // [M] log-weights of the island
     const int c = blockIdx.y, k = blockIdx.x;
     const int M = p.M, N = p.N, dx = p.dx, dy = p.dy, td = p.theta_dim;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     const double* dh_in = p.dh[t % 3] + (size_t)c * N;
     double* dh_out = p.dh[(t + 2) % 3] + (size_t)c * N;
     double* dh_zero = p.dh[(t + 1) % 3] + (size_t)c * N;
-    const double pik = p.gpi[t & 1][(size_t)c * p.m + k];
+    const R pik_r = (R)p.gpi[t & 1][(size_t)c * p.m + k];
 
     // island softmax of the log-weights
     R mx = (R)(-INFINITY);
@@ -216,14 +216,15 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     __syncthreads();
     mx = rmx[0];
     for (int w = 1; w < nw; ++w) mx = rmx[w] > mx ? rmx[w] : mx;
-    double sum = 0.0;
+    R sum = 0;
     if (mx > (R)(-INFINITY))
-        for (int i = tid; i < M; i += blockDim.x) sum += (double)exp(lsm[i] - mx);
+        for (int i = tid; i < M; i += blockDim.x) sum += exp(lsm[i] - mx);
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) rsum[warp] = sum;
     __syncthreads();
-    sum = 0.0;
+    sum = 0;
     for (int w = 0; w < nw; ++w) sum += rsum[w];
+    const R inv_sum = sum > (R)0 ? (R)1 / sum : (R)0;
 
     // per-thread sums in the pass's precision (a thread holds few particles),
     // the CTA and grid reductions in double
@@ -235,9 +236,9 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     }
     for (int i = tid; i < M; i += blockDim.x) {
         const int g = k * M + i;
-        const R wi = (sum > 0.0 && lsm[i] > (R)(-INFINITY)) ? (R)((double)exp(lsm[i] - mx) / sum) : (R)0;
-        const R lhat = (R)pik * wi;                                  // d log Z / d l_t(k,i)
-        const double delta_d = (t == p.T) ? pik * (double)wi : dh_in[g];   // descendant weight
+        const R wi = (lsm[i] > (R)(-INFINITY)) ? exp(lsm[i] - mx) * inv_sum : (R)0;
+        const R lhat = pik_r * wi;                                   // d log Z / d l_t(k,i)
+        const double delta_d = (t == p.T) ? (double)lhat : dh_in[g];      // descendant weight
         const R delta = (R)delta_d;
         const int par = parent_of(p, c, t, g);
         R x[DX], xp[DX], mu[DX];

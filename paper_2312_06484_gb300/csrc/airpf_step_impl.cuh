@@ -73,7 +73,8 @@ namespace {
 constexpr int kMaxThreads = 512;      // per-step and grid-persistent CTAs
 constexpr int kMaxCtaThreads = 512;   // a whole filter in one CTA
 constexpr int kMinCtasPerSm = 2;      // register budget: 64 per thread at 512 threads
-constexpr int kCascadeThreads = 256;  // the cascade kernel's CTA
+constexpr int kCascadeThreads = 1024; // the cascade kernel's CTA (split steps: one per filter)
+constexpr int kMaxWarps = 32;         // per-warp partial slots of the cascade
 constexpr int kDefaultThreads = 256;  // default CTA size of the per-step launch (measured best, fused steps)
 constexpr unsigned long long kWaitNs = 1000000000ull;   // bounded barrier wait: 1 s
 constexpr unsigned kSpinLimit = 1u << 26;               // iteration backstop
@@ -102,7 +103,7 @@ struct Layout {
 // partial sums [16 warps][kQw], per-level sums [kMaxStages], a few integers
 __host__ __device__ inline size_t cascade_slots(const StepParams& p)
 {
-    return (p.split ? 0 : 2 * (size_t)p.P) + 2 * (size_t)p.G + 16 * kQw + kMaxStages + 8 + 3 * 16;
+    return (p.split ? 0 : 2 * (size_t)p.P) + 2 * (size_t)p.G + kMaxWarps * kQw + kMaxStages + 8 + 3 * kMaxWarps;
 }
 
 __host__ __device__ inline Layout make_layout(const StepParams& p)
@@ -436,12 +437,12 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     const int uo = p.split ? 0 : 2 * P;
     V* ut = p.split ? reinterpret_cast<V*>(p.utg) + (size_t)c * 2 * P : reinterpret_cast<V*>(raw);
     Qt* Qw = reinterpret_cast<Qt*>(raw + uo + 2 * G);             // [nw][kQw]
-    Qt* Q = reinterpret_cast<Qt*>(raw + uo + 2 * G + 16 * kQw);   // [kMaxStages]
-    int* iscal = reinterpret_cast<int*>(raw + uo + 2 * G + 16 * kQw + kMaxStages);
-    double* wpart = raw + uo + 2 * G + 16 * kQw + kMaxStages + 8;     // [3][16] per-warp partials
+    Qt* Q = reinterpret_cast<Qt*>(raw + uo + 2 * G + kMaxWarps * kQw);   // [kMaxStages]
+    int* iscal = reinterpret_cast<int*>(raw + uo + 2 * G + kMaxWarps * kQw + kMaxStages);
+    double* wpart = raw + uo + 2 * G + kMaxWarps * kQw + kMaxStages + 8;     // [3][kMaxWarps] per-warp partials
     int* w_emax = reinterpret_cast<int*>(wpart);
-    V* w_tot = reinterpret_cast<V*>(wpart + 16);
-    Qt* w_q0 = reinterpret_cast<Qt*>(wpart + 32);
+    V* w_tot = reinterpret_cast<V*>(wpart + kMaxWarps);
+    Qt* w_q0 = reinterpret_cast<Qt*>(wpart + 2 * kMaxWarps);
 
     // 1. the lane's records (read once, all fields at once) and the largest
     //    exponent over the records with a nonzero top
