@@ -45,6 +45,7 @@ struct WsLayout {
 
 struct airpf_ctx {
     airpf_config cfg;
+    double md_host[airpf::kModelDataMax];   // LGSSM A and C (host copy, for the backward pass)
     int S, N, theta_dim;
     unsigned char* ws;
     size_t ws_bytes;
@@ -481,6 +482,7 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
 
     if (cfg->model == AIRPF_MODEL_LGSSM) {
         const size_t n = sizeof(double) * (size_t)(cfg->dx * cfg->dx + cfg->dy * cfg->dx);
+        std::memcpy(ctx->md_host, model_data, n);
         e = cudaMemcpyAsync(at<void>(ctx, L.mdata), model_data, n, cudaMemcpyDefault, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) {
@@ -612,7 +614,7 @@ airpf_status airpf_grad(airpf_ctx* ctx, const double* d_theta, const double* d_y
     if (!ctx->graph_bwd_ready) {
         cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
-        cudaError_t le = airpf::launch_grad_backward(ctx->sp, ctx->cap_stream);
+        cudaError_t le = airpf::launch_grad_backward(ctx->sp, ctx->md_host, ctx->cap_stream);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (le != cudaSuccess) {

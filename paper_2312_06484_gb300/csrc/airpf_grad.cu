@@ -54,25 +54,70 @@ __device__ __forceinline__ int parent_of(const StepParams& p, int c, int t, int 
     return t == 1 ? g : __ldcg(&p.anc[((size_t)c * p.T + (t - 2)) * p.N + g]);
 }
 
+// The LGSSM's A and C as a kernel parameter, rows padded to kMaxDx: with the
+// loops over rows and columns unrolled, every element is a constant operand
+// of its instruction (no load).
 template <typename R>
-__device__ void load_model_matrices(const StepParams& p, R* A, R* C)
+struct ModelMat {
+    R A[kMaxDx * kMaxDx];
+    R C[kMaxDy * kMaxDx];
+};
+
+// transition x = A parent + sqrt(q) z in the order of the forward pass's
+// model_transition (diagonal of A from theta), so recomputed states equal the
+// recorded ones
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ void transition_mm(const ModelPar<R>& mp, int dx, const R* xp, R* x, const ModelMat<R>& mm,
+                                              const R* z)
 {
-    const int dx = p.dx, dy = p.dy;
-    for (int q = threadIdx.x; q < dx * dx + dy * dx; q += blockDim.x) {
-        const R v = (R)p.mdata[q];
-        if (q < dx * dx) A[q] = v;
-        else C[q - dx * dx] = v;
+    if (MODEL == AR1) {
+        x[0] = mp.th[0] * xp[0] + mp.th[1] * z[0];
+    } else {
+#pragma unroll
+        for (int r = 0; r < DX; ++r) {
+            if (r < dx) {
+                R acc = 0;
+#pragma unroll
+                for (int cc = 0; cc < DX; ++cc)
+                    if (cc < dx) acc += ((r == cc) ? mp.th[r] : mm.A[r * kMaxDx + cc]) * xp[cc];
+                x[r] = acc + mp.c0 * z[r];
+            }
+        }
     }
+}
+
+// log g(y | x) in the order of the forward pass's model_logg
+template <typename R, int MODEL, int DX>
+__device__ __forceinline__ R logg_mm(const ModelPar<R>& mp, const R* y, int dx, int dy, const R* x,
+                                     const ModelMat<R>& mm)
+{
+    R l;
+    if (MODEL == AR1) {
+        const R e = (y[0] - x[0]) * mp.c1;
+        l = mp.c0 - (R)0.5 * e * e;
+    } else {
+        R ss = 0;
+#pragma unroll
+        for (int o = 0; o < kMaxDy; ++o) {
+            if (o < dy) {
+                R e = y[o];
+#pragma unroll
+                for (int cc = 0; cc < DX; ++cc)
+                    if (cc < dx) e -= mm.C[o * kMaxDx + cc] * x[cc];
+                ss += e * e;
+            }
+        }
+        l = mp.c2 - ss * mp.c1;
+    }
+    return (l > -INFINITY) ? l : (R)(-INFINITY);
 }
 
 // x_t of the particles between checkpoints: x_t(g) = f(x_{t-1}(parent), z_t(g))
 template <typename R, int MODEL, int DX>
-__global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, int t)
+__global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
+                                                              int t)
 {
-    __shared__ R Am[kMaxDx * kMaxDx + kMaxDy * kMaxDx];
     const int c = blockIdx.y;
-    if (MODEL == LGSSM) load_model_matrices<R>(p, Am, Am + p.dx * p.dx);
-    __syncthreads();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= p.N) return;
     const ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
@@ -87,7 +132,7 @@ __global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, int t
     for (int d = 0; d < DX; ++d) xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
     uint32_t w0, w2;
     model_step_noise<R, MODEL, DX>(st, (uint32_t)g, (uint32_t)t, dx, z, w0, w2);
-    model_transition<R, MODEL, DX>(mp, dx, xp, x, Am, z, w0);
+    transition_mm<R, MODEL, DX>(mp, dx, xp, x, mm, z);
 #pragma unroll
     for (int d = 0; d < DX; ++d)
         if (d < dx) xt[(size_t)d * N + g] = x[d];
@@ -146,8 +191,8 @@ __global__ void __launch_bounds__(256) grad_pi_step_kernel(StepParams p, int t)
 
 // mean of the transition from the parent, and its scale (z = (x - mean) / scale)
 template <typename R, int MODEL, int DX>
-__device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, const R* xp, const R* A, R* mu,
-                                                R& s)
+__device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, const R* xp, const ModelMat<R>& mm,
+                                                R* mu, R& s)
 {
     if (MODEL == AR1) {
         mu[0] = mp.th[0] * xp[0];
@@ -159,7 +204,7 @@ __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, c
                 R acc = 0;
 #pragma unroll
                 for (int cc = 0; cc < DX; ++cc)
-                    if (cc < dx) acc += ((r == cc) ? mp.th[r] : A[r * dx + cc]) * xp[cc];
+                    if (cc < dx) acc += ((r == cc) ? mp.th[r] : mm.A[r * kMaxDx + cc]) * xp[cc];
                 mu[r] = acc;
             }
         }
@@ -169,10 +214,10 @@ __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, c
 
 // Step t of the backward pass: one CTA per island.
 template <typename R, int MODEL, int DX>
-__global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p, int t)
+__global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
+                                                                   int t)
 {
     extern __shared__ __align__(16) unsigned char gsm[];
-    __shared__ R Am[kMaxDx * kMaxDx + kMaxDy * kMaxDx];
     __shared__ R yv[kMaxDy];
     __shared__ double red[2 * kMaxTheta][kGradThreads / 32];
     __shared__ R rmx[kGradThreads / 32];
@@ -181,10 +226,8 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     const int c = blockIdx.y, k = blockIdx.x;
     const int M = p.M, N = p.N, dx = p.dx, dy = p.dy, td = p.theta_dim;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    if (MODEL == LGSSM) load_model_matrices<R>(p, Am, Am + dx * dx);
     for (int o = tid; o < dy; o += blockDim.x) yv[o] = (R)p.y[(size_t)(t - 1) * dy + o];
     __syncthreads();
-    const R* Cm = Am + dx * dx;
     const ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
     const R* xt = xstate<R>(p, c, t);
     const R* xprev = xstate<R>(p, c, t - 1);
@@ -204,7 +247,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
         R x[DX];
 #pragma unroll
         for (int d = 0; d < DX; ++d) x[d] = (d < dx) ? xt[(size_t)d * N + g] : (R)0;
-        const R l = model_logg<R, MODEL, DX>(mp, yv, dx, dy, x, Cm);
+        const R l = logg_mm<R, MODEL, DX>(mp, yv, dx, dy, x, mm);
         lsm[i] = l;
         mx = l > mx ? l : mx;
     }
@@ -248,7 +291,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
             x[d] = (d < dx) ? xt[(size_t)d * N + g] : (R)0;
             xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
         }
-        transition_mean<R, MODEL, DX>(mp, dx, xp, Am, mu, s);
+        transition_mean<R, MODEL, DX>(mp, dx, xp, mm, mu, s);
         R xhat[DX], v[DX];
 #pragma unroll
         for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? xh_in[(size_t)d * N + g] : (R)0;
@@ -280,7 +323,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
                     R e = yv[o];
 #pragma unroll
                     for (int cc = 0; cc < DX; ++cc)
-                        if (cc < dx) e -= Cm[o * dx + cc] * x[cc];
+                        if (cc < dx) e -= mm.C[o * kMaxDx + cc] * x[cc];
                     ee[o] = e;
                     ss += e * e;
                 }
@@ -294,7 +337,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
                     R dl = 0;
 #pragma unroll
                     for (int o = 0; o < kMaxDy; ++o)
-                        if (o < dy) dl += Cm[o * dx + d] * ee[o];
+                        if (o < dy) dl += mm.C[o * kMaxDx + d] * ee[o];
                     xhat[d] += lhat * dl * inv_r;
                     const R zd = (x[d] - mu[d]) * inv_s;
                     ga[d] += xhat[d] * xp[d];                   // A_dd
@@ -313,7 +356,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
                 if (cc < dx) {
 #pragma unroll
                     for (int rr = 0; rr < DX; ++rr)
-                        if (rr < dx) v[cc] += ((rr == cc) ? mp.th[rr] : Am[rr * dx + cc]) * xhat[rr];
+                        if (rr < dx) v[cc] += ((rr == cc) ? mp.th[rr] : mm.A[rr * kMaxDx + cc]) * xhat[rr];
                 }
             }
         }
@@ -356,8 +399,17 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
 }
 
 template <typename R, int MODEL, int DX>
-cudaError_t backward_typed(const StepParams& p, cudaStream_t stream)
+cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStream_t stream)
 {
+    ModelMat<R> mm;
+    for (int i = 0; i < kMaxDx * kMaxDx; ++i) mm.A[i] = (R)0;
+    for (int i = 0; i < kMaxDy * kMaxDx; ++i) mm.C[i] = (R)0;
+    if (MODEL == LGSSM && host_md) {
+        for (int r = 0; r < p.dx; ++r)
+            for (int cc = 0; cc < p.dx; ++cc) mm.A[r * kMaxDx + cc] = (R)host_md[r * p.dx + cc];
+        for (int o = 0; o < p.dy; ++o)
+            for (int cc = 0; cc < p.dx; ++cc) mm.C[o * kMaxDx + cc] = (R)host_md[p.dx * p.dx + o * p.dx + cc];
+    }
     const size_t xbytes = (size_t)p.B * p.dx * p.N * sizeof(R);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemsetAsync(p.xh[i], 0, xbytes, stream);
@@ -374,9 +426,9 @@ cudaError_t backward_typed(const StepParams& p, cudaStream_t stream)
     for (int b = nb - 1; b >= 0 && e == cudaSuccess; --b) {
         const int lo = b * K + 1, hi = (b + 1) * K < p.T ? (b + 1) * K : p.T;
         for (int t = lo; t <= hi; ++t)
-            if (t % K != 0 && t != p.T) grad_recompute_kernel<R, MODEL, DX><<<pgrid, 256, 0, stream>>>(p, t);
+            if (t % K != 0 && t != p.T) grad_recompute_kernel<R, MODEL, DX><<<pgrid, 256, 0, stream>>>(p, mm, t);
         for (int t = hi; t >= lo; --t) {
-            grad_island_kernel<R, MODEL, DX><<<igrid, kGradThreads, smem, stream>>>(p, t);
+            grad_island_kernel<R, MODEL, DX><<<igrid, kGradThreads, smem, stream>>>(p, mm, t);
             if (t >= 2) grad_pi_step_kernel<<<bgrid, 256, 0, stream>>>(p, t);
         }
         e = cudaGetLastError();
@@ -385,10 +437,10 @@ cudaError_t backward_typed(const StepParams& p, cudaStream_t stream)
 }
 
 template <typename R>
-cudaError_t backward_r(const StepParams& p, cudaStream_t stream)
+cudaError_t backward_r(const StepParams& p, const double* host_md, cudaStream_t stream)
 {
-    if (p.model == AR1) return backward_typed<R, AR1, 1>(p, stream);
-    if (p.model == LGSSM) return backward_typed<R, LGSSM, kMaxDx>(p, stream);
+    if (p.model == AR1) return backward_typed<R, AR1, 1>(p, host_md, stream);
+    if (p.model == LGSSM) return backward_typed<R, LGSSM, kMaxDx>(p, host_md, stream);
     return cudaErrorInvalidValue;
 }
 
@@ -396,10 +448,10 @@ cudaError_t backward_r(const StepParams& p, cudaStream_t stream)
 
 bool grad_supported(int model) { return model == AR1 || model == LGSSM; }
 
-cudaError_t launch_grad_backward(const StepParams& p, cudaStream_t stream)
+cudaError_t launch_grad_backward(const StepParams& p, const double* host_md, cudaStream_t stream)
 {
     if (p.M * (p.fp64 ? 8 : 4) > 48 * 1024) return cudaErrorInvalidValue;
-    return p.fp64 ? backward_r<double>(p, stream) : backward_r<float>(p, stream);
+    return p.fp64 ? backward_r<double>(p, host_md, stream) : backward_r<float>(p, host_md, stream);
 }
 
 }  // namespace airpf
