@@ -135,7 +135,7 @@ typedef struct {
 #define AIRPF_RECORD_ENF 2
 #define AIRPF_RECORD_TRACE 4
 #define AIRPF_RECORD_TIMING 8   /* STEPS launch only: CUDA events around each kernel (airpf_kernel_times) */
-#define AIRPF_RECORD_GRAD 16    /* keep what airpf_grad's backward pass needs (AR1 and LGSSM) */
+#define AIRPF_RECORD_GRAD 16    /* keep what airpf_grad's backward pass needs (all models but TOY) */
 
 typedef struct airpf_ctx airpf_ctx;
 
@@ -307,7 +307,7 @@ airpf_status airpf_autotune(const airpf_config* cfg, void* d_workspace, size_t w
  * AIRPF_ERR_CUDA for a CUDA error. */
 airpf_status airpf_sync(airpf_ctx* ctx);
 
-/* Gradient of log Z^N_T with respect to theta for each filter (AR1 and LGSSM;
+/* Gradient of log Z^N_T with respect to theta for each filter (AR1, SV, NGM, LGSSM;
  * a context created with AIRPF_RECORD_GRAD).  Runs the pass (as airpf_run,
  * writing d_log_z), then a backward pass over t = T..1 that needs the pass's
  * lineage, s*, island log-weights and the states kept every `ckpt` steps

@@ -305,7 +305,7 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         return AIRPF_ERR_ARG;
     }
     if ((cfg->record & AIRPF_RECORD_GRAD) && !airpf::grad_supported(cfg->model)) {
-        set_err(nullptr, "the gradient pass supports the AR1 and LGSSM models");
+        set_err(nullptr, "the gradient pass supports the AR1, SV, NGM and LGSSM models");
         return AIRPF_ERR_UNSUPPORTED;
     }
     const WsLayout L = make_ws_layout(cfg);

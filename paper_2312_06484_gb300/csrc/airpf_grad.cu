@@ -70,8 +70,8 @@ template <typename R, int MODEL, int DX>
 __device__ __forceinline__ void transition_mm(const ModelPar<R>& mp, int dx, const R* xp, R* x, const ModelMat<R>& mm,
                                               const R* z)
 {
-    if (MODEL == AR1) {
-        x[0] = mp.th[0] * xp[0] + mp.th[1] * z[0];
+    if (MODEL != LGSSM) {
+        model_transition<R, MODEL, DX>(mp, dx, xp, x, nullptr, z, 0u);
     } else {
 #pragma unroll
         for (int r = 0; r < DX; ++r) {
@@ -91,11 +91,9 @@ template <typename R, int MODEL, int DX>
 __device__ __forceinline__ R logg_mm(const ModelPar<R>& mp, const R* y, int dx, int dy, const R* x,
                                      const ModelMat<R>& mm)
 {
+    if (MODEL != LGSSM) return model_logg<R, MODEL, DX>(mp, y, dx, dy, x, nullptr);
     R l;
-    if (MODEL == AR1) {
-        const R e = (y[0] - x[0]) * mp.c1;
-        l = mp.c0 - (R)0.5 * e * e;
-    } else {
+    {
         R ss = 0;
 #pragma unroll
         for (int o = 0; o < kMaxDy; ++o) {
@@ -120,7 +118,8 @@ __global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, const
     const int c = blockIdx.y;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= p.N) return;
-    const ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+    ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+    if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
     const RunParams run = *p.run;
     const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
     const int dx = p.dx, N = p.N;
@@ -197,6 +196,13 @@ __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, c
     if (MODEL == AR1) {
         mu[0] = mp.th[0] * xp[0];
         s = mp.th[1];
+    } else if (MODEL == SV) {
+        mu[0] = mp.th[0] + mp.th[1] * (xp[0] - mp.th[0]);
+        s = mp.th[2];
+    } else if (MODEL == NGM) {
+        const R v = xp[0];
+        mu[0] = (R)0.5 * v + (R)25 * v / ((R)1 + v * v) + mp.drift;
+        s = mp.c0;                       // sqrt(q)
     } else {
 #pragma unroll
         for (int r = 0; r < DX; ++r) {
@@ -228,7 +234,8 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int o = tid; o < dy; o += blockDim.x) yv[o] = (R)p.y[(size_t)(t - 1) * dy + o];
     __syncthreads();
-    const ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+    ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+    if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
     const R* xt = xstate<R>(p, c, t);
     const R* xprev = xstate<R>(p, c, t - 1);
     const size_t xo = (size_t)c * dx * N;
@@ -312,6 +319,49 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
                 const R x0 = xp[0];
                 ga[3] += v[0] * x0 / s0;
                 gs[3] += delta * (x0 * x0 / (s0 * s0) - (R)1) / s0;
+            }
+        } else if (MODEL == SV) {
+            // x = mu + phi (parent - mu) + sigma z;  l = -x/2 - y^2 e^-x / 2 + const
+            const R mu_ = mp.th[0], phi = mp.th[1], sg = mp.th[2];
+            const R zz = (x[0] - mu[0]) / sg;
+            xhat[0] += lhat * ((R)(-0.5) + (R)0.5 * yv[0] * yv[0] * exp(-x[0]));
+            ga[0] += xhat[0] * ((R)1 - phi);
+            ga[1] += xhat[0] * (xp[0] - mu_);
+            ga[2] += xhat[0] * zz;
+            v[0] = phi * xhat[0];
+            gs[0] += delta * zz * ((R)1 - phi) / sg;
+            gs[1] += delta * zz * (xp[0] - mu_) / sg;
+            gs[2] += delta * (zz * zz - (R)1) / sg;
+            if (t == 1) {                          // x_0 = mu + sigma (1 - phi^2)^-1/2 z_0
+                const R om = (R)1 - phi * phi;
+                const R sd0 = sg / sqrt(om);
+                const R z0 = (xp[0] - mu_) / sd0;
+                ga[0] += v[0];
+                ga[1] += v[0] * z0 * sd0 * phi / om;
+                ga[2] += v[0] * z0 * sd0 / sg;
+                gs[0] += delta * z0 / sd0;
+                gs[1] += delta * (z0 * z0 - (R)1) * phi / om;
+                gs[2] += delta * (z0 * z0 - (R)1) / sg;
+            }
+        } else if (MODEL == NGM) {
+            // x = p/2 + 25 p / (1 + p^2) + drift + sqrt(q) z;  l = -log(2 pi r)/2 - (y - x^2/20)^2 / (2 r)
+            const R q = mp.th[0], r = mp.th[1], p0 = mp.th[2];
+            const R sq = mp.c0;
+            const R zz = (x[0] - mu[0]) / sq;
+            const R e = yv[0] - x[0] * x[0] / (R)20;
+            const R dlr = (R)(-0.5) / r + e * e / ((R)2 * r * r);
+            xhat[0] += lhat * e * (x[0] / (R)10) / r;
+            ga[0] += xhat[0] * zz / ((R)2 * sq);
+            ga[1] += lhat * dlr;
+            const R pv = xp[0], den = (R)1 + pv * pv;
+            v[0] = xhat[0] * ((R)0.5 + (R)25 * ((R)1 - pv * pv) / (den * den));
+            gs[0] += delta * (zz * zz - (R)1) / ((R)2 * q);
+            gs[1] += delta * dlr;
+            if (t == 1) {                          // x_0 = sqrt(p0) z_0
+                const R sp0 = sqrt(p0);
+                const R z0 = pv / sp0;
+                ga[2] += v[0] * z0 / ((R)2 * sp0);
+                gs[2] += delta * (z0 * z0 - (R)1) / ((R)2 * p0);
             }
         } else {
             const R inv_r = (R)2 * mp.c1;          // c1 = 1/(2r)
@@ -440,13 +490,15 @@ template <typename R>
 cudaError_t backward_r(const StepParams& p, const double* host_md, cudaStream_t stream)
 {
     if (p.model == AR1) return backward_typed<R, AR1, 1>(p, host_md, stream);
+    if (p.model == SV) return backward_typed<R, SV, 1>(p, host_md, stream);
+    if (p.model == NGM) return backward_typed<R, NGM, 1>(p, host_md, stream);
     if (p.model == LGSSM) return backward_typed<R, LGSSM, kMaxDx>(p, host_md, stream);
     return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-bool grad_supported(int model) { return model == AR1 || model == LGSSM; }
+bool grad_supported(int model) { return model == AR1 || model == SV || model == NGM || model == LGSSM; }
 
 cudaError_t launch_grad_backward(const StepParams& p, const double* host_md, cudaStream_t stream)
 {

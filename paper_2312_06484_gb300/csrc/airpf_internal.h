@@ -106,7 +106,7 @@ bool persistent_grid_fits(const StepParams& p);
 int max_cta_threads();
 
 // The backward pass of the gradient (after a recorded forward pass), enqueued
-// on `stream`: AR1 and LGSSM only (host_md: the LGSSM's A then C, row-major).
+// on `stream`: every model but TOY (host_md: the LGSSM's A then C, row-major).
 // Zeroes its accumulators first.
 constexpr int kModelDataMax = 8 * 8 + 8 * 8;
 cudaError_t launch_grad_backward(const StepParams& p, const double* host_md, cudaStream_t stream);

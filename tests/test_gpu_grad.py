@@ -109,3 +109,19 @@ def test_fp32_score_estimates_the_kalman_score_lgssm_dx8():
     g64 = _gpu_grad(synth.MODEL_LGSSM, th, y, m=64, M=128, B=2, dx=dx, dy=dy, mode="adaptive", tau=0.3, seed=1,
                     precision="fp64", model_data=md)
     assert np.all(np.abs(g["grad"][:2] - g64["grad"]) <= 0.05 * np.abs(g64["grad"]) + 0.5)
+
+
+@pytest.mark.parametrize("model,theta,ymaker,tau", [
+    (synth.MODEL_SV, [-1.0, 0.9, 0.35], lambda T: synth.sv_observations(T, 2), 0.5),
+    (synth.MODEL_NGM, [10.0, 1.0, 5.0], lambda T: synth.ngm_observations(T, 5), 0.5),
+])
+def test_nonlinear_models_gradient_and_score_match_oracle(model, theta, ymaker, tau):
+    """SV (theta = mu, phi, sigma; the stationary prior depends on all three) and NGM
+    (theta = q, r, p0), FP64, against the oracle's references."""
+    y = ymaker(25)
+    th = np.asarray(theta, float)
+    B = 2
+    g = _gpu_grad(model, th, y, m=8, M=32, B=B, mode="adaptive", tau=tau, seed=6, chain0=1, iter=2)
+    checked = sum(_check_against_oracle(model, th, y, m=8, M=32, mode="adaptive", tau=tau, seed=6, chain=1 + b,
+                                        iter=2, g=g, b=b) for b in range(B))
+    assert checked >= 1
