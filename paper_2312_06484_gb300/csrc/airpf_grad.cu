@@ -23,8 +23,8 @@
 //
 // States between checkpoints are recomputed from the previous state, the
 // lineage and the regenerated transition noise.  Particle arithmetic and the
-// per-thread sums in the pass's precision R; smoothing weights, descendant
-// weights and the CTA and grid sums of the theta terms in double.
+// per-thread and per-warp sums in the pass's precision R; smoothing weights,
+// descendant weights and the CTA and grid sums of the theta terms in double.
 #include <climits>
 
 #include "airpf_device.cuh"
@@ -425,14 +425,14 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
 #pragma unroll
     for (int d = 0; d < kMaxTheta; ++d) {
         if (d < td) {
-            double a = (double)ga[d], b = (double)gs[d];
+            R a = ga[d], b = gs[d];          // warp sums in R, then double from the warp on
             for (int o = 16; o > 0; o >>= 1) {
                 a += __shfl_xor_sync(0xffffffffu, a, o);
                 b += __shfl_xor_sync(0xffffffffu, b, o);
             }
             if (lane == 0) {
-                red[d][warp] = a;
-                red[kMaxTheta + d][warp] = b;
+                red[d][warp] = (double)a;
+                red[kMaxTheta + d][warp] = (double)b;
             }
         }
     }
