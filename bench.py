@@ -445,11 +445,12 @@ def run_gpu(args) -> None:
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "airpf_step_kernel (+ airpf_cascade_kernel, one time step)",
+        "roofline": {"bound": "alu", "kernel": "airpf_step_kernel (one fused time step: cascade + island work)"
+                     if f.launch_mode == 1 else "airpf_step_kernel + airpf_cascade_kernel (one time step)",
                      "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                      "traffic": None, "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
                      "units_per_launch": M_ISL * M_PART, "launch_avg_us": step_us,
-                     "launch_avg_source": "timed region: pass time / T (both kernels of a step and the gaps)",
+                     "launch_avg_source": "timed region: pass time / T (the step's kernels and the gaps)",
                      "event_nodes": {"island_kernel_us": isl_us, "cascade_kernel_us": cas_us,
                                      "island_share": isl_us / (isl_us + cas_us), "passes": n_k,
                                      "ms_per_pass_with_event_nodes": pass_ms / n_k,
