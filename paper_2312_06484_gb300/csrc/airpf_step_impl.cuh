@@ -444,6 +444,16 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     V* w_tot = reinterpret_cast<V*>(wpart + kMaxWarps);
     Qt* w_q0 = reinterpret_cast<Qt*>(wpart + 2 * kMaxWarps);
 
+    // 0. (own islands) the CTA's own record, needed on the common path s* = 1,
+    //    loaded together with the other records
+    V own_leaf = (V)0;
+    int own_e = INT_MIN;
+    if (OWN && tid < G) {
+        const int jo = own->k0 >> g;
+        own_leaf = __ldcg(&pt[(size_t)jo * 2 * G + tid]);
+        own_e = __ldcg(&pe[jo]);
+    }
+
     // 1. the lane's records (read once, all fields at once) and the largest
     //    exponent over the records with a nonzero top
     constexpr int kRec = kCachedChunks;
@@ -539,7 +549,18 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
                 cascade_records<FX>(p, c, tp, 1, tot, emax, Q);
             }
             if (OWN) {
-                own_outputs<FX>(p, c, tp, st, ut, false, 1, emax, *own);
+                // s* = 1: every own island keeps its weight (level 0 of the own
+                // record, or the rescaled record top when the CTA is one island)
+                // and its block
+                if (tid < G) {
+                    XW w{0ull, 0};
+                    if (!dead && own_e != INT_MIN)
+                        w = g >= 1 ? C::weight(own_leaf, own_e - C::frac(p))
+                                   : C::weight(C::rescale(own_leaf, emax - own_e), emax - C::frac(p));
+                    own->w[tid] = w.bits;
+                    own->we[tid] = w.e;
+                    own->src[tid] = own->k0 + tid;
+                }
                 return;
             }
             if (tid == 0) {
