@@ -898,6 +898,15 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
     }
 
+    // the step's observation (and the LGSSM matrices): inputs that no kernel of
+    // the pass writes, loaded now so that their latency is off the critical path
+    if (t <= p.T) {
+        if (MODEL == LGSSM)
+            for (int q = tid; q < dx * dx + p.dy * dx; q += blockDim.x) mshared[q] = (R)p.mdata[q];
+        for (int q = tid; q < p.dy; q += blockDim.x)
+            mshared[dx * dx + p.dy * dx + q] = (R)p.y[(size_t)(t - 1) * p.dy + q];
+    }
+
     // ---- 2. everything below reads what earlier kernels of the pass wrote ----
     if (dep) {
         dependency_wait();
@@ -1003,14 +1012,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     R* mxr_all = reinterpret_cast<R*>(smem + L.island + L.mxr);
     const int nwi = (p.tpi + 31) >> 5;
 
-    R* Am = mshared;
+    R* Am = mshared;                 // filled before the dependency wait
     R* Cm = mshared + dx * dx;
     R* yv = Cm + p.dy * dx;
-    if (MODEL == LGSSM) {
-        for (int q = tid; q < dx * dx + p.dy * dx; q += blockDim.x) mshared[q] = (R)p.mdata[q];
-    }
-    for (int q = tid; q < p.dy; q += blockDim.x) yv[q] = (R)p.y[(size_t)(t - 1) * p.dy + q];
-    __syncthreads();     // also orders the cascade's smem reads before the island work reuses it
+    __syncthreads();     // orders those writes, and the cascade's smem reads before the island work reuses it
 
     const int par = own_src[g];
     Cdf* cdf = cdf_all + (size_t)g * M;
