@@ -13,7 +13,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libairpf.so")
-SOURCES = ["airpf_launch_f32.cu", "airpf_launch_f64.cu", "airpf_step.cu", "airpf_api.cu", "airpf_pmmh.cu", "airpf_static.cu", "airpf_group.cu", "airpf_grad.cu"]
+SOURCES = ["airpf_step.cu", "airpf_api.cu", "airpf_pmmh.cu", "airpf_static.cu", "airpf_group.cu", "airpf_grad.cu"]
+# the step kernels: airpf_launch_inst.cu compiled once per precision, model and
+# particles per thread
+INST_SOURCE = "airpf_launch_inst.cu"
+INST_UNITS = [(r, model, ppt) for r in ("float", "double") for model in ("AR1", "SV", "NGM", "LGSSM", "TOY")
+              for ppt in (2, 4)]
 HEADERS = ["airpf_device.cuh", "airpf_internal.h", "airpf_step_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -37,12 +42,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     deps_common = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(include, "airpf.h")]
     objs = []
     jobs = []
-    for src in SOURCES:
+    units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
+    units += [(INST_SOURCE, f"airpf_launch_{'f32' if r == 'float' else 'f64'}_{model.lower()}_ppt{ppt}.o",
+               [f"-DAIRPF_INST_R={r}", f"-DAIRPF_INST_MODEL={model}", f"-DAIRPF_INST_PPT={ppt}"])
+              for r, model, ppt in INST_UNITS]
+    for src, obj, defs in units:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        o = os.path.join(OUT_DIR, obj)
         objs.append(o)
         if force or _stale(o, [s] + deps_common):
-            cmd = [_nvcc(), *ARCH, *FLAGS, *extra_flags, "-I", include, "-c", s, "-o", o]
+            cmd = [_nvcc(), *ARCH, *FLAGS, *extra_flags, *defs, "-I", include, "-c", s, "-o", o]
             jobs.append(cmd)
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         results = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

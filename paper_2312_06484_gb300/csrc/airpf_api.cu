@@ -436,6 +436,9 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         delete ctx;
         return AIRPF_ERR_CUDA;
     }
+    // fused steps: the 128-register instantiation when the grid is one wave at its
+    // occupancy (measured faster there; on larger grids the halved occupancy costs more)
+    p.wide = (p.fused && airpf::wide_fused_fits(p)) ? 1 : 0;
     {
         unsigned zero[4] = {0, 0, 0, 0};
         e = cudaMemcpy(p.bar, zero, sizeof(zero), cudaMemcpyHostToDevice);

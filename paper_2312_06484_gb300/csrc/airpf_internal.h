@@ -46,6 +46,8 @@ struct StepParams {
     int pdl;                      // per-step launches: programmatic dependent launch
     int fused;                    // per-step launches: each CTA runs the previous step's cascade itself
     int split;                    // per-step launches with a cascade kernel that leaves the tree in utg
+    int wide;                     // fused steps: the instantiation with up to 128 registers a thread
+                                  // (taken when the whole grid is one wave at its occupancy)
     void* utg;                    // [B][2P] upper tree of the last cascade (split steps)
     // gradient pass (record AIRPF_RECORD_GRAD): states x_t at checkpoints
     // (slot 0 = x_0, slot t/ckpt, and slot nck-1 = x_T when T is no multiple
@@ -101,6 +103,9 @@ cudaError_t launch_persistent(const StepParams& p, bool grid, cudaStream_t strea
 
 // Whether every CTA of the grid-persistent launch can be resident at once.
 bool persistent_grid_fits(const StepParams& p);
+// can every CTA of a fused-steps grid be resident at once at the occupancy of
+// the 128-register instantiation?
+bool wide_fused_fits(const StepParams& p);
 
 // Largest CTA of the one-CTA-per-filter launch.
 int max_cta_threads();

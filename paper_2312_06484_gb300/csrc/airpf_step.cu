@@ -1,13 +1,34 @@
 // airpf_step.cu -- host-side entry points of the AIRPF step kernels: launch
-// geometry, shared-memory sizing, and dispatch to the per-precision
-// instantiations (airpf_launch_f32.cu, airpf_launch_f64.cu) of the templates in
-// airpf_step_impl.cuh.
+// geometry, shared-memory sizing, and dispatch to the instantiations
+// (airpf_launch_inst.cu) of the templates in airpf_step_impl.cuh.
 #include "airpf_step_impl.cuh"
 
 namespace airpf {
 
-cudaError_t dispatch_f32(const StepParams& p, int t, cudaStream_t stream, int op, int* fits);
-cudaError_t dispatch_f64(const StepParams& p, int t, cudaStream_t stream, int op, int* fits);
+// the instantiations compiled in airpf_launch_inst.cu, one object per triple
+#define AIRPF_EXTERN_DISPATCH(R, MODEL, PPT) \
+    extern template cudaError_t dispatch_inst<R, MODEL, PPT>(const StepParams&, int, cudaStream_t, int, int*);
+AIRPF_EXTERN_DISPATCH(float, AR1, 2)
+AIRPF_EXTERN_DISPATCH(float, AR1, 4)
+AIRPF_EXTERN_DISPATCH(float, SV, 2)
+AIRPF_EXTERN_DISPATCH(float, SV, 4)
+AIRPF_EXTERN_DISPATCH(float, NGM, 2)
+AIRPF_EXTERN_DISPATCH(float, NGM, 4)
+AIRPF_EXTERN_DISPATCH(float, LGSSM, 2)
+AIRPF_EXTERN_DISPATCH(float, LGSSM, 4)
+AIRPF_EXTERN_DISPATCH(float, TOY, 2)
+AIRPF_EXTERN_DISPATCH(float, TOY, 4)
+AIRPF_EXTERN_DISPATCH(double, AR1, 2)
+AIRPF_EXTERN_DISPATCH(double, AR1, 4)
+AIRPF_EXTERN_DISPATCH(double, SV, 2)
+AIRPF_EXTERN_DISPATCH(double, SV, 4)
+AIRPF_EXTERN_DISPATCH(double, NGM, 2)
+AIRPF_EXTERN_DISPATCH(double, NGM, 4)
+AIRPF_EXTERN_DISPATCH(double, LGSSM, 2)
+AIRPF_EXTERN_DISPATCH(double, LGSSM, 4)
+AIRPF_EXTERN_DISPATCH(double, TOY, 2)
+AIRPF_EXTERN_DISPATCH(double, TOY, 4)
+#undef AIRPF_EXTERN_DISPATCH
 
 // ---------------------------------------------------------------------------
 size_t step_smem_bytes(const StepParams& p) { return make_layout(p).total; }
@@ -42,58 +63,30 @@ void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, 
 
 int max_cta_threads() { return kMaxCtaThreads; }
 
-template <typename R, int MODEL, int DX>
-static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
+template <typename R, int MODEL>
+static cudaError_t dispatch_model(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
 {
-    const size_t smem = step_smem_bytes(p);
-    const int block = p.G * p.tpi;
-    const int grid = p.B * (p.m / p.G);
-    const int want = smem > 48 * 1024 ? (int)smem : 48 * 1024;
-    if (op == OP_PREPARE) {
-        // opt in to more than 48 KB of dynamic shared memory (outside any capture)
-        cudaError_t e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-        return e;
+    if (p.ppt == 2) return dispatch_inst<R, MODEL, 2>(p, t, stream, op, fits);
+    if (p.ppt == 4) return dispatch_inst<R, MODEL, 4>(p, t, stream, op, fits);
+    return cudaErrorInvalidValue;
+}
+
+template <typename R>
+static cudaError_t dispatch_typed(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
+{
+    switch (p.model) {
+    case AR1: return dispatch_model<R, AR1>(p, t, stream, op, fits);
+    case SV: return dispatch_model<R, SV>(p, t, stream, op, fits);
+    case NGM: return dispatch_model<R, NGM>(p, t, stream, op, fits);
+    case LGSSM: return dispatch_model<R, LGSSM>(p, t, stream, op, fits);
+    case TOY: return dispatch_model<R, TOY>(p, t, stream, op, fits);
     }
-    if (op == OP_FITS) {
-        // can every CTA of the grid-persistent kernel be resident at once?
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, airpf_persistent_kernel<R, MODEL, DX, true>,
-                                                              block, smem);
-        *fits = (e == cudaSuccess && block <= kMaxThreads && (long long)per_sm * sms >= grid) ? 1 : 0;
-        return e;
-    }
-    if (op == OP_PERSIST_GRID) {
-        StepParams q = p;
-        void* args[] = {&q};
-        return cudaLaunchCooperativeKernel((const void*)airpf_persistent_kernel<R, MODEL, DX, true>, dim3(grid),
-                                           dim3(block), args, smem, stream);
-    }
-    if (op == OP_PERSIST_CTA) {
-        airpf_persistent_kernel<R, MODEL, DX, false><<<grid, block, smem, stream>>>(p);
-        return cudaGetLastError();
-    }
-    if (t == 0) {
-        const int n = p.B > p.T ? p.B : p.T;
-        airpf_prologue_kernel<R, MODEL><<<(n + 127) / 128, 128, 0, stream>>>(p);
-        return cudaGetLastError();
-    }
-    airpf_step_kernel<R, MODEL, DX><<<grid, block, smem, stream>>>(p, t);
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 static cudaError_t dispatch(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
 {
-    return p.fp64 ? dispatch_f64(p, t, stream, op, fits) : dispatch_f32(p, t, stream, op, fits);
+    return p.fp64 ? dispatch_typed<double>(p, t, stream, op, fits) : dispatch_typed<float>(p, t, stream, op, fits);
 }
 
 cudaError_t prepare_step(const StepParams& p) { return dispatch(p, 0, nullptr, OP_PREPARE, nullptr); }
@@ -117,6 +110,12 @@ bool persistent_grid_fits(const StepParams& p)
 {
     int fits = 0;
     return dispatch(p, 0, nullptr, OP_FITS, &fits) == cudaSuccess && fits;
+}
+
+bool wide_fused_fits(const StepParams& p)
+{
+    int fits = 0;
+    return dispatch(p, 0, nullptr, OP_WIDE_FITS, &fits) == cudaSuccess && fits;
 }
 
 __global__ void set_run_kernel(RunParams* r, uint32_t iter, uint32_t chain0)

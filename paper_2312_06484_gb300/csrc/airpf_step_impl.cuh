@@ -1,5 +1,6 @@
 // airpf_step_impl.cuh -- the AIRPF time step on sm_103a (kernel templates;
-// instantiated per precision in airpf_launch_f32.cu / airpf_launch_f64.cu).
+// instantiated per precision, model and particles per thread in
+// airpf_launch_inst.cu).
 //
 // A pass of Algorithm 1 (Heine, arXiv 2312.06484, main loop) is a prologue
 // launch that derives every filter's model constants, then, for t = 1..T, an
@@ -814,7 +815,8 @@ __device__ void publish_record(const StepParams& p, int c, int t, int jo, const 
     if (lane == 0) p.pe[t & 1][(size_t)c * p.P + jo] = ej;
 }
 
-enum { OP_STEP = 0, OP_PREPARE = 1, OP_FITS = 2, OP_PERSIST_GRID = 3, OP_PERSIST_CTA = 4, OP_CASCADE = 5 };
+enum { OP_STEP = 0, OP_PREPARE = 1, OP_FITS = 2, OP_PERSIST_GRID = 3, OP_PERSIST_CTA = 4, OP_CASCADE = 5,
+       OP_WIDE_FITS = 6 };
 
 __host__ __device__ inline size_t cascade_smem_bytes(const StepParams& p) { return align16(sizeof(double) * cascade_slots(p)); }
 
@@ -945,7 +947,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             own_src[gi] = k0 + gi;
         }
         if (designated && tid == 0 && p.enf) p.enf[(size_t)c * p.T * (p.S + 1)] = 1.0;
-    } else if (LV == 1 || (LV == 0 && p.fused)) {
+    } else if (LV == 1 || LV == 3 || (LV == 0 && p.fused)) {
         // this CTA runs the cascade of step t-1 itself, from every CTA record of
         // the filter (the first CTA also writes log Z and the run's records)
         const CascadeOwn own{k0, own_w, own_we, own_src};
@@ -1278,9 +1280,12 @@ static __device__ bool grid_barrier(unsigned* bar, unsigned* err)
 }
 
 // REC = false: a leaner instantiation for passes that record no lineage and
-// keep nothing for the gradient (shorter instruction stream)
+// keep nothing for the gradient (shorter instruction stream).  LV: 1 fused
+// steps, 2 split steps, 0 either (and the recording passes); 3 fused steps
+// with up to 128 registers a thread instead of 64 (no spills, half the resident
+// CTAs: for grids that are one wave either way)
 template <typename R, int MODEL, int DX, int PPT, bool REC, int LV>
-__global__ void __launch_bounds__(kMaxThreads, kMinCtasPerSm) airpf_step_kernel(StepParams p, int t)
+__global__ void __launch_bounds__(kMaxThreads, LV == 3 ? 1 : kMinCtasPerSm) airpf_step_kernel(StepParams p, int t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int cpf = p.m / p.G;                 // CTAs per filter
@@ -1378,6 +1383,9 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
             e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 2>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 3>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
         if (e == cudaSuccess)
@@ -1397,6 +1405,16 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
                                                               block, smem);
         *fits = (e == cudaSuccess && block <= kMaxThreads && (long long)per_sm * sms >= grid) ? 1 : 0;
+        return e;
+    }
+    if (op == OP_WIDE_FITS) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, airpf_step_kernel<R, MODEL, DX, PPT, false, 3>,
+                                                              block, smem);
+        *fits = (e == cudaSuccess && (long long)per_sm * sms >= grid) ? 1 : 0;
         return e;
     }
     if (op == OP_PERSIST_GRID) {
@@ -1429,33 +1447,18 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         kernel<<<grid, block, smem, stream>>>(p, t);
         return cudaGetLastError();
     };
-    if (!rec && p.fused) return go(airpf_step_kernel<R, MODEL, DX, PPT, false, 1>);
+    if (!rec && p.fused)
+        return p.wide ? go(airpf_step_kernel<R, MODEL, DX, PPT, false, 3>) : go(airpf_step_kernel<R, MODEL, DX, PPT, false, 1>);
     if (!rec && p.split) return go(airpf_step_kernel<R, MODEL, DX, PPT, false, 2>);
     return go(airpf_step_kernel<R, MODEL, DX, PPT, true, 0>);
 }
 
-// dispatch over model and particles per thread for one precision
-template <typename R>
-static cudaError_t dispatch_typed(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
+// the kernels of one precision, model and particles-per-thread count (one
+// explicit instantiation per triple in airpf_launch_inst.cu)
+template <typename R, int MODEL, int PPT>
+cudaError_t dispatch_inst(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
 {
-    if (p.ppt == 2) {
-        switch (p.model) {
-        case AR1: return launch_typed<R, AR1, 1, 2>(p, t, stream, op, fits);
-        case SV: return launch_typed<R, SV, 1, 2>(p, t, stream, op, fits);
-        case NGM: return launch_typed<R, NGM, 1, 2>(p, t, stream, op, fits);
-        case TOY: return launch_typed<R, TOY, 1, 2>(p, t, stream, op, fits);
-        case LGSSM: return launch_typed<R, LGSSM, kMaxDx, 2>(p, t, stream, op, fits);
-        }
-    } else if (p.ppt == 4) {
-        switch (p.model) {
-        case AR1: return launch_typed<R, AR1, 1, 4>(p, t, stream, op, fits);
-        case SV: return launch_typed<R, SV, 1, 4>(p, t, stream, op, fits);
-        case NGM: return launch_typed<R, NGM, 1, 4>(p, t, stream, op, fits);
-        case TOY: return launch_typed<R, TOY, 1, 4>(p, t, stream, op, fits);
-        case LGSSM: return launch_typed<R, LGSSM, kMaxDx, 4>(p, t, stream, op, fits);
-        }
-    }
-    return cudaErrorInvalidValue;
+    return launch_typed<R, MODEL, MODEL == LGSSM ? kMaxDx : 1, PPT>(p, t, stream, op, fits);
 }
 
 }  // namespace airpf

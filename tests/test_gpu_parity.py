@@ -159,3 +159,25 @@ def test_ngm_m65536_full_size_fp64():
     o = oracle.airpf(synth.MODEL_NGM, synth.NGM_THETA, y, m=m, M=M, mode=oracle.MODE_ADAPTIVE, tau=0.3, seed=1)
     upto = compare_filter(g, 0, o, m=m, what="NGM m=65536")
     assert upto >= 1
+
+
+@pytest.mark.parametrize("launch,B", [("steps", 1), ("steps", 3), ("split", 1)])
+def test_lean_passes_match_oracle(gpu_lib, launch, B):
+    """Passes that record nothing run the lean instantiations: fused steps with up to 128
+    registers a thread where the grid is one wave at that occupancy (B = 1 at m=1024 x
+    M=256), with 64 otherwise (B = 3), and split steps.  FP64 log Z against the oracle, and
+    equal, bit for bit, to the recording pass's; FP32 log Z independent of the batch size
+    (filter b draws the same numbers whichever instantiation runs it)."""
+    y = synth.sv_observations(1000, seed=2)[:6]
+    kw = dict(m=1024, M=256, mode="adaptive", tau=0.3, seed=9, launch=launch)
+    lean = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, B=B, record=0, **kw)
+    rec = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, B=B, record=7, **kw)
+    np.testing.assert_array_equal(lean["log_z"], rec["log_z"])
+    for b in range(B):
+        o = oracle.airpf(synth.MODEL_SV, synth.SV_THETA, y, m=1024, M=256, mode=oracle.MODE_ADAPTIVE, tau=0.3,
+                         seed=9, chain=b, record=False)
+        if o["tie"][0] == 0:
+            assert abs(float(lean["log_z"][b]) - o["log_z"]) <= 1e-10 * abs(o["log_z"]), (b, lean["log_z"][b])
+    f32_one = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, B=1, record=0, precision="fp32", **kw)
+    f32_many = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, B=3, record=0, precision="fp32", **kw)
+    assert f32_one["log_z"][0] == f32_many["log_z"][0]
