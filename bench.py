@@ -43,6 +43,14 @@ L2_FLUSH_BYTES = 256 << 20
 # integer prefix sum 10, CDF and particle stores 2, draw target 4, binary search over
 # M = 256 (8 levels x 7) 56, gather 4.
 OPS_PER_PARTICLE_STEP = 210
+# DRAM bytes (read + write) per launch of the fused SV step kernel
+# (airpf_step_kernel<float, SV, 1, 4, false, 3>), from one ncu capture with a cold cache:
+# dram__bytes_read.sum 1.158 MB, dram__bytes_write.sum 0.  Set to None when that kernel changes
+# until it is captured again.
+SV_STEP_DRAM_BYTES = 1158144
+SV_STEP_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
+                       "airpf_step_kernel<float, SV, 1, 4, false, 3>, cold cache "
+                       "(profiles/airpf_step_kernel_sv_m1024_M256_T1000.md)")
 SM_COUNT, LANES_PER_SM = 152, 128
 
 
@@ -448,7 +456,10 @@ def run_gpu(args) -> None:
         "roofline": {"bound": "alu", "kernel": "airpf_step_kernel (one fused time step: cascade + island work)"
                      if f.launch_mode == 1 else "airpf_step_kernel + airpf_cascade_kernel (one time step)",
                      "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None, "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
+                     "traffic": SV_STEP_DRAM_BYTES if f.launch_mode == 1 else None,
+                     "traffic_source": SV_STEP_DRAM_SOURCE if f.launch_mode == 1 else None,
+                     "algorithmic_bytes_per_launch": 8 * M_ISL * M_PART,
+                     "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
                      "units_per_launch": M_ISL * M_PART, "launch_avg_us": step_us,
                      "launch_avg_source": "timed region: pass time / T (the step's kernels and the gaps)",
                      "event_nodes": {"island_kernel_us": isl_us, "cascade_kernel_us": cas_us,
