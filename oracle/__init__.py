@@ -230,15 +230,23 @@ def logz_fixed(model, theta, y, anc, sstar, *, m, M, dx=1, dy=1, seed=0, chain=0
 
 
 def logz_fixed_gradient(model, theta, y, anc, sstar, *, h=1e-5, **kw) -> np.ndarray:
-    """Central differences of logz_fixed in every component of theta (step h max(1, |theta_d|))."""
+    """Gradient of logz_fixed in every component of theta: central differences D(h) and
+    D(h/2) (step h max(1, |theta_d|)) combined by one Richardson step, (4 D(h/2) - D(h)) / 3,
+    which cancels the h^2 term of the central-difference error (Richardson, 1911).  A
+    plain central difference at h = 1e-5 was off by 1e-4 relative on a nonlinear-growth
+    path whose log Z bends sharply in q."""
     th = _f64(theta).copy()
     g = np.zeros(len(th))
-    for d in range(len(th)):
-        hd = h * max(1.0, abs(th[d]))
+
+    def central(d, hd):
         tp, tm = th.copy(), th.copy()
         tp[d] += hd
         tm[d] -= hd
-        g[d] = (logz_fixed(model, tp, y, anc, sstar, **kw) - logz_fixed(model, tm, y, anc, sstar, **kw)) / (2 * hd)
+        return (logz_fixed(model, tp, y, anc, sstar, **kw) - logz_fixed(model, tm, y, anc, sstar, **kw)) / (2 * hd)
+
+    for d in range(len(th)):
+        hd = h * max(1.0, abs(th[d]))
+        g[d] = (4.0 * central(d, hd / 2) - central(d, hd)) / 3.0
     return g
 
 

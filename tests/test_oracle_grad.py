@@ -127,3 +127,27 @@ def test_fisher_score_estimates_the_kalman_score():
     mean = runs.mean(axis=0)
     se = runs.std(axis=0, ddof=1) / np.sqrt(len(runs))
     assert np.all(np.abs(mean - ref) < 4 * se + 0.05 * np.abs(ref) + 0.2), (mean, ref, se)
+
+
+def test_gradient_reference_converges_on_ngm():
+    """The gradient reference (central differences with one Richardson step at h = 1e-5)
+    equals plain central differences at a ten times smaller step on the nonlinear growth
+    model, whose log Z bends sharply in q: the reference carries no truncation error at the
+    1e-6 level the GPU comparison uses."""
+    y = synth.ngm_observations(25, 5)
+    th = np.array([10.0, 1.0, 5.0])
+    for chain in (1, 2):
+        kw = dict(m=8, M=32, seed=6, chain=chain, iter=2)
+        r = oracle.airpf(synth.MODEL_NGM, th, y, mode=oracle.MODE_ADAPTIVE, tau=0.5, **kw)
+        ref = oracle.logz_fixed_gradient(synth.MODEL_NGM, th, y, r["anc"], r["sstar"], **kw)
+        fine = np.zeros(3)
+        for d in range(3):
+            hd = 1e-6 * max(1.0, abs(th[d]))
+            tp, tm = th.copy(), th.copy()
+            tp[d] += hd
+            tm[d] -= hd
+            fine[d] = (oracle.logz_fixed(synth.MODEL_NGM, tp, y, r["anc"], r["sstar"], **kw)
+                       - oracle.logz_fixed(synth.MODEL_NGM, tm, y, r["anc"], r["sstar"], **kw)) / (2 * hd)
+        # the fine step's own rounding error: a few ulps of log Z over 1e-6
+        atol = 4 * np.finfo(float).eps * abs(r["log_z"]) / 1e-6
+        np.testing.assert_allclose(ref, fine, rtol=1e-7, atol=atol)
