@@ -151,6 +151,29 @@ __device__ __forceinline__ V warp_sum(V v)
     return v;
 }
 
+// max / sum over each aligned group of n lanes (n a power of 2, at most 32)
+template <typename V>
+__device__ __forceinline__ V group_max(V v, int n)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (o < n) {
+            const V w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = (w > v) ? w : v;
+        }
+    }
+    return v;
+}
+
+template <typename V>
+__device__ __forceinline__ V group_sum(V v, int n)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        if (o < n) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <typename V>
 __device__ __forceinline__ V warp_incl_scan(V v, int lane)
 {
@@ -782,7 +805,7 @@ __device__ void publish_record(const StepParams& p, int c, int t, int jo, const 
     const u64 b = has ? nw_bits[lane] : 0ull;
     const int e = has ? nw_e[lane] : INT_MIN;
     const bool ok = has && C::positive(b);
-    const int ej = warp_max(ok ? e : INT_MIN);
+    const int ej = group_max(ok ? e : INT_MIN, G);     // G <= 16: lanes G.. hold no island
     V v = (ok && ej != INT_MIN) ? C::leaf(b, e - ej, C::frac(p)) : (V)0;
     V* rec = reinterpret_cast<V*>(p.pt[t & 1]) + ((size_t)c * p.P + jo) * 2 * G;
     Qt* pq = reinterpret_cast<Qt*>(p.pq[t & 1]) + ((size_t)c * p.P + jo) * 8;
@@ -808,7 +831,7 @@ __device__ void publish_record(const StepParams& p, int c, int t, int jo, const 
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         if (l < g) {
-            const Qt s = warp_sum(q[l]);
+            const Qt s = group_sum(q[l], G);
             if (lane == 0) pq[l] = s;
         }
     }
@@ -1088,6 +1111,15 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     }
     const bool alive = (mx > (R)(-INFINITY));
 
+    // The CDF in shared memory, each 128-byte row of it XOR-swizzled by its row
+    // index: the binary search's probes at one depth share their low address
+    // bits (all are -1 modulo a power of 2), which would put them in one bank;
+    // the swizzle spreads them.  Only when M fills whole rows (islands stay
+    // row-aligned); a thread's PPT consecutive entries stay in one 16-byte group.
+    constexpr int kRowShift = sizeof(Cdf) == 4 ? 5 : 4;
+    const int rowmask = (M & ((1 << kRowShift) - 1)) == 0 ? (1 << kRowShift) - 1 : 0;
+    auto cdf_ix = [rowmask](int i) { return i ^ ((i >> kRowShift) & rowmask); };
+
     // weights and the thread-local inclusive prefix
     Cdf part[PPT];
     Cdf run_sum = 0;
@@ -1115,7 +1147,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     for (int r = 0; r < PPT; ++r) {
         const int i = li * PPT + r;
         if (i < M) {
-            cdf[i] = excl + part[r];
+            cdf[cdf_ix(i)] = excl + part[r];
 #pragma unroll
             for (int d = 0; d < DX; ++d)
                 if (d < dx) xs[(size_t)d * M + i] = xv[r][d];
@@ -1123,7 +1155,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     }
     if (nwi > 1) __syncthreads();       // an island of one warp needs only the warp
     else __syncwarp();
-    const Cdf total = cdf[M - 1];
+    const Cdf total = cdf[cdf_ix(M - 1)];
 
     // multinomial draws: ancestor of draw j = first i with C_i > u_j C_{M-1}.
     // Fixed-depth branchless lower bound, the thread's draws advanced together.
@@ -1140,7 +1172,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         const int half = n >> 1;
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
-            const Cdf v = cdf[base[r] + half - 1];
+            const Cdf v = cdf[cdf_ix(base[r] + half - 1)];
             base[r] = (v > target[r]) ? base[r] : base[r] + half;
         }
         n -= half;
