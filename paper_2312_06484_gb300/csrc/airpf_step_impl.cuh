@@ -151,6 +151,14 @@ __device__ __forceinline__ V warp_sum(V v)
     return v;
 }
 
+// Barrier of the nthreads threads (a multiple of 32) that execute it with this
+// id (1..15; id 0 is __syncthreads): the warps of one island sync among
+// themselves without waiting for the CTA's other islands.
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // max / sum over each aligned group of n lanes (n a power of 2, at most 32)
 template <typename V>
 __device__ __forceinline__ V group_max(V v, int n)
@@ -1102,9 +1110,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
 #pragma unroll
     for (int r = 1; r < PPT; ++r) mx = (lv[r] > mx) ? lv[r] : mx;
     mx = warp_max(mx);
+    // an island of several warps (then G <= 8) syncs on its own barrier 1 + g
     if (nwi > 1) {
         if (lane == 0) mxr[wi] = mx;
-        __syncthreads();
+        named_sync(1 + g, p.tpi);
         R v = mxr[0];
         for (int w = 1; w < nwi; ++w) v = (mxr[w] > v) ? mxr[w] : v;
         mx = v;
@@ -1138,7 +1147,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     Cdf excl = incl - run_sum;
     if (nwi > 1) {
         if (lane == 31) red[wi] = incl;
-        __syncthreads();
+        named_sync(1 + g, p.tpi);
         Cdf off = 0;
         for (int w = 0; w < wi; ++w) off += red[w];
         excl += off;
@@ -1153,7 +1162,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
                 if (d < dx) xs[(size_t)d * M + i] = xv[r][d];
         }
     }
-    if (nwi > 1) __syncthreads();       // an island of one warp needs only the warp
+    if (nwi > 1) named_sync(1 + g, p.tpi);    // an island of one warp needs only the warp
     else __syncwarp();
     const Cdf total = cdf[cdf_ix(M - 1)];
 
