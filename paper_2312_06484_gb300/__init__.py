@@ -322,7 +322,48 @@ def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: i
     return log_z
 
 
-__all__ = ["AIRPF", "AirpfError", "Group", "autotune", "theta_dim", "run_static", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
+_LOGZ_FUNCTION = None
+
+
+def _logz_function():
+    """The torch.autograd.Function behind log_z (defined on first use: torch is
+    imported lazily)."""
+    global _LOGZ_FUNCTION
+    if _LOGZ_FUNCTION is None:
+        import torch
+
+        class AirpfLogZ(torch.autograd.Function):
+            """log Z [B] of a context's filters as a function of theta [B, d]: the forward
+            pass is airpf_grad (the filter with its lineage, island choices and s* recorded,
+            then the adjoint with them held fixed), which keeps d log Z / d theta for the
+            backward pass; y and the stream identity are not differentiated."""
+
+            @staticmethod
+            def forward(ctx, theta, y, f, chain0, iter):
+                out = f.grad(theta, y, chain0=chain0, iter=iter)
+                ctx.theta_shape = theta.shape
+                ctx.theta_dtype = theta.dtype
+                ctx.save_for_backward(out["grad"])
+                return out["log_z"]
+
+            @staticmethod
+            def backward(ctx, g_logz):
+                (grad,) = ctx.saved_tensors
+                g = (g_logz.to(grad.dtype)[:, None] * grad).reshape(ctx.theta_shape).to(ctx.theta_dtype)
+                return g, None, None, None, None
+
+        _LOGZ_FUNCTION = AirpfLogZ
+    return _LOGZ_FUNCTION
+
+
+def log_z(f: AIRPF, theta, y, *, chain0: int = 0, iter: int = 0):
+    """Differentiable log Z [B] of context ``f`` (created with ``record=RECORD_GRAD``) at
+    theta [B, d] (or [d] for one filter): ``log_z(f, th, y).sum().backward()`` leaves the
+    adjoint gradient of each filter's log Z in ``th.grad``."""
+    return _logz_function().apply(theta, y, f, chain0, iter)
+
+
+__all__ = ["AIRPF", "AirpfError", "Group", "autotune", "theta_dim", "run_static", "log_z", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
            "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
            "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "RECORD_GRAD", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
            "LAUNCH_PERSISTENT_GRID", "LAUNCH_STEPS_SPLIT"]

@@ -125,3 +125,44 @@ def test_nonlinear_models_gradient_and_score_match_oracle(model, theta, ymaker, 
     checked = sum(_check_against_oracle(model, th, y, m=8, M=32, mode="adaptive", tau=tau, seed=6, chain=1 + b,
                                         iter=2, g=g, b=b) for b in range(B))
     assert checked >= 1
+
+
+def test_autograd_log_z_matches_gpu_finite_differences():
+    """log_z(...).backward() leaves the adjoint gradient in theta.grad; it equals central
+    differences of the GPU filter's own FP64 log Z at the same streams (a perturbation of
+    1e-6 changes no ancestor, island choice or s* here), and the oracle's gradient."""
+    import torch
+    import paper_2312_06484_gb300 as gp
+    y = synth.ar1_observations(30, seed=1)
+    th0 = np.array([0.85, 1.1, 0.9, 1.3])
+    kw = dict(m=8, M=32, T=len(y), B=1, mode="adaptive", tau=0.5, precision="fp64", seed=5)
+    f = gp.AIRPF(synth.MODEL_AR1, record=gp.RECORD_GRAD, **kw)
+    yy = torch.tensor(y, device="cuda")
+    th = torch.tensor(th0, device="cuda", requires_grad=True)
+    lz = gp.log_z(f, th, yy, chain0=3, iter=1)
+    lz.sum().backward()
+    f.sync()
+    g = th.grad.cpu().numpy()
+    f.close()
+    plain = gp.AIRPF(synth.MODEL_AR1, record=0, **kw)
+
+    def logz_at(v):
+        out = plain.run(torch.tensor(v[None, :], device="cuda"), yy, chain0=3, iter=1)
+        plain.sync()
+        return float(out["log_z"][0])
+
+    assert logz_at(th0) == float(lz.detach()[0])
+    fd = np.zeros(4)
+    for d in range(4):
+        h = 1e-6 * max(1.0, abs(th0[d]))
+        tp, tm = th0.copy(), th0.copy()
+        tp[d] += h
+        tm[d] -= h
+        fd[d] = (logz_at(tp) - logz_at(tm)) / (2 * h)
+    plain.close()
+    np.testing.assert_allclose(g, fd, rtol=1e-5, atol=1e-6)
+    r = oracle.airpf(synth.MODEL_AR1, th0, y, m=8, M=32, mode=oracle.MODE_ADAPTIVE, tau=0.5, seed=5, chain=3, iter=1)
+    if r["tie"][0] == 0:
+        ref = oracle.logz_fixed_gradient(synth.MODEL_AR1, th0, y, r["anc"], r["sstar"], m=8, M=32, seed=5, chain=3,
+                                         iter=1)
+        np.testing.assert_allclose(g, ref, rtol=1e-6, atol=1e-6 * (1 + np.abs(ref).max()))
