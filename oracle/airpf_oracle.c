@@ -21,6 +21,10 @@
  *   kind 2 ISLAND: time t, unit = island j, sub = interaction stage s; word 0
  *   kind 3 MH    : PMMH iteration `iter`, t = 0; sub 0 unit b -> proposal
  *                  normals 2b, 2b+1; sub 1 unit 0 word 0 -> accept uniform
+ *   change-point model (Beta draws): sub 0 words 0 (jump uniform, STEP only),
+ *                  1 and 3 (boosts of the two gammas), 2 (resampling uniform);
+ *                  gamma attempt j of X ~ Gamma(alpha) in sub 1 + 2j, of
+ *                  Y ~ Gamma(beta) in sub 2 + 2j (words 0, 1 normal, word 2 uniform)
  *   uniform(w)    = (w + 0.5) * 2^-32
  *   normals(w0,w1): r = sqrt(-2 ln u(w0)), a = 2 pi u(w1); (r cos a, r sin a)
  *   the normal of dimension d is component (d & 1) of pair b = d >> 1.
@@ -35,7 +39,10 @@
  *     {k, k xor 2^(s-1)} iff u * (W_lo + W_hi) < W_lo, one uniform per
  *     (t, s, k), independently over k (Section 3.3, eqs. (28)-(29));
  *   - adaptive interaction uses the strict test ENF < tau (Algorithm 1);
- *   - a NaN log-weight counts as -inf (weight zero).
+ *   - a NaN log-weight counts as -inf (weight zero);
+ *   - change-point model (Section 4.2): the daily count k_t of the n_t articles
+ *     is Binomial(n_t, x_t), y_t = (k_t, n_t); theta = (p, alpha, beta), p in
+ *     [0, 1] (p = 0 and p = 1 are the closed-form special cases).
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,7 +77,7 @@ void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
 }
 
 enum { KIND_INIT = 0, KIND_STEP = 1, KIND_ISLAND = 2, KIND_MH = 3 };
-enum { MODEL_AR1 = 0, MODEL_SV = 1, MODEL_NGM = 2, MODEL_LGSSM = 3, MODEL_TOY = 4 };
+enum { MODEL_AR1 = 0, MODEL_SV = 1, MODEL_NGM = 2, MODEL_LGSSM = 3, MODEL_TOY = 4, MODEL_CP = 5 };
 enum { MODE_NEVER = 0, MODE_ALWAYS = 1, MODE_ADAPTIVE = 2 };
 enum { TIE_NONE = 0, TIE_RESAMPLE = 1, TIE_ISLAND = 2, TIE_ENF = 3 };
 
@@ -143,12 +150,62 @@ int oracle_model_valid(int model, int dx, const double* th)
     case MODEL_NGM: return th[0] > 0 && th[1] > 0 && th[2] > 0;
     case MODEL_TOY: return th[0] > 0 && th[0] < 1 && th[1] > 0 && th[1] < 1;
     case MODEL_LGSSM: return isfinite(th[dx]) && isfinite(th[dx + 1]);
+    case MODEL_CP:  return th[0] >= 0 && th[0] <= 1 && th[1] > 0 && th[2] > 0;
     }
     return 0;
 }
 
+/* Gamma(a, 1) by the method of Marsaglia and Tsang (ACM TOMS 26(3), 2000): with
+ * a' = a (a >= 1, else a + 1), d = a' - 1/3 and c = 1/sqrt(9 d), an attempt takes
+ * a normal z and a uniform u, and with v = (1 + c z)^3 accepts d v if 1 + c z > 0
+ * and log u < z^2/2 + d - d v + d log v.  Attempt j reads sub-block first + 2j of
+ * the stream: the cosine normal of words 0 and 1, the uniform of word 2.  After
+ * GAMMA_TRIES rejections the draw is d (each attempt is accepted with probability
+ * above 0.95 for a' >= 1).  For a < 1 the draw is then scaled by U^(1/a), U from
+ * the word wboost (Marsaglia and Tsang's boost). */
+#define GAMMA_TRIES 15
+static double gamma_draw(const stream_id* s, uint32_t kind, uint32_t unit, uint32_t t, uint32_t first,
+                         double a, uint32_t wboost)
+{
+    double ap = a < 1.0 ? a + 1.0 : a;
+    double d = ap - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+    double g = d;
+    for (int j = 0; j < GAMMA_TRIES; ++j) {
+        uint32_t w[4];
+        double z, z1;
+        draw(s, unit, t, kind, first + 2u * (uint32_t)j, w);
+        normal_pair(w[0], w[1], &z, &z1);
+        double x1 = 1.0 + c * z;
+        if (x1 <= 0.0) continue;
+        double v = x1 * x1 * x1;
+        if (log(unif(w[2])) < 0.5 * z * z + d - d * v + d * log(v)) {
+            g = d * v;
+            break;
+        }
+    }
+    if (a < 1.0) g *= exp(log(unif(wboost)) / a);
+    return g;
+}
+
+/* Beta(alpha, beta) = X / (X + Y) with X ~ Gamma(alpha) from sub-blocks 1, 3, 5, ...
+ * and Y ~ Gamma(beta) from sub-blocks 2, 4, 6, ...; w0blk is sub-block 0, whose
+ * words 3 and 1 are the two boosts. */
+static double beta_draw(const stream_id* s, uint32_t kind, uint32_t unit, uint32_t t, double alpha,
+                        double beta, const uint32_t w0blk[4])
+{
+    double x = gamma_draw(s, kind, unit, t, 1u, alpha, w0blk[3]);
+    double y = gamma_draw(s, kind, unit, t, 2u, beta, w0blk[1]);
+    return x / (x + y);
+}
+
 static void prior_sample(const model_t* md, const stream_id* s, uint32_t unit, double* x)
 {
+    if (md->model == MODEL_CP) {            /* x_0 ~ Beta(alpha, beta) */
+        uint32_t w[4];
+        draw(s, unit, 0, KIND_INIT, 0, w);
+        x[0] = beta_draw(s, KIND_INIT, unit, 0, md->th[1], md->th[2], w);
+        return;
+    }
     double z[64];
     uint32_t w0;
     int nz = md->model == MODEL_TOY ? 0 : md->dx;
@@ -169,6 +226,14 @@ static void prior_sample(const model_t* md, const stream_id* s, uint32_t unit, d
 static uint32_t transition(const model_t* md, const stream_id* s, uint32_t unit,
                            uint32_t t, const double* xp, double* x)
 {
+    if (md->model == MODEL_CP) {
+        /* K(x, .) = (1 - p) delta_x + p Beta(alpha, beta): the jump iff u(word 0) < p;
+         * word 2 is the internal-resampling uniform, as for every model */
+        uint32_t w[4];
+        draw(s, unit, t, KIND_STEP, 0, w);
+        x[0] = unif(w[0]) < md->th[0] ? beta_draw(s, KIND_STEP, unit, t, md->th[1], md->th[2], w) : xp[0];
+        return w[2];
+    }
     double z[64];
     uint32_t w0, w2;
     int nz = md->model == MODEL_TOY ? 0 : md->dx;
@@ -225,6 +290,13 @@ static double log_g(const model_t* md, const double* y, const double* x)
     case MODEL_TOY:
         l = (y[0] == x[0]) ? log(th[1]) : log(1.0 - th[1]);
         break;
+    case MODEL_CP: {                        /* y = (k, n): k ~ Binomial(n, x) */
+        double k = y[0], n = y[1];
+        l = lgamma(n + 1.0) - lgamma(k + 1.0) - lgamma(n - k + 1.0);
+        if (k > 0) l += k * log(x[0]);
+        if (n - k > 0) l += (n - k) * log1p(-x[0]);
+        break;
+    }
     case MODEL_LGSSM: {
         int dx = md->dx, dy = md->dy;
         const double* C = md->md + dx * dx;

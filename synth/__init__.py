@@ -29,18 +29,21 @@ from __future__ import annotations
 
 import numpy as np
 
-MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY = 0, 1, 2, 3, 4
+MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY, MODEL_CP = 0, 1, 2, 3, 4, 5
 MODEL_NAMES = {MODEL_AR1: "ar1", MODEL_SV: "sv", MODEL_NGM: "ngm",
-               MODEL_LGSSM: "lgssm", MODEL_TOY: "toy"}
+               MODEL_LGSSM: "lgssm", MODEL_TOY: "toy", MODEL_CP: "changepoint"}
 
 AR1_THETA = np.array([0.9, 1.0, 1.0, 1.0])
 SV_THETA = np.array([-1.0, 0.95, 0.3])
 NGM_THETA = np.array([10.0, 1.0, 5.0])
 TOY_THETA = np.array([0.75, 0.75])
+# change-point model (p, alpha, beta): a jump every 50 days on average to a rate drawn from
+# Beta(2, 20) (mean 0.09)
+CP_THETA = np.array([0.02, 2.0, 20.0])
 
 
 def theta_dim(model: int, dx: int = 1) -> int:
-    return {MODEL_AR1: 4, MODEL_SV: 3, MODEL_NGM: 3, MODEL_TOY: 2}.get(model, dx + 2)
+    return {MODEL_AR1: 4, MODEL_SV: 3, MODEL_NGM: 3, MODEL_TOY: 2, MODEL_CP: 3}.get(model, dx + 2)
 
 
 def ar1_observations(T: int, seed: int = 1, theta=AR1_THETA) -> np.ndarray:
@@ -115,6 +118,23 @@ def toy_observations(T: int, seed: int = 3, theta=TOY_THETA) -> np.ndarray:
     return y
 
 
+def cp_observations(T: int, seed: int = 6, theta=CP_THETA, n_lo: int = 400, n_hi: int = 1200) -> np.ndarray:
+    """Synthetic daily counts for the change-point model: n_t articles a day, uniform on
+    [n_lo, n_hi], of which k_t ~ Binomial(n_t, x_t) carry the keyword; x_0 ~ Beta(alpha, beta),
+    and each day x jumps with probability p to a fresh Beta(alpha, beta) draw.  Returns
+    (k_1, n_1, k_2, n_2, ...) (d_y = 2)."""
+    p, a, b = (float(v) for v in theta)
+    rng = np.random.default_rng(seed)
+    x = rng.beta(a, b)
+    y = np.empty((T, 2))
+    for t in range(T):
+        if rng.random() < p:
+            x = rng.beta(a, b)
+        n = int(rng.integers(n_lo, n_hi + 1))
+        y[t] = (rng.binomial(n, x), n)
+    return y.ravel()
+
+
 def batched_sv_thetas(B: int, seed: int = 7) -> tuple[np.ndarray, int]:
     """theta_c ~ N((-1, .95, .3), diag(.1, .01, .05)^2), redrawn until |phi|<1, sigma>0.
 
@@ -149,4 +169,8 @@ WORKLOADS = {
                                 theta=SV_THETA, y=lambda: sv_observations(1000, 2)),
     "ngm_m65536_M256_T1000": dict(model=MODEL_NGM, dx=1, dy=1, m=65536, M=256, T=1000,
                                   theta=NGM_THETA, y=lambda: ngm_observations(1000, 5)),
+    "changepoint_m64_M200_T523": dict(model=MODEL_CP, dx=1, dy=2, m=64, M=200, T=523,
+                                      theta=CP_THETA, y=lambda: cp_observations(523, 6)),
+    "changepoint_m64_M500_T523": dict(model=MODEL_CP, dx=1, dy=2, m=64, M=500, T=523,
+                                      theta=CP_THETA, y=lambda: cp_observations(523, 6)),
 }
