@@ -62,13 +62,18 @@ typedef enum {
  *   SV    [mu, phi, sigma]
  *   NGM   [q, r, p0]                       (variances)
  *   LGSSM [A_11..A_dd, log q, log r]       model_data = A (dx*dx), C (dy*dx), row-major
- *   TOY   [p_stay, p_correct]              binary HMM of Section 4.1 */
+ *   TOY   [p_stay, p_correct]              binary HMM of Section 4.1
+ *   CP    [p, alpha, beta]                 change-point model of Section 4.2: x_0 ~ Beta(alpha,
+ *                                          beta), x jumps w.p. p to a fresh Beta(alpha, beta)
+ *                                          draw; y_t = (k_t, n_t), k_t ~ Binomial(n_t, x_t);
+ *                                          dx = 1, dy = 2; no gradient (the jump is discrete) */
 typedef enum {
     AIRPF_MODEL_AR1 = 0,
     AIRPF_MODEL_SV = 1,
     AIRPF_MODEL_NGM = 2,
     AIRPF_MODEL_LGSSM = 3,
-    AIRPF_MODEL_TOY = 4
+    AIRPF_MODEL_TOY = 4,
+    AIRPF_MODEL_CP = 5
 } airpf_model;
 
 /* Interaction rule of Algorithm 1, adaptation line: NEVER gives m independent
@@ -135,7 +140,7 @@ typedef struct {
 #define AIRPF_RECORD_ENF 2
 #define AIRPF_RECORD_TRACE 4
 #define AIRPF_RECORD_TIMING 8   /* STEPS launch only: CUDA events around each kernel (airpf_kernel_times) */
-#define AIRPF_RECORD_GRAD 16    /* keep what airpf_grad's backward pass needs (all models but TOY) */
+#define AIRPF_RECORD_GRAD 16    /* keep what airpf_grad's backward pass needs (all models but TOY and CP) */
 
 typedef struct airpf_ctx airpf_ctx;
 

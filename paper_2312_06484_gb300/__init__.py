@@ -15,7 +15,7 @@ import numpy as np
 from . import _binding
 from ._binding import AirpfConfig, AirpfError
 
-MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY = 0, 1, 2, 3, 4
+MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY, MODEL_CP = 0, 1, 2, 3, 4, 5
 NEVER, ALWAYS, ADAPTIVE = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
 RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE, RECORD_TIMING, RECORD_GRAD = 1, 2, 4, 8, 16
@@ -364,6 +364,6 @@ def log_z(f: AIRPF, theta, y, *, chain0: int = 0, iter: int = 0):
 
 
 __all__ = ["AIRPF", "AirpfError", "Group", "autotune", "theta_dim", "run_static", "log_z", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
-           "MODEL_TOY", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
+           "MODEL_TOY", "MODEL_CP", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
            "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "RECORD_GRAD", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
            "LAUNCH_PERSISTENT_GRID", "LAUNCH_STEPS_SPLIT"]

@@ -77,6 +77,7 @@ int theta_dim_of(int model, int dx)
     case AIRPF_MODEL_NGM: return 3;
     case AIRPF_MODEL_LGSSM: return dx + 2;
     case AIRPF_MODEL_TOY: return 2;
+    case AIRPF_MODEL_CP: return 3;
     }
     return 0;
 }
@@ -84,9 +85,11 @@ int theta_dim_of(int model, int dx)
 const char* check_config(const airpf_config* c)
 {
     if (!c) return "config is NULL";
-    if (c->model < 0 || c->model > 4) return "unknown model";
+    if (c->model < 0 || c->model > 5) return "unknown model";
     if (c->model == AIRPF_MODEL_LGSSM) {
         if (c->dx < 1 || c->dx > 8 || c->dy < 1 || c->dy > 8) return "LGSSM needs 1 <= dx, dy <= 8";
+    } else if (c->model == AIRPF_MODEL_CP) {
+        if (c->dx != 1 || c->dy != 2) return "the change-point model needs dx = 1, dy = 2 (y_t = (k_t, n_t))";
     } else if (c->dx != 1 || c->dy != 1) {
         return "scalar models need dx = dy = 1";
     }

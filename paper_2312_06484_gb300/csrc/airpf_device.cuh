@@ -12,7 +12,7 @@
 namespace airpf {
 
 enum Kind : uint32_t { KIND_INIT = 0, KIND_STEP = 1, KIND_ISLAND = 2, KIND_MH = 3 };
-enum Model : int { AR1 = 0, SV = 1, NGM = 2, LGSSM = 3, TOY = 4 };
+enum Model : int { AR1 = 0, SV = 1, NGM = 2, LGSSM = 3, TOY = 4, CP = 5 };
 
 constexpr int kMaxDx = 8;
 constexpr int kMaxDy = 8;
@@ -123,6 +123,14 @@ __device__ __forceinline__ void model_setup(ModelPar<R>& p, const double* theta,
         p.c0 = (R)(1.0 - theta[0]);
         p.c1 = (R)log(theta[1]);
         p.c2 = (R)log(1.0 - theta[1]);
+    } else if (MODEL == CP) {      // p, alpha, beta: the gamma draws' d and c for alpha and beta
+        const double aa = theta[1] < 1.0 ? theta[1] + 1.0 : theta[1];
+        const double bb = theta[2] < 1.0 ? theta[2] + 1.0 : theta[2];
+        const double da = aa - 1.0 / 3.0, db = bb - 1.0 / 3.0;
+        p.c0 = (R)da;
+        p.c1 = (R)(1.0 / sqrt(9.0 * da));
+        p.c2 = (R)db;
+        p.c3 = (R)(1.0 / sqrt(9.0 * db));
     } else {                       // LGSSM: sqrt(q), 1/(2r), -dy/2 log(2 pi r)
         const double r = exp(theta[dx + 1]);
         p.c0 = (R)sqrt(exp(theta[dx]));
@@ -167,11 +175,60 @@ __device__ __forceinline__ void stream_normals(const Stream& st, uint32_t kind, 
     }
 }
 
+template <typename R> __device__ __forceinline__ R unif_r(uint32_t w);
+template <> __device__ __forceinline__ double unif_r<double>(uint32_t w) { return unif_f64(w); }
+template <> __device__ __forceinline__ float unif_r<float>(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
+
+// Gamma(a, 1) by the method of Marsaglia and Tsang (ACM TOMS 26(3), 2000), with
+// d = a' - 1/3 and c = 1/sqrt(9 d), a' = a (a >= 1, else a + 1): an attempt
+// takes a normal z and a uniform u, v = (1 + c z)^3, and accepts d v if
+// 1 + c z > 0 and log u < z^2/2 + d - d v + d log v.  Attempt j reads
+// sub-block first + 2j of the stream (cosine normal of words 0 and 1, uniform
+// of word 2); after kGammaTries rejections the draw is d.  For a < 1 the draw
+// is scaled by U^(1/a), U from the word wboost.
+constexpr int kGammaTries = 15;
+
+template <typename R>
+__device__ R gamma_draw(const Stream& st, uint32_t kind, uint32_t unit, uint32_t t, uint32_t first, R a, R d,
+                        R c, uint32_t wboost)
+{
+    R g = d;
+    for (int j = 0; j < kGammaTries; ++j) {
+        const U4 b = st.draw(unit, t, kind, first + 2u * (uint32_t)j);
+        R z, z1;
+        normal_pair(b.x, b.y, z, z1);
+        const R x1 = (R)1 + c * z;
+        if (x1 <= (R)0) continue;
+        const R v = x1 * x1 * x1;
+        if (flog<R>(unif_r<R>(b.z)) < (R)0.5 * z * z + d - d * v + d * flog<R>(v)) {
+            g = d * v;
+            break;
+        }
+    }
+    if (a < (R)1) g *= fexp<R>(flog<R>(unif_r<R>(wboost)) / a);
+    return g;
+}
+
+// Beta(alpha, beta) = X / (X + Y): X ~ Gamma(alpha) from sub-blocks 1, 3, 5, ...,
+// Y ~ Gamma(beta) from 2, 4, 6, ...; b0 is sub-block 0, whose words 3 and 1 are
+// the two boosts.
+template <typename R>
+__device__ R beta_draw(const ModelPar<R>& p, const Stream& st, uint32_t kind, uint32_t unit, uint32_t t, const U4& b0)
+{
+    const R x = gamma_draw<R>(st, kind, unit, t, 1u, p.th[1], p.c0, p.c1, b0.w);
+    const R y = gamma_draw<R>(st, kind, unit, t, 2u, p.th[2], p.c2, p.c3, b0.y);
+    return x / (x + y);
+}
+
 // x_0 ~ pi_0
 template <typename R, int MODEL, int DX>
 __device__ __forceinline__ void model_prior(const ModelPar<R>& p, const Stream& st, uint32_t unit,
                                             int dx, R* x)
 {
+    if (MODEL == CP) {            // Beta(alpha, beta)
+        x[0] = beta_draw<R>(p, st, KIND_INIT, unit, 0u, st.draw(unit, 0u, KIND_INIT, 0));
+        return;
+    }
     R z[DX > 1 ? DX : 1];
     uint32_t w0, w2;
     stream_normals<R, (MODEL == TOY) ? 0 : DX>(st, KIND_INIT, unit, 0u, dx, z, w0, w2);
@@ -198,6 +255,7 @@ __device__ __forceinline__ void model_transition(const ModelPar<R>& p, int dx, c
         x[0] = (R)0.5 * v + (R)25 * v / ((R)1 + v * v) + p.drift + p.c0 * z[0];
     }
     if (MODEL == TOY) x[0] = (unif_f64(w0) < (double)p.c0) ? (R)1 - xp[0] : xp[0];
+    if (MODEL == CP) x[0] = (unif_f64(w0) < (double)p.th[0]) ? z[0] : xp[0];   // z: the jump's Beta draw
     if (MODEL == LGSSM) {
 #pragma unroll
         for (int r = 0; r < DX; ++r) {
@@ -214,10 +272,20 @@ __device__ __forceinline__ void model_transition(const ModelPar<R>& p, int dx, c
 
 // The step's random numbers of one unit: the transition normals z, word 0
 // (binary model) and word 2 (internal-resampling draw) of sub-block 0.
+// The change-point model draws its jump uniform (word 0) and, when it jumps
+// (u < p), the Beta draw into z[0].
 template <typename R, int MODEL, int DX>
-__device__ __forceinline__ void model_step_noise(const Stream& st, uint32_t unit, uint32_t t, int dx, R* z,
-                                                 uint32_t& w0, uint32_t& w2)
+__device__ __forceinline__ void model_step_noise(const ModelPar<R>& p, const Stream& st, uint32_t unit, uint32_t t,
+                                                 int dx, R* z, uint32_t& w0, uint32_t& w2)
 {
+    if (MODEL == CP) {
+        const U4 b = st.draw(unit, t, KIND_STEP, 0);
+        w0 = b.x;
+        w2 = b.z;
+        z[0] = (R)0;
+        if (unif_f64(b.x) < (double)p.th[0]) z[0] = beta_draw<R>(p, st, KIND_STEP, unit, t, b);
+        return;
+    }
     stream_normals<R, (MODEL == TOY) ? 0 : DX>(st, KIND_STEP, unit, t, dx, z, w0, w2);
 }
 
@@ -228,7 +296,7 @@ __device__ __forceinline__ uint32_t model_step(const ModelPar<R>& p, const Strea
 {
     R z[DX > 1 ? DX : 1];
     uint32_t w0, w2;
-    model_step_noise<R, MODEL, DX>(st, unit, t, dx, z, w0, w2);
+    model_step_noise<R, MODEL, DX>(p, st, unit, t, dx, z, w0, w2);
     model_transition<R, MODEL, DX>(p, dx, xp, x, A, z, w0);
     return w2;
 }
@@ -249,6 +317,11 @@ __device__ __forceinline__ R model_logg(const ModelPar<R>& p, const R* y, int dx
         l = p.c1 - e * e * p.c2;
     } else if (MODEL == TOY) {
         l = (y[0] == x[0]) ? p.c1 : p.c2;
+    } else if (MODEL == CP) {      // y = (k, n, log C(n, k)): k ~ Binomial(n, x)
+        const R k = y[0], nk = y[1] - y[0];
+        l = y[2];
+        if (k > (R)0) l += k * flog<R>(x[0]);
+        if (nk > (R)0) l += nk * log1p(-x[0]);
     } else {
         R ss = 0;
 #pragma unroll

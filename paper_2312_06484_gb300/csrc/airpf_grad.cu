@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, const
 #pragma unroll
     for (int d = 0; d < DX; ++d) xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
     uint32_t w0, w2;
-    model_step_noise<R, MODEL, DX>(st, (uint32_t)g, (uint32_t)t, dx, z, w0, w2);
+    model_step_noise<R, MODEL, DX>(mp, st, (uint32_t)g, (uint32_t)t, dx, z, w0, w2);
     transition_mm<R, MODEL, DX>(mp, dx, xp, x, mm, z);
 #pragma unroll
     for (int d = 0; d < DX; ++d)

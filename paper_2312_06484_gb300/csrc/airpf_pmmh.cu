@@ -26,6 +26,7 @@ __device__ bool theta_in_domain(int model, int dx, const double* th)
     case NGM: return th[0] > 0.0 && th[1] > 0.0 && th[2] > 0.0;
     case TOY: return th[0] > 0.0 && th[0] < 1.0 && th[1] > 0.0 && th[1] < 1.0;
     case LGSSM: return isfinite(th[dx]) && isfinite(th[dx + 1]);
+    case CP: return th[0] >= 0.0 && th[0] <= 1.0 && th[1] > 0.0 && th[2] > 0.0;
     }
     return false;
 }

@@ -18,6 +18,8 @@ AIRPF_EXTERN_DISPATCH(float, LGSSM, 2)
 AIRPF_EXTERN_DISPATCH(float, LGSSM, 4)
 AIRPF_EXTERN_DISPATCH(float, TOY, 2)
 AIRPF_EXTERN_DISPATCH(float, TOY, 4)
+AIRPF_EXTERN_DISPATCH(float, CP, 2)
+AIRPF_EXTERN_DISPATCH(float, CP, 4)
 AIRPF_EXTERN_DISPATCH(double, AR1, 2)
 AIRPF_EXTERN_DISPATCH(double, AR1, 4)
 AIRPF_EXTERN_DISPATCH(double, SV, 2)
@@ -28,6 +30,8 @@ AIRPF_EXTERN_DISPATCH(double, LGSSM, 2)
 AIRPF_EXTERN_DISPATCH(double, LGSSM, 4)
 AIRPF_EXTERN_DISPATCH(double, TOY, 2)
 AIRPF_EXTERN_DISPATCH(double, TOY, 4)
+AIRPF_EXTERN_DISPATCH(double, CP, 2)
+AIRPF_EXTERN_DISPATCH(double, CP, 4)
 #undef AIRPF_EXTERN_DISPATCH
 
 // ---------------------------------------------------------------------------
@@ -80,6 +84,7 @@ static cudaError_t dispatch_typed(const StepParams& p, int t, cudaStream_t strea
     case NGM: return dispatch_model<R, NGM>(p, t, stream, op, fits);
     case LGSSM: return dispatch_model<R, LGSSM>(p, t, stream, op, fits);
     case TOY: return dispatch_model<R, TOY>(p, t, stream, op, fits);
+    case CP: return dispatch_model<R, CP>(p, t, stream, op, fits);
     }
     return cudaErrorInvalidValue;
 }

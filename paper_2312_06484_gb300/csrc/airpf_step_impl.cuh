@@ -926,7 +926,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             if (i < M) {
                 const uint32_t unit = (uint32_t)(k * M + i);
                 if (t == 1) model_prior<R, MODEL, DX>(mp, st, unit, dx, xp[r]);
-                model_step_noise<R, MODEL, DX>(st, unit, (uint32_t)t, dx, z[r], w0[r], wres[r]);
+                model_step_noise<R, MODEL, DX>(mp, st, unit, (uint32_t)t, dx, z[r], w0[r], wres[r]);
             }
         }
     }
@@ -938,6 +938,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             for (int q = tid; q < dx * dx + p.dy * dx; q += blockDim.x) mshared[q] = (R)p.mdata[q];
         for (int q = tid; q < p.dy; q += blockDim.x)
             mshared[dx * dx + p.dy * dx + q] = (R)p.y[(size_t)(t - 1) * p.dy + q];
+        if (MODEL == CP && tid == 0) {      // the step's log C(n, k), after y = (k, n)
+            const double kk = p.y[(size_t)(t - 1) * p.dy], nn = p.y[(size_t)(t - 1) * p.dy + 1];
+            mshared[dx * dx + p.dy * dx + 2] = (R)(lgamma(nn + 1.0) - lgamma(kk + 1.0) - lgamma(nn - kk + 1.0));
+        }
     }
 
     // ---- 2. everything below reads what earlier kernels of the pass wrote ----
