@@ -290,6 +290,42 @@ def ngm_leg(gp, torch, ws: int, T: int = 1000) -> dict:
     return out
 
 
+def changepoint_leg(gp, torch, ws: int, T: int = 523) -> dict:
+    """Change-point workload of Section 4.2 on synthetic counts: m = 64 islands, M in
+    {200, 500}, T = 523, adaptive tau = 0.3; random-walk PMMH on p (step 0.01, U(0, 1)
+    prior, alpha and beta fixed), FP32 and FP64, one chain and 256 chains side by side
+    (one context, B = 256).  Times PMMH iterations after two untimed ones."""
+    y = torch.tensor(synth.cp_observations(T, seed=6), device="cuda")
+    a, b = float(synth.CP_THETA[1]), float(synth.CP_THETA[2])
+    step, lo, hi = [0.01, 0.0, 0.0], [0.0, a, b], [1.0, a, b]
+    out = {"workload": f"changepoint_m64_T{T}", "points": []}
+    for M in (200, 500):
+        for prec in ("fp32", "fp64"):
+            for B in (1, 256):
+                f = gp.AIRPF(synth.MODEL_CP, m=64, M=M, T=T, B=B, dy=2, mode="adaptive", tau=TAU, precision=prec,
+                             seed=1)
+                th = torch.tensor(np.tile(synth.CP_THETA, (B, 1)), device="cuda")
+                lz = torch.full((B,), float("nan"), dtype=torch.float64, device="cuda")
+                acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+                f.pmmh(y, th, lz, step=step, lo=lo, hi=hi, iters=2, chain0=0, iter0=0, n_accept=acc)
+                f.sync()
+                iters = 40 if B == 1 else 8
+                acc.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(f.stream)
+                f.pmmh(y, th, lz, step=step, lo=lo, hi=hi, iters=iters, chain0=0, iter0=2, n_accept=acc)
+                e1.record(f.stream)
+                f.sync()
+                ms = e0.elapsed_time(e1)
+                out["points"].append({"M": M, "precision": prec, "chains": B, "ms_per_iter": ms / iters,
+                                      "pmmh_iters_per_s": B * ws * iters / (ms / 1e3),
+                                      "particle_steps_per_s": B * ws * iters * 64 * M * T / (ms / 1e3),
+                                      "accept_rate": float(acc.sum().item()) / (B * iters),
+                                      "launch_mode": f.launch_mode})
+                f.close()
+    return out
+
+
 def run_gpu(args) -> None:
     import torch
     import paper_2312_06484_gb300 as gp
@@ -432,6 +468,7 @@ def run_gpu(args) -> None:
     batched = None if args.no_batched else batched_leg(gp, torch, ws)
     gradient = None if args.no_grad else grad_leg(gp, torch, ws)
     ngm = None if args.no_ngm else ngm_leg(gp, torch, ws)
+    changepoint = None if args.no_changepoint else changepoint_leg(gp, torch, ws)
 
     peaks, peak_src = _peaks()
     ms_step = tot_ms / args.steps
@@ -472,6 +509,7 @@ def run_gpu(args) -> None:
         "batched": batched,
         "gradient": gradient,
         "ngm_large": ngm,
+        "changepoint": changepoint,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
@@ -526,6 +564,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-chains leg")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient leg")
     ap.add_argument("--no-ngm", action="store_true", help="skip the large NGM leg")
+    ap.add_argument("--no-changepoint", action="store_true", help="skip the change-point PMMH leg")
     ap.add_argument("--profile-case", choices=["ngm256", "grad"], default=None,
                     help="run one small workload for a profiler capture instead of the bench line")
     ap.add_argument("--launch", default="auto", choices=["auto", "steps", "split", "grid"])
