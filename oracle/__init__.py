@@ -97,14 +97,20 @@ def _model_data(model_data):
 
 
 def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, seed=0, chain=0,
-          iter=0, model_data=None, record=True, tie_rel=1e-12):
+          iter=0, model_data=None, record=True, tie_rel=1e-12, moments=False):
     """Literal Algorithm 1 (FP64).  Returns a dict with log_z and, if record,
     logz_trace[T], anc[T, N], src[T, m], enf[T, S+1], sstar[T], xfinal[N, dx], tie.
     tie_rel: relative width of the band around a threshold in which a draw, an island
-    choice or an ENF test is flagged as a tie (a diagnostic; the arithmetic is unchanged)."""
+    choice or an ENF test is flagged as a tie (a diagnostic; the arithmetic is unchanged).
+    moments: also return moments[T, 2, 2, dx], the output measures of the paper's output-
+    measure equation at step t: [0] the prediction filter (the mutated particles weighted by
+    W_{t,0}), [1] the filter after internal resampling (weighted by W_{t,1}); [., 0] E[x_d],
+    [., 1] E[x_d^2]."""
     lib().oracle_set_tie_rel(tie_rel)
     y = _f64(y)
     T = len(y) // dy
+    mom = np.zeros((T, 2, 2, dx)) if moments else None
+    lib().oracle_set_moments_out(_dp(mom))
     S = int(round(math.log2(m)))
     N = m * M
     th, md = _f64(theta), _model_data(model_data)
@@ -120,8 +126,11 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
                             _ip(out.get("anc")), _ip(out.get("src")), _dp(out.get("enf")),
                             _ip(out.get("sstar")), _dp(out.get("xfinal")), _ip(tie))
     lib().oracle_set_tie_rel(1e-12)
+    lib().oracle_set_moments_out(None)
     if rc:
         raise ValueError("oracle_airpf rejected its arguments")
+    if moments:
+        out["moments"] = mom
     out["log_z"] = float(lz[0])
     out["tie"] = (int(tie[0]), int(tie[1]))
     return out

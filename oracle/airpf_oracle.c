@@ -87,6 +87,38 @@ static double TIE_REL = 1e-12;
 
 void oracle_set_tie_rel(double v) { TIE_REL = v > 0 ? v : 1e-12; }
 
+/* when set, oracle_airpf writes the output measures' moments [T][2][2][dx] here */
+static double* MOMENTS_OUT = NULL;
+
+void oracle_set_moments_out(double* p) { MOMENTS_OUT = p; }
+
+/* Eq. (output measure) of Section 2: pi^N_{t,s}(phi) = sum_k W^k_{t,s} M^-1 sum_i
+ * phi(xi^{k,i}_{t,s}) / sum_k W^k_{t,s}, for phi = x_d (out[d]) and x_d^2
+ * (out[dx + d]); lwk = log W^k_{t,s}, xs the particles.  NaN if every W is 0. */
+static void output_moments(const double* lwk, const double* xs, int m, int M, int dx, double* out)
+{
+    double mx = -INFINITY;
+    for (int k = 0; k < m; ++k) if (lwk[k] > mx) mx = lwk[k];
+    for (int j = 0; j < 2 * dx; ++j) out[j] = mx > -INFINITY ? 0.0 : NAN;
+    if (!(mx > -INFINITY)) return;
+    double den = 0.0;
+    for (int k = 0; k < m; ++k) {
+        double wk = exp(lwk[k] - mx);
+        den += wk;
+        for (int d = 0; d < dx; ++d) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int i = 0; i < M; ++i) {
+                double v = xs[((size_t)k * M + i) * dx + d];
+                s1 += v;
+                s2 += v * v;
+            }
+            out[d] += wk * s1 / M;
+            out[dx + d] += wk * s2 / M;
+        }
+    }
+    for (int j = 0; j < 2 * dx; ++j) out[j] /= den;
+}
+
 typedef struct {
     uint64_t seed;
     uint32_t chain;
@@ -458,6 +490,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
         /* ENF_{t,0} (diagnostic, Algorithm 1) */
         if (enf) enf[(size_t)(t - 1) * (S + 1)] = enf_of(lw, m);
 
+        if (MOMENTS_OUT) memcpy(lw2, lw, sizeof(double) * m);      /* log W^k_{t,0} */
         /* mutation of every island's block through K_t, then weighting */
         #pragma omp parallel for schedule(static)
         for (int k = 0; k < m; ++k) {
@@ -477,6 +510,12 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
                        sizeof(double) * dx);
         }
         for (int k = 0; k < m; ++k) if (tie_isl[k]) tie_now = TIE_RESAMPLE;
+        if (MOMENTS_OUT) {
+            /* s = 0: the mutated particles with W_{t,0}; s = 1: the internally
+             * resampled particles with W_{t,1} (before the interaction stages) */
+            output_moments(lw2, x, m, M, dx, MOMENTS_OUT + (size_t)(t - 1) * 4 * dx);
+            output_moments(lw, xr, m, M, dx, MOMENTS_OUT + (size_t)(t - 1) * 4 * dx + 2 * dx);
+        }
 
         /* interaction stages s = 1..S (butterfly matrices A_s) */
         for (int k = 0; k < m; ++k) idx[k] = k;
