@@ -126,7 +126,7 @@ typedef struct {
     double tau;             /* ENF threshold in (0, 1] (ENF normalised to [1/m, 1]) */
     int32_t precision;      /* airpf_precision */
     int32_t record;         /* bit 0: ancestors, bit 1: ENF and s*, bit 2: log Z trace, bit 3: kernel timing,
-                               bit 4: gradient pass */
+                               bit 4: gradient pass, bit 5: output measures (airpf_moments) */
     uint64_t seed;
     int32_t launch;         /* airpf_launch (a requested mode that cannot run: AIRPF_ERR_UNSUPPORTED) */
     int32_t reserved;       /* must be 0 */
@@ -141,6 +141,7 @@ typedef struct {
 #define AIRPF_RECORD_TRACE 4
 #define AIRPF_RECORD_TIMING 8   /* STEPS launch only: CUDA events around each kernel (airpf_kernel_times) */
 #define AIRPF_RECORD_GRAD 16    /* keep what airpf_grad's backward pass needs (all models but TOY and CP) */
+#define AIRPF_RECORD_MOMENTS 32 /* keep what airpf_moments needs (the output measures' island terms) */
 
 typedef struct airpf_ctx airpf_ctx;
 
@@ -340,6 +341,16 @@ airpf_status airpf_grad(airpf_ctx* ctx, const double* d_theta, const double* d_y
 airpf_status airpf_kernel_times(airpf_ctx* ctx, double* step_ms, double* cascade_ms);
 
 /* The airpf_launch mode the context resolved to (never AUTO). */
+/* The output measures of the last airpf_run (the paper's output-measure equation,
+ * Section 2): pi^N_{t,s} = sum_k W^k_{t,s} M^-1 sum_i delta(xi^{k,i}_{t,s}) / sum_k W^k_{t,s}
+ * at s = 0 (the prediction filter: the mutated particles of step t with the island weights
+ * before weighting with y_t) and s = 1 (the filter: the internally resampled particles with
+ * the weights after it).  d_moments (device, caller-owned, B*T*2*2*dx doubles) receives
+ * [b][t][s][0][d] = E[x_d] and [b][t][s][1][d] = E[x_d^2]; NaN where every island weight is
+ * 0.  Needs a context created with AIRPF_RECORD_MOMENTS (else AIRPF_ERR_UNSUPPORTED);
+ * asynchronous on the context's stream, after the run it describes. */
+airpf_status airpf_moments(airpf_ctx* ctx, double* d_moments);
+
 int32_t airpf_launch_mode(const airpf_ctx* ctx);
 
 /* Fault injection for tests of the failure path, no counterpart in the paper.

@@ -18,7 +18,7 @@ from ._binding import AirpfConfig, AirpfError
 MODEL_AR1, MODEL_SV, MODEL_NGM, MODEL_LGSSM, MODEL_TOY, MODEL_CP = 0, 1, 2, 3, 4, 5
 NEVER, ALWAYS, ADAPTIVE = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
-RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE, RECORD_TIMING, RECORD_GRAD = 1, 2, 4, 8, 16
+RECORD_LINEAGE, RECORD_ENF, RECORD_TRACE, RECORD_TIMING, RECORD_GRAD, RECORD_MOMENTS = 1, 2, 4, 8, 16, 32
 LAUNCH_AUTO, LAUNCH_STEPS, LAUNCH_PERSISTENT_CTA, LAUNCH_PERSISTENT_GRID, LAUNCH_STEPS_SPLIT = 0, 1, 2, 3, 4
 
 _MODES = {"never": NEVER, "always": ALWAYS, "adaptive": ADAPTIVE}
@@ -167,6 +167,16 @@ class AIRPF:
         self._keep = (theta, y)
         _binding.check(self.lib.airpf_grad(self.ctx, _ptr(theta), _ptr(y), chain0, iter, _ptr(out["log_z"]),
                                            _ptr(out["grad"]), _ptr(out["score"])), self.ctx)
+        return out
+
+    def moments(self):
+        """Output measures of the last run (context created with RECORD_MOMENTS): a CUDA
+        tensor [B, T, 2, 2, dx]; [:, t, 0] the prediction filter (mutated particles, weights
+        before y_t), [:, t, 1] the filter (internally resampled particles, weights after y_t);
+        [..., 0, d] E[x_d], [..., 1, d] E[x_d^2]."""
+        torch = self._torch
+        out = torch.empty((self.B, self.T, 2, 2, self.dx), dtype=torch.float64, device="cuda")
+        _binding.check(self.lib.airpf_moments(self.ctx, _ptr(out)), self.ctx)
         return out
 
     def kernel_times(self):
@@ -365,5 +375,5 @@ def log_z(f: AIRPF, theta, y, *, chain0: int = 0, iter: int = 0):
 
 __all__ = ["AIRPF", "AirpfError", "Group", "autotune", "theta_dim", "run_static", "log_z", "MODEL_AR1", "MODEL_SV", "MODEL_NGM", "MODEL_LGSSM",
            "MODEL_TOY", "MODEL_CP", "NEVER", "ALWAYS", "ADAPTIVE", "FP64", "FP32_MIXED", "RECORD_LINEAGE",
-           "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "RECORD_GRAD", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
+           "RECORD_ENF", "RECORD_TRACE", "RECORD_TIMING", "RECORD_GRAD", "RECORD_MOMENTS", "LAUNCH_AUTO", "LAUNCH_STEPS", "LAUNCH_PERSISTENT_CTA",
            "LAUNCH_PERSISTENT_GRID", "LAUNCH_STEPS_SPLIT"]

@@ -38,6 +38,8 @@ struct WsLayout {
         sstar, anc, active, mpar, drift, bar;
     size_t pm_prop, pm_logz_prop, pm_stats, pm_gprop, pm_lqf;
     size_t xck, xblk, logw, gpi[2], xh[3], dh[3], gout, sout;   // gradient pass
+    size_t fw, fsum;                                             // output measures
+    int fm_nw;
     size_t total;
 };
 
@@ -102,7 +104,7 @@ const char* check_config(const airpf_config* c)
     if (c->mode < 0 || c->mode > 2) return "unknown interaction mode";
     if (!(c->tau > 0.0 && c->tau <= 1.0)) return "tau must be in (0, 1]";
     if (c->precision != AIRPF_FP64 && c->precision != AIRPF_FP32_MIXED) return "unknown precision";
-    if (c->record < 0 || c->record > 31) return "unknown record bits";
+    if (c->record < 0 || c->record > 63) return "unknown record bits";
     if (c->ckpt < 0 || c->ckpt > c->T) return "ckpt must be in [0, T]";
     if (c->launch < 0 || c->launch > 4) return "unknown launch mode";
     if (c->reserved != 0) return "reserved must be 0";
@@ -167,6 +169,16 @@ WsLayout make_ws_layout(const airpf_config* c)
         for (int i = 0; i < 3; ++i) L.dh[i] = take(sizeof(double) * B * N);
         L.gout = take(sizeof(double) * B * td);
         L.sout = take(sizeof(double) * B * td);
+    }
+    L.fw = L.fsum = 0;
+    L.fm_nw = 0;
+    if (c->record & AIRPF_RECORD_MOMENTS) {
+        // warps per island: the threads per island depend only on M and the requested ppt
+        int tpi = 0, pp = 0, G = 0;
+        airpf::choose_mapping(c->m, c->M, c->precision == AIRPF_FP64, c->ppt, 0, &tpi, &pp, &G);
+        L.fm_nw = tpi / 32;
+        L.fw = take(sizeof(double) * B * T * c->m * 2);
+        L.fsum = take(sizeof(double) * B * T * c->m * L.fm_nw * 4 * c->dx);
     }
     L.total = o;
     return L;
@@ -483,6 +495,21 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         p.gout = at<double>(ctx, L.gout);
         p.sout = at<double>(ctx, L.sout);
     }
+    p.fmom = 0;
+    p.fm_nw = 0;
+    p.fw = p.fsum = nullptr;
+    if (cfg->record & AIRPF_RECORD_MOMENTS) {
+        if (p.tpi / 32 != L.fm_nw) {
+            set_err(nullptr, "internal: warps per island %d, workspace sized for %d", p.tpi / 32, L.fm_nw);
+            cudaStreamDestroy(ctx->cap_stream);
+            delete ctx;
+            return AIRPF_ERR_UNSUPPORTED;
+        }
+        p.fmom = 1;
+        p.fm_nw = L.fm_nw;
+        p.fw = at<double>(ctx, L.fw);
+        p.fsum = at<double>(ctx, L.fsum);
+    }
     ctx->sp_pm = p;
     ctx->sp_pm.active = at<int>(ctx, L.active);
 
@@ -667,6 +694,18 @@ airpf_status airpf_kernel_times(airpf_ctx* ctx, double* step_ms, double* cascade
     }
     *step_ms = a;
     *cascade_ms = b;
+    return AIRPF_OK;
+}
+
+airpf_status airpf_moments(airpf_ctx* ctx, double* d_moments)
+{
+    if (!ctx || !d_moments) return AIRPF_ERR_ARG;
+    if (!(ctx->cfg.record & AIRPF_RECORD_MOMENTS)) {
+        set_err(ctx, "the context was created without AIRPF_RECORD_MOMENTS");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    const cudaError_t e = airpf::launch_moments(ctx->sp, d_moments, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "moments kernel launch");
     return AIRPF_OK;
 }
 

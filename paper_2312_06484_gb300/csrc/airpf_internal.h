@@ -58,6 +58,12 @@ struct StepParams {
     void* xck;                    // [B][nck][dx][N]
     void* xblk;                   // [B][ckpt][dx][N]
     double* logw;                 // [B][T][m]
+    // output measures (record AIRPF_RECORD_MOMENTS): per island and step, log W_{t,0} and
+    // log W_{t,1}, and every warp's sums of x_d and x_d^2 over its mutated and its
+    // internally resampled particles
+    int fmom, fm_nw;              // recording on; warps per island
+    double* fw;                   // [B][T][m][2]
+    double* fsum;                 // [B][T][m][fm_nw][4 dx]
     double* gpi[2];               // [B][m]
     void* xh[3];                  // [B][dx][N]
     double* dh[3];                // [B][N]
@@ -103,6 +109,8 @@ cudaError_t launch_persistent(const StepParams& p, bool grid, cudaStream_t strea
 
 // Whether every CTA of the grid-persistent launch can be resident at once.
 bool persistent_grid_fits(const StepParams& p);
+// the output measures' moments of the last pass, out [B][T][2][2][dx]
+cudaError_t launch_moments(const StepParams& p, double* out, cudaStream_t stream);
 // can every CTA of a fused-steps grid be resident at once at the occupancy of
 // the 128-register instantiation?
 bool wide_fused_fits(const StepParams& p);

@@ -123,6 +123,74 @@ bool wide_fused_fits(const StepParams& p)
     return dispatch(p, 0, nullptr, OP_WIDE_FITS, &fits) == cudaSuccess && fits;
 }
 
+// The output measures' moments of step t + 1 for filter c (grid T x min(B, 65535),
+// 256 threads): out[c][t][s][0..dx) = E[x_d], out[c][t][s][dx..2dx) = E[x_d^2] under
+// pi^N_{t,s} = sum_k W^k_{t,s} M^-1 sum_i delta(xi^{k,i}_{t,s}) / sum_k W^k_{t,s}, with
+// s = 0 the mutated particles and W_{t,0}, s = 1 the internally resampled particles and
+// W_{t,1}.  Every sum runs in a fixed order (deterministic); NaN when every W is 0.
+constexpr int kMomThreads = 256;
+
+__global__ void __launch_bounds__(kMomThreads) moments_kernel(StepParams p, double* out)
+{
+    __shared__ double part[kMomThreads / 32][2 * kMaxDx + 1];
+    __shared__ double wmax[kMomThreads / 32];
+    const int t = blockIdx.x, dx = p.dx, m = p.m, nw = p.fm_nw, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int c = blockIdx.y; c < p.B; c += gridDim.y) {
+        const double* fw = p.fw + ((size_t)c * p.T + t) * m * 2;
+        const double* fs = p.fsum + ((size_t)c * p.T + t) * m * nw * 4 * dx;
+        for (int s = 0; s < 2; ++s) {
+            double mx = -INFINITY;
+            for (int k = tid; k < m; k += blockDim.x) mx = fmax(mx, fw[k * 2 + s]);
+            mx = warp_max(mx);
+            if (lane == 0) wmax[warp] = mx;
+            __syncthreads();
+            mx = -INFINITY;
+            for (int w = 0; w < nwarps; ++w) mx = fmax(mx, wmax[w]);
+            double acc[2 * kMaxDx + 1];
+#pragma unroll
+            for (int j = 0; j <= 2 * kMaxDx; ++j) acc[j] = 0.0;
+            if (mx > -INFINITY) {
+                for (int k = tid; k < m; k += blockDim.x) {
+                    const double wk = exp(fw[k * 2 + s] - mx);
+                    acc[2 * kMaxDx] += wk;
+#pragma unroll
+                    for (int j = 0; j < 2 * kMaxDx; ++j) {
+                        if (j < 2 * dx) {
+                            double sj = 0.0;
+                            for (int v = 0; v < nw; ++v) sj += fs[((size_t)k * nw + v) * 4 * dx + s * 2 * dx + j];
+                            acc[j] += wk * sj;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j <= 2 * kMaxDx; ++j) {
+                const double v = warp_sum(acc[j]);
+                if (lane == 0) part[warp][j] = v;
+            }
+            __syncthreads();
+            if (tid < 2 * dx) {
+                double num = 0.0, den = 0.0;
+                for (int w = 0; w < nwarps; ++w) {
+                    num += part[w][tid];
+                    den += part[w][2 * kMaxDx];
+                }
+                out[(((size_t)c * p.T + t) * 2 + s) * 2 * dx + tid] = mx > -INFINITY ? num / (den * (double)p.M) : NAN;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_moments(const StepParams& p, double* out, cudaStream_t stream)
+{
+    if (p.fmom == 0 || p.fw == nullptr || p.fsum == nullptr) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)p.T, (unsigned)(p.B < 65535 ? p.B : 65535));
+    moments_kernel<<<grid, kMomThreads, 0, stream>>>(p, out);
+    return cudaGetLastError();
+}
+
 __global__ void set_run_kernel(RunParams* r, uint32_t iter, uint32_t chain0)
 {
     r->iter = iter;

@@ -801,6 +801,36 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     }
 }
 
+// log of an island weight as stored (FP32-mixed: 64-bit mantissa times
+// 2^(e-64), the common factor M^-t left out; FP64: a double times 2^e)
+template <bool FX>
+__device__ __forceinline__ double xw_log(u64 bits, int e)
+{
+    if (bits == 0ull) return -INFINITY;
+    return FX ? log((double)bits) + (double)(e - 64) * 0.6931471805599453
+              : log(__longlong_as_double((long long)bits)) + (double)e * 0.6931471805599453;
+}
+
+// One warp's sums of x_d and x_d^2 over its particles of island k at step t (the
+// island terms of the output measures), written to the warp's slot: part s = 0
+// the mutated particles, s = 1 the internally resampled ones.
+template <typename R, int DX>
+__device__ __forceinline__ void moment_sums(const StepParams& p, int c, int t, int k, int wi, int lane, int dx,
+                                            int s, const R* s1, const R* s2)
+{
+    double* slot = p.fsum + ((((size_t)c * p.T + (t - 1)) * p.m + k) * p.fm_nw + wi) * 4 * dx + (size_t)s * 2 * dx;
+#pragma unroll
+    for (int d = 0; d < DX; ++d) {
+        if (d < dx) {
+            const R a = warp_sum(s1[d]), b = warp_sum(s2[d]);
+            if (lane == 0) {
+                slot[d] = (double)a;
+                slot[dx + d] = (double)b;
+            }
+        }
+    }
+}
+
 // Record of the CTA's island weights after step t (see file comment); warp 0.
 template <bool FX>
 __device__ void publish_record(const StepParams& p, int c, int t, int jo, const u64* nw_bits, const int* nw_e)
@@ -1109,6 +1139,23 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
     }
 
+    if (REC && p.fmom) {       // output measure at s = 0: the mutated particles
+        R s1[DX], s2[DX];
+#pragma unroll
+        for (int d = 0; d < DX; ++d) {
+            s1[d] = (R)0;
+            s2[d] = (R)0;
+#pragma unroll
+            for (int r = 0; r < PPT; ++r) {
+                if (li * PPT + r < M) {
+                    s1[d] += xv[r][d];
+                    s2[d] += xv[r][d] * xv[r][d];
+                }
+            }
+        }
+        moment_sums<R, DX>(p, c, t, k, wi, lane, dx, 0, s1, s2);
+    }
+
     // island maximum of the log-weights
     R mx = lv[0];
 #pragma unroll
@@ -1190,6 +1237,12 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
         n -= half;
     }
+    R f1[DX], f2[DX];          // output measure at s = 1: the resampled particles
+#pragma unroll
+    for (int d = 0; d < DX; ++d) {
+        f1[d] = (R)0;
+        f2[d] = (R)0;
+    }
     if (vec) {
         if (li * PPT < M) {
 #pragma unroll
@@ -1199,6 +1252,13 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
 #pragma unroll
                     for (int r = 0; r < PPT; ++r) v[r] = xs[(size_t)d * M + (alive ? base[r] : li * PPT + r)];
                     store_run<R, PPT>(&Xc[((size_t)c * dx + d) * N + (size_t)k * M + li * PPT], v);
+                    if (REC && p.fmom) {
+#pragma unroll
+                        for (int r = 0; r < PPT; ++r) {
+                            f1[d] += v[r];
+                            f2[d] += v[r] * v[r];
+                        }
+                    }
                 }
             }
             if (ires_out) {
@@ -1213,12 +1273,21 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             if (j < M) {
                 const int a = alive ? base[r] : j;
 #pragma unroll
-                for (int d = 0; d < DX; ++d)
-                    if (d < dx) Xc[((size_t)c * dx + d) * N + (size_t)k * M + j] = xs[(size_t)d * M + a];
+                for (int d = 0; d < DX; ++d) {
+                    if (d < dx) {
+                        const R v = xs[(size_t)d * M + a];
+                        Xc[((size_t)c * dx + d) * N + (size_t)k * M + j] = v;
+                        if (REC && p.fmom) {
+                            f1[d] += v;
+                            f2[d] += v * v;
+                        }
+                    }
+                }
                 if (ires_out) ires_out[j] = a;
             }
         }
     }
+    if (REC && p.fmom) moment_sums<R, DX>(p, c, t, k, wi, lane, dx, 1, f1, f2);
 
     // island weight W^k_{t,1} = W^k_{t,0} exp(max) (sum_i w_i) / M, extended range
     if (li == 0) {
@@ -1256,12 +1325,13 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
         new_w[g] = w.bits;
         new_we[g] = w.e;
+        if (REC && p.fmom) {        // the output measures' island weights W_{t,0}, W_{t,1}
+            double* fw = p.fw + (((size_t)c * p.T + (t - 1)) * p.m + k) * 2;
+            fw[0] = xw_log<FX>(own_w[g], own_we[g]);
+            fw[1] = xw_log<FX>(w.bits, w.e);
+        }
         if (REC && p.grad) {        // log W^k_{t,1} (the FP32-mixed weights leave out M^-t)
-            double lw = -INFINITY;
-            if (w.bits != 0ull)
-                lw = FX ? log((double)w.bits) + (double)(w.e - 64) * 0.6931471805599453
-                        : log(__longlong_as_double((long long)w.bits)) + (double)w.e * 0.6931471805599453;
-            p.logw[((size_t)c * p.T + (t - 1)) * p.m + k] = lw;
+            p.logw[((size_t)c * p.T + (t - 1)) * p.m + k] = xw_log<FX>(w.bits, w.e);
         }
     }
     __syncthreads();
@@ -1486,7 +1556,7 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     // step 1 follows the prologue in plain stream order; later steps may start
     // launching while the previous cascade runs (programmatic dependent launch)
     // the lean instantiations (no recording, one launch form) where they apply
-    const bool rec = p.anc != nullptr || p.grad != 0 || p.ires[0] != nullptr;
+    const bool rec = p.anc != nullptr || p.grad != 0 || p.ires[0] != nullptr || p.fmom != 0;
     auto go = [&](auto kernel) -> cudaError_t {
         if (p.pdl && t >= 2) return launch_dependent(kernel, dim3(grid), dim3(block), smem, stream, p, t);
         kernel<<<grid, block, smem, stream>>>(p, t);

@@ -41,7 +41,7 @@ def test_workspace_size_and_argument_checks():
     assert 2 * 262144 * 4 <= n.value < 2 * 262144 * 4 + (1 << 20)
     bad = [dict(m=3), dict(m=131072), dict(M=0), dict(M=1025), dict(T=0), dict(B=0), dict(tau=0.0),
            dict(tau=1.01), dict(mode=3), dict(model=9), dict(dx=2), dict(model=3, dx=9),
-           dict(precision=7), dict(record=32), dict(launch=5), dict(reserved=1),
+           dict(precision=7), dict(record=64), dict(launch=5), dict(reserved=1),
            dict(ppt=3), dict(ppt=8), dict(islands_per_cta=3), dict(islands_per_cta=-2)]
     for kw in bad:
         assert lib.airpf_workspace_bytes(ctypes.byref(_cfg(**kw)), ctypes.byref(n)) == 1, kw
