@@ -16,8 +16,12 @@
  *   key     = (seed & 0xffffffff, seed >> 32)
  *   counter = (unit, t, iter, (chain << 8) | (kind << 5) | sub)
  *   kind 0 INIT  : prior draw of particle unit = k*M+i, t = 0, sub = normal pair b
- *   kind 1 STEP  : time t >= 1, unit = k*M+i, sub = normal pair b;
- *                  word 2 of sub 0 is the internal-resampling uniform of draw i
+ *   kind 1 STEP  : time t >= 1, g = k*M+i.  A transition with one normal:
+ *                  counter unit = g >> 1, sub 0 (particles 2j, 2j+1 share
+ *                  block j); g even takes the cosine normal and word 2 as its
+ *                  internal-resampling uniform, g odd the sine normal and
+ *                  word 3.  Otherwise unit = g, sub = normal pair b, and word 2
+ *                  of sub 0 is the internal-resampling uniform of draw i
  *   kind 2 ISLAND: time t, unit = island j, sub = interaction stage s; word 0
  *   kind 3 MH    : PMMH iteration `iter`, t = 0; sub 0 unit b -> proposal
  *                  normals 2b, 2b+1; sub 1 unit 0 word 0 -> accept uniform
@@ -144,10 +148,26 @@ static void normal_pair(uint32_t w0, uint32_t w1, double* n0, double* n1)
 }
 
 /* fills z[0..n-1] with the normals of (kind, unit, t); returns word 2 of
- * sub-block 0 and word 0 of sub-block 0 through w2/w0 when non-NULL */
+ * sub-block 0 and word 0 of sub-block 0 through w2/w0 when non-NULL.
+ * A transition with one normal (n = 1) shares its block with the unit next
+ * to it: units 2j and 2j+1 both draw block j; the even unit takes the cosine
+ * normal and words 0 and 2, the odd unit the sine normal and words 1 and 3.
+ * (The paper fixes the draws only in distribution; the two normals of one
+ * Box-Muller pair are independent, as are the four words.) */
 static void normals(const stream_id* s, uint32_t kind, uint32_t unit, uint32_t t,
                     int n, double* z, uint32_t* w0, uint32_t* w2)
 {
+    if (kind == KIND_STEP && n == 1) {
+        uint32_t w[4];
+        double a, c;
+        int odd = (int)(unit & 1u);
+        draw(s, unit >> 1, t, kind, 0, w);
+        normal_pair(w[0], w[1], &a, &c);
+        z[0] = odd ? c : a;
+        if (w0) *w0 = odd ? w[1] : w[0];
+        if (w2) *w2 = odd ? w[3] : w[2];
+        return;
+    }
     int pairs = n > 0 ? (n + 1) / 2 : 1;
     for (int b = 0; b < pairs; ++b) {
         uint32_t w[4];

@@ -148,11 +148,24 @@ __device__ __forceinline__ void model_step_setup(ModelPar<R>& p, int t)
 }
 
 // Normals z[0..n-1] of (kind, unit, t): pair b gives z[2b], z[2b+1].  Also
-// returns word 0 and word 2 of sub-block 0.
+// returns word 0 and word 2 of sub-block 0.  A transition with one normal
+// shares its block with the neighbouring unit: units 2j and 2j+1 both draw
+// block j of counter unit j; the even unit takes the cosine normal and words 0
+// and 2, the odd unit the sine normal and words 1 and 3.
 template <typename R, int NZ>
 __device__ __forceinline__ void stream_normals(const Stream& st, uint32_t kind, uint32_t unit,
                                                uint32_t t, int n, R* z, uint32_t& w0, uint32_t& w2)
 {
+    if (NZ >= 1 && kind == KIND_STEP && n == 1) {
+        const U4 b = st.draw(unit >> 1, t, kind, 0);
+        R a, c;
+        normal_pair(b.x, b.y, a, c);
+        const bool odd = (unit & 1u) != 0u;
+        z[0] = odd ? c : a;
+        w0 = odd ? b.y : b.x;
+        w2 = odd ? b.w : b.z;
+        return;
+    }
     const U4 b0 = st.draw(unit, t, kind, 0);
     w0 = b0.x;
     w2 = b0.z;
@@ -287,6 +300,20 @@ __device__ __forceinline__ void model_step_noise(const ModelPar<R>& p, const Str
         return;
     }
     stream_normals<R, (MODEL == TOY) ? 0 : DX>(st, KIND_STEP, unit, t, dx, z, w0, w2);
+}
+
+// The step's random numbers of units u and u+1 (u even) of a one-normal model
+// from their shared block (the rule of stream_normals, one draw for both).
+template <typename R>
+__device__ __forceinline__ void step_noise_pair(const Stream& st, uint32_t u_even, uint32_t t, R& za, R& zb,
+                                                uint32_t& w0a, uint32_t& w0b, uint32_t& w2a, uint32_t& w2b)
+{
+    const U4 b = st.draw(u_even >> 1, t, KIND_STEP, 0);
+    normal_pair(b.x, b.y, za, zb);
+    w0a = b.x;
+    w0b = b.y;
+    w2a = b.z;
+    w2b = b.w;
 }
 
 // x_t ~ K_t(x_{t-1}, .); returns the internal-resampling word of the unit.

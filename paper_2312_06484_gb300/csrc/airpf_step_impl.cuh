@@ -950,12 +950,25 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
-            const int i = li * PPT + r;
             w0[r] = 0;
             wres[r] = 0;
+        }
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int i = li * PPT + r;
             if (i < M) {
                 const uint32_t unit = (uint32_t)(k * M + i);
                 if (t == 1) model_prior<R, MODEL, DX>(mp, st, unit, dx, xp[r]);
+                // one-normal models: the thread's particles 2q, 2q+1 share a block
+                // (a vector run starts at an even unit: M is a multiple of PPT)
+                if constexpr (DX == 1 && MODEL != TOY && MODEL != CP && PPT % 2 == 0) {
+                    if (vec) {
+                        if ((r & 1) == 0)
+                            step_noise_pair<R>(st, unit, (uint32_t)t, z[r][0], z[r + 1][0], w0[r], w0[r + 1], wres[r],
+                                               wres[r + 1]);
+                        continue;
+                    }
+                }
                 model_step_noise<R, MODEL, DX>(mp, st, unit, (uint32_t)t, dx, z[r], w0[r], wres[r]);
             }
         }

@@ -88,8 +88,8 @@ def test_resampling_matches_searchsorted_rederivation():
             x1 = oracle.model_step(synth.MODEL_SV, synth.SV_THETA, x0, unit=unit, t=1,
                                    seed=seed, chain=chain, iter=it)
             g[i] = np.exp(oracle.model_logg(synth.MODEL_SV, synth.SV_THETA, y[:1], x1))
-            w = oracle.philox([unit, 1, it, (chain << 8) | (1 << 5)], key)
-            u[i] = _unif(w[2])
+            w = oracle.philox([unit >> 1, 1, it, (chain << 8) | (1 << 5)], key)
+            u[i] = _unif(w[3] if unit & 1 else w[2])
         cdf = np.cumsum(g)
         want = np.searchsorted(cdf, u * cdf[-1], side="right")
         assert np.array_equal(a["anc"][0, k * M:(k + 1) * M], k * M + want)

@@ -95,14 +95,46 @@ def test_stream_normals_are_standard_normal():
 
 
 def test_stream_keying_spec():
-    """The transition noise of unit g at time t is the cosine Box-Muller normal of
-    Philox(counter=(g, t, iter, chain<<8 | 1<<5 | 0), key=seed)."""
+    """A one-normal transition of particle g at time t takes the Box-Muller pair of
+    Philox(counter=(g >> 1, t, iter, chain<<8 | 1<<5 | 0), key=seed): the cosine normal
+    for even g, the sine normal for odd g (particles 2j and 2j+1 share block j)."""
     seed, chain, it = 0x1234_5678_9ABC_DEF0, 3, 11
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    for g, t in [(0, 1), (5, 2), (1000, 99)]:
-        w = oracle.philox([g, t, it, (chain << 8) | (1 << 5)], key)
+    for g, t in [(0, 1), (1, 1), (5, 2), (1000, 99), (1001, 99)]:
+        w = oracle.philox([g >> 1, t, it, (chain << 8) | (1 << 5)], key)
         u0, u1 = (w[0] + 0.5) * 2.0 ** -32, (w[1] + 0.5) * 2.0 ** -32
-        z = np.sqrt(-2 * np.log(u0)) * np.cos(2 * np.pi * u1)
+        r, a = np.sqrt(-2 * np.log(u0)), 2 * np.pi * u1
+        z = r * (np.sin(a) if g & 1 else np.cos(a))
         x = oracle.model_step(synth.MODEL_AR1, [0.0, 1.0, 1.0, 1.0], [0.0], unit=g, t=t,
                               seed=seed, chain=chain, iter=it)[0]
         assert x == pytest.approx(z, rel=1e-15, abs=1e-15)
+
+
+def test_stream_keying_spec_several_normals():
+    """A transition with d_x >= 2 normals keeps a block of its own: normal d of particle g is
+    component d & 1 of the pair of Philox(counter=(g, t, iter, chain<<8 | 1<<5 | d >> 1))."""
+    seed, chain, it = 99, 1, 4
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    dx = 3
+    th = np.array([0.0, 0.0, 0.0, 0.0, 0.0])          # A = 0 (no off-diagonal data), q = e^0 = 1
+    md = np.zeros(dx * dx + 1 * dx)
+    for g, t in [(0, 1), (7, 3)]:
+        x = oracle.model_step(synth.MODEL_LGSSM, th, np.zeros(dx), unit=g, t=t, dx=dx, dy=1, model_data=md,
+                              seed=seed, chain=chain, iter=it)
+        for d in range(dx):
+            w = oracle.philox([g, t, it, (chain << 8) | (1 << 5) | (d >> 1)], key)
+            u0, u1 = (w[0] + 0.5) * 2.0 ** -32, (w[1] + 0.5) * 2.0 ** -32
+            r, a = np.sqrt(-2 * np.log(u0)), 2 * np.pi * u1
+            assert x[d] == pytest.approx(r * (np.sin(a) if d & 1 else np.cos(a)), rel=1e-14, abs=1e-14)
+
+
+def test_paired_transition_normals_are_independent():
+    """Particles 2j and 2j+1 share one block: their normals are the two halves of one
+    Box-Muller pair, so (z_2j, z_2j+1) is standard bivariate normal: correlation 0 and
+    (z_2j^2 + z_2j+1^2) / 2 exponential with mean 1."""
+    z = np.array([oracle.model_step(synth.MODEL_AR1, [0.0, 1.0, 1.0, 1.0], [0.0], unit=u, t=4,
+                                    seed=5)[0] for u in range(20000)])
+    a, b = z[0::2], z[1::2]
+    assert abs(np.corrcoef(a, b)[0, 1]) < 4.0 / np.sqrt(a.size)
+    assert stats.kstest((a * a + b * b) / 2, "expon").pvalue > 1e-3
+    assert stats.kstest(b, "norm").pvalue > 1e-3
