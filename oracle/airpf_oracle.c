@@ -83,13 +83,25 @@ void oracle_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]
 enum { KIND_INIT = 0, KIND_STEP = 1, KIND_ISLAND = 2, KIND_MH = 3 };
 enum { MODEL_AR1 = 0, MODEL_SV = 1, MODEL_NGM = 2, MODEL_LGSSM = 3, MODEL_TOY = 4, MODEL_CP = 5 };
 enum { MODE_NEVER = 0, MODE_ALWAYS = 1, MODE_ADAPTIVE = 2 };
-enum { TIE_NONE = 0, TIE_RESAMPLE = 1, TIE_ISLAND = 2, TIE_ENF = 3 };
+enum { TIE_NONE = 0, TIE_RESAMPLE = 1, TIE_ISLAND = 2, TIE_ENF = 3, TIE_ESS = 4 };
 
 /* relative width of the tie band; 1e-12 for FP64 comparisons, set wider to
  * compare a float implementation draw by draw */
 static double TIE_REL = 1e-12;
 
 void oracle_set_tie_rel(double v) { TIE_REL = v > 0 ? v : 1e-12; }
+
+/* Adaptive internal resampling (the paper's remark that its analysis holds for adaptive
+ * internal resampling schemes): with tau_int in (0, 1], island k resamples internally at
+ * step t only when the ESS of its particle weights w_i = omega_i g_t(x_i) is below
+ * tau_int M, ESS = (sum w)^2 / sum w^2 (strict test, as the ENF test); otherwise its
+ * particles stay and carry omega_i = w_i / sum w.  The island weight becomes W_{t,1} =
+ * W_{t,0} sum_i omega_i g_t(x_i), with omega normalised per island (1/M after resampling),
+ * which is M^-1 sum_i g_t(x_i) when every island resamples.  tau_int = 0: resample at every
+ * step (Algorithm 1 as printed). */
+static double TAU_INT = 0.0;
+
+void oracle_set_tau_int(double v) { TAU_INT = (v > 0.0 && v <= 1.0) ? v : 0.0; }
 
 /* when set, oracle_airpf writes the output measures' moments [T][2][2][dx] here */
 static double* MOMENTS_OUT = NULL;
@@ -482,6 +494,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
 {
     if (m < 1 || (m & (m - 1)) || M < 1 || T < 1 || dx < 1 || dx > 64 || dy < 1) return 1;
     if (!(tau > 0.0 && tau <= 1.0)) return 1;
+    if (TAU_INT > 0.0 && MOMENTS_OUT) return 1;   /* the output measures assume resampling */
     const int N = m * M, S = ilog2(m);
     model_t md = { model, dx, dy, theta, mdat };
     stream_id st = { seed, chain, iter };
@@ -493,6 +506,8 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
     double* cdf = malloc(sizeof(double) * N);
     uint32_t* wres = malloc(sizeof(uint32_t) * N);
     int32_t* a = malloc(sizeof(int32_t) * N);
+    double* lom = malloc(sizeof(double) * N);      /* log omega (adaptive internal resampling) */
+    double* lom2 = malloc(sizeof(double) * N);
     double* lw = malloc(sizeof(double) * m);        /* log W^k */
     double* lw2 = malloc(sizeof(double) * m);
     int* idx = malloc(sizeof(int) * m);
@@ -503,6 +518,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
     /* initialisation: W^k_{0,0} = 1, particles from the prior */
     for (int g = 0; g < N; ++g) prior_sample(&md, &st, (uint32_t)g, xa + (size_t)g * dx);
     for (int k = 0; k < m; ++k) lw[k] = 0.0;
+    for (int g = 0; g < N; ++g) lom[g] = -log((double)M);
 
     for (int t = 1; t <= T; ++t) {
         const double* yt = y + (size_t)(t - 1) * dy;
@@ -519,17 +535,44 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
                 wres[g] = transition(&md, &st, (uint32_t)g, (uint32_t)t, xa + (size_t)g * dx,
                                      x + (size_t)g * dx);
                 l[g] = log_g(&md, yt, x + (size_t)g * dx);
+                if (TAU_INT > 0.0) l[g] += lom[g];     /* log(omega_i g_t(xi^{k,i})) */
             }
-            /* W^k_{t,1} = W^k_{t,0} * M^-1 sum_i g_t(xi^{k,i}) */
-            lw[k] += log_sum_exp(l + (size_t)k * M, M) - log((double)M);
-            /* internal resampling within island k */
-            tie_isl[k] = resample_island(l + (size_t)k * M, M, wres + (size_t)k * M,
-                                         cdf + (size_t)k * M, a + (size_t)k * M);
+            const double* lk = l + (size_t)k * M;
+            const double lse = log_sum_exp(lk, M);
+            /* W^k_{t,1} = W^k_{t,0} * M^-1 sum_i g_t(xi^{k,i})  (sum_i omega_i g_t with
+             * adaptive internal resampling) */
+            lw[k] += TAU_INT > 0.0 ? lse : lse - log((double)M);
+            /* internal resampling within island k: always, or when its ESS is below tau_int M */
+            int resample = 1;
+            tie_isl[k] = 0;
+            if (TAU_INT > 0.0 && lse > -INFINITY) {
+                double s1 = 0.0, s2 = 0.0, mx = -INFINITY;
+                for (int i = 0; i < M; ++i) if (lk[i] > mx) mx = lk[i];
+                for (int i = 0; i < M; ++i) {
+                    double w = exp(lk[i] - mx);
+                    s1 += w;
+                    s2 += w * w;
+                }
+                double ess = s1 * s1 / s2, thr = TAU_INT * M;
+                resample = ess < thr;
+                if (fabs(ess - thr) < TIE_REL * thr) tie_isl[k] = 2;
+            }
+            if (resample) {
+                if (resample_island(lk, M, wres + (size_t)k * M, cdf + (size_t)k * M, a + (size_t)k * M))
+                    tie_isl[k] = tie_isl[k] ? tie_isl[k] : 1;
+                for (int j = 0; j < M; ++j) lom2[(size_t)k * M + j] = -log((double)M);
+            } else {
+                for (int j = 0; j < M; ++j) {
+                    a[k * M + j] = j;
+                    lom2[(size_t)k * M + j] = lk[j] - lse;
+                }
+            }
             for (int j = 0; j < M; ++j)
                 memcpy(xr + ((size_t)k * M + j) * dx, x + ((size_t)k * M + a[k * M + j]) * dx,
                        sizeof(double) * dx);
         }
-        for (int k = 0; k < m; ++k) if (tie_isl[k]) tie_now = TIE_RESAMPLE;
+        for (int k = 0; k < m; ++k)
+            if (tie_isl[k] && tie_now == TIE_NONE) tie_now = tie_isl[k] == 2 ? TIE_ESS : TIE_RESAMPLE;
         if (MOMENTS_OUT) {
             /* s = 0: the mutated particles with W_{t,0}; s = 1: the internally
              * resampled particles with W_{t,1} (before the interaction stages) */
@@ -576,6 +619,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
         /* island k now holds the internally resampled block of island idx[k] */
         for (int k = 0; k < m; ++k) {
             memcpy(xa + (size_t)k * M * dx, xr + (size_t)idx[k] * M * dx, sizeof(double) * M * dx);
+            memcpy(lom + (size_t)k * M, lom2 + (size_t)idx[k] * M, sizeof(double) * M);
             if (anc)
                 for (int i = 0; i < M; ++i)
                     anc[(size_t)(t - 1) * N + k * M + i] = idx[k] * M + a[idx[k] * M + i];
@@ -589,7 +633,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
     if (xfinal) memcpy(xfinal, xa, sizeof(double) * N * dx);
 
     free(xa); free(x); free(xr); free(l); free(cdf); free(wres); free(a);
-    free(lw); free(lw2); free(idx); free(idx2); free(tie_isl);
+    free(lw); free(lw2); free(idx); free(idx2); free(tie_isl); free(lom); free(lom2);
     return 0;
 }
 
