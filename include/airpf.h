@@ -134,6 +134,14 @@ typedef struct {
     int32_t islands_per_cta;/* islands per CTA: a power of 2, 0 = automatic (capped at 512 threads) */
     int32_t ckpt;           /* AIRPF_RECORD_GRAD: states kept every ckpt steps, recomputed in
                                between during the backward pass (0 = every step) */
+    double tau_int;         /* adaptive internal resampling (the remark after Algorithm 1): 0 = every
+                               island resamples at every step (Algorithm 1 as printed); in (0, 1], island
+                               k resamples at step t only when the ESS of its particle weights
+                               w_i = omega_i g_t(x_i), (sum w)^2 / sum w^2, is below tau_int M, and
+                               otherwise keeps its particles with omega_i = w_i / sum w; then
+                               W_{t,1} = W_{t,0} sum_i omega_i g_t(x_i) (M^-1 sum_i g_t(x_i) when
+                               omega = 1/M).  Not with AIRPF_RECORD_GRAD or AIRPF_RECORD_MOMENTS, nor
+                               with airpf_run_static (AIRPF_ERR_UNSUPPORTED). */
 } airpf_config;
 
 #define AIRPF_RECORD_LINEAGE 1

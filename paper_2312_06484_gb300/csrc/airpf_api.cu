@@ -39,6 +39,7 @@ struct WsLayout {
     size_t pm_prop, pm_logz_prop, pm_stats, pm_gprop, pm_lqf;
     size_t xck, xblk, logw, gpi[2], xh[3], dh[3], gout, sout;   // gradient pass
     size_t fw, fsum;                                             // output measures
+    size_t lom[2];                                               // adaptive internal resampling
     int fm_nw;
     size_t total;
 };
@@ -106,6 +107,7 @@ const char* check_config(const airpf_config* c)
     if (c->precision != AIRPF_FP64 && c->precision != AIRPF_FP32_MIXED) return "unknown precision";
     if (c->record < 0 || c->record > 63) return "unknown record bits";
     if (c->ckpt < 0 || c->ckpt > c->T) return "ckpt must be in [0, T]";
+    if (!(c->tau_int >= 0.0 && c->tau_int <= 1.0)) return "tau_int must be in [0, 1]";
     if (c->launch < 0 || c->launch > 4) return "unknown launch mode";
     if (c->reserved != 0) return "reserved must be 0";
     if (c->ppt != 0 && c->ppt != 2 && c->ppt != 4) return "ppt must be 0, 2 or 4";
@@ -170,6 +172,9 @@ WsLayout make_ws_layout(const airpf_config* c)
         L.gout = take(sizeof(double) * B * td);
         L.sout = take(sizeof(double) * B * td);
     }
+    L.lom[0] = L.lom[1] = 0;
+    if (c->tau_int > 0.0)
+        for (int i = 0; i < 2; ++i) L.lom[i] = take(rsz * B * N);
     L.fw = L.fsum = 0;
     L.fm_nw = 0;
     if (c->record & AIRPF_RECORD_MOMENTS) {
@@ -321,6 +326,11 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     }
     if ((cfg->record & AIRPF_RECORD_GRAD) && !airpf::grad_supported(cfg->model)) {
         set_err(nullptr, "the gradient pass supports the AR1, SV, NGM and LGSSM models");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    if (cfg->tau_int > 0.0 && (cfg->record & (AIRPF_RECORD_GRAD | AIRPF_RECORD_MOMENTS))) {
+        set_err(nullptr, "adaptive internal resampling (tau_int > 0) runs without the gradient and "
+                         "output-measure records");
         return AIRPF_ERR_UNSUPPORTED;
     }
     const WsLayout L = make_ws_layout(cfg);
@@ -495,6 +505,9 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         p.gout = at<double>(ctx, L.gout);
         p.sout = at<double>(ctx, L.sout);
     }
+    p.air = cfg->tau_int > 0.0 ? 1 : 0;
+    p.tau_int = cfg->tau_int;
+    for (int i = 0; i < 2; ++i) p.lom[i] = L.lom[i] ? at<void>(ctx, L.lom[i]) : nullptr;
     p.fmom = 0;
     p.fm_nw = 0;
     p.fw = p.fsum = nullptr;

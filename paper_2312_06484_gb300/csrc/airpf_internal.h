@@ -61,6 +61,11 @@ struct StepParams {
     // output measures (record AIRPF_RECORD_MOMENTS): per island and step, log W_{t,0} and
     // log W_{t,1}, and every warp's sums of x_d and x_d^2 over its mutated and its
     // internally resampled particles
+    // adaptive internal resampling: on when tau_int > 0; lom holds log(M omega) of every
+    // particle (0 after the island resampled), double-buffered like X
+    int air;
+    double tau_int;
+    void* lom[2];                 // [B][N]
     int fmom, fm_nw;              // recording on; warps per island
     double* fw;                   // [B][T][m][2]
     double* fsum;                 // [B][T][m][fm_nw][4 dx]

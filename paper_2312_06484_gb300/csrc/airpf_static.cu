@@ -118,6 +118,10 @@ extern "C" airpf_status airpf_run_static(const airpf_config* cfg, const double* 
         airpf::set_create_error("airpf_run_static runs AUTO, STEPS or PERSISTENT_CTA launches only");
         return AIRPF_ERR_UNSUPPORTED;
     }
+    if (cfg->tau_int > 0.0) {
+        airpf::set_create_error("airpf_run_static resamples every island at every step: tau_int must be 0");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
     if ((uint64_t)chain0 + (uint64_t)cfg->B > (1u << 24)) {
         airpf::set_create_error("airpf_run_static: chain0 + B must not exceed 2^24");
         return AIRPF_ERR_ARG;

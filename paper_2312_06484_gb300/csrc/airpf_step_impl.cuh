@@ -96,7 +96,7 @@ __host__ __device__ __forceinline__ int tree_off(int n, int l) { return 2 * n - 
 
 struct Layout {
     size_t tree, island, small, total;   // byte offsets
-    size_t cdf, xs, red, mxr;            // island sub-offsets
+    size_t cdf, xs, red, mxr, sqr;       // island sub-offsets
     size_t cdf_stride, xs_stride, red_stride;
 };
 
@@ -120,7 +120,8 @@ __host__ __device__ inline Layout make_layout(const StepParams& p)
     L.xs = L.cdf + align16(L.cdf_stride * p.G);
     L.red = L.xs + L.xs_stride * p.G;
     L.mxr = L.red + align16(L.red_stride * p.G);
-    const size_t islandb = L.mxr + align16(L.red_stride * p.G);
+    L.sqr = L.mxr + align16(L.red_stride * p.G);              // per-warp sums of squared weights
+    const size_t islandb = L.sqr + align16(L.red_stride * p.G);
     L.tree = 0;
     L.island = 0;                                             // overlaps the cascade region
     L.small = align16(treeb > islandb ? treeb : islandb);
@@ -1102,6 +1103,21 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     R* xs = reinterpret_cast<R*>(reinterpret_cast<unsigned char*>(xs_all) + L.xs_stride * g);
     Cdf* red = red_all + (size_t)g * (L.red_stride / sizeof(Cdf));
     R* mxr = mxr_all + (size_t)g * (L.red_stride / sizeof(R));
+    double* sqr = reinterpret_cast<double*>(smem + L.island + L.sqr) + (size_t)g * (L.red_stride / sizeof(double));
+    // adaptive internal resampling: log(M omega) of the parents, from the inherited block
+    // (0 after the parent island resampled; the prior draws at t = 1 carry 0)
+    const bool air = REC && p.air;
+    R lo[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) lo[r] = (R)0;
+    if (air && t >= 2) {
+        const R* Lp = reinterpret_cast<const R*>(p.lom[(t - 1) & 1]);
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int i = li * PPT + r;
+            if (i < M) lo[r] = __ldcg(&Lp[(size_t)c * N + (size_t)par * M + i]);
+        }
+    }
     R* Xc = reinterpret_cast<R*>(p.X[t & 1]);
 
     R xv[PPT][DX];
@@ -1129,6 +1145,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             }
             model_transition<R, MODEL, DX>(mp, dx, xp[r], xv[r], Am, z[r], w0[r]);
             lv[r] = model_logg<R, MODEL, DX>(mp, yv, dx, p.dy, xv[r], Cm);
+            if (air) lv[r] += lo[r];             // log(M omega_i g_t(x_i))
         }
     }
     if (REC && p.grad) {
@@ -1196,6 +1213,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     // weights and the thread-local inclusive prefix
     Cdf part[PPT];
     Cdf run_sum = 0;
+    double sq = 0.0;                // sum of squared weights (adaptive internal resampling)
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
         Cdf w = 0;
@@ -1205,16 +1223,23 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
         run_sum += w;
         part[r] = run_sum;
+        if (air) sq += (double)w * (double)w;
     }
+    if (air) sq = warp_sum(sq);
     // island-wide exclusive offset of this thread
     Cdf incl = warp_incl_scan(run_sum, lane);
     Cdf excl = incl - run_sum;
     if (nwi > 1) {
         if (lane == 31) red[wi] = incl;
+        if (air && lane == 0) sqr[wi] = sq;
         named_sync(1 + g, p.tpi);
         Cdf off = 0;
         for (int w = 0; w < wi; ++w) off += red[w];
         excl += off;
+        if (air) {
+            sq = 0.0;
+            for (int w = 0; w < nwi; ++w) sq += sqr[w];
+        }
     }
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
@@ -1241,14 +1266,33 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         if constexpr (!FX) target[r] = unif_f64(wres[r]) * total;
         else target[r] = __umulhi(wres[r], total);       // floor(w total / 2^32) < total
     }
-    for (int n = M; n > 1;) {
-        const int half = n >> 1;
+    // adaptive internal resampling: the island resamples only when the ESS of its
+    // weights, total^2 / sum w^2, is below tau_int M (the same for every thread of it)
+    const bool resample = !(air && alive) || ((double)total * (double)total / sq < p.tau_int * (double)M);
+    if (resample) {
+        for (int n = M; n > 1;) {
+            const int half = n >> 1;
+#pragma unroll
+            for (int r = 0; r < PPT; ++r) {
+                const Cdf v = cdf[cdf_ix(base[r] + half - 1)];
+                base[r] = (v > target[r]) ? base[r] : base[r] + half;
+            }
+            n -= half;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) base[r] = li * PPT + r;
+    }
+    if (air) {                      // the particles' log(M omega) after this step
+        R* Lc = reinterpret_cast<R*>(p.lom[t & 1]) + (size_t)c * N + (size_t)k * M;
+        // a kept particle: log(M w_i / total), w_i = exp(lv_i - max) (total in the CDF's scale)
+        const R lnorm = resample ? (R)0
+                                 : (R)(log((double)M) - log((double)total) + (FX ? log((double)p.cdf_scale) : 0.0));
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
-            const Cdf v = cdf[cdf_ix(base[r] + half - 1)];
-            base[r] = (v > target[r]) ? base[r] : base[r] + half;
+            const int i = li * PPT + r;
+            if (i < M) Lc[i] = resample ? (R)0 : lv[r] - mx + lnorm;
         }
-        n -= half;
     }
     R f1[DX], f2[DX];          // output measure at s = 1: the resampled particles
 #pragma unroll
@@ -1569,7 +1613,7 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     // step 1 follows the prologue in plain stream order; later steps may start
     // launching while the previous cascade runs (programmatic dependent launch)
     // the lean instantiations (no recording, one launch form) where they apply
-    const bool rec = p.anc != nullptr || p.grad != 0 || p.ires[0] != nullptr || p.fmom != 0;
+    const bool rec = p.anc != nullptr || p.grad != 0 || p.ires[0] != nullptr || p.fmom != 0 || p.air != 0;
     auto go = [&](auto kernel) -> cudaError_t {
         if (p.pdl && t >= 2) return launch_dependent(kernel, dim3(grid), dim3(block), smem, stream, p, t);
         kernel<<<grid, block, smem, stream>>>(p, t);
