@@ -54,6 +54,7 @@ def lib():
         _lib.oracle_model_valid.argtypes = [ctypes.c_int, ctypes.c_int, _D]
         _lib.oracle_set_tie_rel.argtypes = [ctypes.c_double]
         _lib.oracle_set_tau_int.argtypes = [ctypes.c_double]
+        _lib.oracle_set_radix.argtypes = [ctypes.c_int]
         _lib.oracle_airpf_batch.argtypes = [ctypes.c_int] * 6 + [ctypes.c_int, ctypes.c_double,
                                             ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.c_int, _D, _D, _D, _D]
@@ -98,7 +99,7 @@ def _model_data(model_data):
 
 
 def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, seed=0, chain=0,
-          iter=0, model_data=None, record=True, tie_rel=1e-12, moments=False, tau_int=0.0):
+          iter=0, model_data=None, record=True, tie_rel=1e-12, moments=False, tau_int=0.0, radix=2):
     """Literal Algorithm 1 (FP64).  Returns a dict with log_z and, if record,
     logz_trace[T], anc[T, N], src[T, m], enf[T, S+1], sstar[T], xfinal[N, dx], tie.
     tie_rel: relative width of the band around a threshold in which a draw, an island
@@ -108,9 +109,11 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
     W_{t,0}), [1] the filter after internal resampling (weighted by W_{t,1}); [., 0] E[x_d],
     [., 1] E[x_d^2].
     tau_int: adaptive internal resampling (an island resamples only when the ESS of its
-    particle weights is below tau_int M); 0 resamples at every step."""
+    particle weights is below tau_int M); 0 resamples at every step.
+    radix: interactions over groups of radix islands (a power of 2; m a power of it)."""
     lib().oracle_set_tie_rel(tie_rel)
     lib().oracle_set_tau_int(tau_int)
+    lib().oracle_set_radix(radix)
     y = _f64(y)
     T = len(y) // dy
     mom = np.zeros((T, 2, 2, dx)) if moments else None
@@ -132,6 +135,7 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
     lib().oracle_set_tie_rel(1e-12)
     lib().oracle_set_moments_out(None)
     lib().oracle_set_tau_int(0.0)
+    lib().oracle_set_radix(2)
     if rc:
         raise ValueError("oracle_airpf rejected its arguments")
     if moments:
@@ -142,15 +146,17 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
 
 
 def airpf_batch(model, theta, y, *, m, M, runs, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1,
-                seed=0, chain0=0, iter=0, model_data=None, tau_int=0.0) -> np.ndarray:
+                seed=0, chain0=0, iter=0, model_data=None, tau_int=0.0, radix=2) -> np.ndarray:
     """log Z of `runs` independent AIRPF runs keyed by chains chain0, chain0+1, ..."""
     y = _f64(y)
     T = len(y) // dy
     out = np.zeros(runs)
     lib().oracle_set_tau_int(tau_int)
+    lib().oracle_set_radix(radix)
     rc = lib().oracle_airpf_batch(model, dx, dy, m, M, T, mode, tau, seed, chain0, iter, runs,
                                   _dp(_f64(theta)), _dp(_model_data(model_data)), _dp(y), _dp(out))
     lib().oracle_set_tau_int(0.0)
+    lib().oracle_set_radix(2)
     if rc:
         raise ValueError("oracle_airpf_batch rejected its arguments")
     return out

@@ -103,6 +103,23 @@ static double TAU_INT = 0.0;
 
 void oracle_set_tau_int(double v) { TAU_INT = (v > 0.0 && v <= 1.0) ? v : 0.0; }
 
+/* Radix r = 2^b interactions (Section 2 fixes r = 2 "for simplicity"; m = r^(S/b)): stage
+ * s' = 1..S/b averages every aligned group of r islands (A_s = I (x) r^-1 1_r (x) I) and each
+ * island takes the block of one island of its group, chosen with probability proportional
+ * to the weights.  That is b binary stages that all interact: the pair means of b levels are
+ * the group mean, and the b pair choices compose to the r-way choice (P(a) = (W_a + W_b) /
+ * sum W * W_a / (W_a + W_b) for r = 4).  So the stage loop below stays binary and takes the
+ * adaptive decision only at the first binary stage of each group, with the ENF of the
+ * weights there (the r-ary stage's ENF), for the whole group. */
+static int RADIX_BITS = 1;
+
+void oracle_set_radix(int r)
+{
+    int b = 0;
+    while ((1 << b) < r) ++b;
+    RADIX_BITS = (r >= 2 && (1 << b) == r) ? b : 1;
+}
+
 /* when set, oracle_airpf writes the output measures' moments [T][2][2][dx] here */
 static double* MOMENTS_OUT = NULL;
 
@@ -495,6 +512,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
     if (m < 1 || (m & (m - 1)) || M < 1 || T < 1 || dx < 1 || dx > 64 || dy < 1) return 1;
     if (!(tau > 0.0 && tau <= 1.0)) return 1;
     if (TAU_INT > 0.0 && MOMENTS_OUT) return 1;   /* the output measures assume resampling */
+    if (ilog2(m) % RADIX_BITS != 0) return 1;      /* m must be a power of the radix */
     const int N = m * M, S = ilog2(m);
     model_t md = { model, dx, dy, theta, mdat };
     stream_id st = { seed, chain, iter };
@@ -583,12 +601,16 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
         /* interaction stages s = 1..S (butterfly matrices A_s) */
         for (int k = 0; k < m; ++k) idx[k] = k;
         int first_quiet = S + 1;
+        int group_interact = 1;
         for (int s = 1; s <= S; ++s) {
             double e = enf_of(lw, m);
             if (enf) enf[(size_t)(t - 1) * (S + 1) + s] = e;
-            int interact = (mode == MODE_ALWAYS) || (mode == MODE_ADAPTIVE && e < tau);
-            if (mode == MODE_ADAPTIVE && fabs(e - tau) < TIE_REL * tau && tie_now == TIE_NONE)
-                tie_now = TIE_ENF;
+            if ((s - 1) % RADIX_BITS == 0) {       /* the first binary stage of an r-ary stage */
+                group_interact = (mode == MODE_ALWAYS) || (mode == MODE_ADAPTIVE && e < tau);
+                if (mode == MODE_ADAPTIVE && fabs(e - tau) < TIE_REL * tau && tie_now == TIE_NONE)
+                    tie_now = TIE_ENF;
+            }
+            int interact = group_interact;
             if (!interact) {
                 if (first_quiet == S + 1) first_quiet = s;
                 continue;            /* alpha_s = I: weights and blocks unchanged */
