@@ -142,6 +142,13 @@ typedef struct {
                                W_{t,1} = W_{t,0} sum_i omega_i g_t(x_i) (M^-1 sum_i g_t(x_i) when
                                omega = 1/M).  Not with AIRPF_RECORD_GRAD or AIRPF_RECORD_MOMENTS, nor
                                with airpf_run_static (AIRPF_ERR_UNSUPPORTED). */
+    int32_t radix;          /* islands averaged per interaction stage, r = 2^b (0 or 2: the paper's
+                               binary stages); m must be a power of r.  Stage s averages aligned groups
+                               of r islands (A_s = I (x) r^-1 1_r (x) I) and each island takes one
+                               group member's block with probability proportional to its weight;
+                               computed as b binary stages that all interact or all stay quiet, decided
+                               by the ENF at the group's first binary stage (ENF records keep every
+                               binary stage) */
 } airpf_config;
 
 #define AIRPF_RECORD_LINEAGE 1

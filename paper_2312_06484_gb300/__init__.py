@@ -44,7 +44,7 @@ class AIRPF:
     def __init__(self, model: int, *, m: int, M: int, T: int, B: int = 1, dx: int = 1, dy: int = 1,
                  mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, record: int = 0,
                  model_data=None, stream=None, launch="auto", ppt: int = 0, islands_per_cta: int = 0,
-                 ckpt: int = 0, tau_int: float = 0.0):
+                 ckpt: int = 0, tau_int: float = 0.0, radix: int = 2):
         import torch
         self._torch = torch
         self.lib = _binding.load()
@@ -53,7 +53,7 @@ class AIRPF:
         launch = _LAUNCH[launch] if isinstance(launch, str) else int(launch)
         self.cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau,
                                precision=precision, record=record, seed=seed, launch=launch, reserved=0,
-                               ppt=ppt, islands_per_cta=islands_per_cta, ckpt=ckpt, tau_int=tau_int)
+                               ppt=ppt, islands_per_cta=islands_per_cta, ckpt=ckpt, tau_int=tau_int, radix=radix)
         nbytes = ctypes.c_size_t()
         _binding.check(self.lib.airpf_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)))
         self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
@@ -312,7 +312,8 @@ def autotune(model, theta, y, *, m: int, M: int, B: int = 1, dx: int = 1, dy: in
 
 def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: int = 1, dy: int = 1,
                mode="adaptive", tau: float = 0.3, precision="fp64", seed: int = 0, chain0: int = 0,
-               iter: int = 0, model_data=None, launch="auto", stream=None, tau_int: float = 0.0):
+               iter: int = 0, model_data=None, launch="auto", stream=None, tau_int: float = 0.0,
+               radix: int = 2):
     """One pass through airpf_run_static: no context and no device allocation (the library's
     static scratch serves as workspace).  theta [B, d], y [T*dy], log_z [B] (out) and the
     optional model_data are float64 CUDA tensors, used in place."""
@@ -323,7 +324,7 @@ def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: i
     launch = _LAUNCH[launch] if isinstance(launch, str) else int(launch)
     T = y.numel() // dy
     cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau, precision=precision,
-                      record=0, seed=seed, launch=launch, reserved=0, tau_int=tau_int)
+                      record=0, seed=seed, launch=launch, reserved=0, tau_int=tau_int, radix=radix)
     for t in (theta, y, log_z) + ((model_data,) if model_data is not None else ()):
         assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
     stream = stream if stream is not None else torch.cuda.current_stream()

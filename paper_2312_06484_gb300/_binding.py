@@ -22,7 +22,8 @@ class AirpfConfig(ctypes.Structure):
                 ("M", c_int32), ("T", c_int32), ("B", c_int32), ("mode", c_int32),
                 ("tau", c_double), ("precision", c_int32), ("record", c_int32),
                 ("seed", c_uint64), ("launch", c_int32), ("reserved", c_int32), ("ppt", c_int32),
-                ("islands_per_cta", c_int32), ("ckpt", c_int32), ("tau_int", c_double)]
+                ("islands_per_cta", c_int32), ("ckpt", c_int32), ("tau_int", c_double),
+                ("radix", c_int32)]
 
 
 # every symbol include/airpf.h declares, with (restype, argtypes)

@@ -108,6 +108,12 @@ const char* check_config(const airpf_config* c)
     if (c->record < 0 || c->record > 63) return "unknown record bits";
     if (c->ckpt < 0 || c->ckpt > c->T) return "ckpt must be in [0, T]";
     if (!(c->tau_int >= 0.0 && c->tau_int <= 1.0)) return "tau_int must be in [0, 1]";
+    if (c->radix != 0) {
+        if (c->radix < 2 || (c->radix & (c->radix - 1))) return "radix must be 0 or a power of 2";
+        int b = 0;
+        while ((1 << b) < c->radix) ++b;
+        if (ilog2_exact(c->m) % b != 0) return "m must be a power of the radix";
+    }
     if (c->launch < 0 || c->launch > 4) return "unknown launch mode";
     if (c->reserved != 0) return "reserved must be 0";
     if (c->ppt != 0 && c->ppt != 2 && c->ppt != 4) return "ppt must be 0, 2 or 4";
@@ -505,6 +511,8 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         p.gout = at<double>(ctx, L.gout);
         p.sout = at<double>(ctx, L.sout);
     }
+    p.rb = 1;
+    while (cfg->radix > 2 && (1 << p.rb) < cfg->radix) ++p.rb;
     p.air = cfg->tau_int > 0.0 ? 1 : 0;
     p.tau_int = cfg->tau_int;
     for (int i = 0; i < 2; ++i) p.lom[i] = L.lom[i] ? at<void>(ctx, L.lom[i]) : nullptr;

@@ -65,6 +65,7 @@ struct StepParams {
     // particle (0 after the island resampled), double-buffered like X
     int air;
     double tau_int;
+    int rb;                       // radix bits: an r-ary stage is rb binary stages (1: binary)
     void* lom[2];                 // [B][N]
     int fmom, fm_nw;              // recording on; warps per island
     double* fw;                   // [B][T][m][2]

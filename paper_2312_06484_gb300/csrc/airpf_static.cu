@@ -138,6 +138,8 @@ extern "C" airpf_status airpf_run_static(const airpf_config* cfg, const double* 
 
     StepParams p;
     std::memset(&p, 0, sizeof(p));
+    p.rb = 1;
+    while (cfg->radix > 2 && (1 << p.rb) < cfg->radix) ++p.rb;
     p.B = cfg->B; p.m = cfg->m; p.M = cfg->M; p.N = cfg->m * cfg->M; p.dx = cfg->dx; p.dy = cfg->dy;
     p.T = cfg->T; p.mode = cfg->mode; p.model = cfg->model;
     while ((1 << p.S) < cfg->m) ++p.S;

@@ -743,8 +743,9 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
         bool quiet = false;
         if (lane < S) {
             const int s = lane + 1;
-            // stage s interacts iff ENF_s < tau, i.e. Tot^2 2^(s-1) < tau m Q_{s-1}
-            quiet = pos_v(tot) && !(tq * tq * (Qt)(1u << (s - 1)) < C::tau(p) * (Qt)m * Q[s - 1]);
+            // stage s interacts iff ENF_s < tau, i.e. Tot^2 2^(s-1) < tau m Q_{s-1}; with radix
+            // 2^rb only the first binary stage of each group decides (for the whole group)
+            quiet = (s - 1) % p.rb == 0 && pos_v(tot) && !(tq * tq * (Qt)(1u << (s - 1)) < C::tau(p) * (Qt)m * Q[s - 1]);
         }
         const unsigned qm = __ballot_sync(0xffffffffu, quiet);
         if (lane == 0) {

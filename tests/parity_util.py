@@ -11,12 +11,12 @@ ENF_RTOL = 1e-10
 
 
 def run_gpu(model, theta, y, *, m, M, B=1, mode, tau=0.3, dx=1, dy=1, seed=0, chain0=0, iter=0,
-            model_data=None, precision="fp64", record=7, launch="auto", tau_int=0.0):
+            model_data=None, precision="fp64", record=7, launch="auto", tau_int=0.0, radix=2):
     import torch
     import paper_2312_06484_gb300 as gp
     f = gp.AIRPF(model, m=m, M=M, T=len(y) // dy, B=B, dx=dx, dy=dy, mode=mode, tau=tau,
                  precision=precision, seed=seed, record=record, model_data=model_data, launch=launch,
-                 tau_int=tau_int)
+                 tau_int=tau_int, radix=radix)
     th = torch.tensor(np.tile(np.asarray(theta, np.float64), (B, 1)), device="cuda")
     if np.ndim(theta) == 2:
         th = torch.tensor(np.asarray(theta, np.float64), device="cuda")
