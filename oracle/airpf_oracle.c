@@ -103,7 +103,7 @@ static double TAU_INT = 0.0;
 
 void oracle_set_tau_int(double v) { TAU_INT = (v > 0.0 && v <= 1.0) ? v : 0.0; }
 
-/* Radix r = 2^b interactions (Section 2 fixes r = 2 "for simplicity"; m = r^(S/b)): stage
+/* Radix r = 2^b interactions (Section 2 restricts itself to r = 2; m = r^(S/b)): stage
  * s' = 1..S/b averages every aligned group of r islands (A_s = I (x) r^-1 1_r (x) I) and each
  * island takes the block of one island of its group, chosen with probability proportional
  * to the weights.  That is b binary stages that all interact: the pair means of b levels are
