@@ -188,6 +188,12 @@ __device__ __forceinline__ void stream_normals(const Stream& st, uint32_t kind, 
     }
 }
 
+// a / b: IEEE in double; the SFU reciprocal and a multiply in float (within 2 ulp for
+// |b| < 2^126)
+template <typename R> __device__ __forceinline__ R fdiv(R a, R b);
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 template <typename R> __device__ __forceinline__ R unif_r(uint32_t w);
 template <> __device__ __forceinline__ double unif_r<double>(uint32_t w) { return unif_f64(w); }
 template <> __device__ __forceinline__ float unif_r<float>(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
@@ -265,7 +271,7 @@ __device__ __forceinline__ void model_transition(const ModelPar<R>& p, int dx, c
     if (MODEL == SV) x[0] = p.th[0] + p.th[1] * (xp[0] - p.th[0]) + p.th[2] * z[0];
     if (MODEL == NGM) {
         const R v = xp[0];
-        x[0] = (R)0.5 * v + (R)25 * v / ((R)1 + v * v) + p.drift + p.c0 * z[0];
+        x[0] = (R)0.5 * v + fdiv<R>((R)25 * v, (R)1 + v * v) + p.drift + p.c0 * z[0];
     }
     if (MODEL == TOY) x[0] = (unif_f64(w0) < (double)p.c0) ? (R)1 - xp[0] : xp[0];
     if (MODEL == CP) x[0] = (unif_f64(w0) < (double)p.th[0]) ? z[0] : xp[0];   // z: the jump's Beta draw
