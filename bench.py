@@ -47,7 +47,7 @@ OPS_PER_PARTICLE_STEP = 210
 # (airpf_step_kernel<float, SV, 1, 4, false, 3>), from one ncu capture with a cold cache:
 # dram__bytes_read.sum 1.160 MB, dram__bytes_write.sum 0.  Set to None when that kernel changes
 # until it is captured again.
-SV_STEP_DRAM_BYTES = 1159936
+SV_STEP_DRAM_BYTES = 1159680
 SV_STEP_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
                        "airpf_step_kernel<float, SV, 1, 4, false, 3>, cold cache "
                        "(profiles/airpf_step_kernel_sv_m1024_M256_T1000.md)")
