@@ -201,7 +201,7 @@ __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, c
         s = mp.th[2];
     } else if (MODEL == NGM) {
         const R v = xp[0];
-        mu[0] = (R)0.5 * v + (R)25 * v / ((R)1 + v * v) + mp.drift;
+        mu[0] = (R)0.5 * v + fdiv<R>((R)25 * v, (R)1 + v * v) + mp.drift;   // as the forward transition
         s = mp.c0;                       // sqrt(q)
     } else {
 #pragma unroll
