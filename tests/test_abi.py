@@ -63,3 +63,12 @@ def test_lineage_record_sizes_grow_workspace():
     lib.airpf_workspace_bytes(ctypes.byref(_cfg(m=16, M=64, T=100)), ctypes.byref(a))
     lib.airpf_workspace_bytes(ctypes.byref(_cfg(m=16, M=64, T=100, record=7)), ctypes.byref(b))
     assert b.value - a.value >= 100 * 1024 * 4
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built CUDA library the binding raises."""
+    from paper_2312_06484_gb300 import _binding, build as _build
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing" / "libairpf.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        _binding.load(build_if_needed=False)
