@@ -42,7 +42,9 @@ def test_workspace_size_and_argument_checks():
     bad = [dict(m=3), dict(m=131072), dict(M=0), dict(M=1025), dict(T=0), dict(B=0), dict(tau=0.0),
            dict(tau=1.01), dict(mode=3), dict(model=9), dict(dx=2), dict(model=3, dx=9),
            dict(precision=7), dict(record=64), dict(launch=5), dict(reserved=1),
-           dict(ppt=3), dict(ppt=8), dict(islands_per_cta=3), dict(islands_per_cta=-2)]
+           dict(ppt=3), dict(ppt=8), dict(islands_per_cta=3), dict(islands_per_cta=-2),
+           dict(tau_int=-0.1), dict(tau_int=1.5), dict(radix=3), dict(radix=1), dict(radix=8),
+           dict(model=5), dict(model=5, dy=1)]
     for kw in bad:
         assert lib.airpf_workspace_bytes(ctypes.byref(_cfg(**kw)), ctypes.byref(n)) == 1, kw
         assert lib.airpf_last_error(None)
@@ -52,7 +54,15 @@ def test_workspace_size_and_argument_checks():
     assert out.value is None
     assert lib.airpf_create(ctypes.byref(_cfg(model=3, dx=2, dy=2)), None, 0, None, None,
                             ctypes.byref(out)) == 1          # LGSSM without model data
-    assert lib.airpf_theta_dim(0, 1) == 4 and lib.airpf_theta_dim(3, 8) == 10
+    # valid: radix 4 and 1024 = 4^5 islands, adaptive internal resampling, the change-point model
+    for kw in (dict(radix=4), dict(radix=1024), dict(tau_int=0.5), dict(model=5, dy=2)):
+        assert lib.airpf_workspace_bytes(ctypes.byref(_cfg(**kw)), ctypes.byref(n)) == 0, kw
+    # tau_int keeps one log-weight per particle per buffer (two buffers of N floats)
+    base, air = ctypes.c_size_t(), ctypes.c_size_t()
+    lib.airpf_workspace_bytes(ctypes.byref(_cfg()), ctypes.byref(base))
+    lib.airpf_workspace_bytes(ctypes.byref(_cfg(tau_int=0.5)), ctypes.byref(air))
+    assert air.value - base.value >= 2 * 262144 * 4
+    assert lib.airpf_theta_dim(0, 1) == 4 and lib.airpf_theta_dim(3, 8) == 10 and lib.airpf_theta_dim(5, 1) == 3
     assert lib.airpf_status_string(4) == b"AIRPF_ERR_TIMEOUT"
     assert lib.airpf_run(None, None, None, 0, 0, None, None, None, None, None) == 1
 
