@@ -428,12 +428,9 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     // 512 CTAs, where reading all CTA records in every CTA would cost more)
     if (ctx->launch == AIRPF_LAUNCH_AUTO)
         ctx->launch = p.P <= 512 ? AIRPF_LAUNCH_STEPS : AIRPF_LAUNCH_STEPS_SPLIT;
-    if (ctx->launch == AIRPF_LAUNCH_STEPS_SPLIT && cfg->islands_per_cta == 0) {
-        // split steps: 512-thread CTAs, so the one-CTA cascade reads half as many records
-        airpf::choose_mapping(cfg->m, cfg->M, p.fp64, cfg->ppt, 512 / p.tpi, &p.tpi, &p.ppt, &p.G);
-        p.P = cfg->m / p.G;
-        p.g = ilog2_exact(p.G);
-    }
+    // (split steps keep the default 256-thread CTAs: on the m = 65536 workload they beat
+    // 512-thread CTAs by 5-6% at M = 256 and 512 -- the block barriers of 16 warps cost more
+    // than the cascade kernel's twice as many records -- and lose 1% at M = 64)
     // per-step launches overlap each kernel's start with the previous one
     // (programmatic dependent launch); fused steps have no cascade kernel
     p.pdl = is_steps(ctx->launch) ? 1 : 0;
