@@ -11,6 +11,18 @@
 // cascade itself between block barriers); the cooperative-grid launch runs the
 // cascade in the filter's first CTA between two bounded grid barriers.
 // CTA j of a filter owns the G islands j*G .. j*G+G-1.
+// The default launch form is fused steps: one island-step launch per step in
+// which every CTA first runs the previous step's cascade itself from all m/G
+// CTA records (the stage-1 test alone on most steps), then its islands; split
+// steps (above 512 CTAs per filter) keep the separate one-CTA cascade kernel,
+// which leaves the upper tree in global memory for the island CTAs.  With
+// programmatic dependent launch each kernel draws its random numbers before it
+// waits for the previous one.
+//
+// Variants on the same kernels: radix r = 2^b interactions take the adaptive
+// decision only at the first binary stage of each group of b; adaptive internal
+// resampling (recording instantiation) carries log(M omega) per particle and
+// skips an island's resampling while its ESS is at least tau_int M.
 //
 // Island weights W^k are kept unnormalised, as in Algorithm 1, in an extended
 // range (mantissa plus integer binary exponent).  At the end of step t each
