@@ -184,10 +184,12 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.fw = L.fsum = 0;
     L.fm_nw = 0;
     if (c->record & AIRPF_RECORD_MOMENTS) {
-        // warps per island: the threads per island depend only on M and the requested ppt
-        int tpi = 0, pp = 0, G = 0;
+        // warps per island: the threads per island depend only on M and the particles per
+        // thread (the requested count, or the default and the small-grid choice of two)
+        int tpi = 0, pp = 0, G = 0, tpi2 = 0;
         airpf::choose_mapping(c->m, c->M, c->precision == AIRPF_FP64, c->ppt, 0, &tpi, &pp, &G);
-        L.fm_nw = tpi / 32;
+        if (c->ppt == 0) airpf::choose_mapping(c->m, c->M, c->precision == AIRPF_FP64, 2, 1, &tpi2, &pp, &G);
+        L.fm_nw = (tpi > tpi2 ? tpi : tpi2) / 32;
         L.fw = take(sizeof(double) * B * T * c->m * 2);
         L.fsum = take(sizeof(double) * B * T * c->m * L.fm_nw * 4 * c->dx);
     }
@@ -405,6 +407,16 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
             }
         }
         ctx->launch = mode;
+        // per-step launches whose default tiling leaves SMs idle (fewer CTAs than SMs): two
+        // particles per thread and one island per CTA spread the filters over more SMs
+        // (measured 9-18% faster per pass for one filter of m = 64..256 islands)
+        if (mode != AIRPF_LAUNCH_PERSISTENT_CTA && cfg->ppt == 0 && cfg->islands_per_cta == 0) {
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                (long long)cfg->B * (cfg->m / p.G) < sms)
+                airpf::choose_mapping(cfg->m, cfg->M, p.fp64, 2, 1, &p.tpi, &p.ppt, &p.G);
+        }
     }
     p.P = cfg->m / p.G;
     p.g = ilog2_exact(p.G);
@@ -517,14 +529,14 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.fm_nw = 0;
     p.fw = p.fsum = nullptr;
     if (cfg->record & AIRPF_RECORD_MOMENTS) {
-        if (p.tpi / 32 != L.fm_nw) {
+        if (p.tpi / 32 > L.fm_nw) {
             set_err(nullptr, "internal: warps per island %d, workspace sized for %d", p.tpi / 32, L.fm_nw);
             cudaStreamDestroy(ctx->cap_stream);
             delete ctx;
             return AIRPF_ERR_UNSUPPORTED;
         }
         p.fmom = 1;
-        p.fm_nw = L.fm_nw;
+        p.fm_nw = p.tpi / 32;
         p.fw = at<double>(ctx, L.fw);
         p.fsum = at<double>(ctx, L.fsum);
     }
