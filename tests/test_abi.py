@@ -82,3 +82,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing" / "libairpf.so"))
     with pytest.raises(RuntimeError, match="missing"):
         _binding.load(build_if_needed=False)
+
+
+def test_moments_workspace_covers_the_small_grid_tiling():
+    """With AIRPF_RECORD_MOMENTS the per-warp island sums are sized for the larger of the
+    default tiling (4 particles a thread: 64 threads for M = 200) and the small-grid one
+    (2 a thread: 128 threads, 4 warps per island), which a context of few CTAs takes."""
+    lib = _binding.load()
+    base, mom = ctypes.c_size_t(), ctypes.c_size_t()
+    kw = dict(model=5, dy=2, m=64, M=200, T=50, B=3)
+    assert lib.airpf_workspace_bytes(ctypes.byref(_cfg(**kw)), ctypes.byref(base)) == 0
+    assert lib.airpf_workspace_bytes(ctypes.byref(_cfg(record=32, **kw)), ctypes.byref(mom)) == 0
+    B, T, m, dx = 3, 50, 64, 1
+    need = 8 * B * T * m * 2 + 8 * B * T * m * 4 * 4 * dx       # log W pairs, 4 warps x 4 dx sums
+    assert need <= mom.value - base.value < need + 2 * 256
