@@ -55,6 +55,7 @@ def lib():
         _lib.oracle_set_tie_rel.argtypes = [ctypes.c_double]
         _lib.oracle_set_tau_int.argtypes = [ctypes.c_double]
         _lib.oracle_set_radix.argtypes = [ctypes.c_int]
+        _lib.oracle_set_tie_masks.argtypes = [ctypes.c_void_p] * 3
         _lib.oracle_airpf_batch.argtypes = [ctypes.c_int] * 6 + [ctypes.c_int, ctypes.c_double,
                                             ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.c_int, _D, _D, _D, _D]
@@ -99,9 +100,11 @@ def _model_data(model_data):
 
 
 def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, seed=0, chain=0,
-          iter=0, model_data=None, record=True, tie_rel=1e-12, moments=False, tau_int=0.0, radix=2):
+          iter=0, model_data=None, record=True, tie_rel=1e-12, moments=False, tau_int=0.0, radix=2,
+          tie_masks=False):
     """Literal Algorithm 1 (FP64).  Returns a dict with log_z and, if record,
-    logz_trace[T], anc[T, N], src[T, m], enf[T, S+1], sstar[T], xfinal[N, dx], tie.
+    logz_trace[T], anc[T, N], src[T, m], enf[T, S_r+1], sstar[T], xfinal[N, dx], tie, where
+    S_r = log_radix(m) is the number of interaction stages and s* counts them.
     tie_rel: relative width of the band around a threshold in which a draw, an island
     choice or an ENF test is flagged as a tie (a diagnostic; the arithmetic is unchanged).
     moments: also return moments[T, 2, 2, dx], the output measures of the paper's output-
@@ -110,7 +113,12 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
     [., 1] E[x_d^2].
     tau_int: adaptive internal resampling (an island resamples only when the ESS of its
     particle weights is below tau_int M); 0 resamples at every step.
-    radix: interactions over groups of radix islands (a power of 2; m a power of it)."""
+    radix: interactions over groups of radix islands (a power of 2; m a power of it): each
+    stage averages every group of r islands and each island draws one member of its group
+    with probability proportional to the weights.
+    tie_masks: also return tie_draw[T, N] (internal draw j of island k, index k*M+j, within
+    the tie band), tie_src[T, m] (a tied island choice on the walk that gives island k its
+    block) and tie_step[T] (a tied ENF test), as booleans."""
     lib().oracle_set_tie_rel(tie_rel)
     lib().oracle_set_tau_int(tau_int)
     lib().oracle_set_radix(radix)
@@ -118,7 +126,13 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
     T = len(y) // dy
     mom = np.zeros((T, 2, 2, dx)) if moments else None
     lib().oracle_set_moments_out(_dp(mom))
-    S = int(round(math.log2(m)))
+    masks = None
+    if tie_masks:
+        masks = dict(tie_draw=np.zeros((T, m * M), np.uint8), tie_src=np.zeros((T, m), np.uint8),
+                     tie_step=np.zeros(T, np.uint8))
+        lib().oracle_set_tie_masks(masks["tie_draw"].ctypes.data, masks["tie_src"].ctypes.data,
+                                   masks["tie_step"].ctypes.data)
+    S = int(round(math.log2(m))) // max(1, int(round(math.log2(radix))))
     N = m * M
     th, md = _f64(theta), _model_data(model_data)
     lz = np.zeros(1)
@@ -134,12 +148,15 @@ def airpf(model, theta, y, *, m, M, mode=MODE_ADAPTIVE, tau=0.3, dx=1, dy=1, see
                             _ip(out.get("sstar")), _dp(out.get("xfinal")), _ip(tie))
     lib().oracle_set_tie_rel(1e-12)
     lib().oracle_set_moments_out(None)
+    lib().oracle_set_tie_masks(None, None, None)
     lib().oracle_set_tau_int(0.0)
     lib().oracle_set_radix(2)
     if rc:
         raise ValueError("oracle_airpf rejected its arguments")
     if moments:
         out["moments"] = mom
+    if masks:
+        out.update({k: v.astype(bool) for k, v in masks.items()})
     out["log_z"] = float(lz[0])
     out["tie"] = (int(tie[0]), int(tie[1]))
     return out
@@ -236,16 +253,18 @@ def model_logmu(model, theta, x, *, dx=1, dy=1, model_data=None) -> float:
 
 
 def logz_fixed(model, theta, y, anc, sstar, *, m, M, dx=1, dy=1, seed=0, chain=0, iter=0,
-               model_data=None) -> float:
+               model_data=None, radix=2) -> float:
     """log Z of a run with its random numbers, lineage anc [T, N] and s* [T] held fixed,
-    as a function of theta (FP64)."""
+    as a function of theta (FP64).  radix: the run's (s* counts stages of r islands)."""
     y = _f64(y)
     T = len(y) // dy
     anc = np.ascontiguousarray(np.asarray(anc, dtype=np.int32).reshape(T, m * M))
     sstar = np.ascontiguousarray(np.asarray(sstar, dtype=np.int32).reshape(T))
     out = np.zeros(1)
+    lib().oracle_set_radix(radix)
     rc = lib().oracle_logz_fixed(model, dx, dy, m, M, T, seed, chain, iter, _dp(_f64(theta)),
                                  _dp(_model_data(model_data)), _dp(y), _ip(anc), _ip(sstar), _dp(out))
+    lib().oracle_set_radix(2)
     if rc:
         raise ValueError("oracle_logz_fixed rejected its arguments")
     return float(out[0])
@@ -273,17 +292,19 @@ def logz_fixed_gradient(model, theta, y, anc, sstar, *, h=1e-5, **kw) -> np.ndar
 
 
 def fisher_score(model, theta, y, anc, sstar, *, m, M, dx=1, dy=1, seed=0, chain=0, iter=0,
-                 model_data=None) -> np.ndarray:
-    """Fisher-identity score along the lineages of a run (FP64)."""
+                 model_data=None, radix=2) -> np.ndarray:
+    """Fisher-identity score along the lineages of a run (FP64); radix as for logz_fixed."""
     y = _f64(y)
     T = len(y) // dy
     th = _f64(theta)
     anc = np.ascontiguousarray(np.asarray(anc, dtype=np.int32).reshape(T, m * M))
     sstar = np.ascontiguousarray(np.asarray(sstar, dtype=np.int32).reshape(T))
     out = np.zeros(len(th))
+    lib().oracle_set_radix(radix)
     rc = lib().oracle_fisher_score(model, dx, dy, m, M, T, seed, chain, iter, _dp(th),
                                    _dp(_model_data(model_data)), _dp(y), _ip(anc), _ip(sstar), len(th),
                                    _dp(out))
+    lib().oracle_set_radix(2)
     if rc:
         raise ValueError("oracle_fisher_score rejected its arguments")
     return out

@@ -41,7 +41,9 @@
  *   - an island whose particle weights are all zero keeps a_j = j;
  *   - a stage picks, for island k, the lower island of the pair
  *     {k, k xor 2^(s-1)} iff u * (W_lo + W_hi) < W_lo, one uniform per
- *     (t, s, k), independently over k (Section 3.3, eqs. (28)-(29));
+ *     (t, s, k), independently over k (Section 3.3, eqs. (28)-(29)); with
+ *     radix r, the first member c of k's group with C_c > u * sum W
+ *     (C the cumulative member weights in member order);
  *   - adaptive interaction uses the strict test ENF < tau (Algorithm 1);
  *   - a NaN log-weight counts as -inf (weight zero);
  *   - change-point model (Section 4.2): the daily count k_t of the n_t articles
@@ -103,14 +105,15 @@ static double TAU_INT = 0.0;
 
 void oracle_set_tau_int(double v) { TAU_INT = (v > 0.0 && v <= 1.0) ? v : 0.0; }
 
-/* Radix r = 2^b interactions (Section 2 restricts itself to r = 2; m = r^(S/b)): stage
- * s' = 1..S/b averages every aligned group of r islands (A_s = I (x) r^-1 1_r (x) I) and each
- * island takes the block of one island of its group, chosen with probability proportional
- * to the weights.  That is b binary stages that all interact: the pair means of b levels are
- * the group mean, and the b pair choices compose to the r-way choice (P(a) = (W_a + W_b) /
- * sum W * W_a / (W_a + W_b) for r = 4).  So the stage loop below stays binary and takes the
- * adaptive decision only at the first binary stage of each group, with the ENF of the
- * weights there (the r-ary stage's ENF), for the whole group. */
+/* Radix r = 2^b interactions (Section 2 restricts itself to r = 2 and states that the
+ * analysis does not rely on it): m = r^S_r islands interact in S_r stages, stage s with
+ * A_s = I_{r^(S_r - s)} (x) r^-1 1_r (x) I_{r^(s-1)}.  Island k's group at stage s is the r
+ * islands whose base-r digits equal k's except digit s-1.  When the stage interacts
+ * (Algorithm 1's adaptation line with the ENF of the weights before the stage), every
+ * island's new weight is its group's mean (the normaliser line) and every island draws, from
+ * its own uniform, one member of its group with probability proportional to the members'
+ * weights (the selection line), independently of the other islands.  r = 2 is the binary
+ * butterfly of eq. (3). */
 static int RADIX_BITS = 1;
 
 void oracle_set_radix(int r)
@@ -124,6 +127,22 @@ void oracle_set_radix(int r)
 static double* MOMENTS_OUT = NULL;
 
 void oracle_set_moments_out(double* p) { MOMENTS_OUT = p; }
+
+/* When set, oracle_airpf marks, for every step t, which decisions fell within the tie band
+ * (a diagnostic for comparing an implementation draw by draw; the arithmetic is unchanged):
+ *   TIE_DRAW [T*N]: internal draw j of island k (index k*M+j) within the band of a CDF boundary
+ *                   (or, with adaptive internal resampling, island k's ESS test);
+ *   TIE_SRC  [T*m]: some island choice on the walk that gives island k its block was within
+ *                   the band of a boundary;
+ *   TIE_STEP [T]  : some ENF test of step t was within the band of tau. */
+static uint8_t *TIE_DRAW = NULL, *TIE_SRC = NULL, *TIE_STEP = NULL;
+
+void oracle_set_tie_masks(uint8_t* draw, uint8_t* src, uint8_t* step)
+{
+    TIE_DRAW = draw;
+    TIE_SRC = src;
+    TIE_STEP = step;
+}
 
 /* Eq. (output measure) of Section 2: pi^N_{t,s}(phi) = sum_k W^k_{t,s} M^-1 sum_i
  * phi(xi^{k,i}_{t,s}) / sum_k W^k_{t,s}, for phi = x_d (out[d]) and x_d^2
@@ -452,14 +471,16 @@ static double enf_of(const double* lw, int m)
 
 /* Multinomial internal resampling of one island (Algorithm 1, internal
  * resample): draw j takes the first i with C_i > u_j * C_{M-1}.  Returns 1 if
- * some draw fell within TIE_REL * C_{M-1} of a CDF boundary. */
+ * some draw fell within TIE_REL * C_{M-1} of a CDF boundary; flags[j] (if not
+ * NULL) marks those draws. */
 static int resample_island(const double* l, int M, const uint32_t* wres,
-                           double* cdf, int32_t* a)
+                           double* cdf, int32_t* a, uint8_t* flags)
 {
     double mx = -INFINITY;
     for (int i = 0; i < M; ++i) if (l[i] > mx) mx = l[i];
     if (mx == -INFINITY) {                 /* all weights zero */
         for (int j = 0; j < M; ++j) a[j] = j;
+        if (flags) memset(flags, 0, (size_t)M);
         return 0;
     }
     double acc = 0.0;
@@ -475,8 +496,9 @@ static int resample_island(const double* l, int M, const uint32_t* wres,
         while (i < M - 1 && !(cdf[i] > target)) ++i;
         a[j] = i;
         double tol = TIE_REL * total;
-        if (fabs(cdf[i] - target) < tol) tie = 1;
-        if (i > 0 && fabs(cdf[i - 1] - target) < tol) tie = 1;
+        int near = fabs(cdf[i] - target) < tol || (i > 0 && fabs(cdf[i - 1] - target) < tol);
+        if (near) tie = 1;
+        if (flags) flags[j] = (uint8_t)near;
     }
     return tie;
 }
@@ -497,8 +519,8 @@ typedef struct {
     int32_t* anc;        /* [T*N] parent (among the time-t particles) of the
                             particle k*M+i held after step t, or NULL */
     int32_t* src;        /* [T*m] island whose block island k holds after step t */
-    double* enf;         /* [T*(S+1)] ENF_{t,0..S}, or NULL */
-    int32_t* sstar;      /* [T] first non-interacting stage (S+1 if all interact) */
+    double* enf;         /* [T*(S_r+1)] ENF_{t,0..S_r}, or NULL (S_r = log_r m stages) */
+    int32_t* sstar;      /* [T] first non-interacting stage (S_r+1 if all interact) */
     double* xfinal;      /* [N*dx] particles after step T (before mutation), or NULL */
     int32_t* tie;        /* [2] first flagged tie: time t (0 = none) and kind */
 } airpf_out;
@@ -513,7 +535,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
     if (!(tau > 0.0 && tau <= 1.0)) return 1;
     if (TAU_INT > 0.0 && MOMENTS_OUT) return 1;   /* the output measures assume resampling */
     if (ilog2(m) % RADIX_BITS != 0) return 1;      /* m must be a power of the radix */
-    const int N = m * M, S = ilog2(m);
+    const int N = m * M, S = ilog2(m), Sr = S / RADIX_BITS, radix = 1 << RADIX_BITS;
     model_t md = { model, dx, dy, theta, mdat };
     stream_id st = { seed, chain, iter };
 
@@ -531,6 +553,10 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
     int* idx = malloc(sizeof(int) * m);
     int* idx2 = malloc(sizeof(int) * m);
     int* tie_isl = calloc((size_t)m, sizeof(int));
+    double* wc = malloc(sizeof(double) * radix);    /* group members' weights (relative) */
+    double* cum = malloc(sizeof(double) * radix);   /* their cumulative sums */
+    uint8_t* sflag = malloc((size_t)m);             /* a tied choice on island k's walk */
+    uint8_t* sflag2 = malloc((size_t)m);
     if (tie) { tie[0] = 0; tie[1] = TIE_NONE; }
 
     /* initialisation: W^k_{0,0} = 1, particles from the prior */
@@ -542,7 +568,7 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
         const double* yt = y + (size_t)(t - 1) * dy;
         int tie_now = TIE_NONE;
         /* ENF_{t,0} (diagnostic, Algorithm 1) */
-        if (enf) enf[(size_t)(t - 1) * (S + 1)] = enf_of(lw, m);
+        if (enf) enf[(size_t)(t - 1) * (Sr + 1)] = enf_of(lw, m);
 
         if (MOMENTS_OUT) memcpy(lw2, lw, sizeof(double) * m);      /* log W^k_{t,0} */
         /* mutation of every island's block through K_t, then weighting */
@@ -575,8 +601,9 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
                 resample = ess < thr;
                 if (fabs(ess - thr) < TIE_REL * thr) tie_isl[k] = 2;
             }
+            uint8_t* dflag = TIE_DRAW ? TIE_DRAW + (size_t)(t - 1) * N + (size_t)k * M : NULL;
             if (resample) {
-                if (resample_island(lk, M, wres + (size_t)k * M, cdf + (size_t)k * M, a + (size_t)k * M))
+                if (resample_island(lk, M, wres + (size_t)k * M, cdf + (size_t)k * M, a + (size_t)k * M, dflag))
                     tie_isl[k] = tie_isl[k] ? tie_isl[k] : 1;
                 for (int j = 0; j < M; ++j) lom2[(size_t)k * M + j] = -log((double)M);
             } else {
@@ -584,7 +611,11 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
                     a[k * M + j] = j;
                     lom2[(size_t)k * M + j] = lk[j] - lse;
                 }
+                if (dflag)
+                    for (int j = 0; j < M; ++j) dflag[j] = 0;
             }
+            if (dflag && tie_isl[k] == 2)                  /* the ESS test itself */
+                for (int j = 0; j < M; ++j) dflag[j] = 1;
             for (int j = 0; j < M; ++j)
                 memcpy(xr + ((size_t)k * M + j) * dx, x + ((size_t)k * M + a[k * M + j]) * dx,
                        sizeof(double) * dx);
@@ -598,45 +629,58 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
             output_moments(lw, xr, m, M, dx, MOMENTS_OUT + (size_t)(t - 1) * 4 * dx + 2 * dx);
         }
 
-        /* interaction stages s = 1..S (butterfly matrices A_s) */
+        /* interaction stages s = 1..S_r (matrices A_s over groups of r islands) */
         for (int k = 0; k < m; ++k) idx[k] = k;
-        int first_quiet = S + 1;
-        int group_interact = 1;
-        for (int s = 1; s <= S; ++s) {
+        for (int k = 0; k < m; ++k) sflag[k] = 0;
+        int step_flag = 0;
+        int first_quiet = Sr + 1;
+        for (int s = 1; s <= Sr; ++s) {
             double e = enf_of(lw, m);
-            if (enf) enf[(size_t)(t - 1) * (S + 1) + s] = e;
-            if ((s - 1) % RADIX_BITS == 0) {       /* the first binary stage of an r-ary stage */
-                group_interact = (mode == MODE_ALWAYS) || (mode == MODE_ADAPTIVE && e < tau);
-                if (mode == MODE_ADAPTIVE && fabs(e - tau) < TIE_REL * tau && tie_now == TIE_NONE)
-                    tie_now = TIE_ENF;
+            if (enf) enf[(size_t)(t - 1) * (Sr + 1) + s] = e;
+            int interact = (mode == MODE_ALWAYS) || (mode == MODE_ADAPTIVE && e < tau);
+            if (mode == MODE_ADAPTIVE && fabs(e - tau) < TIE_REL * tau) {
+                step_flag = 1;
+                if (tie_now == TIE_NONE) tie_now = TIE_ENF;
             }
-            int interact = group_interact;
             if (!interact) {
-                if (first_quiet == S + 1) first_quiet = s;
+                if (first_quiet == Sr + 1) first_quiet = s;
                 continue;            /* alpha_s = I: weights and blocks unchanged */
             }
-            int b = 1 << (s - 1);
+            const int stride = 1 << (RADIX_BITS * (s - 1));      /* r^(s-1) */
             for (int k = 0; k < m; ++k) {
-                int lo = k & ~b, hi = k | b;
-                double ref = lw[lo] > lw[hi] ? lw[lo] : lw[hi];
-                double wlo = 0.0, whi = 0.0;
-                if (ref > -INFINITY) {
-                    wlo = exp(lw[lo] - ref);
-                    whi = exp(lw[hi] - ref);
+                /* the group of k: base + c * stride, c = 0..r-1 */
+                const int base = k & ~((radix - 1) * stride);
+                double ref = -INFINITY;
+                for (int c = 0; c < radix; ++c)
+                    if (lw[base + c * stride] > ref) ref = lw[base + c * stride];
+                double wsum = 0.0;
+                for (int c = 0; c < radix; ++c) {
+                    wc[c] = ref > -INFINITY ? exp(lw[base + c * stride] - ref) : 0.0;
+                    wsum += wc[c];
+                    cum[c] = wsum;
                 }
                 uint32_t w[4];
                 draw(&st, (uint32_t)k, (uint32_t)t, KIND_ISLAND, (uint32_t)s, w);
-                double lhs = unif(w[0]) * (wlo + whi);
-                int pick = (lhs < wlo) ? lo : hi;
-                if (fabs(lhs - wlo) < TIE_REL * (wlo + whi) && tie_now == TIE_NONE)
-                    tie_now = TIE_ISLAND;
-                idx2[k] = idx[pick];
-                /* W^k_{t,s+1} = sum_l alpha_s^{kl} W^l_{t,s} = (W_lo + W_hi)/2 */
-                lw2[k] = (ref > -INFINITY) ? ref + log(0.5 * (wlo + whi)) : -INFINITY;
+                /* member c with probability W_c / sum W: the first c with C_c > u sum W
+                 * (the last member when every weight is zero) */
+                const double target = unif(w[0]) * wsum;
+                int pick = 0;
+                while (pick < radix - 1 && !(cum[pick] > target)) ++pick;
+                int near = 0;
+                for (int c = 0; c < radix - 1; ++c)
+                    if (fabs(cum[c] - target) < TIE_REL * wsum) near = 1;
+                if (near && tie_now == TIE_NONE) tie_now = TIE_ISLAND;
+                idx2[k] = idx[base + pick * stride];
+                sflag2[k] = (uint8_t)(sflag[base + pick * stride] | near);
+                /* W^k_{t,s+1} = sum_l alpha_s^{kl} W^l_{t,s} = r^-1 sum_c W_c */
+                lw2[k] = (ref > -INFINITY) ? ref + log(wsum / radix) : -INFINITY;
             }
             memcpy(idx, idx2, sizeof(int) * m);
+            memcpy(sflag, sflag2, (size_t)m);
             memcpy(lw, lw2, sizeof(double) * m);
         }
+        if (TIE_SRC) memcpy(TIE_SRC + (size_t)(t - 1) * m, sflag, (size_t)m);
+        if (TIE_STEP) TIE_STEP[t - 1] = (uint8_t)step_flag;
 
         /* island k now holds the internally resampled block of island idx[k] */
         for (int k = 0; k < m; ++k) {
@@ -655,7 +699,8 @@ int oracle_airpf(int model, int dx, int dy, int m, int M, int T, int mode, doubl
     if (xfinal) memcpy(xfinal, xa, sizeof(double) * N * dx);
 
     free(xa); free(x); free(xr); free(l); free(cdf); free(wres); free(a);
-    free(lw); free(lw2); free(idx); free(idx2); free(tie_isl); free(lom); free(lom2);
+    free(lw); free(lw2); free(idx); free(idx2); free(tie_isl); free(lom); free(lom2); free(wc); free(cum);
+    free(sflag); free(sflag2);
     return 0;
 }
 
@@ -687,7 +732,7 @@ int oracle_bpf(int model, int dx, int dy, int M, int T, uint64_t seed, uint32_t 
             l[i] = log_g(&md, y + (size_t)(t - 1) * dy, x + (size_t)i * dx);
         }
         lz += log_sum_exp(l, M) - log((double)M);
-        int tf = resample_island(l, M, wres, cdf, a);
+        int tf = resample_island(l, M, wres, cdf, a, NULL);
         if (tie && tie[0] == 0 && tf) { tie[0] = t; tie[1] = TIE_RESAMPLE; }
         for (int j = 0; j < M; ++j) {
             memcpy(xp + (size_t)j * dx, x + (size_t)a[j] * dx, sizeof(double) * dx);
@@ -862,7 +907,7 @@ double oracle_model_logmu(int model, int dx, int dy, const double* th, const dou
  * given: the random numbers are the run's, the ancestors and island choices
  * are held fixed, and the weights follow Algorithm 1 with the interacting
  * stages 1..s*_t-1 (after them every island weight is the mean of its block
- * of 2^(s*_t-1) islands).  xs [(T+1)*N*dx] and lw1 [T*m] may be NULL. */
+ * of r^(s*_t-1) islands, r the radix).  xs [(T+1)*N*dx] and lw1 [T*m] may be NULL. */
 static void fixed_lineage_pass(const model_t* md, const stream_id* st, int m, int M, int T, const double* y,
                                const int32_t* anc, const int32_t* sstar, double* xs, double* lw1,
                                double* logz, double* l_out)
@@ -886,8 +931,8 @@ static void fixed_lineage_pass(const model_t* md, const stream_id* st, int m, in
         if (xs) memcpy(xs + (size_t)t * N * dx, x, sizeof(double) * N * dx);
         for (int k = 0; k < m; ++k) lw[k] += log_sum_exp(l + (size_t)k * M, M) - log((double)M);
         if (lw1) memcpy(lw1 + (size_t)(t - 1) * m, lw, sizeof(double) * m);
-        /* block means at level s*_t - 1 */
-        int lvl = sstar[t - 1] - 1, bs = 1 << lvl;
+        /* block means over r^(s*_t - 1) = 2^lvl islands */
+        int lvl = (sstar[t - 1] - 1) * RADIX_BITS, bs = 1 << lvl;
         for (int b = 0; b < m; b += bs) {
             double v = log_sum_exp(lw + b, bs) - lvl * log(2.0);
             for (int k = b; k < b + bs; ++k) lwn[k] = v;

@@ -11,9 +11,13 @@ Three independent computations, used to pin each other and the sampling code:
   the collision case C_1 (one block, kept on the diagonal).  The internal
   resampling kernel is R_t of eq. (22); an interaction stage with alpha = A_s
   mixes the pair over {k, k xor b} x {l, l xor b} with weights 1/4 (eqs.
-  (28)-(29)).  The island at the end of step q is the island at the start of
-  step q+1.  Only fixed interaction (always / never, and m = 1) closes this
-  recursion; adaptive interaction needs the brute force below.
+  (28)-(29)).  With radix r (A_s = I (x) r^-1 1_r (x) I, m a power of r) a stage
+  mixes the pair over grp(k) x grp(l) with weights 1/r^2: islands k != l draw
+  their group members independently, so when grp(k) = grp(l) they land on the
+  same member (the collision term) with probability sum_c W_c^2 / (sum_c W_c)^2.
+  The island at the end of step q is the island at the start of step q+1.  Only
+  fixed interaction (always / never, and m = 1) closes this recursion; adaptive
+  interaction needs the brute force below.
 * ``brute_force_moments``: enumerates every random outcome of Algorithm 1
   (prior, mutation, resampling, island choices, adaptive ENF tests) in exact
   rational arithmetic for tiny sizes.
@@ -56,9 +60,18 @@ def _blocks(M, nx):
     return list(itertools.product(range(nx), repeat=M))
 
 
-def pair_moments(pi0, K, gs, m, M, interact):
+def _group(k, s, radix):
+    """The islands of k's group at stage s (base-radix digit s-1 of k varied), member order."""
+    bits = int(round(np.log2(radix)))
+    stride = 1 << (bits * (s - 1))
+    base = k & ~((radix - 1) * stride)
+    return [base + c * stride for c in range(radix)]
+
+
+def pair_moments(pi0, K, gs, m, M, interact, radix=2):
     """(E[Z^N_T], E[(Z^N_T)^2]) for AIRPF with m islands of M particles and
-    fixed interaction (interact=True: every stage uses A_s; False: alpha = I)."""
+    fixed interaction (interact=True: every stage uses A_s; False: alpha = I);
+    radix r: stages over groups of r islands (m a power of r)."""
     pi0 = np.asarray(pi0, dtype=np.float64)
     nx = len(pi0)
     blocks = _blocks(M, nx)
@@ -68,7 +81,8 @@ def pair_moments(pi0, K, gs, m, M, interact):
     Kb = np.ones((nb, nb))
     for i in range(M):
         Kb *= K[bidx[:, i]][:, bidx[:, i]]              # K^{(x)M}(x, y)
-    S = int(round(np.log2(m)))
+    S = int(round(np.log2(m))) // int(round(np.log2(radix)))
+    r2 = float(radix * radix)
 
     F = np.tile(pb, (m, 1))                            # E[W^k 1{x}]
     P = np.zeros((m, m, nb, nb))
@@ -107,27 +121,30 @@ def pair_moments(pi0, K, gs, m, M, interact):
         # interaction stages with alpha_s = A_s
         if interact:
             for s in range(1, S + 1):
-                b = 1 << (s - 1)
                 Fn = np.empty_like(F)
                 Pn = np.empty_like(P)
                 for k in range(m):
-                    Fn[k] = 0.5 * (F[k] + F[k ^ b])
+                    gk = _group(k, s, radix)
+                    Fn[k] = sum(F[a] for a in gk) / radix
                     for l in range(m):
-                        acc = P[k, l] + P[k, l ^ b] + P[k ^ b, l] + P[k ^ b, l ^ b]
-                        Pn[k, l] = 0.25 * acc if k != l else np.diag(0.25 * acc.sum(axis=1))
+                        gl = _group(l, s, radix)
+                        acc = sum(P[a, b] for a in gk for b in gl)
+                        Pn[k, l] = acc / r2 if k != l else np.diag(acc.sum(axis=1) / r2)
                 F, P = Fn, Pn
     ez = F.sum() / m
     ez2 = P.sum() / (m * m)
     return float(ez), float(ez2)
 
 
-def brute_force_moments(p_stay, p_correct, ys, m, M, mode, tau=Fraction(1)):
+def brute_force_moments(p_stay, p_correct, ys, m, M, mode, tau=Fraction(1), radix=2):
     """Exact (E[Z], E[Z^2]) as Fractions by enumerating all outcomes of
     Algorithm 1 on the binary HMM.  mode: 0 never, 1 always, 2 adaptive with
-    the strict test ENF < tau.  Tiny sizes only (m*M <= 4, T <= 3)."""
+    the strict test ENF < tau; radix r: stages over groups of r islands, each
+    island drawing one member of its group with probability proportional to
+    the weights.  Tiny sizes only (m*M <= 4, T <= 3)."""
     ps, pc = Fraction(p_stay), Fraction(p_correct)
     tau = Fraction(tau)
-    S = int(round(np.log2(m)))
+    S = int(round(np.log2(m))) // int(round(np.log2(radix)))
     N = m * M
     # state: (blocks: tuple of m tuples of M values, weights: tuple of m Fractions) -> prob
     dist = {}
@@ -177,7 +194,6 @@ def brute_force_moments(p_stay, p_correct, ys, m, M, mode, tau=Fraction(1)):
         dist = nd
         # interaction stages
         for s in range(1, S + 1):
-            b = 1 << (s - 1)
             nd = {}
             for (blocks, W), p in dist.items():
                 if mode == 0:
@@ -192,13 +208,14 @@ def brute_force_moments(p_stay, p_correct, ys, m, M, mode, tau=Fraction(1)):
                 if not interact:
                     add(nd, (blocks, W), p)
                     continue
-                Wn = tuple((W[k] + W[k ^ b]) / 2 for k in range(m))
+                groups = [_group(k, s, radix) for k in range(m)]
+                Wn = tuple(sum(W[a] for a in groups[k]) / radix for k in range(m))
                 choices = []
                 for k in range(m):
-                    lo, hi = k & ~b, k | b
-                    tot = W[lo] + W[hi]
-                    plo = W[lo] / tot if tot > 0 else Fraction(0)
-                    choices.append([(lo, plo), (hi, 1 - plo)])
+                    tot = sum(W[a] for a in groups[k])
+                    # every weight zero: the last member (the rule of the sampling code)
+                    choices.append([(a, W[a] / tot if tot > 0 else Fraction(int(a == groups[k][-1])))
+                                    for a in groups[k]])
                 for combo in itertools.product(*choices):
                     q = p
                     for _, qq in combo:
