@@ -1,8 +1,11 @@
 #!/usr/bin/env python3
-"""AIRPF throughput on one GB300: particle-steps/s on the stochastic-volatility workload
-(m = 1024 islands x M = 256 particles, T = 1000 observations simulated from seed 2,
-(mu, phi, sigma) = (-1, 0.95, 0.3), adaptive interaction tau = 0.3, FP32 particles with
-FP64 island weights and log Z).
+"""AIRPF throughput on one GB300: particle-steps/s on the large nonlinear-growth workload
+(m = 65536 islands x M = 256 particles, N = 16.8 M, T = 1000 observations simulated from seed 5,
+x_t = x/2 + 25 x / (1 + x^2) + 8 cos(1.2 t) + v, v ~ N(0, 10), y_t = x_t^2 / 20 + w, w ~ N(0, 1),
+adaptive interaction tau = 0.3, FP32 particles with FP64 island weights and log Z), the largest
+single-GPU configuration of the workloads; further legs: the stochastic-volatility workload
+(m = 1024 x M = 256), the all-FP64 paths, an M sweep, batched chains, gradients, PMMH and the
+change-point model.
 
 A step is one full AIRPF pass over y_1..y_T (every row of the hot path: propagate, weight,
 island log-sum-exp, internal resampling, ENF-controlled island interaction, log Z
@@ -32,26 +35,45 @@ import synth  # noqa: E402
 
 METRIC = "AIRPF particle-steps/s and PMCMC iters/s on 1 GB300 at stated log-\u1e90 error"
 UNIT = "particle-steps/s"
-WORKLOAD = "sv_m1024_M256_T1000"
-M_ISL, M_PART, T_OBS = 1024, 256, 1000
+WORKLOAD = "ngm_m65536_M256_T1000"
+M_ISL, M_PART, T_OBS = 65536, 256, 1000
+SV_WORKLOAD = "sv_m1024_M256_T1000"
+SV_M_ISL, SV_M_PART = 1024, 256
 TAU = 0.3
 L2_FLUSH_BYTES = 256 << 20
+LANES_PER_SM = 128
 
-# Algorithmic lane-operations per particle-step of the FP32 SV path (definition, counted
-# from the algorithm, not from the compiler): Philox4x32-10 block 100, Box-Muller normal 13,
-# SV transition 3, SV log-density 9, island max 4, weight and fixed-point conversion 5,
-# integer prefix sum 10, CDF and particle stores 2, draw target 4, binary search over
-# M = 256 (8 levels x 7) 56, gather 4.
-OPS_PER_PARTICLE_STEP = 210
-# DRAM bytes (read + write) per launch of the fused SV step kernel
-# (airpf_step_kernel<float, SV, 1, 4, false, 3>), from one ncu capture with a cold cache:
-# dram__bytes_read.sum 1.160 MB, dram__bytes_write.sum 0.  Set to None when that kernel changes
-# until it is captured again.
-SV_STEP_DRAM_BYTES = 1159680
-SV_STEP_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
-                       "airpf_step_kernel<float, SV, 1, 4, false, 3>, cold cache "
-                       "(profiles/airpf_step_kernel_sv_m1024_M256_T1000.md)")
-SM_COUNT, LANES_PER_SM = 152, 128
+# Algorithmic lane operations per particle-step of the FP32-mixed path (a definition,
+# counted from the algorithm, not from the compiler).  Two particles share one
+# Philox4x32-10 block (10 rounds of two 32x32->64 multiplies, counted as 4 operations, and 4
+# xors, 9 key-schedule steps of 2 adds: about 100) and one Box-Muller pair (13); the binary
+# search over M = 256 takes 8 levels of 7 (index, swizzle, shared-memory load, compare,
+# select).
+OPS_COMMON = {"philox_half_block": 50, "box_muller_half_pair": 6.5, "island_max": 4,
+              "weight_fixed_point": 5, "integer_prefix_sum": 10, "cdf_and_particle_stores": 2,
+              "draw_target": 4, "binary_search_M256": 56, "gather": 4}
+OPS_MODEL = {"NGM": {"transition": 8, "log_density": 4}, "SV": {"transition": 3, "log_density": 9}}
+
+
+def ops_per_particle_step(model: str) -> float:
+    return sum(OPS_COMMON.values()) + sum(OPS_MODEL[model].values())
+
+
+# Figures from the committed ncu captures of the kernels named (set to None when the kernel
+# changes, until it is captured again): DRAM read + write per launch, issue-active fraction.
+NCU = {
+    "ngm_island_step": {"dram_bytes_per_launch": None, "issue_active": None,
+                        "source": "ncu capture of airpf_step_kernel<float, NGM, 1, 4, false, 2> pending"},
+    "sv_fused_step": {"dram_bytes_per_launch": 1159680, "issue_active": 0.258,
+                      "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, one "
+                                "launch of airpf_step_kernel<float, SV, 1, 4, false, 3>, cold cache"},
+    "fp64_ngm_island_step": {"fp64_pipe": 0.857, "issue_active": 0.111,
+                             "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
+                                       "airpf_step_kernel<double, NGM, 1, 4, false, 2>"},
+    "fp64_sv_fused_step": {"fp64_pipe": 0.761, "issue_active": 0.103,
+                           "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
+                                     "airpf_step_kernel<double, SV, 1, 4, false, 3>"},
+}
 
 
 def _peaks():
@@ -117,12 +139,12 @@ def _dist():
     return ws, rank, local
 
 
-def oracle_sample(T_s: int, iter_: int, threads: int | None = None):
-    """The CPU oracle on the first T_s observations of the workload; returns seconds."""
+def oracle_sample(T_s: int, iter_: int):
+    """The CPU oracle on the first T_s observations of the headline workload; returns seconds."""
     import oracle
-    y = synth.sv_observations(T_OBS, seed=2)[:T_s]
+    y = synth.ngm_observations(T_OBS, seed=5)[:T_s]
     t0 = time.perf_counter()
-    oracle.airpf(synth.MODEL_SV, synth.SV_THETA, y, m=M_ISL, M=M_PART, mode=oracle.MODE_ADAPTIVE,
+    oracle.airpf(synth.MODEL_NGM, synth.NGM_THETA, y, m=M_ISL, M=M_PART, mode=oracle.MODE_ADAPTIVE,
                  tau=TAU, seed=1, chain=0, iter=iter_, record=False)
     return time.perf_counter() - t0
 
@@ -139,8 +161,8 @@ def calibrate_oracle(target_s: float) -> int:
 
 
 def cpu_baseline_leg(target_s: float = 12.0) -> dict:
-    """The oracle on a bounded sample of the workload: its first T_s steps, repeated over
-    fresh random streams until about target_s seconds of CPU work."""
+    """The oracle on a bounded sample of the headline workload: its first T_s steps, repeated
+    over fresh random streams until about target_s seconds of CPU work."""
     T_s = calibrate_oracle(target_s)
     secs, runs = 0.0, 0
     while secs < 0.8 * target_s and runs < 64:
@@ -148,7 +170,7 @@ def cpu_baseline_leg(target_s: float = 12.0) -> dict:
         runs += 1
     return {"value": M_ISL * M_PART * T_s * runs / secs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
             "sample": f"FP64 oracle (Algorithm 1, stage by stage, OpenMP over islands) on the first {T_s} of "
-                      f"{T_OBS} steps of the SV workload, m={M_ISL} x M={M_PART}, {runs} run(s), {secs:.1f} s"}
+                      f"{T_OBS} steps of the NGM workload, m={M_ISL} x M={M_PART}, {runs} run(s), {secs:.1f} s"}
 
 
 def run_reference(args) -> None:
@@ -156,7 +178,7 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     budget = 150.0
-    per_step_target = max(0.2, budget / max(1, args.steps + args.warmup))
+    per_step_target = max(0.5, budget / max(1, args.steps + args.warmup))
     T_s = calibrate_oracle(per_step_target)
     for w in range(args.warmup):
         oracle_sample(T_s, 0xFFFE0000 + w)
@@ -166,7 +188,7 @@ def run_reference(args) -> None:
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (SV observations simulated from seed 2)",
+            "data": "synthetic (NGM observations simulated from seed 5)",
             "config": {"workload": WORKLOAD, "sample_steps": T_s, "note": "each step: the oracle on the "
                        f"first {T_s} observations"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
@@ -208,7 +230,17 @@ def batched_leg(gp, torch, ws: int, n_chains: int = 256, T: int = 500, passes: i
     torch.cuda.synchronize()
     ms_pass = e0.elapsed_time(e1) / passes
     ps = float((ms_ * Ms_).sum()) * T
+    # the group's roofline: the FP32 path's lane operations per particle-step, with the
+    # binary search over each chain's own M (7 per level)
+    ops = sum((ops_per_particle_step("SV") - OPS_COMMON["binary_search_M256"] + 7 * np.ceil(np.log2(M))) * m * M * T
+              for m, M in zip(ms_.tolist(), Ms_.tolist()))
+    peaks, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = sms * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops / (ms_pass / 1e3) / 1e12
     out = {"workload": f"batched_sv_{n_chains}chains_T{T}", "particles": int((ms_ * Ms_).sum()),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                        "note": "all classes' island-step kernels of one group pass"},
            "classes": len(keys), "ms_per_pass": ms_pass,
            "particle_steps_per_s": ps * ws / (ms_pass / 1e3),
            "chain_iters_per_s": n_chains * ws / (ms_pass / 1e3), "passes": passes,
@@ -262,20 +294,24 @@ def grad_leg(gp, torch, ws: int, passes: int = 2) -> dict:
            "langevin_pmmh_iters_per_s": ws / (ms_pm / 1e3), "langevin_accepted": int(pm["n_accept"].item()),
            "langevin_iters": n_pm,
            "forward_ms": ms_fwd, "backward_over_forward": (ms - ms_fwd) / ms_fwd, "ckpt": 10,
+           "roofline": {"bound": "latency", "kernel": "grad_island_kernel<float, LGSSM, 8>",
+                        "backward_ms_per_step": (ms - ms_fwd) / T, "frac": None,
+                        "note": "latency and atomics: issue active 37-38%, long and short scoreboard stalls "
+                                "(ncu capture of the backward island kernel)"},
            "precision": "fp32", "score_norm": float(out["score"].norm()), "grad_norm": float(out["grad"].norm())}
     f.close()
     return res
 
 
-def ngm_leg(gp, torch, ws: int, T: int = 1000) -> dict:
-    """Large nonlinear-growth workload: m = 65536 islands, adaptive tau = 0.3, T = 1000; FP32
-    over M in {64, 128, 256, 512}, and FP64 at M = 256 (one timed pass each, after one
-    untimed pass)."""
+def ngm_sweep_leg(gp, torch, ws: int, T: int = 1000) -> dict:
+    """The large nonlinear-growth workload at the other particle counts of its sweep: m = 65536
+    islands, M in {64, 128, 512}, FP32, adaptive tau = 0.3, T = 1000 (one timed pass each,
+    after one untimed pass; M = 256 is the headline)."""
     y = torch.tensor(synth.ngm_observations(T, seed=5), device="cuda")
     th = torch.tensor(synth.NGM_THETA[None, :], device="cuda")
     out = {"workload": f"ngm_m65536_T{T}", "points": []}
-    for prec, M in [("fp32", 64), ("fp32", 128), ("fp32", 256), ("fp32", 512), ("fp64", 256)]:
-        f = gp.AIRPF(synth.MODEL_NGM, m=65536, M=M, T=T, B=1, mode="adaptive", tau=TAU, precision=prec, seed=1)
+    for M in (64, 128, 512):
+        f = gp.AIRPF(synth.MODEL_NGM, m=65536, M=M, T=T, B=1, mode="adaptive", tau=TAU, precision="fp32", seed=1)
         f.run(th, y, iter=0xFFFF0000)
         f.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -284,10 +320,112 @@ def ngm_leg(gp, torch, ws: int, T: int = 1000) -> dict:
         e1.record(f.stream)
         f.sync()
         ms = e0.elapsed_time(e1)
-        out["points"].append({"M": M, "precision": prec, "ms_per_pass": ms,
+        out["points"].append({"M": M, "precision": "fp32", "ms_per_pass": ms,
                               "particle_steps_per_s": 65536 * M * T * ws / (ms / 1e3), "log_z": float(lz.item())})
         f.close()
     return out
+
+
+def kernel_times(gp, torch, model, theta, y, *, m, M, T, prec, passes, flush, chain=0, **tiling):
+    """Per-kernel durations of one pass, live: the same workload through a graph with CUDA
+    event-record nodes around each kernel of every step (island-step kernel; cascade kernel
+    where there is one).  Returns (island us per step, cascade us per step, ms per pass)."""
+    ft = gp.AIRPF(model, m=m, M=M, T=T, B=1, mode="adaptive", tau=TAU, precision=prec, seed=1,
+                  record=gp.RECORD_TIMING, **tiling)
+    ft.run(theta, y, chain0=chain, iter=0xFFFE0000)
+    ft.sync()
+    isl_ms = cas_ms = pass_ms = 0.0
+    for j in range(passes):
+        flush.fill_(j & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ft.stream)
+        ft.run(theta, y, chain0=chain, iter=j)
+        e1.record(ft.stream)
+        a, b = ft.kernel_times()
+        isl_ms += a
+        cas_ms += b
+        pass_ms += e0.elapsed_time(e1)
+    mode = ft.launch_mode
+    ft.close()
+    return 1e3 * isl_ms / (passes * T), 1e3 * cas_ms / (passes * T), pass_ms / passes, mode
+
+
+def alu_roofline(model: str, N: int, step_us: float, sms: int, peaks: dict, peak_src: str) -> dict:
+    ops = ops_per_particle_step(model)
+    achieved = ops * N / (step_us / 1e6) / 1e12
+    peak = sms * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "ops_per_particle_step": ops, "units_per_launch": N, "launch_avg_us": step_us,
+            "peak_source": f"{sms} SMs (device property) x {LANES_PER_SM} lanes x sm_max_mhz ({peak_src})"}
+
+
+def sv_leg(gp, torch, ws, chain, flush, peaks, peak_src, sms, n_fp32=20, n_fp64=10) -> dict:
+    """The stochastic-volatility workload (m = 1024 x M = 256, T = 1000, (mu, phi, sigma) =
+    (-1, 0.95, 0.3), adaptive tau = 0.3): FP32-mixed and all-FP64 passes on the same random
+    streams (the stated log Z error), the fused step kernel's roofline, and PMMH on (mu, phi,
+    sigma) with a box prior mu ~ U(-5, 5), phi ~ U(-1, 1), sigma ~ U(0, 2)."""
+    y = torch.tensor(synth.sv_observations(T_OBS, seed=2), device="cuda")
+    th = torch.tensor(synth.SV_THETA[None, :], device="cuda")
+    N = SV_M_ISL * SV_M_PART
+    res = {"workload": SV_WORKLOAD}
+    lz = {}
+    for prec, n in (("fp32", n_fp32), ("fp64", n_fp64)):
+        f = gp.AIRPF(synth.MODEL_SV, m=SV_M_ISL, M=SV_M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
+                     seed=1)
+        for w in range(3):
+            f.run(th, y, chain0=chain, iter=0xFFFF0000 + w)
+        f.sync()
+        tot, out = 0.0, []
+        for j in range(n):
+            flush.fill_(j & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(f.stream)
+            out.append(f.run(th, y, chain0=chain, iter=j)["log_z"])
+            e1.record(f.stream)
+            f.sync()
+            tot += e0.elapsed_time(e1)
+        lz[prec] = torch.cat(out).cpu().numpy()
+        res[prec] = {"ms_per_pass": tot / n, "particle_steps_per_s": N * T_OBS * ws * n / (tot / 1e3), "passes": n,
+                     "launch_mode": f.launch_mode}
+        if prec == "fp32":
+            # PMMH on (mu, phi, sigma)
+            n_pm = 20
+            st_th = th.clone()
+            st_lz = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+            pm_kw = dict(step=[0.05, 0.01, 0.02], lo=[-5.0, -1.0, 0.0], hi=[5.0, 1.0, 2.0], chain0=chain)
+            f.pmmh(y, st_th, st_lz, iters=1, iter0=0, **pm_kw)
+            f.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(f.stream)
+            pm = f.pmmh(y, st_th, st_lz, iters=n_pm, iter0=1, **pm_kw)
+            e1.record(f.stream)
+            f.sync()
+            res["pmmh"] = {"iters_per_s": n_pm * ws / (e0.elapsed_time(e1) / 1e3), "iters": n_pm,
+                           "accepted": int(pm["n_accept"].item()),
+                           "proposal": "random walk, steps (0.05, 0.01, 0.02) on (mu, phi, sigma), box prior "
+                                       "U(-5,5) x U(-1,1) x U(0,2)"}
+        f.close()
+    n = min(len(lz["fp32"]), len(lz["fp64"]))
+    res["log_z"] = {"fp32_mean": float(lz["fp32"].mean()), "fp32_sd": float(lz["fp32"].std(ddof=1)),
+                    "fp64_mean": float(lz["fp64"].mean()), "fp64_sd": float(lz["fp64"].std(ddof=1)),
+                    "same_stream_abs_diff_mean": float(np.mean(np.abs(lz["fp32"][:n] - lz["fp64"][:n])))}
+    isl, cas, pms, mode = kernel_times(gp, torch, synth.MODEL_SV, th, y, m=SV_M_ISL, M=SV_M_PART, T=T_OBS,
+                                       prec="fp32", passes=5, flush=flush, chain=chain, launch="steps")
+    step_us = 1e3 * res["fp32"]["ms_per_pass"] / T_OBS
+    rf = alu_roofline("SV", N, step_us, sms, peaks, peak_src)
+    rf.update({"kernel": "airpf_step_kernel<float, SV, 1, 4, false, 3> (fused step: cascade + island work)",
+               "launch_avg_source": "timed passes: pass time / T (one kernel per step and the gaps)",
+               "algorithmic_bytes_per_launch": 8 * N,
+               "traffic": NCU["sv_fused_step"]["dram_bytes_per_launch"],
+               "ncu_issue_active": NCU["sv_fused_step"]["issue_active"], "ncu_source": NCU["sv_fused_step"]["source"],
+               "event_nodes": {"step_kernel_us": isl, "ms_per_pass_with_event_nodes": pms}})
+    res["roofline"] = rf
+    res["fp64"]["roofline"] = {"bound": "fp64", "kernel": "airpf_step_kernel<double, SV, 1, 4, false, 3>",
+                               "fp64_pipe_frac_ncu": NCU["fp64_sv_fused_step"]["fp64_pipe"],
+                               "ncu_issue_active": NCU["fp64_sv_fused_step"]["issue_active"],
+                               "ncu_source": NCU["fp64_sv_fused_step"]["source"],
+                               "over_fp32": res["fp64"]["ms_per_pass"] / res["fp32"]["ms_per_pass"]}
+    return res
 
 
 def changepoint_leg(gp, torch, ws: int, T: int = 523) -> dict:
@@ -337,19 +475,22 @@ def run_gpu(args) -> None:
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks, peak_src = _peaks()
 
     prec = args.precision
-    y_np = synth.sv_observations(T_OBS, seed=2)
-    theta = torch.tensor(synth.SV_THETA[None, :], device="cuda")
+    y_np = synth.ngm_observations(T_OBS, seed=5)
+    theta = torch.tensor(synth.NGM_THETA[None, :], device="cuda")
     y = torch.tensor(y_np, device="cuda")
     tile = dict(ppt=args.ppt, islands_per_cta=args.islands_per_cta)
-    f = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
+    f = gp.AIRPF(synth.MODEL_NGM, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
                  seed=1, launch=args.launch, **tile)
-    launch_name = {1: "one kernel per step (CUDA graph, programmatic dependent launch)",
+    launch_name = {1: "fused steps: one kernel per step (CUDA graph, programmatic dependent launch)",
                    2: "persistent, CTA per filter", 3: "persistent cooperative grid",
-                   4: "island-step + cascade kernel per step (CUDA graph)"}[f.launch_mode]
+                   4: "split steps: one island kernel per step, the cascade in the tail of its last CTAs "
+                      "(CUDA graph, programmatic dependent launch)"}[f.launch_mode]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
+    stream = f.stream
     chain = replicas.chain_base(rank)      # one independent chain per rank
 
     def one(j):
@@ -378,18 +519,19 @@ def run_gpu(args) -> None:
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     tot_ms = sum(step_ms)
     tot_ms = replicas.max_over_ranks(tot_ms, device="cuda")   # the slowest rank's time
-    ps = M_ISL * M_PART * T_OBS
+    N = M_ISL * M_PART
+    ps = N * T_OBS
     value = replicas.job_rate(ps * args.steps, tot_ms / 1e3, ws)
-    lz32 = torch.stack(lzs).cpu().numpy().ravel()
+    lz32 = torch.cat(lzs).cpu().numpy()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    th_h = torch.tensor(synth.SV_THETA[None, :], dtype=torch.float64).pin_memory()
+    th_h = torch.tensor(synth.NGM_THETA[None, :], dtype=torch.float64).pin_memory()
     y_h = torch.tensor(y_np, dtype=torch.float64).pin_memory()
     lz_h = torch.empty(1, dtype=torch.float64).pin_memory()
-    n_e2e = max(3, min(args.steps, 50))
+    n_e2e = max(3, min(args.steps, 10))
     import ctypes
     lib = f.lib
     torch.cuda.synchronize()
@@ -400,115 +542,96 @@ def run_gpu(args) -> None:
         gp._binding.check(st, f.ctx)
     e2e_s = time.perf_counter() - t0
     e2e = {"value": ps * n_e2e * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * (3 + T_OBS),
-           "d2h_bytes_per_step": 8, "steps": n_e2e}
+           "d2h_bytes_per_step": 8, "steps": n_e2e, "call": "airpf_run_host (host theta, y, log Z)"}
 
-    # all-FP64 path on the same workload, for the stated log-Z error
+    # the all-FP64 path on the same workload and the same random streams (the stated log Z error)
     fp64 = None
     if not args.no_fp64 and prec != "fp64":
-        f64 = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU,
-                       precision="fp64", seed=1, launch=args.launch)
+        f64 = gp.AIRPF(synth.MODEL_NGM, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU,
+                       precision="fp64", seed=1)
         f64.run(theta, y, chain0=chain, iter=0xFFFF0000)
-        torch.cuda.synchronize()
-        n64 = max(3, min(args.steps, 40))
+        f64.sync()
+        n64 = 2
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0.record(f64.stream)
         l64 = [f64.run(theta, y, chain0=chain, iter=j)["log_z"] for j in range(n64)]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        lz64 = torch.stack(l64).cpu().numpy().ravel()
-        n = min(len(lz32), len(lz64))
-        fp64 = {"value": ps * n64 / (ms64 / 1e3), "ms_per_step": ms64 / n64,
-                "log_z_fp32_mean": float(lz32.mean()), "log_z_fp32_sd": float(lz32.std(ddof=1)),
-                "log_z_fp64_mean": float(lz64.mean()), "log_z_fp64_sd": float(lz64.std(ddof=1)),
-                "log_z_same_stream_abs_diff_mean": float(np.mean(np.abs(lz32[:n] - lz64[:n]))),
-                "runs": [len(lz32), len(lz64)]}
+        e1.record(f64.stream)
+        f64.sync()
+        ms64 = e0.elapsed_time(e1) / n64
+        lz64 = torch.cat(l64).cpu().numpy()
+        fp64 = {"workload": WORKLOAD, "value": ps * ws / (ms64 / 1e3), "ms_per_pass": ms64, "passes": n64,
+                "over_fp32": ms64 / (tot_ms / args.steps),
+                "log_z_fp64": lz64.tolist(), "log_z_fp32_same_streams": lz32[:n64].tolist(),
+                "log_z_abs_diff_mean": float(np.mean(np.abs(lz32[:n64] - lz64))),
+                "log_z_fp32_sd_over_passes": float(lz32.std(ddof=1)) if lz32.size > 1 else None,
+                "roofline": {"bound": "fp64", "kernel": "airpf_step_kernel<double, NGM, 1, 4, false, 2>",
+                             "fp64_pipe_frac_ncu": NCU["fp64_ngm_island_step"]["fp64_pipe"],
+                             "ncu_issue_active": NCU["fp64_ngm_island_step"]["issue_active"],
+                             "ncu_source": NCU["fp64_ngm_island_step"]["source"]}}
         f64.close()
 
-    # per-kernel durations, live: the same workload through a graph with CUDA event-record
-    # nodes around each kernel (island-step kernel, cascade kernel), on the same stream
-    ft = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T_OBS, B=1, mode="adaptive", tau=TAU, precision=prec,
-                  seed=1, launch=f.launch_mode if f.launch_mode in (1, 4) else "steps", record=gp.RECORD_TIMING,
-                  **tile)
-    ft.run(theta, y, chain0=chain, iter=0xFFFE0000)
-    ft.sync()
-    n_k = max(3, min(args.steps, 10))
-    isl_ms, cas_ms, pass_ms = 0.0, 0.0, 0.0
-    for j in range(n_k):
-        flush.fill_(j & 0xFF)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ft.run(theta, y, chain0=chain, iter=j)
-        e1.record(stream)
-        a, b = ft.kernel_times()
-        isl_ms += a
-        cas_ms += b
-        pass_ms += e0.elapsed_time(e1)
-    ft.close()
-    isl_us = 1e3 * isl_ms / (n_k * T_OBS)
-    cas_us = 1e3 * cas_ms / (n_k * T_OBS)
+    # per-kernel durations, live (event-record nodes around each kernel)
+    isl_us, cas_us, pass_evt_ms, kmode = kernel_times(gp, torch, synth.MODEL_NGM, theta, y, m=M_ISL, M=M_PART,
+                                                      T=T_OBS, prec=prec, passes=3, flush=flush, chain=chain,
+                                                      launch=args.launch, **tile)
 
-    # PMMH on (mu, phi, sigma): box prior mu ~ U(-5, 5), phi ~ U(-1, 1), sigma ~ U(0, 2)
-    n_pm = max(5, min(args.steps, 20))
-    st_th = torch.tensor(synth.SV_THETA[None, :], device="cuda")
-    st_lz = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
-    pm_kw = dict(step=[0.05, 0.01, 0.02], lo=[-5.0, -1.0, 0.0], hi=[5.0, 1.0, 2.0], chain0=chain)
-    f.pmmh(y, st_th, st_lz, iters=1, iter0=0, **pm_kw)        # initial estimate + one iteration
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pm = f.pmmh(y, st_th, st_lz, iters=n_pm, iter0=1, **pm_kw)
-    e1.record(stream)
-    f.sync()
-    pm_ms = e0.elapsed_time(e1)
-    pmmh = {"iters_per_s": n_pm * ws / (pm_ms / 1e3), "iters": n_pm, "accepted": int(pm["n_accept"].item()),
-            "proposal": "random walk, steps (0.05, 0.01, 0.02) on (mu, phi, sigma), box prior "
-                        "U(-5,5) x U(-1,1) x U(0,2)"}
-
+    sv = None if args.no_sv else sv_leg(gp, torch, ws, chain, flush, peaks, peak_src, sms)
+    sweep = None if args.no_ngm else ngm_sweep_leg(gp, torch, ws)
     batched = None if args.no_batched else batched_leg(gp, torch, ws)
     gradient = None if args.no_grad else grad_leg(gp, torch, ws)
-    ngm = None if args.no_ngm else ngm_leg(gp, torch, ws)
     changepoint = None if args.no_changepoint else changepoint_leg(gp, torch, ws)
 
-    peaks, peak_src = _peaks()
     ms_step = tot_ms / args.steps
-    step_us = 1e3 * ms_step / T_OBS           # one time step: island-step kernel + cascade kernel
-    achieved = OPS_PER_PARTICLE_STEP * M_ISL * M_PART / (step_us / 1e6) / 1e12
-    peak = SM_COUNT * LANES_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    step_us = 1e3 * ms_step / T_OBS           # one time step: the island kernel (with its tail cascade) and gaps
+    roof = alu_roofline("NGM", N, step_us, sms, peaks, peak_src)
+    roof.update({
+        "kernel": "airpf_step_kernel<float, NGM, 1, 4, false, 2> (split step: island work, then the cascade in "
+                  "the tail of the last CTAs)" if f.launch_mode == 4 else "airpf_step_kernel (one time step)",
+        "launch_avg_source": "timed region: pass time / T (the step's kernel and the gap to the next)",
+        "algorithmic_bytes_per_launch": 8 * N,
+        "traffic": NCU["ngm_island_step"]["dram_bytes_per_launch"],
+        "ncu_issue_active": NCU["ngm_island_step"]["issue_active"],
+        "ncu_source": NCU["ngm_island_step"]["source"],
+        "ops_breakdown": {**OPS_COMMON, **OPS_MODEL["NGM"]},
+        "event_nodes": {"island_kernel_us": isl_us, "cascade_kernel_us": cas_us,
+                        "ms_per_pass_with_event_nodes": pass_evt_ms, "launch_mode": kmode,
+                        "note": "events around each kernel in the graph; each interval also holds the "
+                                "node-to-node latency, so compare the share with the ncu launch list"}})
+    kernels = {"ngm_island_step_fp32": {k: roof[k] for k in ("bound", "frac", "achieved", "peak", "unit")}}
+    if fp64:
+        kernels["ngm_island_step_fp64"] = fp64["roofline"]
+    if sv:
+        kernels["sv_fused_step_fp32"] = {k: sv["roofline"][k] for k in ("bound", "frac", "achieved", "peak", "unit")}
+        kernels["sv_fused_step_fp64"] = sv["fp64"]["roofline"]
+    if batched:
+        kernels["batched_group"] = batched.get("roofline")
+    if gradient:
+        kernels["gradient"] = gradient.get("roofline")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
-        "data": "synthetic (SV observations simulated from seed 2)",
-        "config": {"workload": WORKLOAD, "model": "SV", "m": M_ISL, "M": M_PART, "N": M_ISL * M_PART,
+        "data": "synthetic (NGM observations simulated from seed 5)",
+        "config": {"workload": WORKLOAD, "model": "NGM", "m": M_ISL, "M": M_PART, "N": N,
                    "T": T_OBS, "interaction": f"adaptive tau={TAU}", "precision": prec,
-                   "l2": "flushed between timed steps (256 MiB write, outside the step events)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "launch": launch_name},
-        "pmcmc_iters_per_s": pmmh["iters_per_s"],
-        "pmmh": pmmh,
+                   "l2": "flushed between timed steps (256 MiB write, outside the step events); the particle "
+                         "stores (2 x 67 MB) exceed L2 as well",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU", "launch": launch_name,
+                   "sms": sms},
+        "pmcmc_iters_per_s": sv["pmmh"]["iters_per_s"] if sv else None,
+        "pmcmc_workload": SV_WORKLOAD,
         "filter_passes_per_s": args.steps * ws / (tot_ms / 1e3),
+        "log_z": {"mean": float(lz32.mean()), "sd": float(lz32.std(ddof=1)) if lz32.size > 1 else None},
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "airpf_step_kernel (one fused time step: cascade + island work)"
-                     if f.launch_mode == 1 else "airpf_step_kernel + airpf_cascade_kernel (one time step)",
-                     "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": SV_STEP_DRAM_BYTES if f.launch_mode == 1 else None,
-                     "traffic_source": SV_STEP_DRAM_SOURCE if f.launch_mode == 1 else None,
-                     "algorithmic_bytes_per_launch": 8 * M_ISL * M_PART,
-                     "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
-                     "units_per_launch": M_ISL * M_PART, "launch_avg_us": step_us,
-                     "launch_avg_source": "timed region: pass time / T (the step's kernels and the gaps)",
-                     "event_nodes": {"island_kernel_us": isl_us, "cascade_kernel_us": cas_us,
-                                     "island_share": isl_us / (isl_us + cas_us), "passes": n_k,
-                                     "ms_per_pass_with_event_nodes": pass_ms / n_k,
-                                     "note": "events around each kernel in the graph; each interval also "
-                                             "holds the node-to-node latency, so compare the share"},
-                     "peak_source": f"{SM_COUNT} SMs x {LANES_PER_SM} lanes x sm_max_mhz ({peak_src})"},
+        "roofline": roof,
+        "kernels": kernels,
         "fp64_path": fp64,
+        "sv": sv,
+        "ngm_sweep": sweep,
         "batched": batched,
         "gradient": gradient,
-        "ngm_large": ngm,
         "changepoint": changepoint,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -521,16 +644,24 @@ def run_gpu(args) -> None:
 
 
 def run_profile_case(args) -> None:
-    """One workload for a profiler capture: the m = 65536 x M = 256 NGM pass (FP32, T = 20;
-    split steps), or the d_x = 8 gradient evaluation (T = 20).  Prints the time of the last
+    """One workload for a profiler capture (T = 20): the m = 65536 x M = 256 NGM pass (split
+    steps; FP32 or FP64), the m = 1024 x M = 256 SV pass (fused steps; FP32 or FP64), or the
+    d_x = 8 gradient evaluation.  Prints the time of the last
     of --steps runs (a capture's timing is not a bench value)."""
     import torch
     import paper_2312_06484_gb300 as gp
     T = 20
-    if args.profile_case == "ngm256":
-        f = gp.AIRPF(synth.MODEL_NGM, m=65536, M=256, T=T, B=1, mode="adaptive", tau=TAU, precision="fp32", seed=1)
+    if args.profile_case in ("ngm256", "ngm256_fp64"):
+        prec = "fp64" if args.profile_case.endswith("fp64") else "fp32"
+        f = gp.AIRPF(synth.MODEL_NGM, m=65536, M=256, T=T, B=1, mode="adaptive", tau=TAU, precision=prec, seed=1)
         y = torch.tensor(synth.ngm_observations(T, seed=5), device="cuda")
         th = torch.tensor(synth.NGM_THETA[None, :], device="cuda")
+        run = lambda j: f.run(th, y, iter=j)
+    elif args.profile_case in ("sv", "sv_fp64"):
+        prec = "fp64" if args.profile_case.endswith("fp64") else "fp32"
+        f = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T, B=1, mode="adaptive", tau=TAU, precision=prec, seed=1)
+        y = torch.tensor(synth.sv_observations(T, seed=2), device="cuda")
+        th = torch.tensor(synth.SV_THETA[None, :], device="cuda")
         run = lambda j: f.run(th, y, iter=j)
     else:
         dx, dy = 8, 4
@@ -555,7 +686,7 @@ def run_profile_case(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="airpf", choices=["airpf", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -563,9 +694,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-chains leg")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient leg")
-    ap.add_argument("--no-ngm", action="store_true", help="skip the large NGM leg")
+    ap.add_argument("--no-ngm", action="store_true", help="skip the NGM particle-count sweep")
+    ap.add_argument("--no-sv", action="store_true", help="skip the stochastic-volatility leg")
     ap.add_argument("--no-changepoint", action="store_true", help="skip the change-point PMMH leg")
-    ap.add_argument("--profile-case", choices=["ngm256", "grad"], default=None,
+    ap.add_argument("--profile-case", choices=["ngm256", "ngm256_fp64", "sv", "sv_fp64", "grad"], default=None,
                     help="run one small workload for a profiler capture instead of the bench line")
     ap.add_argument("--launch", default="auto", choices=["auto", "steps", "split", "grid"])
     ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0: automatic)")

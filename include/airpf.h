@@ -143,12 +143,12 @@ typedef struct {
                                omega = 1/M).  Not with AIRPF_RECORD_GRAD or AIRPF_RECORD_MOMENTS, nor
                                with airpf_run_static (AIRPF_ERR_UNSUPPORTED). */
     int32_t radix;          /* islands averaged per interaction stage, r = 2^b (0 or 2: the paper's
-                               binary stages); m must be a power of r.  Stage s averages aligned groups
-                               of r islands (A_s = I (x) r^-1 1_r (x) I) and each island takes one
-                               group member's block with probability proportional to its weight;
-                               computed as b binary stages that all interact or all stay quiet, decided
-                               by the ENF at the group's first binary stage (ENF records keep every
-                               binary stage) */
+                               binary stages; Section 2 allows any r with m a power of r); m must be a
+                               power of r.  There are S_r = log_r m stages; stage s averages aligned
+                               groups of r islands (A_s = I (x) r^-1 1_r (x) I) and each island draws,
+                               from its own uniform, one member of its group with probability
+                               proportional to the members' weights, independently of the other
+                               islands.  ENF records and s* count these S_r stages */
 } airpf_config;
 
 #define AIRPF_RECORD_LINEAGE 1
@@ -183,8 +183,9 @@ airpf_status airpf_destroy(airpf_ctx* ctx);
  *   d_anc     [B * T * N] out or NULL: int32 parent index (0..N-1, among the
  *             time-t particles) of particle k*M+i held after step t, t = 1..T
  *             (needs AIRPF_RECORD_LINEAGE)
- *   d_enf     [B * T * (S+1)] out or NULL: ENF_{t,0..S} (needs AIRPF_RECORD_ENF)
- *   d_sstar   [B * T] out or NULL: first non-interacting stage (S+1 = all interact)
+ *   d_enf     [B * T * (S_r+1)] out or NULL: ENF_{t,0..S_r} (needs AIRPF_RECORD_ENF);
+ *             S_r = log2 m, or log_r m with radix r
+ *   d_sstar   [B * T] out or NULL: first non-interacting stage (S_r+1 = all interact)
  *   d_trace   [B * T] out or NULL: log Z^N_t after step t (needs AIRPF_RECORD_TRACE)
  * Asynchronous on the context's stream. */
 airpf_status airpf_run(airpf_ctx* ctx, const double* d_theta, const double* d_y,
@@ -211,7 +212,9 @@ airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y
  * The pass runs on a static scratch of AIRPF_STATIC_SCRATCH_BYTES per device;
  * nothing in it needs to start at zero (each pass writes every word it reads).
  *   cfg           as for airpf_create; record must be 0; launch AUTO, STEPS or
- *                 PERSISTENT_CTA (PERSISTENT_GRID: AIRPF_ERR_UNSUPPORTED)
+ *                 PERSISTENT_CTA, with the default tiling (ppt = islands_per_cta = 0);
+ *                 PERSISTENT_GRID, STEPS_SPLIT, a tiling request, tau_int > 0, or a
+ *                 step needing more than 227 KB of shared memory: AIRPF_ERR_UNSUPPORTED
  *   d_theta       [B * d_theta] device, read in place
  *   d_y           [T * dy] device, read in place
  *   d_model_data  LGSSM: device array A (dx*dx) then C (dy*dx); else NULL
@@ -223,7 +226,9 @@ airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y
  * sizes); give it a context with its own workspace instead.  The first call on
  * each device does a one-time set-up (it looks up the scratch address, which
  * also loads the library's module onto that device); make it before any stream
- * capture.  Calls that overlap in time on one device (different streams, or
+ * capture.  The address is kept for the life of the process: a cudaDeviceReset
+ * (or any teardown of the device's primary context) voids it, so do not call
+ * airpf_run_static on a device after resetting it.  Calls that overlap in time on one device (different streams, or
  * host threads without ordering between them) share the scratch and race:
  * order them on one stream or with events.  Asynchronous on `stream`; failures
  * leave their message for airpf_last_error(NULL). */

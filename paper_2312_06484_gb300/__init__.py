@@ -69,6 +69,8 @@ class AIRPF:
         self.m, self.M, self.T, self.B, self.dx, self.dy = m, M, T, B, dx, dy
         self.N = m * M
         self.S = int(round(np.log2(m)))
+        # interaction stages: S_r = log_r m for radix r (S for r = 2)
+        self.S_r = self.S // max(1, int(round(np.log2(radix)))) if radix > 2 else self.S
         self.theta_dim = theta_dim(model, dx)
         self.record = record
 
@@ -76,7 +78,8 @@ class AIRPF:
     def run(self, theta, y, *, chain0: int = 0, iter: int = 0, lineage=False, enf=False, trace=False):
         """One pass of Algorithm 1 for every filter of the batch.  theta: [B, d] float64 CUDA;
         y: [T*dy] float64 CUDA.  Returns dict of CUDA tensors (log_z [B], optional
-        anc [B, T, N], enf [B, T, S+1], sstar [B, T], trace [B, T])."""
+        anc [B, T, N], enf [B, T, S_r+1], sstar [B, T], trace [B, T]; S_r the number of
+        interaction stages, log_r m for radix r)."""
         torch = self._torch
         theta = theta.reshape(self.B, self.theta_dim).to(device="cuda", dtype=torch.float64).contiguous()
         y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
@@ -84,7 +87,7 @@ class AIRPF:
         if lineage:
             out["anc"] = torch.empty((self.B, self.T, self.N), dtype=torch.int32, device="cuda")
         if enf:
-            out["enf"] = torch.empty((self.B, self.T, self.S + 1), dtype=torch.float64, device="cuda")
+            out["enf"] = torch.empty((self.B, self.T, self.S_r + 1), dtype=torch.float64, device="cuda")
             out["sstar"] = torch.empty((self.B, self.T), dtype=torch.int32, device="cuda")
         if trace:
             out["trace"] = torch.empty((self.B, self.T), dtype=torch.float64, device="cuda")
@@ -325,8 +328,24 @@ def run_static(model: int, theta, y, log_z, *, m: int, M: int, B: int = 1, dx: i
     T = y.numel() // dy
     cfg = AirpfConfig(model=model, dx=dx, dy=dy, m=m, M=M, T=T, B=B, mode=mode, tau=tau, precision=precision,
                       record=0, seed=seed, launch=launch, reserved=0, tau_int=tau_int, radix=radix)
+    # the kernels read theta[B*d], y[T*dy] and the model data and write log_z[B] through raw
+    # pointers: every size is checked here, before the call
+    d = int(lib.airpf_theta_dim(model, dx))
+    if d <= 0:
+        raise AirpfError(f"ARG: unknown model {model} (dx = {dx})")
+    if theta.numel() != B * d:
+        raise AirpfError(f"ARG: theta holds {theta.numel()} values, B * theta_dim = {B * d}")
+    if log_z.numel() < B:
+        raise AirpfError(f"ARG: log_z holds {log_z.numel()} values, fewer than B = {B}")
+    if y.numel() == 0 or y.numel() % dy:
+        raise AirpfError(f"ARG: y holds {y.numel()} values, not a positive multiple of dy = {dy}")
+    if model == MODEL_LGSSM:
+        if model_data is None or model_data.numel() != dx * dx + dy * dx:
+            n = None if model_data is None else model_data.numel()
+            raise AirpfError(f"ARG: the LGSSM needs model_data of dx*dx + dy*dx = {dx * dx + dy * dx} values, got {n}")
     for t in (theta, y, log_z) + ((model_data,) if model_data is not None else ()):
-        assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+        if not (t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()):
+            raise AirpfError("ARG: theta, y, log_z and model_data must be contiguous float64 CUDA tensors")
     stream = stream if stream is not None else torch.cuda.current_stream()
     _binding.check(lib.airpf_run_static(ctypes.byref(cfg), _ptr(theta), _ptr(y), _ptr(model_data), chain0, iter,
                                         _ptr(log_z), ctypes.c_void_p(stream.cuda_stream)))

@@ -34,6 +34,7 @@ int ilog2_exact(int m)
 
 // Byte offsets of every buffer inside the workspace.
 struct WsLayout {
+    size_t tick, ge[2], gtr[2], gqs[2];
     size_t run, theta, mdata, y, X[2], pe[2], pt[2], pq[2], csum, cup, nsrc, utg, ires[2], logz, trace, enf,
         sstar, anc, active, mpar, drift, bar;
     size_t pm_prop, pm_logz_prop, pm_stats, pm_gprop, pm_lqf;
@@ -122,6 +123,14 @@ const char* check_config(const airpf_config* c)
     return nullptr;
 }
 
+// binary stages per interaction stage: radix r = 2^b (0 and 2 both mean r = 2)
+static int radix_bits(const airpf_config* c)
+{
+    int b = 1;
+    while (c->radix > 2 && (1 << b) < c->radix) ++b;
+    return b;
+}
+
 WsLayout make_ws_layout(const airpf_config* c)
 {
     WsLayout L;
@@ -148,10 +157,20 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.cup = take(sizeof(unsigned long long) * B * c->m);
     L.nsrc = take(sizeof(int) * B * c->m);
     L.utg = take(sizeof(double) * B * 2 * c->m);
+    // split steps' group cascade: at most max(1, m / 2^7) groups of at most 2^7 CTA records
+    {
+        const size_t ngmax = c->m >> airpf::kTailGroupLog > 0 ? (size_t)(c->m >> airpf::kTailGroupLog) : 1;
+        L.tick = take(sizeof(unsigned) * B);
+        for (int i = 0; i < 2; ++i) {
+            L.ge[i] = take(sizeof(int) * B * ngmax);
+            L.gtr[i] = take(sizeof(double) * B * 2 * c->m);
+            L.gqs[i] = take(sizeof(double) * B * ngmax * 16);
+        }
+    }
     for (int i = 0; i < 2; ++i) L.ires[i] = lin ? take(sizeof(int) * B * N) : 0;
     L.logz = take(sizeof(double) * B);
     L.trace = tr ? take(sizeof(double) * B * T) : 0;
-    L.enf = enf ? take(sizeof(double) * B * T * (S + 1)) : 0;
+    L.enf = enf ? take(sizeof(double) * B * T * (S / radix_bits(c) + 1)) : 0;
     L.sstar = enf ? take(sizeof(int) * B * T) : 0;
     L.anc = lin ? take(sizeof(int) * B * T * N) : 0;
     L.active = take(sizeof(int) * B);
@@ -409,8 +428,11 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         ctx->launch = mode;
         // per-step launches whose default tiling leaves SMs idle (fewer CTAs than SMs): two
         // particles per thread and one island per CTA spread the filters over more SMs
-        // (measured 9-18% faster per pass for one filter of m = 64..256 islands)
-        if (mode != AIRPF_LAUNCH_PERSISTENT_CTA && cfg->ppt == 0 && cfg->islands_per_cta == 0) {
+        // (measured 9-18% faster per pass for one filter of m = 64..256 islands).  Not for the
+        // cooperative grid (every grid barrier would wait on m CTAs instead of m/G), and only
+        // up to m = 512, where the island-per-CTA grid still takes fused steps.
+        if ((mode == AIRPF_LAUNCH_AUTO || mode == AIRPF_LAUNCH_STEPS || mode == AIRPF_LAUNCH_STEPS_SPLIT) &&
+            cfg->m <= 512 && cfg->ppt == 0 && cfg->islands_per_cta == 0) {
             int dev = 0, sms = 0;
             if (cudaGetDevice(&dev) == cudaSuccess &&
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
@@ -448,6 +470,8 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.pdl = is_steps(ctx->launch) ? 1 : 0;
     p.fused = ctx->launch == AIRPF_LAUNCH_STEPS ? 1 : 0;
     p.split = ctx->launch == AIRPF_LAUNCH_STEPS_SPLIT ? 1 : 0;
+    p.gs = p.g + airpf::kTailGroupLog <= p.S ? airpf::kTailGroupLog : p.S - p.g;   // 2^gs records a group
+    p.NG = p.P >> p.gs;
     if (airpf::step_smem_bytes(p) > 227 * 1024) {
         set_err(nullptr, "the step kernel would need %zu bytes of shared memory (m/G = %d CTA records per filter); "
                 "use AIRPF_LAUNCH_STEPS_SPLIT or more islands per CTA", airpf::step_smem_bytes(p), p.P);
@@ -500,6 +524,12 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     p.cup = at<void>(ctx, L.cup);
     p.nsrc = at<int>(ctx, L.nsrc);
     p.utg = at<void>(ctx, L.utg);
+    p.tick = at<unsigned>(ctx, L.tick);
+    for (int i = 0; i < 2; ++i) {
+        p.ge[i] = at<int>(ctx, L.ge[i]);
+        p.gtr[i] = at<void>(ctx, L.gtr[i]);
+        p.gqs[i] = at<void>(ctx, L.gqs[i]);
+    }
     p.logz = at<double>(ctx, L.logz);
     p.trace = (cfg->record & AIRPF_RECORD_TRACE) ? at<double>(ctx, L.trace) : nullptr;
     p.enf = L.enf ? at<double>(ctx, L.enf) : nullptr;
@@ -520,8 +550,7 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         p.gout = at<double>(ctx, L.gout);
         p.sout = at<double>(ctx, L.sout);
     }
-    p.rb = 1;
-    while (cfg->radix > 2 && (1 << p.rb) < cfg->radix) ++p.rb;
+    p.rb = radix_bits(cfg);
     p.air = cfg->tau_int > 0.0 ? 1 : 0;
     p.tau_int = cfg->tau_int;
     for (int i = 0; i < 2; ++i) p.lom[i] = L.lom[i] ? at<void>(ctx, L.lom[i]) : nullptr;
@@ -625,7 +654,8 @@ airpf_status airpf_run(airpf_ctx* ctx, const double* d_theta, const double* d_y,
     if ((s = enqueue_pass(ctx))) return s;
     if ((s = copy_async(ctx, d_log_z, at<void>(ctx, ctx->L.logz), sizeof(double) * B))) return s;
     if (d_anc && (s = copy_async(ctx, d_anc, at<void>(ctx, ctx->L.anc), sizeof(int) * B * T * N))) return s;
-    if (d_enf && (s = copy_async(ctx, d_enf, at<void>(ctx, ctx->L.enf), sizeof(double) * B * T * (ctx->S + 1))))
+    if (d_enf && (s = copy_async(ctx, d_enf, at<void>(ctx, ctx->L.enf),
+                                 sizeof(double) * B * T * (ctx->S / radix_bits(&c) + 1))))
         return s;
     if (d_sstar && (s = copy_async(ctx, d_sstar, at<void>(ctx, ctx->L.sstar), sizeof(int) * B * T))) return s;
     if (d_trace && (s = copy_async(ctx, d_trace, at<void>(ctx, ctx->L.trace), sizeof(double) * B * T))) return s;

@@ -164,12 +164,12 @@ __global__ void __launch_bounds__(256) grad_pi_final_kernel(StepParams p)
         pi[k] = (sum > 0.0 && lw[k] > -INFINITY) ? exp(lw[k] - mx) / sum : 0.0;
 }
 
-// pi_{t-1} from pi_t: the blocks of 2^(s*_{t-1} - 1) islands redistribute their
-// pi_t mass in proportion to W_{t-1,1}; one thread per block
+// pi_{t-1} from pi_t: the blocks of r^(s*_{t-1} - 1) = 2^lvl islands (r = 2^rb the
+// radix) redistribute their pi_t mass in proportion to W_{t-1,1}; one thread per block
 __global__ void __launch_bounds__(256) grad_pi_step_kernel(StepParams p, int t)
 {
     const int c = blockIdx.y, m = p.m;
-    const int lvl = p.sstar[(size_t)c * p.T + (t - 2)] - 1;
+    const int lvl = (p.sstar[(size_t)c * p.T + (t - 2)] - 1) * p.rb;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= (m >> lvl)) return;
     const int j0 = b << lvl, n = 1 << lvl;

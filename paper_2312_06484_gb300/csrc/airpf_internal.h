@@ -7,6 +7,10 @@
 
 namespace airpf {
 
+// split steps' group cascade: 2^kTailGroupLog CTA records per group (fewer when a
+// filter has fewer CTAs)
+constexpr int kTailGroupLog = 7;
+
 // Per-run values the captured graph reads from device memory, so that one
 // graph serves every (iter, chain0) and every PMMH iteration.
 struct RunParams {
@@ -45,10 +49,18 @@ struct StepParams {
     int inject_stall;             // test hook (grid-persistent launch only)
     int pdl;                      // per-step launches: programmatic dependent launch
     int fused;                    // per-step launches: each CTA runs the previous step's cascade itself
-    int split;                    // per-step launches with a cascade kernel that leaves the tree in utg
+    int split;                    // per-step launches with a group cascade kernel (NG x B CTAs)
     int wide;                     // fused steps: the instantiation with up to 128 registers a thread
                                   // (taken when the whole grid is one wave at its occupancy)
-    void* utg;                    // [B][2P] upper tree of the last cascade (split steps)
+    void* utg;                    // [B][2NG] top tree of the last cascade (split steps)
+    // split steps' group cascade: NG groups of 2^gs CTA records per filter; a ticket
+    // per filter [B]; per group, double-buffered by step: exponent, block-sum subtree
+    // of levels g .. g+gs [2^(gs+1)], sums of squares of levels 0 .. g+gs-1 [16]
+    int NG, gs;
+    unsigned* tick;
+    int* ge[2];
+    void* gtr[2];
+    void* gqs[2];
     // gradient pass (record AIRPF_RECORD_GRAD): states x_t at checkpoints
     // (slot 0 = x_0, slot t/ckpt, and slot nck-1 = x_T when T is no multiple
     // of ckpt), the recomputed states between checkpoints, log W^k_{t,1}, the

@@ -122,6 +122,11 @@ extern "C" airpf_status airpf_run_static(const airpf_config* cfg, const double* 
         airpf::set_create_error("airpf_run_static resamples every island at every step: tau_int must be 0");
         return AIRPF_ERR_UNSUPPORTED;
     }
+    if (cfg->ppt != 0 || cfg->islands_per_cta != 0 || cfg->launch == AIRPF_LAUNCH_STEPS_SPLIT) {
+        airpf::set_create_error("airpf_run_static takes the default tiling and launch forms: ppt and "
+                                "islands_per_cta must be 0, launch not STEPS_SPLIT");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
     if ((uint64_t)chain0 + (uint64_t)cfg->B > (1u << 24)) {
         airpf::set_create_error("airpf_run_static: chain0 + B must not exceed 2^24");
         return AIRPF_ERR_ARG;
@@ -166,6 +171,12 @@ extern "C" airpf_status airpf_run_static(const airpf_config* cfg, const double* 
     if (!cta) airpf::choose_mapping(cfg->m, cfg->M, p.fp64, 0, 0, &p.tpi, &p.ppt, &p.G);
     p.P = cfg->m / p.G;
     while ((1 << p.g) < p.G) ++p.g;
+    if (airpf::step_smem_bytes(p) > 227 * 1024) {
+        airpf::set_create_error("airpf_run_static: a step needs %zu bytes of shared memory (%d CTAs per filter), "
+                                "above 227 KB; use a context with AIRPF_LAUNCH_STEPS_SPLIT",
+                                airpf::step_smem_bytes(p), p.P);
+        return AIRPF_ERR_UNSUPPORTED;
+    }
     p.theta_dim = airpf_theta_dim(cfg->model, cfg->dx);
     p.seed_lo = (uint32_t)(cfg->seed & 0xffffffffu);
     p.seed_hi = (uint32_t)(cfg->seed >> 32);

@@ -19,8 +19,10 @@
 // programmatic dependent launch each kernel draws its random numbers before it
 // waits for the previous one.
 //
-// Variants on the same kernels: radix r = 2^b interactions take the adaptive
-// decision only at the first binary stage of each group of b; adaptive internal
+// Variants on the same kernels: radix r = 2^b interactions (stages over groups of
+// r islands) take the adaptive decision at the first binary stage of each group
+// of b, where the r-ary stage's ENF lies in the same tree, and walk one r-way
+// choice per island and stage (walk_src); adaptive internal
 // resampling (recording instantiation) carries log(M omega) per particle and
 // skips an island's resampling while its ESS is at least tau_int M.
 //
@@ -95,6 +97,9 @@ constexpr int kMaxStages = 16;
 constexpr int kShuffleLevels = 5;
 constexpr int kCachedChunks = 2;      // record chunks a lane keeps in registers
 constexpr int kQw = 16;               // per-warp partial slots (one per tree level)
+constexpr int kGroupLog = kTailGroupLog;   // split steps: CTA records per group of the tail cascade
+constexpr int kGroupQ = 16;           // a group record's sums of squares (levels 0 .. g+gs-1)
+constexpr int kGroupThreads = 128;    // the group cascade kernel's CTA (one thread per record)
 using u64 = unsigned long long;
 
 template <typename R> struct CdfType;
@@ -117,6 +122,15 @@ struct Layout {
 __host__ __device__ inline size_t cascade_slots(const StepParams& p)
 {
     return (p.split ? 0 : 2 * (size_t)p.P) + 2 * (size_t)p.G + kMaxWarps * kQw + kMaxStages + 8 + 3 * kMaxWarps;
+}
+
+// shared-memory bytes of the split steps' group cascade kernel: tree nodes over the
+// larger of a group's records and the filter's groups, their exponents, reduction slots
+__host__ __device__ inline size_t group_cascade_smem_bytes(const StepParams& p)
+{
+    const size_t n = (size_t)((1 << p.gs) > p.NG ? (1 << p.gs) : p.NG);
+    return align16(sizeof(double) * 2 * n) + align16(sizeof(int) * n)
+           + align16(sizeof(double) * (kMaxWarps * kGroupQ + kMaxStages + kMaxWarps + 4));
 }
 
 __host__ __device__ inline Layout make_layout(const StepParams& p)
@@ -204,6 +218,20 @@ __device__ __forceinline__ V warp_incl_scan(V v, int lane)
         if (lane >= o) v += w;
     }
     return v;
+}
+
+// max / sum over the whole CTA (blockDim a multiple of 32); sh: kMaxWarps slots
+template <typename V>
+__device__ __forceinline__ V block_max(V v, V* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    V r = sh[0];
+    for (int w = 1; w < nw; ++w) r = sh[w] > r ? sh[w] : r;
+    return r;
 }
 
 // Programmatic dependent launch: wait until the previous kernel of the stream
@@ -317,7 +345,8 @@ template <> struct Casc<false> {
     __device__ static double to_d(V v) { return v; }
     __device__ static XW weight(V bsum, int e_add) { return xw_from_double(bsum, e_add); }
     __device__ static Qt tau(const StepParams& p) { return p.tau; }
-    __device__ static bool pick_lo(V lo, V hi, uint32_t w) { return unif_f64(w) * (lo + hi) < lo; }
+    // u tot < x, u = (w + 0.5) 2^-32
+    __device__ static bool below(uint32_t w, V tot, V x) { return unif_f64(w) * tot < x; }
 };
 template <> struct Casc<true> {
     using V = u64;
@@ -338,13 +367,12 @@ template <> struct Casc<true> {
     __device__ static double to_d(V v) { return (double)v; }
     __device__ static XW weight(V bsum, int e_add) { return xw_from_u64(bsum, e_add); }
     __device__ static Qt tau(const StepParams& p) { return p.tau_f; }
-    // u (lo + hi) < lo with u = (2w+1) 2^-33, exactly: (2w+1)(lo+hi) < 2^33 lo in 128 bits
-    __device__ static bool pick_lo(V lo, V hi, uint32_t w)
+    // u tot < x with u = (2w+1) 2^-33, exactly: (2w+1) tot < 2^33 x in 128 bits
+    __device__ static bool below(uint32_t w, V tot, V x)
     {
         const u64 w2 = 2ull * (u64)w + 1ull;
-        const u64 sum = lo + hi;
-        const u64 p_lo = w2 * sum, p_hi = __umul64hi(w2, sum);
-        const u64 r_lo = lo << 33, r_hi = lo >> 31;
+        const u64 p_lo = w2 * tot, p_hi = __umul64hi(w2, tot);
+        const u64 r_lo = x << 33, r_hi = x >> 31;
         return (p_hi < r_hi) || (p_hi == r_hi && p_lo < r_lo);
     }
 };
@@ -381,19 +409,129 @@ __device__ void cascade_records(const StepParams& p, int c, int tp, int ss, type
         if (p.trace) p.trace[(size_t)c * p.T + (tp - 1)] = lz;
         if (tp == p.T) p.logz[c] = lz;
     }
-    if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ss;
+    // the records count stages of r = 2^rb islands: stage s starts at binary stage
+    // rb (s-1) + 1, and s* - 1 binary stages interacted (a multiple of rb, or S)
+    const int Sr = S / p.rb, ssr = (ss - 1) / p.rb + 1;
+    if (p.sstar) p.sstar[(size_t)c * p.T + (tp - 1)] = ssr;
     if (p.enf) {
-        double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (S + 1);
+        double* e = p.enf + ((size_t)c * p.T + (tp - 1)) * (Sr + 1);
         double last = 1.0;
-        for (int s = 1; s <= S; ++s) {
-            const int sr = s <= ss ? s : ss;
+        for (int s = 1; s <= Sr; ++s) {
+            const int sb = p.rb * (s - 1) + 1;
+            const int sr = sb <= ss ? sb : ss;
             const double v = pos_v(tot)
                 ? (double)tq * (double)tq * ldexp(1.0, sr - 1) / ((double)m * (double)Q[sr - 1]) : 0.0;
             e[s] = v;
-            if (s == ss) last = v;
+            if (s == ssr) last = v;
         }
-        if (tp < p.T) p.enf[((size_t)c * p.T + tp) * (S + 1)] = pos_v(tot) ? (ss <= S ? last : 1.0) : 0.0;
+        if (tp < p.T) p.enf[((size_t)c * p.T + tp) * (Sr + 1)] = pos_v(tot) ? (ssr <= Sr ? last : 1.0) : 0.0;
     }
+}
+
+// The block sums of step tp (tree level l: sums over aligned blocks of 2^l
+// islands), where the island CTAs of step tp+1 find them:
+//  * levels below g: the CTA records, each in its own scale 2^pe;
+//  * split steps, levels g .. g+gs-1: the group records of the tail cascade
+//    (groups of 2^gs CTAs), each in its own scale 2^ge;
+//  * above: the upper tree ut in the 2^emax scale (fused steps: from level g,
+//    in shared memory; split steps: from level g+gs, the top tree in utg).
+// at(l, q, false) gives a node in its source's scale, at(l, q, true) in the
+// 2^emax scale; weight(l, q) the extended-range weight of a block mean.
+template <bool FX>
+struct BlockSums {
+    using C = Casc<FX>;
+    using V = typename C::V;
+    const StepParams& p;
+    int c, tp, emax;
+    const V* ut;             // upper tree (shared or global memory)
+    bool ut_global;
+    bool tail;               // split steps: group records between the CTA records and ut
+
+    __device__ const int* pe() const { return p.pe[tp & 1] + (size_t)c * p.P; }
+    __device__ const V* pt() const { return reinterpret_cast<const V*>(p.pt[tp & 1]) + (size_t)c * p.P * 2 * p.G; }
+    __device__ int top_level() const { return tail ? p.g + p.gs : p.g; }
+    __device__ V utv(int i) const { return ut_global ? __ldcg(&ut[i]) : ut[i]; }
+    // does the tree between levels L and Lt (a group of r members) lie in one source?
+    __device__ bool local(int L, int Lt) const
+    {
+        const int g = p.g, h = top_level();
+        return Lt <= g || L >= h || (tail && L >= g && Lt <= h);
+    }
+    // node q of level l and its source's binary exponent (the node is V * 2^(exp - frac))
+    __device__ V raw(int l, int q, int& ex) const
+    {
+        const int g = p.g;
+        if (l < g) {
+            const int jc = q >> (g - l);
+            ex = __ldcg(&pe()[jc]);
+            return __ldcg(&pt()[(size_t)jc * 2 * p.G + tree_off(p.G, l) + (q - (jc << (g - l)))]);
+        }
+        if (l < top_level()) {
+            const int u = l - g, gr = q >> (p.gs - u), GS = 1 << p.gs;
+            ex = __ldcg(&p.ge[tp & 1][(size_t)c * p.NG + gr]);
+            const V* gt = reinterpret_cast<const V*>(p.gtr[tp & 1]) + ((size_t)c * p.NG + gr) * 2 * GS;
+            return __ldcg(&gt[tree_off(GS, u) + (q - (gr << (p.gs - u)))]);
+        }
+        ex = emax;
+        return utv(tree_off(tail ? p.NG : p.P, l - top_level()) + q);
+    }
+    __device__ V at(int l, int q, bool common) const
+    {
+        int ex;
+        const V v = raw(l, q, ex);
+        if (!common || l >= top_level()) return v;
+        return ex == INT_MIN ? (V)0 : C::rescale(v, emax - ex);
+    }
+    // W = (block sum at level l) / 2^l, extended range
+    __device__ XW weight(int l, int q) const
+    {
+        int ex;
+        const V v = raw(l, q, ex);
+        if (ex == INT_MIN) return XW{0ull, 0};
+        return C::weight(v, ex - C::frac(p) - l);
+    }
+};
+
+// src(k), the block island k holds after the interacting stages of step tp:
+// lvl = s*-1 binary levels, i.e. lvl/rb stages of r = 2^rb islands, walked from
+// the last interacting stage down, j = k at the top.  At stage s the island j
+// draws a member of its group (the r aligned blocks of level L = rb (s-1) under
+// j's block of level L + rb) with probability proportional to the members'
+// block sums, which are proportional to their weights before the stage: the
+// first member c with u tot < C_c (C the cumulative sums in member order, tot
+// the group's sum), found by descending the rb binary tree levels under the
+// group's node with the one uniform u of (tp, s, j).  With every weight zero it
+// takes the last member.  A group whose tree lies in one source (a CTA record,
+// a group record, the upper tree) is compared in that source's scale, else in
+// the 2^emax scale.
+template <bool FX>
+__device__ int walk_src(const BlockSums<FX>& bs, const Stream& st, int k, int lvl)
+{
+    using C = Casc<FX>;
+    using V = typename C::V;
+    const int rb = bs.p.rb, tp = bs.tp;
+    int j = k;
+    for (int s = lvl / rb; s >= 1; --s) {
+        const int L = rb * (s - 1), Lt = L + rb;
+        const bool common = !bs.local(L, Lt);
+        const uint32_t wu = st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x;
+        int n = (j >> Lt) << 1;                   // left child of the group's node, level Lt-1
+        V left = bs.at(Lt - 1, n, common);
+        const V tot = left + bs.at(Lt - 1, n + 1, common);
+        V acc = (V)0;
+        for (int l = Lt - 1;; --l) {
+            if (!C::below(wu, tot, acc + left)) {
+                acc += left;
+                ++n;
+            }
+            if (l == L) break;
+            n <<= 1;
+            left = bs.at(l - 1, n, common);
+        }
+        const int mask = ((1 << rb) - 1) << L;
+        j = (j & ~mask) | ((n << L) & mask);
+    }
+    return j;
 }
 
 // Where the cascade's result goes: to global memory for the next step's CTAs
@@ -407,59 +545,32 @@ struct CascadeOwn {
 };
 
 // A CTA's own islands after the cascade of step tp: the weight W^k_{tp+1,0}
-// (block mean at level s*-1: from the CTA's record below the CTA level, from
-// the upper tree ut above it) and the inherited block src(k), walked from
-// stage s*-1 down (stage levels below g from the records of step tp).
+// (the block mean at level s*-1) and the inherited block src(k), walked from
+// stage s*-1 down.
 template <bool FX>
-__device__ void own_outputs(const StepParams& p, int c, int tp, const Stream& st, const typename Casc<FX>::V* ut,
-                            bool ut_global, int ss, int emax, const CascadeOwn& own)
+__device__ void own_outputs(const BlockSums<FX>& bs, const Stream& st, int ss, const CascadeOwn& own)
 {
     using C = Casc<FX>;
-    using V = typename C::V;
-    const int P = p.P, G = p.G, g = p.g;
-    const int* pe = p.pe[tp & 1] + (size_t)c * P;
-    const V* pt = reinterpret_cast<const V*>(p.pt[tp & 1]) + (size_t)c * P * 2 * G;
+    const StepParams& p = bs.p;
+    const int G = p.G, g = p.g;
     const int lvl = ss - 1;
-    const bool dead = (emax == INT_MIN);
-    const int jo = own.k0 >> g;
-    auto utv = [&](int i) { return ut_global ? __ldcg(&ut[i]) : ut[i]; };
+    const bool dead = (bs.emax == INT_MIN);
     for (int gi = threadIdx.x; gi < G; gi += blockDim.x) {
         const int k = own.k0 + gi;
         XW w{0ull, 0};
         if (!dead) {
-            const int ej = __ldcg(&pe[jo]);
-            if (lvl == 0 && g == 0) {          // the island is the CTA: its rescaled record top
+            if (lvl == 0 && g == 0 && !bs.tail) {   // the island is the CTA: its record top, rescaled
+                const int ej = __ldcg(&bs.pe()[own.k0]);
                 if (ej != INT_MIN)
-                    w = C::weight(C::rescale(__ldcg(&pt[(size_t)jo * 2 * G]), emax - ej), emax - C::frac(p));
-            } else if (lvl < g) {
-                if (ej != INT_MIN)
-                    w = C::weight(__ldcg(&pt[(size_t)jo * 2 * G + tree_off(G, lvl) + (gi >> lvl)]),
-                                  ej - C::frac(p) - lvl);
+                    w = C::weight(C::rescale(__ldcg(&bs.pt()[(size_t)own.k0 * 2 * G]), bs.emax - ej),
+                                  bs.emax - C::frac(p));
             } else {
-                w = C::weight(utv(tree_off(P, lvl - g) + (k >> lvl)), emax - C::frac(p) - lvl);
+                w = bs.weight(lvl, k >> lvl);
             }
         }
         own.w[gi] = w.bits;
         own.we[gi] = w.e;
-        int j = k;
-        for (int s = lvl; s >= 1; --s) {
-            const int l = s - 1, b = 1 << l, pi = j >> l;
-            V lo, hi;
-            if (l >= g) {
-                lo = utv(tree_off(P, l - g) + (pi & ~1));
-                hi = utv(tree_off(P, l - g) + (pi | 1));
-            } else {
-                // both blocks lie in the record of CTA jc, in its own scale
-                const int jc = j >> g;
-                const int li = pi - jc * (G >> l);
-                const int ol = tree_off(G, l);
-                lo = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li & ~1)]);
-                hi = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li | 1)]);
-            }
-            const uint32_t wu = st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x;
-            j = C::pick_lo(lo, hi, wu) ? (j & ~b) : (j | b);
-        }
-        own.src[gi] = j;
+        own.src[gi] = walk_src<FX>(bs, st, k, lvl);
     }
 }
 
@@ -777,7 +888,8 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     const int ss = iscal[1];
     const int lvl = ss - 1;
     if (OWN) {
-        own_outputs<FX>(p, c, tp, st, ut, false, ss, emax, *own);
+        const BlockSums<FX> bs{p, c, tp, emax, ut, false, false};
+        own_outputs<FX>(bs, st, ss, *own);
         return;
     }
     if (tid == 0) {
@@ -791,27 +903,8 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
             reinterpret_cast<V*>(p.cup)[(size_t)c * P + b] = ut[tree_off(P, lvl - g) + b];
     }
     if (lvl >= 1) {
-        for (int k = tid; k < m; k += nthr) {
-            int j = k;
-            for (int s = lvl; s >= 1; --s) {
-                const int l = s - 1, b = 1 << l, pi = j >> l;
-                V lo, hi;
-                if (l >= g) {
-                    lo = ut[tree_off(P, l - g) + (pi & ~1)];
-                    hi = ut[tree_off(P, l - g) + (pi | 1)];
-                } else {
-                    // both blocks lie in the record of CTA jc, in its own scale
-                    const int jc = j >> g;
-                    const int li = pi - jc * (G >> l);
-                    const int ol = tree_off(G, l);
-                    lo = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li & ~1)]);
-                    hi = __ldcg(&pt[(size_t)jc * 2 * G + ol + (li | 1)]);
-                }
-                const uint32_t wu = st.draw((uint32_t)j, (uint32_t)tp, KIND_ISLAND, (uint32_t)s).x;
-                j = C::pick_lo(lo, hi, wu) ? (j & ~b) : (j | b);
-            }
-            p.nsrc[(size_t)c * m + k] = j;
-        }
+        const BlockSums<FX> bs{p, c, tp, emax, ut, false, false};
+        for (int k = tid; k < m; k += nthr) p.nsrc[(size_t)c * m + k] = walk_src<FX>(bs, st, k, lvl);
     }
 }
 
@@ -890,6 +983,207 @@ __device__ void publish_record(const StepParams& p, int c, int t, int jo, const 
     if (lane == 0) p.pe[t & 1][(size_t)c * p.P + jo] = ej;
 }
 
+// Sums of squares of one tree level per slot, reduced over the CTA: every thread adds
+// its part of slot l (l < n), lane 0 of each warp leaves the warp's sums in qw, and the
+// first n threads sum the warps into out.
+template <typename Qt>
+__device__ __forceinline__ void block_sum_slots(const Qt (&part)[kGroupQ], int n, Qt* qw, Qt* out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int l = 0; l < kGroupQ; ++l) {
+        if (l < n) {
+            const Qt v = warp_sum(part[l]);
+            if (lane == 0) qw[warp * kGroupQ + l] = v;
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < n) {
+        Qt v = (Qt)0;
+        for (int w = 0; w < nw; ++w) v += qw[w * kGroupQ + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+    __syncthreads();
+}
+
+// Split steps: the cascade of step tp is a kernel of NG x B CTAs.  The P CTA
+// records of a filter form NG groups of GS = 2^gs consecutive records; CTA grp
+// reduces group grp to a group record: the largest exponent ge over its
+// records, the block-sum subtree of levels g .. g+gs over its record tops
+// (rescaled to 2^ge), and the sums of squares of levels 0 .. g+gs-1 in that
+// scale.  The last CTA of the filter to finish its group (a ticket counter)
+// runs the top of the cascade over the NG group records: the largest exponent
+// emax, the tree above the groups (levels g+gs .. S, in the 2^emax scale),
+// every level's sum of squares, s*, the run's records and the summary (s*,
+// emax) for step tp+1.  Group records are double-buffered by step like the CTA
+// records.  The ticket wraps to zero by itself (atomicInc) and the prologue
+// clears it.  Publication: every thread's stores, a CTA barrier, then one
+// thread's device-scope fence and ticket; the last arrival fences before it
+// reads.  (A version that ran this reduction in the tail of the island kernel,
+// with a ticket per group of island CTAs, was slower: the device-scope fence
+// before every island CTA's ticket held that CTA's slot about a microsecond,
+// over some 27 waves of CTAs per step.)
+template <bool FX>
+__device__ void group_cascade(const StepParams& p, int c, int tp, int grp, unsigned char* sm)
+{
+    using C = Casc<FX>;
+    using V = typename C::V;
+    using Qt = typename C::Qt;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int G = p.G, g = p.g, P = p.P, NG = p.NG, gs = p.gs, GS = 1 << gs, S = p.S, m = p.m;
+    const int h = g + gs;                    // level of the group roots
+    const int nmax = GS > NG ? GS : NG;
+    const int par = tp & 1;
+    V* nd = reinterpret_cast<V*>(sm);                                             // [2 nmax] tree nodes
+    int* ex = reinterpret_cast<int*>(sm + align16(sizeof(double) * 2 * nmax));    // [nmax] leaf exponents
+    double* rs = reinterpret_cast<double*>(sm + align16(sizeof(double) * 2 * nmax) + align16(sizeof(int) * nmax));
+    Qt* qw = reinterpret_cast<Qt*>(rs);                                           // [kMaxWarps][kGroupQ]
+    Qt* Q = reinterpret_cast<Qt*>(rs + kMaxWarps * kGroupQ);                      // [kMaxStages]
+    int* red = reinterpret_cast<int*>(rs + kMaxWarps * kGroupQ + kMaxStages);     // [kMaxWarps]
+    int* flag = reinterpret_cast<int*>(rs + kMaxWarps * kGroupQ + kMaxStages + kMaxWarps);
+    unsigned* tick = p.tick + c;
+
+    // ---- 1. the group record ----
+    {
+        const size_t r0 = (size_t)c * P + (size_t)grp * GS;
+        const int* pe = p.pe[par] + r0;
+        const V* pt = reinterpret_cast<const V*>(p.pt[par]) + r0 * 2 * G;
+        const Qt* pq = reinterpret_cast<const Qt*>(p.pq[par]) + r0 * 8;
+        int em = INT_MIN;
+        for (int i = tid; i < GS; i += nthr) {
+            const int e = __ldcg(&pe[i]);
+            const V top = __ldcg(&pt[(size_t)i * 2 * G + tree_off(G, g)]);
+            const bool ok = pos_v(top) && e != INT_MIN;
+            ex[i] = ok ? e : INT_MIN;
+            nd[i] = top;
+            if (ok && e > em) em = e;
+        }
+        em = block_max(em, red);
+        Qt part[kGroupQ];
+#pragma unroll
+        for (int l = 0; l < kGroupQ; ++l) part[l] = (Qt)0;
+        for (int i = tid; i < GS; i += nthr) {
+            const int e = ex[i];
+            V v = (V)0;
+            if (e != INT_MIN) {
+                const int sh = em - e;
+                v = C::rescale(nd[i], sh);
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    if (l < g) part[l] += C::qscale(__ldcg(&pq[(size_t)i * 8 + l]), 2 * sh);
+            }
+            nd[i] = v;
+            const Qt q = C::qv(v);
+#pragma unroll
+            for (int l = 0; l < kGroupQ; ++l)
+                if (l == g) part[l] += q * q;    // level g: the leaves
+        }
+        // the subtree of levels g+1 .. g+gs
+#pragma unroll
+        for (int u = 1; u <= kGroupLog; ++u) {
+            if (u <= gs) {
+                __syncthreads();
+                const int cnt = GS >> u, o0 = tree_off(GS, u - 1), o1 = tree_off(GS, u);
+                for (int i = tid; i < cnt; i += nthr) {
+                    const V v = nd[o0 + 2 * i] + nd[o0 + 2 * i + 1];
+                    nd[o1 + i] = v;
+                    const Qt q = C::qv(v);
+#pragma unroll
+                    for (int l = 1; l < kGroupQ; ++l)
+                        if (l == g + u && u < gs) part[l] += q * q;
+                }
+            }
+        }
+        __syncthreads();
+        block_sum_slots<Qt>(part, h, qw, Q);
+        V* gt = reinterpret_cast<V*>(p.gtr[par]) + ((size_t)c * NG + grp) * 2 * GS;
+        for (int i = tid; i < 2 * GS - 1; i += nthr) gt[i] = nd[i];
+        Qt* gq = reinterpret_cast<Qt*>(p.gqs[par]) + ((size_t)c * NG + grp) * kGroupQ;
+        if (tid < h) gq[tid] = Q[tid];
+        if (tid == 0) p.ge[par][(size_t)c * NG + grp] = em;
+    }
+
+    // ---- 2. the filter's ticket ----
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        flag[0] = atomicInc(&tick[0], (unsigned)(NG - 1)) == (unsigned)(NG - 1);
+    }
+    __syncthreads();
+    if (!flag[0]) return;
+    __threadfence();
+
+    // ---- 3. the top of the cascade ----
+    const int* ge = p.ge[par] + (size_t)c * NG;
+    const V* gt = reinterpret_cast<const V*>(p.gtr[par]) + (size_t)c * NG * 2 * GS;
+    const Qt* gq = reinterpret_cast<const Qt*>(p.gqs[par]) + (size_t)c * NG * kGroupQ;
+    int emax = INT_MIN;
+    for (int i = tid; i < NG; i += nthr) {
+        const int e = __ldcg(&ge[i]);
+        const V r = __ldcg(&gt[(size_t)i * 2 * GS + tree_off(GS, gs)]);
+        const bool ok = pos_v(r) && e != INT_MIN;
+        ex[i] = ok ? e : INT_MIN;
+        nd[i] = r;
+        if (ok && e > emax) emax = e;
+    }
+    emax = block_max(emax, red);
+    Qt part[kGroupQ];
+#pragma unroll
+    for (int l = 0; l < kGroupQ; ++l) part[l] = (Qt)0;
+    const int ngl = S - h;                   // log2 NG
+    for (int i = tid; i < NG; i += nthr) {
+        const int e = ex[i];
+        V v = (V)0;
+        if (e != INT_MIN) {
+            const int sh = emax - e;
+            v = C::rescale(nd[i], sh);
+#pragma unroll
+            for (int l = 0; l < kGroupQ; ++l)
+                if (l < h) part[l] += C::qscale(__ldcg(&gq[(size_t)i * kGroupQ + l]), 2 * sh);
+        }
+        nd[i] = v;
+        const Qt q = C::qv(v);
+#pragma unroll
+        for (int l = 0; l < kGroupQ; ++l)
+            if (l == h && h < S) part[l] += q * q;
+    }
+    for (int u = 1; u <= ngl; ++u) {
+        __syncthreads();
+        const int cnt = NG >> u, o0 = tree_off(NG, u - 1), o1 = tree_off(NG, u);
+        for (int i = tid; i < cnt; i += nthr) {
+            const V v = nd[o0 + 2 * i] + nd[o0 + 2 * i + 1];
+            nd[o1 + i] = v;
+            const Qt q = C::qv(v);
+#pragma unroll
+            for (int l = 0; l < kGroupQ; ++l)
+                if (l == h + u && l < S) part[l] += q * q;
+        }
+    }
+    __syncthreads();
+    block_sum_slots<Qt>(part, S, qw, Q);
+    const V tot = nd[tree_off(NG, ngl)];
+    if (warp == 0) {
+        const Qt tq = C::qv(tot);
+        bool quiet = false;
+        if (lane < S) {
+            const int s = lane + 1;
+            // as in cascade_all: stage s interacts iff ENF_s < tau; with radix 2^rb only the
+            // first binary stage of each group decides
+            quiet = (s - 1) % p.rb == 0 && pos_v(tot) &&
+                    !(tq * tq * (Qt)(1u << (s - 1)) < C::tau(p) * (Qt)m * Q[s - 1]);
+        }
+        const unsigned qm = __ballot_sync(0xffffffffu, quiet);
+        if (lane == 0) {
+            const int ss = p.mode == 0 ? 1 : (p.mode == 1 ? S + 1 : (qm ? __ffs(qm) : S + 1));
+            cascade_records<FX>(p, c, tp, ss, tot, emax, Q);
+            p.csum[(size_t)c * 4 + 0] = ss;
+            p.csum[(size_t)c * 4 + 1] = emax;
+        }
+    }
+    V* ut = reinterpret_cast<V*>(p.utg) + (size_t)c * 2 * P;
+    for (int i = tid; i < 2 * NG - 1; i += nthr) ut[i] = nd[i];
+}
+
 enum { OP_STEP = 0, OP_PREPARE = 1, OP_FITS = 2, OP_PERSIST_GRID = 3, OP_PERSIST_CTA = 4, OP_CASCADE = 5,
        OP_WIDE_FITS = 6 };
 
@@ -916,6 +1210,7 @@ __global__ void airpf_prologue_kernel(StepParams p)
         reinterpret_cast<ModelPar<R>*>(p.mpar)[i] = mp;
     }
     if (MODEL == NGM && i < p.T) reinterpret_cast<R*>(p.drift)[i] = (R)(8.0 * cos(1.2 * (double)(i + 1)));
+    if (p.split && i < p.B) p.tick[i] = 0u;       // the group cascade's tickets
 }
 
 // ---------------------------------------------------------------------------
@@ -1038,21 +1333,22 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
             own_we[gi] = 1;
             own_src[gi] = k0 + gi;
         }
-        if (designated && tid == 0 && p.enf) p.enf[(size_t)c * p.T * (p.S + 1)] = 1.0;
+        if (designated && tid == 0 && p.enf) p.enf[(size_t)c * p.T * (p.S / p.rb + 1)] = 1.0;
     } else if (LV == 1 || LV == 3 || (LV == 0 && p.fused)) {
         // this CTA runs the cascade of step t-1 itself, from every CTA record of
         // the filter (the first CTA also writes log Z and the run's records)
         const CascadeOwn own{k0, own_w, own_we, own_src};
         cascade_all<FX, true>(p, c, t - 1, st, tree, &own, designated);
     } else if (LV == 2 || (LV == 0 && p.split)) {
-        // the cascade kernel of step t-1 left s*, the largest exponent and the
-        // upper tree; this CTA derives its islands' weights and walks
+        // the group cascade of step t-1 left s*, the largest exponent, the group
+        // records and the top tree; this CTA derives its islands' weights and walks
         int* csum_sh = reinterpret_cast<int*>(scal) + 4;
         if (tid < 2) csum_sh[tid] = __ldcg(&p.csum[(size_t)c * 4 + tid]);
         __syncthreads();
         const CascadeOwn own{k0, own_w, own_we, own_src};
-        own_outputs<FX>(p, c, t - 1, st, reinterpret_cast<const typename Casc<FX>::V*>(p.utg) + (size_t)c * 2 * p.P,
-                        true, csum_sh[0], csum_sh[1], own);
+        const BlockSums<FX> bs{p, c, t - 1, csum_sh[1],
+                               reinterpret_cast<const typename Casc<FX>::V*>(p.utg) + (size_t)c * 2 * p.P, true, true};
+        own_outputs<FX>(bs, st, csum_sh[0], own);
     } else {
         // the cascade's summary of step t-1, this CTA's record of step t-1 and
         // (used only if some stage interacted) the inherited blocks
@@ -1283,14 +1579,33 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     // weights, total^2 / sum w^2, is below tau_int M (the same for every thread of it)
     const bool resample = !(air && alive) || ((double)total * (double)total / sq < p.tau_int * (double)M);
     if (resample) {
-        for (int n = M; n > 1;) {
-            const int half = n >> 1;
+        if constexpr (!FX) {
+            // FP64: the CDF and the targets are non-negative doubles, whose order is the
+            // order of their bit patterns as 64-bit integers: the same decisions, compared
+            // on the integer pipe instead of the FP64 pipe
+            const long long* cdfb = reinterpret_cast<const long long*>(cdf);
+            long long tb[PPT];
 #pragma unroll
-            for (int r = 0; r < PPT; ++r) {
-                const Cdf v = cdf[cdf_ix(base[r] + half - 1)];
-                base[r] = (v > target[r]) ? base[r] : base[r] + half;
+            for (int r = 0; r < PPT; ++r) tb[r] = __double_as_longlong(target[r]);
+            for (int n = M; n > 1;) {
+                const int half = n >> 1;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    const long long v = cdfb[cdf_ix(base[r] + half - 1)];
+                    base[r] = (v > tb[r]) ? base[r] : base[r] + half;
+                }
+                n -= half;
             }
-            n -= half;
+        } else {
+            for (int n = M; n > 1;) {
+                const int half = n >> 1;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    const Cdf v = cdf[cdf_ix(base[r] + half - 1)];
+                    base[r] = (v > target[r]) ? base[r] : base[r] + half;
+                }
+                n -= half;
+            }
         }
     } else {
 #pragma unroll
@@ -1496,6 +1811,20 @@ __global__ void __launch_bounds__(kCascadeThreads) airpf_cascade_kernel(StepPara
     cascade_all<sizeof(R) == 4>(p, c, t, st, reinterpret_cast<double*>(smem));
 }
 
+// The cascade of step t for split steps: CTA j handles group j mod NG of filter j / NG.
+template <typename R>
+__global__ void __launch_bounds__(kGroupThreads) airpf_group_cascade_kernel(StepParams p, int t)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int c = blockIdx.x / p.NG, grp = blockIdx.x - c * p.NG;
+    if (p.active != nullptr && p.active[c] == 0) return;
+    if (p.pdl) {                  // the records are the island-step kernel's output
+        dependency_wait();
+        allow_dependents();
+    }
+    group_cascade<sizeof(R) == 4>(p, c, t, grp, smem);
+}
+
 // All T+1 steps in one launch.  GRID: the filter spans several co-resident CTAs
 // (cooperative launch); a step's records are published before a grid barrier,
 // the filter's first CTA runs the cascade, and a second barrier releases the
@@ -1610,6 +1939,13 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
     }
     if (op == OP_PERSIST_CTA) {
         airpf_persistent_kernel<R, MODEL, DX, PPT, false><<<grid, block, smem, stream>>>(p);
+        return cudaGetLastError();
+    }
+    if (op == OP_CASCADE && p.split) {
+        const size_t cs = group_cascade_smem_bytes(p);
+        if (p.pdl) return launch_dependent(airpf_group_cascade_kernel<R>, dim3(p.NG * p.B), dim3(kGroupThreads), cs,
+                                           stream, p, t);
+        airpf_group_cascade_kernel<R><<<p.NG * p.B, kGroupThreads, cs, stream>>>(p, t);
         return cudaGetLastError();
     }
     if (op == OP_CASCADE) {

@@ -96,3 +96,29 @@ def test_moments_workspace_covers_the_small_grid_tiling():
     B, T, m, dx = 3, 50, 64, 1
     need = 8 * B * T * m * 2 + 8 * B * T * m * 4 * 4 * dx       # log W pairs, 4 warps x 4 dx sums
     assert need <= mom.value - base.value < need + 2 * 256
+
+
+def test_run_static_checks_sizes_before_the_call():
+    """run_static hands raw pointers to kernels that read theta[B*d] and y[T*dy] and write
+    log_z[B]: short or misshapen tensors are refused on the host (no GPU needed here)."""
+    import torch
+    import paper_2312_06484_gb300 as gp
+    f64 = dict(dtype=torch.float64)
+    th, y, lz = torch.zeros(2 * 3, **f64), torch.zeros(10, **f64), torch.zeros(2, **f64)
+    kw = dict(m=16, M=32, B=2)
+    cases = [(torch.zeros(5, **f64), y, lz, {}, "theta holds"),
+             (th, y, torch.zeros(1, **f64), {}, "log_z holds"),
+             (th, torch.zeros(0, **f64), lz, {}, "y holds"),
+             (th, torch.zeros(9, **f64), lz, dict(dy=2, model=5), "y holds")]
+    for theta, yy, out, extra, msg in cases:
+        model = extra.pop("model", gp.MODEL_SV)
+        with pytest.raises(gp.AirpfError, match=msg):
+            gp.run_static(model, theta, yy, out, **kw, **extra)
+    # the LGSSM's model data: dx*dx + dy*dx values
+    d = gp.theta_dim(gp.MODEL_LGSSM, 2)
+    with pytest.raises(gp.AirpfError, match="model_data"):
+        gp.run_static(gp.MODEL_LGSSM, torch.zeros(2 * d, **f64), torch.zeros(20, **f64), lz, dx=2, dy=2,
+                      model_data=torch.zeros(5, **f64), **kw)
+    # right sizes but host tensors: refused before any pointer reaches the library
+    with pytest.raises(gp.AirpfError, match="CUDA tensors"):
+        gp.run_static(gp.MODEL_SV, th, y, lz, **kw)

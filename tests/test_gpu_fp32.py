@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from parity_util import run_gpu
+from parity_util import compare_first_step, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -54,3 +54,26 @@ def test_fp32_matches_fp64_at_m65536(M):
         lz[prec] = float(f.run(th, y, iter=1)["log_z"].item())
         f.close()
     assert np.isfinite(lz["fp64"]) and abs(lz["fp32"] - lz["fp64"]) < 0.5, lz
+
+
+@pytest.mark.parametrize("model,m,M,mode,launch", [
+    (synth.MODEL_SV, 1024, 256, "adaptive", "auto"),      # the SV workload's fused steps
+    (synth.MODEL_SV, 1024, 256, "always", "auto"),        # every stage: the 64-bit block sums of 256 CTAs
+    (synth.MODEL_SV, 64, 1024, "always", "auto"),         # M = 1024: a multi-warp integer prefix sum
+    (synth.MODEL_NGM, 65536, 256, "adaptive", "auto"),    # the m = 65536 workload's split steps
+    (synth.MODEL_NGM, 65536, 256, "always", "auto"),
+])
+def test_fp32_first_step_at_workload_size(model, m, M, mode, launch):
+    """FP32-mixed step 1 draw by draw at the workloads' sizes: the multi-warp CDF carry, the
+    XOR-swizzled CDF rows and the fixed-point block sums over hundreds of CTAs.  Step 1 is the
+    last step before lineages may legitimately diverge; every draw, island walk and s* the oracle
+    does not mark as within 1e-5 of its threshold must agree."""
+    theta = synth.SV_THETA if model == synth.MODEL_SV else synth.NGM_THETA
+    y = synth.sv_observations(1, 2) if model == synth.MODEL_SV else synth.ngm_observations(1, 5)
+    B = 2 if m * M <= 1 << 18 else 1
+    g = run_gpu(model, theta, y, m=m, M=M, B=B, mode=mode, tau=0.3, seed=31, precision="fp32", launch=launch)
+    for b in range(B):
+        o = oracle.airpf(model, theta, y, m=m, M=M, mode=MODES[mode], tau=0.3, seed=31, chain=b, tie_rel=1e-5,
+                         tie_masks=True)
+        n = compare_first_step(g, b, o, M=M, what=f"m={m} M={M} {mode} b={b}")
+        assert n >= 0.95 * m * M, (n, m * M)
