@@ -230,6 +230,18 @@ def batched_leg(gp, torch, ws: int, n_chains: int = 256, T: int = 500, passes: i
     torch.cuda.synchronize()
     ms_pass = e0.elapsed_time(e1) / passes
     ps = float((ms_ * Ms_).sum()) * T
+    # each class alone on its own stream: the overlap inside a group pass (sum of the classes'
+    # times against the group's) and its critical path (the slowest class)
+    classes = []
+    for (m, M), mb, tht, cb in zip(keys, members, th, c0):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        mb.run(tht, y, chain0=cb, iter=0xFFFF0001)
+        a0.record(mb.stream)
+        mb.run(tht, y, chain0=cb, iter=0)
+        a1.record(mb.stream)
+        mb.sync()
+        classes.append({"m": m, "M": M, "chains": mb.B, "ms_alone": a0.elapsed_time(a1), "launch_mode": mb.launch_mode})
+    classes.sort(key=lambda r: -r["ms_alone"])
     # the group's roofline: the FP32 path's lane operations per particle-step, with the
     # binary search over each chain's own M (7 per level)
     ops = sum((ops_per_particle_step("SV") - OPS_COMMON["binary_search_M256"] + 7 * np.ceil(np.log2(M))) * m * M * T
@@ -241,6 +253,8 @@ def batched_leg(gp, torch, ws: int, n_chains: int = 256, T: int = 500, passes: i
     out = {"workload": f"batched_sv_{n_chains}chains_T{T}", "particles": int((ms_ * Ms_).sum()),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                         "note": "all classes' island-step kernels of one group pass"},
+           "classes_alone": classes, "sum_of_classes_ms": sum(r["ms_alone"] for r in classes),
+           "slowest_class_ms": classes[0]["ms_alone"],
            "classes": len(keys), "ms_per_pass": ms_pass,
            "particle_steps_per_s": ps * ws / (ms_pass / 1e3),
            "chain_iters_per_s": n_chains * ws / (ms_pass / 1e3), "passes": passes,

@@ -38,7 +38,7 @@ struct WsLayout {
     size_t run, theta, mdata, y, X[2], pe[2], pt[2], pq[2], csum, cup, nsrc, utg, ires[2], logz, trace, enf,
         sstar, anc, active, mpar, drift, bar;
     size_t pm_prop, pm_logz_prop, pm_stats, pm_gprop, pm_lqf;
-    size_t xck, xblk, logw, gpi[2], xh[3], dh[3], gout, sout;   // gradient pass
+    size_t xck, xblk, logw, gpi[2], xh[3], dh[3], gout, sout, gacc;   // gradient pass
     size_t fw, fsum;                                             // output measures
     size_t lom[2];                                               // adaptive internal resampling
     int fm_nw;
@@ -182,7 +182,7 @@ WsLayout make_ws_layout(const airpf_config* c)
     L.pm_stats = take(sizeof(int) * B);
     L.pm_gprop = take(sizeof(double) * B * td);
     L.pm_lqf = take(sizeof(double) * B);
-    L.xck = L.xblk = L.logw = L.gout = L.sout = 0;
+    L.xck = L.xblk = L.logw = L.gout = L.sout = L.gacc = 0;
     for (int i = 0; i < 3; ++i) L.xh[i] = L.dh[i] = 0;
     L.gpi[0] = L.gpi[1] = 0;
     if (grad) {
@@ -192,10 +192,12 @@ WsLayout make_ws_layout(const airpf_config* c)
         L.xblk = take(rsz * B * K * c->dx * N);
         L.logw = take(sizeof(double) * B * T * c->m);
         for (int i = 0; i < 2; ++i) L.gpi[i] = take(sizeof(double) * B * c->m);
-        for (int i = 0; i < 3; ++i) L.xh[i] = take(rsz * B * c->dx * N);
-        for (int i = 0; i < 3; ++i) L.dh[i] = take(sizeof(double) * B * N);
+        const size_t dxp = c->model == AIRPF_MODEL_LGSSM ? 8 : (size_t)c->dx;   // adjoints padded per particle
+        for (int i = 0; i < 3; ++i) L.xh[i] = take(rsz * B * dxp * N);
+        for (int i = 0; i < 3; ++i) L.dh[i] = take(rsz * B * N);
         L.gout = take(sizeof(double) * B * td);
         L.sout = take(sizeof(double) * B * td);
+        L.gacc = take(sizeof(double) * B * c->m * 2 * 10);   // 2 x kMaxTheta (8 + 2) per island
     }
     L.lom[0] = L.lom[1] = 0;
     if (c->tau_int > 0.0)
@@ -442,6 +444,7 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     }
     p.P = cfg->m / p.G;
     p.g = ilog2_exact(p.G);
+    p.lg_tpi = ilog2_exact(p.tpi);
     p.theta_dim = ctx->theta_dim;
     p.seed_lo = (uint32_t)(cfg->seed & 0xffffffffu);
     p.seed_hi = (uint32_t)(cfg->seed >> 32);
@@ -545,9 +548,10 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
         for (int i = 0; i < 2; ++i) p.gpi[i] = at<double>(ctx, L.gpi[i]);
         for (int i = 0; i < 3; ++i) {
             p.xh[i] = at<void>(ctx, L.xh[i]);
-            p.dh[i] = at<double>(ctx, L.dh[i]);
+            p.dh[i] = at<void>(ctx, L.dh[i]);
         }
         p.gout = at<double>(ctx, L.gout);
+        p.gacc = at<double>(ctx, L.gacc);
         p.sout = at<double>(ctx, L.sout);
     }
     p.rb = radix_bits(cfg);

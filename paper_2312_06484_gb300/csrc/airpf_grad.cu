@@ -23,8 +23,9 @@
 //
 // States between checkpoints are recomputed from the previous state, the
 // lineage and the regenerated transition noise.  Particle arithmetic and the
-// per-thread and per-warp sums in the pass's precision R; smoothing weights,
-// descendant weights and the CTA and grid sums of the theta terms in double.
+// per-thread and per-warp sums, the particle adjoints and the descendant weights in
+// the pass's precision R; smoothing weights and the CTA and island sums of the
+// theta terms in double.
 #include <climits>
 
 #include "airpf_device.cuh"
@@ -238,13 +239,14 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
     const R* xt = xstate<R>(p, c, t);
     const R* xprev = xstate<R>(p, c, t - 1);
-    const size_t xo = (size_t)c * dx * N;
-    const R* xh_in = reinterpret_cast<const R*>(p.xh[t % 3]) + xo;
+    // particle adjoints x^ [N][DX] (a particle's components together: vector atomics
+    // to its parent) and descendant weights [N], in the pass's precision; buffer t % 3
+    // holds step t's inputs and is cleared as it is read (it is step t-3's output buffer)
+    const size_t xo = (size_t)c * N * DX;
+    R* xh_in = reinterpret_cast<R*>(p.xh[t % 3]) + xo;
     R* xh_out = reinterpret_cast<R*>(p.xh[(t + 2) % 3]) + xo;
-    R* xh_zero = reinterpret_cast<R*>(p.xh[(t + 1) % 3]) + xo;
-    const double* dh_in = p.dh[t % 3] + (size_t)c * N;
-    double* dh_out = p.dh[(t + 2) % 3] + (size_t)c * N;
-    double* dh_zero = p.dh[(t + 1) % 3] + (size_t)c * N;
+    R* dh_in = reinterpret_cast<R*>(p.dh[t % 3]) + (size_t)c * N;
+    R* dh_out = reinterpret_cast<R*>(p.dh[(t + 2) % 3]) + (size_t)c * N;
     const R pik_r = (R)p.gpi[t & 1][(size_t)c * p.m + k];
 
     // island softmax of the log-weights
@@ -288,8 +290,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
         const int g = k * M + i;
         const R wi = (lsm[i] > (R)(-INFINITY)) ? exp(lsm[i] - mx) * inv_sum : (R)0;
         const R lhat = pik_r * wi;                                   // d log Z / d l_t(k,i)
-        const double delta_d = (t == p.T) ? (double)lhat : dh_in[g];      // descendant weight
-        const R delta = (R)delta_d;
+        const R delta = (t == p.T) ? lhat : dh_in[g];                // descendant weight
         const int par = parent_of(p, c, t, g);
         R x[DX], xp[DX], mu[DX];
         R s;
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
         transition_mean<R, MODEL, DX>(mp, dx, xp, mm, mu, s);
         R xhat[DX], v[DX];
 #pragma unroll
-        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? xh_in[(size_t)d * N + g] : (R)0;
+        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? xh_in[(size_t)g * DX + d] : (R)0;
         if (MODEL == AR1) {
             const R a = mp.th[0], sv = mp.th[1], sw = mp.th[2], s0 = mp.th[3];
             const R e = yv[0] - x[0];
@@ -396,10 +397,18 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
                     zn += zd * zd;
                 }
             }
-            ga[dx] += qsum;
-            ga[dx + 1] += lhat * dlr;
-            gs[dx] += delta * (R)0.5 * (zn - (R)dx);
-            gs[dx + 1] += delta * dlr;
+            // slots dx (log q) and dx + 1 (log r), with static indices (registers, not a stack array)
+#pragma unroll
+            for (int d = 0; d < kMaxTheta; ++d) {
+                if (d == dx) {
+                    ga[d] += qsum;
+                    gs[d] += delta * (R)0.5 * (zn - (R)dx);
+                }
+                if (d == dx + 1) {
+                    ga[d] += lhat * dlr;
+                    gs[d] += delta * dlr;
+                }
+            }
 #pragma unroll
             for (int cc = 0; cc < DX; ++cc) {
                 v[cc] = 0;
@@ -411,15 +420,22 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
             }
         }
         if (t >= 2) {                      // to the parent, along the lineage
+            if constexpr (DX == 8 && sizeof(R) == 4) {
+                // two 16-byte vector atomics (sm_90 and later) for the 8 components
+                float4* o = reinterpret_cast<float4*>(&xh_out[(size_t)par * DX]);
+                atomicAdd(o, make_float4(v[0], v[1], v[2], v[3]));
+                atomicAdd(o + 1, make_float4(v[4], v[5], v[6], v[7]));
+            } else {
 #pragma unroll
-            for (int d = 0; d < DX; ++d)
-                if (d < dx) atomicAdd(&xh_out[(size_t)d * N + par], v[d]);
-            atomicAdd(&dh_out[par], delta_d);
+                for (int d = 0; d < DX; ++d)
+                    if (d < dx) atomicAdd(&xh_out[(size_t)par * DX + d], v[d]);
+            }
+            atomicAdd(&dh_out[par], delta);
         }
 #pragma unroll
         for (int d = 0; d < DX; ++d)
-            if (d < dx) xh_zero[(size_t)d * N + g] = (R)0;
-        dh_zero[g] = 0.0;
+            if (d < dx) xh_in[(size_t)g * DX + d] = (R)0;
+        dh_in[g] = (R)0;
     }
     // the CTA's theta sums
 #pragma unroll
@@ -437,14 +453,49 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
         }
     }
     __syncthreads();
+    // the island's running sums over the steps (this CTA alone updates row k: no atomics,
+    // and the final sum over the islands runs in a fixed order)
     if (tid < td) {
         double a = 0.0, b = 0.0;
         for (int w = 0; w < nw; ++w) {
             a += red[tid][w];
             b += red[kMaxTheta + tid][w];
         }
-        atomicAdd(&p.gout[(size_t)c * td + tid], a);
-        atomicAdd(&p.sout[(size_t)c * td + tid], b);
+        double* acc = p.gacc + ((size_t)c * p.m + k) * 2 * kMaxTheta;
+        acc[tid] += a;
+        acc[kMaxTheta + tid] += b;
+    }
+}
+
+// gout, sout: the islands' running sums of the theta terms, added in island order
+__global__ void __launch_bounds__(256) grad_sum_kernel(StepParams p)
+{
+    __shared__ double red[2 * kMaxTheta][8];
+    const int c = blockIdx.x, td = p.theta_dim, m = p.m;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double a[2 * kMaxTheta];
+#pragma unroll
+    for (int d = 0; d < 2 * kMaxTheta; ++d) a[d] = 0.0;
+    for (int k = tid; k < m; k += blockDim.x) {
+        const double* acc = p.gacc + ((size_t)c * m + k) * 2 * kMaxTheta;
+#pragma unroll
+        for (int d = 0; d < 2 * kMaxTheta; ++d) a[d] += acc[d];
+    }
+#pragma unroll
+    for (int d = 0; d < 2 * kMaxTheta; ++d) {
+        double v = a[d];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[d][warp] = v;
+    }
+    __syncthreads();
+    if (tid < td) {
+        double g = 0.0, sc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            g += red[tid][w];
+            sc += red[kMaxTheta + tid][w];
+        }
+        p.gout[(size_t)c * td + tid] = g;
+        p.sout[(size_t)c * td + tid] = sc;
     }
 }
 
@@ -460,13 +511,12 @@ cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStrea
         for (int o = 0; o < p.dy; ++o)
             for (int cc = 0; cc < p.dx; ++cc) mm.C[o * kMaxDx + cc] = (R)host_md[p.dx * p.dx + o * p.dx + cc];
     }
-    const size_t xbytes = (size_t)p.B * p.dx * p.N * sizeof(R);
+    const size_t xbytes = (size_t)p.B * DX * p.N * sizeof(R);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemsetAsync(p.xh[i], 0, xbytes, stream);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
-        e = cudaMemsetAsync(p.dh[i], 0, sizeof(double) * (size_t)p.B * p.N, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.gout, 0, sizeof(double) * (size_t)p.B * p.theta_dim, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.sout, 0, sizeof(double) * (size_t)p.B * p.theta_dim, stream);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemsetAsync(p.dh[i], 0, sizeof(R) * (size_t)p.B * p.N, stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(p.gacc, 0, sizeof(double) * (size_t)p.B * p.m * 2 * kMaxTheta, stream);
     if (e != cudaSuccess) return e;
     grad_pi_final_kernel<<<p.B, 256, 0, stream>>>(p);
     const size_t smem = sizeof(R) * (size_t)p.M;
@@ -483,6 +533,7 @@ cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStrea
         }
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) grad_sum_kernel<<<p.B, 256, 0, stream>>>(p);
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

@@ -35,6 +35,7 @@ struct StepParams {
     float cdf_scale;              // 2^cdf_bits: fixed-point scale of the FP32-mixed CDF
     int cdf_bits;                 // 31 - ceil(log2 M)
     int G, tpi, ppt;              // islands per CTA, threads per island, particles per thread
+    int lg_tpi;                   // log2 tpi
     int theta_dim;
     uint32_t seed_lo, seed_hi;
     const RunParams* run;
@@ -83,8 +84,9 @@ struct StepParams {
     double* fw;                   // [B][T][m][2]
     double* fsum;                 // [B][T][m][fm_nw][4 dx]
     double* gpi[2];               // [B][m]
-    void* xh[3];                  // [B][dx][N]
-    double* dh[3];                // [B][N]
+    void* xh[3];                  // [B][N][DX] particle adjoints (DX = 8 for the LGSSM, else 1)
+    void* dh[3];                  // [B][N] descendant weights, the pass's precision
+    double* gacc;                 // [B][m][2 kMaxTheta] the islands' running sums of the theta terms
     double* gout;                 // [B][theta_dim] adjoint gradient
     double* sout;                 // [B][theta_dim] Fisher score
     void* X[2];                   // particle stores, ping-pong by t & 1

@@ -171,6 +171,7 @@ extern "C" airpf_status airpf_run_static(const airpf_config* cfg, const double* 
     if (!cta) airpf::choose_mapping(cfg->m, cfg->M, p.fp64, 0, 0, &p.tpi, &p.ppt, &p.G);
     p.P = cfg->m / p.G;
     while ((1 << p.g) < p.G) ++p.g;
+    while ((1 << p.lg_tpi) < p.tpi) ++p.lg_tpi;
     if (airpf::step_smem_bytes(p) > 227 * 1024) {
         airpf::set_create_error("airpf_run_static: a step needs %zu bytes of shared memory (%d CTAs per filter), "
                                 "above 227 KB; use a context with AIRPF_LAUNCH_STEPS_SPLIT",

@@ -99,7 +99,6 @@ constexpr int kCachedChunks = 2;      // record chunks a lane keeps in registers
 constexpr int kQw = 16;               // per-warp partial slots (one per tree level)
 constexpr int kGroupLog = kTailGroupLog;   // split steps: CTA records per group of the tail cascade
 constexpr int kGroupQ = 16;           // a group record's sums of squares (levels 0 .. g+gs-1)
-constexpr int kGroupThreads = 128;    // the group cascade kernel's CTA (one thread per record)
 using u64 = unsigned long long;
 
 template <typename R> struct CdfType;
@@ -121,24 +120,18 @@ struct Layout {
 // partial sums [16 warps][kQw], per-level sums [kMaxStages], a few integers
 __host__ __device__ inline size_t cascade_slots(const StepParams& p)
 {
-    return (p.split ? 0 : 2 * (size_t)p.P) + 2 * (size_t)p.G + kMaxWarps * kQw + kMaxStages + 8 + 3 * kMaxWarps;
+    return 2 * (size_t)p.P + 2 * (size_t)p.G + kMaxWarps * kQw + kMaxStages + 8 + 3 * kMaxWarps;
 }
 
-// shared-memory bytes of the split steps' group cascade kernel: tree nodes over the
-// larger of a group's records and the filter's groups, their exponents, reduction slots
-__host__ __device__ inline size_t group_cascade_smem_bytes(const StepParams& p)
-{
-    const size_t n = (size_t)((1 << p.gs) > p.NG ? (1 << p.gs) : p.NG);
-    return align16(sizeof(double) * 2 * n) + align16(sizeof(int) * n)
-           + align16(sizeof(double) * (kMaxWarps * kGroupQ + kMaxStages + kMaxWarps + 4));
-}
 
 __host__ __device__ inline Layout make_layout(const StepParams& p)
 {
     Layout L;
     const size_t rsz = p.fp64 ? 8 : 4;
     const size_t nwi = (size_t)((p.tpi + 31) / 32);           // warps per island
-    const size_t treeb = align16(sizeof(double) * cascade_slots(p));
+    // the cascade region: cascade_all's (fused steps, persistent launches), or the split
+    // steps' top cascade
+    const size_t treeb = p.split ? align16(sizeof(double) * (2 * (size_t)p.G + 16)) : align16(sizeof(double) * cascade_slots(p));
     L.cdf_stride = rsz * (size_t)p.M;                          // double or u32
     L.xs_stride = align16(rsz * (size_t)p.M * p.dx);
     L.red_stride = sizeof(double) * nwi;
@@ -590,8 +583,9 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
     const Qt* pq = reinterpret_cast<const Qt*>(p.pq[tp & 1]) + (size_t)c * P * 8;
     // the upper tree [2P]: in shared memory, or (split steps) in global memory,
     // where the next step's island kernels read it
-    const int uo = p.split ? 0 : 2 * P;
-    V* ut = p.split ? reinterpret_cast<V*>(p.utg) + (size_t)c * 2 * P : reinterpret_cast<V*>(raw);
+    // (split steps run their cascade as group_cascade + top_cascade instead)
+    const int uo = 2 * P;
+    V* ut = reinterpret_cast<V*>(raw);
     Qt* Qw = reinterpret_cast<Qt*>(raw + uo + 2 * G);             // [nw][kQw]
     Qt* Q = reinterpret_cast<Qt*>(raw + uo + 2 * G + kMaxWarps * kQw);   // [kMaxStages]
     int* iscal = reinterpret_cast<int*>(raw + uo + 2 * G + kMaxWarps * kQw + kMaxStages);
@@ -723,7 +717,7 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
                 p.csum[(size_t)c * 4 + 0] = 1;
                 p.csum[(size_t)c * 4 + 1] = emax;
             }
-            if (g == 0 && !p.split) {     // level 0 lies above the CTAs: the rescaled record tops
+            if (g == 0) {     // level 0 lies above the CTAs: the rescaled record tops
                 for (int j = tid; j < P; j += nthr) {
                     const int e = __ldcg(&pe[j]);
                     const V top = __ldcg(&pt[(size_t)j * 2 * G]);
@@ -896,7 +890,6 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
         p.csum[(size_t)c * 4 + 0] = ss;
         p.csum[(size_t)c * 4 + 1] = emax;
     }
-    if (p.split) return;          // the next step's CTAs read the tree in global memory
     if (lvl >= g) {
         const int n = P >> (lvl - g);
         for (int b = tid; b < n; b += nthr)
@@ -1006,169 +999,236 @@ __device__ __forceinline__ void block_sum_slots(const Qt (&part)[kGroupQ], int n
     __syncthreads();
 }
 
-// Split steps: the cascade of step tp is a kernel of NG x B CTAs.  The P CTA
-// records of a filter form NG groups of GS = 2^gs consecutive records; CTA grp
-// reduces group grp to a group record: the largest exponent ge over its
-// records, the block-sum subtree of levels g .. g+gs over its record tops
-// (rescaled to 2^ge), and the sums of squares of levels 0 .. g+gs-1 in that
-// scale.  The last CTA of the filter to finish its group (a ticket counter)
-// runs the top of the cascade over the NG group records: the largest exponent
-// emax, the tree above the groups (levels g+gs .. S, in the 2^emax scale),
-// every level's sum of squares, s*, the run's records and the summary (s*,
-// emax) for step tp+1.  Group records are double-buffered by step like the CTA
-// records.  The ticket wraps to zero by itself (atomicInc) and the prologue
-// clears it.  Publication: every thread's stores, a CTA barrier, then one
-// thread's device-scope fence and ticket; the last arrival fences before it
-// reads.  (A version that ran this reduction in the tail of the island kernel,
-// with a ticket per group of island CTAs, was slower: the device-scope fence
-// before every island CTA's ticket held that CTA's slot about a microsecond,
-// over some 27 waves of CTAs per step.)
+// A block-sum tree over n = 2^ln leaves held one per thread (thread i holds leaf i;
+// blockDim >= n, a multiple of 32): levels 0 .. ln into nd (tree_off(n, l)
+// layout), and the sums of squares of the nodes of levels 0 .. ln-1 into
+// Q[q0 + l].  Warp shuffles for the levels inside a warp, warp 0 above them.
+template <bool FX>
+__device__ void leaf_tree(typename Casc<FX>::V v, int ln, typename Casc<FX>::V* nd, typename Casc<FX>::Qt* qw,
+                          typename Casc<FX>::Qt* Q, int q0)
+{
+    using C = Casc<FX>;
+    using V = typename C::V;
+    using Qt = typename C::Qt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int n = 1 << ln;
+    const bool has = tid < n;
+    auto wsum = [&](Qt x, int l) {
+        x = warp_sum(x);
+        if (lane == 0) qw[warp * kGroupQ + l] = x;
+    };
+    if (has) nd[tid] = v;
+    if (ln > 0) {
+        const Qt x = has ? C::qv(v) : (Qt)0;
+        wsum(x * x, 0);
+    }
+#pragma unroll
+    for (int u = 1; u <= kShuffleLevels; ++u) {
+        if (u <= ln) {
+            v += __shfl_down_sync(0xffffffffu, v, 1 << (u - 1));
+            const bool node = (lane & ((1 << u) - 1)) == 0 && has;
+            if (node) nd[tree_off(n, u) + (tid >> u)] = v;
+            if (u < ln) {
+                const Qt x = node ? C::qv(v) : (Qt)0;
+                wsum(x * x, u);
+            }
+        }
+    }
+    __syncthreads();
+    // the warps' sums cover levels 0 .. min(ln-1, 5)
+    if (tid < (ln < kShuffleLevels + 1 ? ln : kShuffleLevels + 1)) {
+        Qt acc = (Qt)0;
+        for (int w = 0; w < nw; ++w) acc += qw[w * kGroupQ + tid];
+        Q[q0 + tid] = acc;
+    }
+    // levels above a warp: warp 0 over the (at most 32) nodes of level 5
+    if (ln > kShuffleLevels && warp == 0) {
+        const int nt = n >> kShuffleLevels;
+        V w = lane < nt ? nd[tree_off(n, kShuffleLevels) + lane] : (V)0;
+        for (int u = kShuffleLevels + 1; u <= ln; ++u) {
+            const int du = u - kShuffleLevels;
+            w += __shfl_down_sync(0xffffffffu, w, 1 << (du - 1));
+            const bool node = (lane & ((1 << du) - 1)) == 0 && lane < nt;
+            if (node) nd[tree_off(n, u) + (lane >> du)] = w;
+            if (u < ln) {
+                const Qt x = node ? C::qv(w) : (Qt)0;
+                const Qt sq = warp_sum(x * x);
+                if (lane == 0) Q[q0 + u] = sq;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Split steps: the cascade of step tp in one kernel of NG x B CTAs.  The P CTA
+// records of a filter form NG groups of GS = 2^gs consecutive records.
+//  (1) group_cascade: CTA grp reduces group grp to a group record -- the largest
+//      exponent ge over its records, the block-sum subtree of levels g .. g+gs over
+//      its record tops (rescaled to 2^ge), and the sums of squares of levels
+//      0 .. g+gs-1 in that scale.
+//  (2) top_cascade, by the filter's last CTA: the largest exponent emax over the
+//      group records and the stage-1 test; when stage 1 interacts, the tree above
+//      the groups (levels g+gs .. S, 2^emax scale) and every level's sum of
+//      squares, s*, and the top tree (utg) for step tp+1; the run's records and the
+//      summary (s*, emax).
+// The island CTAs of step tp+1 then walk their islands' choices through the CTA
+// records, the group records and the top tree.  Group records are double-buffered
+// by step like the CTA records.  (Measured before: one cascade CTA reading all
+// 16384 CTA records of the m = 65536 workload, 21 us a step; the group reduction
+// in the tail of the island kernel behind per-CTA tickets, slower, the device-scope
+// fence before each island CTA's ticket holding that CTA's slot; the top of the
+// cascade in every island CTA, much slower on that workload, where stage 1
+// interacts on a third to a half of the steps and every CTA then built the top
+// tree.)
 template <bool FX>
 __device__ void group_cascade(const StepParams& p, int c, int tp, int grp, unsigned char* sm)
 {
     using C = Casc<FX>;
     using V = typename C::V;
     using Qt = typename C::Qt;
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const int G = p.G, g = p.g, P = p.P, NG = p.NG, gs = p.gs, GS = 1 << gs, S = p.S, m = p.m;
-    const int h = g + gs;                    // level of the group roots
-    const int nmax = GS > NG ? GS : NG;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int G = p.G, g = p.g, P = p.P, NG = p.NG, gs = p.gs, GS = 1 << gs;
+    const int h = g + gs;                    // level of the group root
     const int par = tp & 1;
-    V* nd = reinterpret_cast<V*>(sm);                                             // [2 nmax] tree nodes
-    int* ex = reinterpret_cast<int*>(sm + align16(sizeof(double) * 2 * nmax));    // [nmax] leaf exponents
-    double* rs = reinterpret_cast<double*>(sm + align16(sizeof(double) * 2 * nmax) + align16(sizeof(int) * nmax));
+    V* nd = reinterpret_cast<V*>(sm);                                             // [2 GS] tree nodes
+    double* rs = reinterpret_cast<double*>(sm + align16(sizeof(double) * 2 * GS));
     Qt* qw = reinterpret_cast<Qt*>(rs);                                           // [kMaxWarps][kGroupQ]
     Qt* Q = reinterpret_cast<Qt*>(rs + kMaxWarps * kGroupQ);                      // [kMaxStages]
     int* red = reinterpret_cast<int*>(rs + kMaxWarps * kGroupQ + kMaxStages);     // [kMaxWarps]
-    int* flag = reinterpret_cast<int*>(rs + kMaxWarps * kGroupQ + kMaxStages + kMaxWarps);
-    unsigned* tick = p.tick + c;
+    Qt* qr = reinterpret_cast<Qt*>(rs + kMaxWarps * kGroupQ + kMaxStages + kMaxWarps);   // [kMaxWarps][4]
 
-    // ---- 1. the group record ----
-    {
-        const size_t r0 = (size_t)c * P + (size_t)grp * GS;
-        const int* pe = p.pe[par] + r0;
-        const V* pt = reinterpret_cast<const V*>(p.pt[par]) + r0 * 2 * G;
-        const Qt* pq = reinterpret_cast<const Qt*>(p.pq[par]) + r0 * 8;
-        int em = INT_MIN;
-        for (int i = tid; i < GS; i += nthr) {
-            const int e = __ldcg(&pe[i]);
-            const V top = __ldcg(&pt[(size_t)i * 2 * G + tree_off(G, g)]);
-            const bool ok = pos_v(top) && e != INT_MIN;
-            ex[i] = ok ? e : INT_MIN;
-            nd[i] = top;
-            if (ok && e > em) em = e;
+    // one record a thread: exponent, top, sums of squares of levels < g
+    const size_t r0 = (size_t)c * P + (size_t)grp * GS;
+    const bool has = tid < GS;
+    int e = INT_MIN;
+    V top = (V)0;
+    Qt q[4] = {(Qt)0, (Qt)0, (Qt)0, (Qt)0};
+    if (has) {
+        e = __ldcg(&p.pe[par][r0 + tid]);
+        top = __ldcg(&reinterpret_cast<const V*>(p.pt[par])[(r0 + tid) * 2 * G + tree_off(G, g)]);
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+            if (l < g) q[l] = __ldcg(&reinterpret_cast<const Qt*>(p.pq[par])[(r0 + tid) * 8 + l]);
+    }
+    const bool ok = has && pos_v(top) && e != INT_MIN;
+    const int em = block_max(ok ? e : INT_MIN, red);
+    const int sh = ok ? em - e : 0;
+    // the records' levels below g, rescaled to 2^em
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (l < g) {
+            const Qt x = warp_sum(ok ? C::qscale(q[l], 2 * sh) : (Qt)0);
+            if (lane == 0) qr[warp * 4 + l] = x;
         }
-        em = block_max(em, red);
-        Qt part[kGroupQ];
+    }
+    leaf_tree<FX>(ok ? C::rescale(top, sh) : (V)0, gs, nd, qw, Q, g);
+    if (tid < g) {
+        Qt acc = (Qt)0;
+        for (int w = 0; w < nw; ++w) acc += qr[w * 4 + tid];
+        Q[tid] = acc;
+    }
+    __syncthreads();
+    V* gt = reinterpret_cast<V*>(p.gtr[par]) + ((size_t)c * NG + grp) * 2 * GS;
+    for (int i = tid; i < 2 * GS - 1; i += blockDim.x) gt[i] = nd[i];
+    Qt* gq = reinterpret_cast<Qt*>(p.gqs[par]) + ((size_t)c * NG + grp) * kGroupQ;
+    if (tid < h) gq[tid] = Q[tid];
+    if (tid == 0) p.ge[par][(size_t)c * NG + grp] = em;
+}
+
+// shared-memory bytes of the split steps' cascade kernels (both): a tree over the
+// larger of a group's records and the filter's groups, reduction slots
+__host__ __device__ inline size_t split_cascade_smem_bytes(const StepParams& p)
+{
+    const size_t n = (size_t)((1 << p.gs) > p.NG ? (1 << p.gs) : p.NG);
+    return align16(sizeof(double) * 2 * n)
+           + align16(sizeof(double) * (kMaxWarps * kGroupQ + kMaxStages + kMaxWarps + kMaxWarps * kGroupQ + 4));
+}
+
+template <bool FX>
+__device__ void top_cascade(const StepParams& p, int c, int tp, unsigned char* sm)
+{
+    using C = Casc<FX>;
+    using V = typename C::V;
+    using Qt = typename C::Qt;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int g = p.g, P = p.P, NG = p.NG, gs = p.gs, GS = 1 << gs, S = p.S, m = p.m;
+    const int h = g + gs, par = tp & 1;
+    V* nd = reinterpret_cast<V*>(sm);                                             // [2 NG]
+    double* rs = reinterpret_cast<double*>(sm + align16(sizeof(double) * 2 * NG));
+    Qt* qw = reinterpret_cast<Qt*>(rs);                                           // [kMaxWarps][kGroupQ]
+    Qt* Q = reinterpret_cast<Qt*>(rs + kMaxWarps * kGroupQ);                      // [kMaxStages]
+    int* red = reinterpret_cast<int*>(rs + kMaxWarps * kGroupQ + kMaxStages);     // [kMaxWarps]
+    Qt* qr = reinterpret_cast<Qt*>(rs + kMaxWarps * kGroupQ + kMaxStages + kMaxWarps);   // [kMaxWarps][kGroupQ]
+    // one group record a thread: exponent, root, sums of squares of levels < h
+    const bool has = tid < NG;
+    int e = INT_MIN;
+    V r = (V)0;
+    if (has) {
+        e = __ldcg(&p.ge[par][(size_t)c * NG + tid]);
+        r = __ldcg(&reinterpret_cast<const V*>(p.gtr[par])[((size_t)c * NG + tid) * 2 * GS + tree_off(GS, gs)]);
+    }
+    // the group's sums of squares of levels < h, loaded with the rest (one round trip)
+    const Qt* gq = reinterpret_cast<const Qt*>(p.gqs[par]) + ((size_t)c * NG + (has ? tid : 0)) * kGroupQ;
+    Qt qg[kGroupQ];
 #pragma unroll
-        for (int l = 0; l < kGroupQ; ++l) part[l] = (Qt)0;
-        for (int i = tid; i < GS; i += nthr) {
-            const int e = ex[i];
-            V v = (V)0;
-            if (e != INT_MIN) {
-                const int sh = em - e;
-                v = C::rescale(nd[i], sh);
-#pragma unroll
-                for (int l = 0; l < 4; ++l)
-                    if (l < g) part[l] += C::qscale(__ldcg(&pq[(size_t)i * 8 + l]), 2 * sh);
-            }
-            nd[i] = v;
-            const Qt q = C::qv(v);
-#pragma unroll
-            for (int l = 0; l < kGroupQ; ++l)
-                if (l == g) part[l] += q * q;    // level g: the leaves
-        }
-        // the subtree of levels g+1 .. g+gs
-#pragma unroll
-        for (int u = 1; u <= kGroupLog; ++u) {
-            if (u <= gs) {
-                __syncthreads();
-                const int cnt = GS >> u, o0 = tree_off(GS, u - 1), o1 = tree_off(GS, u);
-                for (int i = tid; i < cnt; i += nthr) {
-                    const V v = nd[o0 + 2 * i] + nd[o0 + 2 * i + 1];
-                    nd[o1 + i] = v;
-                    const Qt q = C::qv(v);
-#pragma unroll
-                    for (int l = 1; l < kGroupQ; ++l)
-                        if (l == g + u && u < gs) part[l] += q * q;
-                }
-            }
+    for (int l = 0; l < kGroupQ; ++l) qg[l] = (has && l < h) ? __ldcg(&gq[l]) : (Qt)0;
+    const bool ok = has && pos_v(r) && e != INT_MIN;
+    const int emax = block_max(ok ? e : INT_MIN, red);
+    const int sh = ok ? emax - e : 0;
+    const V leaf = ok ? C::rescale(r, sh) : (V)0;
+    // stage 1 first: it needs only the total and level 0's sum of squares (ENF_1 =
+    // Tot^2 / (m Q_0)); when it does not interact (always under NEVER, and on most
+    // adaptive steps) s* = 1, the islands keep their blocks and no tree is needed
+    if (p.mode != 1) {
+        V* vred = reinterpret_cast<V*>(qr);                 // [kMaxWarps] (qr is free until below)
+        const V ts = warp_sum(leaf);
+        const Qt q0s = warp_sum(ok ? C::qscale(qg[0], 2 * sh) : (Qt)0);
+        if (lane == 0) {
+            vred[warp] = ts;
+            qw[warp] = q0s;
         }
         __syncthreads();
-        block_sum_slots<Qt>(part, h, qw, Q);
-        V* gt = reinterpret_cast<V*>(p.gtr[par]) + ((size_t)c * NG + grp) * 2 * GS;
-        for (int i = tid; i < 2 * GS - 1; i += nthr) gt[i] = nd[i];
-        Qt* gq = reinterpret_cast<Qt*>(p.gqs[par]) + ((size_t)c * NG + grp) * kGroupQ;
-        if (tid < h) gq[tid] = Q[tid];
-        if (tid == 0) p.ge[par][(size_t)c * NG + grp] = em;
-    }
-
-    // ---- 2. the filter's ticket ----
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        flag[0] = atomicInc(&tick[0], (unsigned)(NG - 1)) == (unsigned)(NG - 1);
-    }
-    __syncthreads();
-    if (!flag[0]) return;
-    __threadfence();
-
-    // ---- 3. the top of the cascade ----
-    const int* ge = p.ge[par] + (size_t)c * NG;
-    const V* gt = reinterpret_cast<const V*>(p.gtr[par]) + (size_t)c * NG * 2 * GS;
-    const Qt* gq = reinterpret_cast<const Qt*>(p.gqs[par]) + (size_t)c * NG * kGroupQ;
-    int emax = INT_MIN;
-    for (int i = tid; i < NG; i += nthr) {
-        const int e = __ldcg(&ge[i]);
-        const V r = __ldcg(&gt[(size_t)i * 2 * GS + tree_off(GS, gs)]);
-        const bool ok = pos_v(r) && e != INT_MIN;
-        ex[i] = ok ? e : INT_MIN;
-        nd[i] = r;
-        if (ok && e > emax) emax = e;
-    }
-    emax = block_max(emax, red);
-    Qt part[kGroupQ];
-#pragma unroll
-    for (int l = 0; l < kGroupQ; ++l) part[l] = (Qt)0;
-    const int ngl = S - h;                   // log2 NG
-    for (int i = tid; i < NG; i += nthr) {
-        const int e = ex[i];
-        V v = (V)0;
-        if (e != INT_MIN) {
-            const int sh = emax - e;
-            v = C::rescale(nd[i], sh);
-#pragma unroll
-            for (int l = 0; l < kGroupQ; ++l)
-                if (l < h) part[l] += C::qscale(__ldcg(&gq[(size_t)i * kGroupQ + l]), 2 * sh);
+        V tot = (V)0;
+        Qt q0 = (Qt)0;
+        for (int w = 0; w < nw; ++w) {
+            tot += vred[w];
+            q0 += qw[w];
         }
-        nd[i] = v;
-        const Qt q = C::qv(v);
-#pragma unroll
-        for (int l = 0; l < kGroupQ; ++l)
-            if (l == h && h < S) part[l] += q * q;
+        const Qt tq = C::qv(tot);
+        const bool quiet1 = p.mode == 0 || (pos_v(tot) && !(tq * tq < C::tau(p) * (Qt)m * q0));
+        if (quiet1) {
+            if (tid == 0) {
+                Q[0] = q0;
+                cascade_records<FX>(p, c, tp, 1, tot, emax, Q);
+                p.csum[(size_t)c * 4 + 0] = 1;
+                p.csum[(size_t)c * 4 + 1] = emax;
+            }
+            return;
+        }
+        __syncthreads();                                    // vred, qw reused below
     }
-    for (int u = 1; u <= ngl; ++u) {
-        __syncthreads();
-        const int cnt = NG >> u, o0 = tree_off(NG, u - 1), o1 = tree_off(NG, u);
-        for (int i = tid; i < cnt; i += nthr) {
-            const V v = nd[o0 + 2 * i] + nd[o0 + 2 * i + 1];
-            nd[o1 + i] = v;
-            const Qt q = C::qv(v);
 #pragma unroll
-            for (int l = 0; l < kGroupQ; ++l)
-                if (l == h + u && l < S) part[l] += q * q;
+    for (int l = 0; l < kGroupQ; ++l) {
+        if (l < h) {
+            const Qt x = warp_sum(ok ? C::qscale(qg[l], 2 * sh) : (Qt)0);
+            if (lane == 0) qr[warp * kGroupQ + l] = x;
         }
     }
+    leaf_tree<FX>(leaf, S - h, nd, qw, Q, h);
+    if (tid < h) {
+        Qt acc = (Qt)0;
+        for (int w = 0; w < nw; ++w) acc += qr[w * kGroupQ + tid];
+        Q[tid] = acc;
+    }
     __syncthreads();
-    block_sum_slots<Qt>(part, S, qw, Q);
-    const V tot = nd[tree_off(NG, ngl)];
+    const V tot = nd[tree_off(NG, S - h)];
     if (warp == 0) {
         const Qt tq = C::qv(tot);
         bool quiet = false;
         if (lane < S) {
             const int s = lane + 1;
-            // as in cascade_all: stage s interacts iff ENF_s < tau; with radix 2^rb only the
-            // first binary stage of each group decides
+            // stage s interacts iff ENF_s < tau; with radix 2^rb only the first binary
+            // stage of each group of rb decides
             quiet = (s - 1) % p.rb == 0 && pos_v(tot) &&
                     !(tq * tq * (Qt)(1u << (s - 1)) < C::tau(p) * (Qt)m * Q[s - 1]);
         }
@@ -1181,7 +1241,7 @@ __device__ void group_cascade(const StepParams& p, int c, int tp, int grp, unsig
         }
     }
     V* ut = reinterpret_cast<V*>(p.utg) + (size_t)c * 2 * P;
-    for (int i = tid; i < 2 * NG - 1; i += nthr) ut[i] = nd[i];
+    for (int i = tid; i < 2 * NG - 1; i += blockDim.x) ut[i] = nd[i];
 }
 
 enum { OP_STEP = 0, OP_PREPARE = 1, OP_FITS = 2, OP_PERSIST_GRID = 3, OP_PERSIST_CTA = 4, OP_CASCADE = 5,
@@ -1210,7 +1270,7 @@ __global__ void airpf_prologue_kernel(StepParams p)
         reinterpret_cast<ModelPar<R>*>(p.mpar)[i] = mp;
     }
     if (MODEL == NGM && i < p.T) reinterpret_cast<R*>(p.drift)[i] = (R)(8.0 * cos(1.2 * (double)(i + 1)));
-    if (p.split && i < p.B) p.tick[i] = 0u;       // the group cascade's tickets
+    if (p.split && i < p.B) p.tick[i] = 0u;       // the split cascade's tickets
 }
 
 // ---------------------------------------------------------------------------
@@ -1227,7 +1287,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     constexpr bool FX = sizeof(R) == 4;
     const int tid = threadIdx.x;
     const int N = p.N, M = p.M, dx = p.dx;
-    const int jo = k0 / p.G;
+    const int jo = k0 >> p.g;                  // G, tpi and m/G are powers of 2: shifts, not divisions
     const Layout L = make_layout(p);
     double* tree = reinterpret_cast<double*>(smem + L.tree);
     u64* own_w = reinterpret_cast<u64*>(smem + L.small);
@@ -1245,7 +1305,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     // ---- 1. before any dependency: the step's noise (and at t = 1 the prior
     //      draw), from the run parameters and model constants only, which the
     //      kernels of this pass never write ----
-    const int g = tid / p.tpi, li = tid - g * p.tpi;
+    const int g = tid >> p.lg_tpi, li = tid & (p.tpi - 1);
     const int lane = tid & 31, wi = li >> 5;   // warp index within the island
     const int k = k0 + g;
     const R* Xp = reinterpret_cast<const R*>(p.X[(t - 1) & 1]);
@@ -1340,7 +1400,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         const CascadeOwn own{k0, own_w, own_we, own_src};
         cascade_all<FX, true>(p, c, t - 1, st, tree, &own, designated);
     } else if (LV == 2 || (LV == 0 && p.split)) {
-        // the group cascade of step t-1 left s*, the largest exponent, the group
+        // the cascade kernels of step t-1 left s*, the largest exponent, the group
         // records and the top tree; this CTA derives its islands' weights and walks
         int* csum_sh = reinterpret_cast<int*>(scal) + 4;
         if (tid < 2) csum_sh[tid] = __ldcg(&p.csum[(size_t)c * 4 + tid]);
@@ -1518,6 +1578,20 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     constexpr int kRowShift = sizeof(Cdf) == 4 ? 5 : 4;
     const int rowmask = (M & ((1 << kRowShift) - 1)) == 0 ? (1 << kRowShift) - 1 : 0;
     auto cdf_ix = [rowmask](int i) { return i ^ ((i >> kRowShift) & rowmask); };
+    // Islands of M = 2^k particles keep the CDF as a search tree in breadth-first
+    // (Eytzinger) order instead: C_j (j < M-1) at node (r >> (z+1)) + 2^(k-1-z) of the
+    // complete tree over the M-1 boundaries, r = j+1 its in-order rank and z = ctz(r),
+    // and the total C_{M-1} at node 0.  The search then walks node -> 2 node + [C <= u],
+    // one shared-memory load, compare and index update per level, and the answer
+    // (the number of boundaries at or below u) is the first i with C_i > u.  The probes
+    // of one level lie in 2^l consecutive words, so the shallow levels need no swizzle.
+    const bool eyt = M >= 2 && (M & (M - 1)) == 0;
+    const int lgM = 31 - __clz(M);
+    auto eyt_ix = [lgM, M](int j) {
+        if (j == M - 1) return 0;
+        const int r = j + 1, z = __ffs(r) - 1;
+        return (r >> (z + 1)) + (1 << (lgM - 1 - z));
+    };
 
     // weights and the thread-local inclusive prefix
     Cdf part[PPT];
@@ -1554,7 +1628,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     for (int r = 0; r < PPT; ++r) {
         const int i = li * PPT + r;
         if (i < M) {
-            cdf[cdf_ix(i)] = excl + part[r];
+            cdf[eyt ? eyt_ix(i) : cdf_ix(i)] = excl + part[r];
 #pragma unroll
             for (int d = 0; d < DX; ++d)
                 if (d < dx) xs[(size_t)d * M + i] = xv[r][d];
@@ -1562,7 +1636,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     }
     if (nwi > 1) named_sync(1 + g, p.tpi);    // an island of one warp needs only the warp
     else __syncwarp();
-    const Cdf total = cdf[cdf_ix(M - 1)];
+    const Cdf total = cdf[eyt ? 0 : cdf_ix(M - 1)];
 
     // multinomial draws: ancestor of draw j = first i with C_i > u_j C_{M-1}.
     // Fixed-depth branchless lower bound, the thread's draws advanced together.
@@ -1578,7 +1652,29 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     // adaptive internal resampling: the island resamples only when the ESS of its
     // weights, total^2 / sum w^2, is below tau_int M (the same for every thread of it)
     const bool resample = !(air && alive) || ((double)total * (double)total / sq < p.tau_int * (double)M);
-    if (resample) {
+    if (resample && eyt) {
+        int node[PPT];
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) node[r] = 1;
+        if constexpr (!FX) {
+            // FP64: non-negative doubles compared as their bit patterns (integer pipe)
+            const long long* cdfb = reinterpret_cast<const long long*>(cdf);
+            long long tb[PPT];
+#pragma unroll
+            for (int r = 0; r < PPT; ++r) tb[r] = __double_as_longlong(target[r]);
+            for (int l = 0; l < lgM; ++l) {
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) node[r] = 2 * node[r] + (cdfb[node[r]] <= tb[r] ? 1 : 0);
+            }
+        } else {
+            for (int l = 0; l < lgM; ++l) {
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) node[r] = 2 * node[r] + (cdf[node[r]] <= target[r] ? 1 : 0);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) base[r] = node[r] - M;
+    } else if (resample) {
         if constexpr (!FX) {
             // FP64: the CDF and the targets are non-negative doubles, whose order is the
             // order of their bit patterns as 64-bit integers: the same decisions, compared
@@ -1788,8 +1884,8 @@ template <typename R, int MODEL, int DX, int PPT, bool REC, int LV>
 __global__ void __launch_bounds__(kMaxThreads, LV == 3 ? 1 : kMinCtasPerSm) airpf_step_kernel(StepParams p, int t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int cpf = p.m / p.G;                 // CTAs per filter
-    const int c = blockIdx.x / cpf;
+    const int cpf = p.P;                       // CTAs per filter (a power of 2)
+    const int c = blockIdx.x >> (p.S - p.g);
     const int k0 = (blockIdx.x - c * cpf) * p.G;
     if (p.active != nullptr && p.active[c] == 0) return;   // uniform over the CTA
     step_body<R, MODEL, DX, PPT, REC, LV>(p, t, c, k0, smem, p.pdl != 0);
@@ -1811,18 +1907,32 @@ __global__ void __launch_bounds__(kCascadeThreads) airpf_cascade_kernel(StepPara
     cascade_all<sizeof(R) == 4>(p, c, t, st, reinterpret_cast<double*>(smem));
 }
 
-// The cascade of step t for split steps: CTA j handles group j mod NG of filter j / NG.
+// The split steps' cascade of step t: CTA j reduces group j mod NG of filter
+// j / NG; the last of a filter's CTAs to finish its group (a ticket) runs the top.
+// Publication: every thread's stores, a CTA barrier, one thread's device-scope fence
+// and ticket; the last arrival fences before it reads.  The ticket wraps to zero by
+// itself (atomicInc) and the prologue clears it.
 template <typename R>
-__global__ void __launch_bounds__(kGroupThreads) airpf_group_cascade_kernel(StepParams p, int t)
+__global__ void __launch_bounds__(512) airpf_group_cascade_kernel(StepParams p, int t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int c = blockIdx.x / p.NG, grp = blockIdx.x - c * p.NG;
+    __shared__ int last;
+    const int c = blockIdx.x >> (p.S - p.g - p.gs), grp = blockIdx.x & (p.NG - 1);
     if (p.active != nullptr && p.active[c] == 0) return;
     if (p.pdl) {                  // the records are the island-step kernel's output
         dependency_wait();
         allow_dependents();
     }
     group_cascade<sizeof(R) == 4>(p, c, t, grp, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicInc(&p.tick[c], (unsigned)(p.NG - 1)) == (unsigned)(p.NG - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    top_cascade<sizeof(R) == 4>(p, c, t, smem);
 }
 
 // All T+1 steps in one launch.  GRID: the filter spans several co-resident CTAs
@@ -1834,8 +1944,8 @@ template <typename R, int MODEL, int DX, int PPT, bool GRID>
 __global__ void __launch_bounds__(GRID ? kMaxThreads : kMaxCtaThreads, kMinCtasPerSm) airpf_persistent_kernel(StepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int cpf = p.m / p.G;
-    const int c = blockIdx.x / cpf;
+    const int cpf = p.P;
+    const int c = blockIdx.x >> (p.S - p.g);
     const int k0 = (blockIdx.x - c * cpf) * p.G;
     const bool act = (p.active == nullptr || p.active[c] != 0);
     if (!GRID && !act) return;
@@ -1905,8 +2015,9 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        // (split steps use the group cascade kernel, whose shared memory stays small)
         const size_t cs = cascade_smem_bytes(p);
-        if (e == cudaSuccess && cs > 48 * 1024)
+        if (e == cudaSuccess && !p.split && cs > 48 * 1024)
             e = cudaFuncSetAttribute(airpf_cascade_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs);
         return e;
     }
@@ -1942,10 +2053,12 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         return cudaGetLastError();
     }
     if (op == OP_CASCADE && p.split) {
-        const size_t cs = group_cascade_smem_bytes(p);
-        if (p.pdl) return launch_dependent(airpf_group_cascade_kernel<R>, dim3(p.NG * p.B), dim3(kGroupThreads), cs,
-                                           stream, p, t);
-        airpf_group_cascade_kernel<R><<<p.NG * p.B, kGroupThreads, cs, stream>>>(p, t);
+        // CTAs of max(32, GS, NG) threads: one record a thread in both parts
+        const size_t cs = split_cascade_smem_bytes(p);
+        int tg = (1 << p.gs) > p.NG ? (1 << p.gs) : p.NG;
+        if (tg < 32) tg = 32;
+        if (p.pdl) return launch_dependent(airpf_group_cascade_kernel<R>, dim3(p.NG * p.B), dim3(tg), cs, stream, p, t);
+        airpf_group_cascade_kernel<R><<<p.NG * p.B, tg, cs, stream>>>(p, t);
         return cudaGetLastError();
     }
     if (op == OP_CASCADE) {
