@@ -226,17 +226,14 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
 {
     extern __shared__ __align__(16) unsigned char gsm[];
     __shared__ R yv[kMaxDy];
-    __shared__ double red[2 * kMaxTheta][kGradThreads / 32];
+    __shared__ R tsum[2 * kMaxTheta][kGradThreads + 1];   // the threads' theta terms, a row per term
+    __shared__ R tpart[kGradThreads];
     __shared__ R rmx[kGradThreads / 32];
     __shared__ R rsum[kGradThreads / 32];
     R* lsm = reinterpret_cast<R*>(gsm);                  // [M] log-weights of the island
     const int c = blockIdx.y, k = blockIdx.x;
     const int M = p.M, N = p.N, dx = p.dx, dy = p.dy, td = p.theta_dim;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int o = tid; o < dy; o += blockDim.x) yv[o] = (R)p.y[(size_t)(t - 1) * dy + o];
-    __syncthreads();
-    ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
-    if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
     const R* xt = xstate<R>(p, c, t);
     const R* xprev = xstate<R>(p, c, t - 1);
     // particle adjoints x^ [N][DX] (a particle's components together: vector atomics
@@ -247,6 +244,33 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     R* xh_out = reinterpret_cast<R*>(p.xh[(t + 2) % 3]) + xo;
     R* dh_in = reinterpret_cast<R*>(p.dh[t % 3]) + (size_t)c * N;
     R* dh_out = reinterpret_cast<R*>(p.dh[(t + 2) % 3]) + (size_t)c * N;
+    // the thread's first particle (the only one when M <= blockDim): its state, parent,
+    // parent state, adjoint and descendant weight are loaded first, so that these loads
+    // (two dependent rounds) are in flight during the island's softmax
+    const bool pre = tid < M;
+    const int g0 = k * M + tid;
+    int par0 = 0;
+    R x0[DX], xp0[DX], xh0[DX], dh0 = (R)0;
+#pragma unroll
+    for (int d = 0; d < DX; ++d) x0[d] = xp0[d] = xh0[d] = (R)0;
+    if (pre) {
+        par0 = parent_of(p, c, t, g0);
+#pragma unroll
+        for (int d = 0; d < DX; ++d) {
+            if (d < dx) {
+                x0[d] = xt[(size_t)d * N + g0];
+                xh0[d] = xh_in[(size_t)g0 * DX + d];
+            }
+        }
+        if (t < p.T) dh0 = dh_in[g0];
+#pragma unroll
+        for (int d = 0; d < DX; ++d)
+            if (d < dx) xp0[d] = xprev[(size_t)d * N + par0];
+    }
+    for (int o = tid; o < dy; o += blockDim.x) yv[o] = (R)p.y[(size_t)(t - 1) * dy + o];
+    __syncthreads();
+    ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
+    if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
     const R pik_r = (R)p.gpi[t & 1][(size_t)c * p.m + k];
 
     // island softmax of the log-weights
@@ -255,7 +279,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
         const int g = k * M + i;
         R x[DX];
 #pragma unroll
-        for (int d = 0; d < DX; ++d) x[d] = (d < dx) ? xt[(size_t)d * N + g] : (R)0;
+        for (int d = 0; d < DX; ++d) x[d] = (d < dx) ? (i == tid ? x0[d] : xt[(size_t)d * N + g]) : (R)0;
         const R l = logg_mm<R, MODEL, DX>(mp, yv, dx, dy, x, mm);
         lsm[i] = l;
         mx = l > mx ? l : mx;
@@ -290,19 +314,20 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
         const int g = k * M + i;
         const R wi = (lsm[i] > (R)(-INFINITY)) ? exp(lsm[i] - mx) * inv_sum : (R)0;
         const R lhat = pik_r * wi;                                   // d log Z / d l_t(k,i)
-        const R delta = (t == p.T) ? lhat : dh_in[g];                // descendant weight
-        const int par = parent_of(p, c, t, g);
+        const bool first = (i == tid);
+        const R delta = (t == p.T) ? lhat : (first ? dh0 : dh_in[g]);   // descendant weight
+        const int par = first ? par0 : parent_of(p, c, t, g);
         R x[DX], xp[DX], mu[DX];
         R s;
 #pragma unroll
         for (int d = 0; d < DX; ++d) {
-            x[d] = (d < dx) ? xt[(size_t)d * N + g] : (R)0;
-            xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
+            x[d] = (d < dx) ? (first ? x0[d] : xt[(size_t)d * N + g]) : (R)0;
+            xp[d] = (d < dx) ? (first ? xp0[d] : xprev[(size_t)d * N + par]) : (R)0;
         }
         transition_mean<R, MODEL, DX>(mp, dx, xp, mm, mu, s);
         R xhat[DX], v[DX];
 #pragma unroll
-        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? xh_in[(size_t)g * DX + d] : (R)0;
+        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? (first ? xh0[d] : xh_in[(size_t)g * DX + d]) : (R)0;
         if (MODEL == AR1) {
             const R a = mp.th[0], sv = mp.th[1], sw = mp.th[2], s0 = mp.th[3];
             const R e = yv[0] - x[0];
@@ -437,34 +462,39 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
             if (d < dx) xh_in[(size_t)g * DX + d] = (R)0;
         dh_in[g] = (R)0;
     }
-    // the CTA's theta sums
+    // the CTA's theta sums, in the pass's precision and a fixed order: every thread's
+    // 2 td values into shared memory (a row per term), segments of each row summed by
+    // the threads, then the segments; the island's running sums over the steps in double
+    // (this CTA alone updates row k of gacc: no atomics; the final sum over the islands
+    // runs in island order)
+    const int nt = 2 * td;
 #pragma unroll
     for (int d = 0; d < kMaxTheta; ++d) {
         if (d < td) {
-            R a = ga[d], b = gs[d];          // warp sums in R, then double from the warp on
-            for (int o = 16; o > 0; o >>= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-                b += __shfl_xor_sync(0xffffffffu, b, o);
-            }
-            if (lane == 0) {
-                red[d][warp] = (double)a;
-                red[kMaxTheta + d][warp] = (double)b;
-            }
+            tsum[d][tid] = ga[d];
+            tsum[td + d][tid] = gs[d];
         }
     }
     __syncthreads();
-    // the island's running sums over the steps (this CTA alone updates row k: no atomics,
-    // and the final sum over the islands runs in a fixed order)
-    if (tid < td) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < nw; ++w) {
-            a += red[tid][w];
-            b += red[kMaxTheta + tid][w];
-        }
-        double* acc = p.gacc + ((size_t)c * p.m + k) * 2 * kMaxTheta;
-        acc[tid] += a;
-        acc[kMaxTheta + tid] += b;
+    const int nseg = blockDim.x / nt;              // segments per term (at least 1: nt <= 20 < 128)
+    const int seglen = (blockDim.x + nseg - 1) / nseg;
+    if (tid < nt * nseg) {
+        const int r = tid % nt, sg = tid / nt;
+        const int a0 = sg * seglen, a1 = a0 + seglen < (int)blockDim.x ? a0 + seglen : (int)blockDim.x;
+        R acc = (R)0;
+        for (int q = a0; q < a1; ++q) acc += tsum[r][q];
+        tpart[tid] = acc;
     }
+    __syncthreads();
+    if (tid < nt) {
+        R acc = (R)0;
+        for (int sg = 0; sg < nseg; ++sg) acc += tpart[sg * nt + tid];
+        double* gacc = p.gacc + ((size_t)c * p.m + k) * 2 * kMaxTheta;
+        const int slot = tid < td ? tid : kMaxTheta + tid - td;
+        gacc[slot] += (double)acc;
+    }
+    (void)lane;
+    (void)warp;
 }
 
 // gout, sout: the islands' running sums of the theta terms, added in island order
