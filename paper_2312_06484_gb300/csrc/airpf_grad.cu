@@ -165,30 +165,6 @@ __global__ void __launch_bounds__(256) grad_pi_final_kernel(StepParams p)
         pi[k] = (sum > 0.0 && lw[k] > -INFINITY) ? exp(lw[k] - mx) / sum : 0.0;
 }
 
-// pi_{t-1} from pi_t: the blocks of r^(s*_{t-1} - 1) = 2^lvl islands (r = 2^rb the
-// radix) redistribute their pi_t mass in proportion to W_{t-1,1}; one thread per block
-__global__ void __launch_bounds__(256) grad_pi_step_kernel(StepParams p, int t)
-{
-    const int c = blockIdx.y, m = p.m;
-    const int lvl = (p.sstar[(size_t)c * p.T + (t - 2)] - 1) * p.rb;
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= (m >> lvl)) return;
-    const int j0 = b << lvl, n = 1 << lvl;
-    const double* lw = p.logw + ((size_t)c * p.T + (t - 2)) * m;
-    const double* pin = p.gpi[t & 1] + (size_t)c * m;
-    double* pout = p.gpi[(t - 1) & 1] + (size_t)c * m;
-    double mx = -INFINITY, mass = 0.0;
-    for (int j = j0; j < j0 + n; ++j) {
-        mx = fmax(mx, lw[j]);
-        mass += pin[j];
-    }
-    double sw = 0.0;
-    if (mx > -INFINITY)
-        for (int j = j0; j < j0 + n; ++j) sw += exp(lw[j] - mx);
-    for (int j = j0; j < j0 + n; ++j)
-        pout[j] = (sw > 0.0 && lw[j] > -INFINITY) ? exp(lw[j] - mx) / sw * mass : 0.0;
-}
-
 // mean of the transition from the parent, and its scale (z = (x - mean) / scale)
 template <typename R, int MODEL, int DX>
 __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, const R* xp, const ModelMat<R>& mm,
@@ -228,6 +204,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     __shared__ R yv[kMaxDy];
     __shared__ R tsum[2 * kMaxTheta][kGradThreads + 1];   // the threads' theta terms, a row per term
     __shared__ R tpart[kGradThreads];
+    __shared__ double pred[2][kGradThreads / 32];
     __shared__ R rmx[kGradThreads / 32];
     __shared__ R rsum[kGradThreads / 32];
     R* lsm = reinterpret_cast<R*>(gsm);                  // [M] log-weights of the island
@@ -271,7 +248,56 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     __syncthreads();
     ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
     if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
-    const R pik_r = (R)p.gpi[t & 1][(size_t)c * p.m + k];
+    // pi_t(k): at t = T from grad_pi_final_kernel; before, from pi_{t+1} of the block of
+    // r^(s*_t - 1) = 2^lvl islands holding k (r = 2^rb the radix), whose pi_{t+1} mass
+    // the block hands to its members in proportion to W_{t,1} (the averaging of the
+    // interaction stages is linear and symmetric); computed by the island's own CTA and
+    // written for step t-1's CTAs
+    double pik = 0.0;
+    if (t == p.T) {
+        pik = p.gpi[t & 1][(size_t)c * p.m + k];
+    } else {
+        const int lvl = (p.sstar[(size_t)c * p.T + (t - 1)] - 1) * p.rb;
+        const double* pin = p.gpi[(t + 1) & 1] + (size_t)c * p.m;
+        if (lvl == 0) {
+            pik = pin[k];
+        } else {
+            const int n = 1 << lvl, j0 = (k >> lvl) << lvl;
+            const double* lw = p.logw + ((size_t)c * p.T + (t - 1)) * p.m;
+            double lmx = -INFINITY, mass = 0.0;
+            for (int j = j0 + tid; j < j0 + n; j += blockDim.x) {
+                lmx = fmax(lmx, lw[j]);
+                mass += pin[j];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                lmx = fmax(lmx, __shfl_xor_sync(0xffffffffu, lmx, o));
+                mass += __shfl_xor_sync(0xffffffffu, mass, o);
+            }
+            if (lane == 0) {
+                pred[0][warp] = lmx;
+                pred[1][warp] = mass;
+            }
+            __syncthreads();
+            lmx = pred[0][0];
+            mass = pred[1][0];
+            for (int w = 1; w < nw; ++w) {
+                lmx = fmax(lmx, pred[0][w]);
+                mass += pred[1][w];
+            }
+            double sw = 0.0;
+            if (lmx > -INFINITY)
+                for (int j = j0 + tid; j < j0 + n; j += blockDim.x) sw += exp(lw[j] - lmx);
+            for (int o = 16; o > 0; o >>= 1) sw += __shfl_xor_sync(0xffffffffu, sw, o);
+            __syncthreads();                              // pred read above
+            if (lane == 0) pred[0][warp] = sw;
+            __syncthreads();
+            sw = 0.0;
+            for (int w = 0; w < nw; ++w) sw += pred[0][w];
+            pik = (sw > 0.0 && lw[k] > -INFINITY) ? exp(lw[k] - lmx) / sw * mass : 0.0;
+        }
+        if (tid == 0) p.gpi[t & 1][(size_t)c * p.m + k] = pik;
+    }
+    const R pik_r = (R)pik;
 
     // island softmax of the log-weights
     R mx = (R)(-INFINITY);
@@ -550,7 +576,7 @@ cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStrea
     if (e != cudaSuccess) return e;
     grad_pi_final_kernel<<<p.B, 256, 0, stream>>>(p);
     const size_t smem = sizeof(R) * (size_t)p.M;
-    const dim3 pgrid((p.N + 255) / 256, p.B), igrid(p.m, p.B), bgrid((p.m + 255) / 256, p.B);
+    const dim3 pgrid((p.N + 255) / 256, p.B), igrid(p.m, p.B);
     const int K = p.ckpt;
     const int nb = (p.T + K - 1) / K;
     for (int b = nb - 1; b >= 0 && e == cudaSuccess; --b) {
@@ -559,7 +585,6 @@ cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStrea
             if (t % K != 0 && t != p.T) grad_recompute_kernel<R, MODEL, DX><<<pgrid, 256, 0, stream>>>(p, mm, t);
         for (int t = hi; t >= lo; --t) {
             grad_island_kernel<R, MODEL, DX><<<igrid, kGradThreads, smem, stream>>>(p, mm, t);
-            if (t >= 2) grad_pi_step_kernel<<<bgrid, 256, 0, stream>>>(p, t);
         }
         e = cudaGetLastError();
     }
