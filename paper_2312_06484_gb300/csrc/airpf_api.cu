@@ -188,8 +188,9 @@ WsLayout make_ws_layout(const airpf_config* c)
     if (grad) {
         const size_t K = c->ckpt > 0 ? (size_t)c->ckpt : 1;
         const size_t nck = T / K + 1 + (T % K != 0 ? 1 : 0);
-        L.xck = take(rsz * B * nck * c->dx * N);
-        L.xblk = take(rsz * B * K * c->dx * N);
+        const size_t dxs = c->model == AIRPF_MODEL_LGSSM ? 8 : (size_t)c->dx;   // states [N][dx padded]
+        L.xck = take(rsz * B * nck * dxs * N);
+        L.xblk = take(rsz * B * K * dxs * N);
         L.logw = take(sizeof(double) * B * T * c->m);
         for (int i = 0; i < 2; ++i) L.gpi[i] = take(sizeof(double) * B * c->m);
         const size_t dxp = c->model == AIRPF_MODEL_LGSSM ? 8 : (size_t)c->dx;   // adjoints padded per particle

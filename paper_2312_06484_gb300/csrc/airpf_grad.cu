@@ -36,17 +36,45 @@ namespace {
 
 constexpr int kGradThreads = 128;
 
-// time-t particles [dx][N] of filter c: a checkpoint slot or the recomputed block
-template <typename R>
+// time-t particles [N][DX] of filter c (a particle's DX components together):
+// a checkpoint slot or the recomputed block
+template <typename R, int DX>
 __device__ __forceinline__ R* xstate(const StepParams& p, int c, int t)
 {
-    const size_t per = (size_t)p.dx * p.N;
+    const size_t per = (size_t)DX * p.N;
     int slot = -1;
     if (t == 0) slot = 0;
     else if (t % p.ckpt == 0) slot = t / p.ckpt;
     else if (t == p.T) slot = p.nck - 1;
     if (slot >= 0) return reinterpret_cast<R*>(p.xck) + ((size_t)c * p.nck + slot) * per;
     return reinterpret_cast<R*>(p.xblk) + ((size_t)c * p.ckpt + (t % p.ckpt)) * per;
+}
+
+// a particle's DX components from/to the [N][DX] layout (two 16-byte accesses for 8 floats)
+template <typename R, int DX>
+__device__ __forceinline__ void load_state(const R* base, size_t g, int dx, R* x)
+{
+    if constexpr (DX == 8 && sizeof(R) == 4) {
+        const float4 a = __ldcg(reinterpret_cast<const float4*>(base + g * 8));
+        const float4 b = __ldcg(reinterpret_cast<const float4*>(base + g * 8) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int d = 0; d < DX; ++d) x[d] = (d < dx) ? base[g * DX + d] : (R)0;
+    }
+}
+
+template <typename R, int DX>
+__device__ __forceinline__ void store_state(R* base, size_t g, int dx, const R* x)
+{
+    if constexpr (DX == 8 && sizeof(R) == 4) {
+        reinterpret_cast<float4*>(base + g * 8)[0] = make_float4(x[0], x[1], x[2], x[3]);
+        reinterpret_cast<float4*>(base + g * 8)[1] = make_float4(x[4], x[5], x[6], x[7]);
+    } else {
+#pragma unroll
+        for (int d = 0; d < DX; ++d)
+            if (d < dx) base[g * DX + d] = x[d];
+    }
 }
 
 // index among the time-(t-1) particles of the parent of time-t particle g
@@ -124,18 +152,16 @@ __global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, const
     const RunParams run = *p.run;
     const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
     const int dx = p.dx, N = p.N;
-    const R* xprev = xstate<R>(p, c, t - 1);
-    R* xt = xstate<R>(p, c, t);
+    const R* xprev = xstate<R, DX>(p, c, t - 1);
+    R* xt = xstate<R, DX>(p, c, t);
     const int par = parent_of(p, c, t, g);
     R xp[DX], x[DX], z[DX > 1 ? DX : 1];
-#pragma unroll
-    for (int d = 0; d < DX; ++d) xp[d] = (d < dx) ? xprev[(size_t)d * N + par] : (R)0;
+    load_state<R, DX>(xprev, (size_t)par, dx, xp);
     uint32_t w0, w2;
     model_step_noise<R, MODEL, DX>(mp, st, (uint32_t)g, (uint32_t)t, dx, z, w0, w2);
     transition_mm<R, MODEL, DX>(mp, dx, xp, x, mm, z);
-#pragma unroll
-    for (int d = 0; d < DX; ++d)
-        if (d < dx) xt[(size_t)d * N + g] = x[d];
+    store_state<R, DX>(xt, (size_t)g, dx, x);
+    (void)N;
 }
 
 // pi_T(k) = W^k_{T,1} / sum_j W^j_{T,1}: one CTA per filter
@@ -211,8 +237,8 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     const int c = blockIdx.y, k = blockIdx.x;
     const int M = p.M, N = p.N, dx = p.dx, dy = p.dy, td = p.theta_dim;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const R* xt = xstate<R>(p, c, t);
-    const R* xprev = xstate<R>(p, c, t - 1);
+    const R* xt = xstate<R, DX>(p, c, t);
+    const R* xprev = xstate<R, DX>(p, c, t - 1);
     // particle adjoints x^ [N][DX] (a particle's components together: vector atomics
     // to its parent) and descendant weights [N], in the pass's precision; buffer t % 3
     // holds step t's inputs and is cleared as it is read (it is step t-3's output buffer)
@@ -232,17 +258,10 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     for (int d = 0; d < DX; ++d) x0[d] = xp0[d] = xh0[d] = (R)0;
     if (pre) {
         par0 = parent_of(p, c, t, g0);
-#pragma unroll
-        for (int d = 0; d < DX; ++d) {
-            if (d < dx) {
-                x0[d] = xt[(size_t)d * N + g0];
-                xh0[d] = xh_in[(size_t)g0 * DX + d];
-            }
-        }
+        load_state<R, DX>(xt, (size_t)g0, dx, x0);
+        load_state<R, DX>(xh_in, (size_t)g0, dx, xh0);
         if (t < p.T) dh0 = dh_in[g0];
-#pragma unroll
-        for (int d = 0; d < DX; ++d)
-            if (d < dx) xp0[d] = xprev[(size_t)d * N + par0];
+        load_state<R, DX>(xprev, (size_t)par0, dx, xp0);
     }
     for (int o = tid; o < dy; o += blockDim.x) yv[o] = (R)p.y[(size_t)(t - 1) * dy + o];
     __syncthreads();
@@ -304,8 +323,12 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     for (int i = tid; i < M; i += blockDim.x) {
         const int g = k * M + i;
         R x[DX];
+        if (i == tid) {
 #pragma unroll
-        for (int d = 0; d < DX; ++d) x[d] = (d < dx) ? (i == tid ? x0[d] : xt[(size_t)d * N + g]) : (R)0;
+            for (int d = 0; d < DX; ++d) x[d] = x0[d];
+        } else {
+            load_state<R, DX>(xt, (size_t)g, dx, x);
+        }
         const R l = logg_mm<R, MODEL, DX>(mp, yv, dx, dy, x, mm);
         lsm[i] = l;
         mx = l > mx ? l : mx;
@@ -345,15 +368,20 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
         const int par = first ? par0 : parent_of(p, c, t, g);
         R x[DX], xp[DX], mu[DX];
         R s;
+        R xhat[DX], v[DX];
+        if (first) {
 #pragma unroll
-        for (int d = 0; d < DX; ++d) {
-            x[d] = (d < dx) ? (first ? x0[d] : xt[(size_t)d * N + g]) : (R)0;
-            xp[d] = (d < dx) ? (first ? xp0[d] : xprev[(size_t)d * N + par]) : (R)0;
+            for (int d = 0; d < DX; ++d) {
+                x[d] = x0[d];
+                xp[d] = xp0[d];
+                xhat[d] = xh0[d];
+            }
+        } else {
+            load_state<R, DX>(xt, (size_t)g, dx, x);
+            load_state<R, DX>(xprev, (size_t)par, dx, xp);
+            load_state<R, DX>(xh_in, (size_t)g, dx, xhat);
         }
         transition_mean<R, MODEL, DX>(mp, dx, xp, mm, mu, s);
-        R xhat[DX], v[DX];
-#pragma unroll
-        for (int d = 0; d < DX; ++d) xhat[d] = (d < dx) ? (first ? xh0[d] : xh_in[(size_t)g * DX + d]) : (R)0;
         if (MODEL == AR1) {
             const R a = mp.th[0], sv = mp.th[1], sw = mp.th[2], s0 = mp.th[3];
             const R e = yv[0] - x[0];

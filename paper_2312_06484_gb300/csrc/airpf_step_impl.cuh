@@ -1521,7 +1521,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         // states for the gradient pass: the prior draws x_0 (slot 0, at t = 1)
         // and the time-t particles at the checkpoints (every ckpt steps, and T)
         const int slot = (t % p.ckpt == 0) ? t / p.ckpt : (t == p.T ? p.nck - 1 : -1);
-        R* xck = reinterpret_cast<R*>(p.xck) + (size_t)c * p.nck * dx * N;
+        // [slot][N][DX]: a particle's components together (the backward pass gathers
+        // them by parent)
+        R* xck = reinterpret_cast<R*>(p.xck) + (size_t)c * p.nck * DX * N;
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
             const int i = li * PPT + r;
@@ -1530,8 +1532,8 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
 #pragma unroll
                 for (int d = 0; d < DX; ++d) {
                     if (d < dx) {
-                        if (t == 1) xck[(size_t)d * N + gi] = xp[r][d];
-                        if (slot >= 0) xck[((size_t)slot * dx + d) * N + gi] = xv[r][d];
+                        if (t == 1) xck[gi * DX + d] = xp[r][d];
+                        if (slot >= 0) xck[((size_t)slot * N + gi) * DX + d] = xv[r][d];
                     }
                 }
             }
