@@ -223,7 +223,7 @@ __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, c
 
 // Step t of the backward pass: one CTA per island.
 template <typename R, int MODEL, int DX>
-__global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
+__global__ void __launch_bounds__(kGradThreads, 6) grad_island_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
                                                                    int t)
 {
     extern __shared__ __align__(16) unsigned char gsm[];
@@ -353,12 +353,11 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
 
     // per-thread sums in the pass's precision (a thread holds few particles),
     // the CTA and grid reductions in double
-    R ga[kMaxTheta], gs[kMaxTheta];
-#pragma unroll
-    for (int d = 0; d < kMaxTheta; ++d) {
-        ga[d] = (R)0;
-        gs[d] = (R)0;
-    }
+    // the thread's theta terms accumulate in its column of tsum (rows 0..td-1 the adjoint
+    // terms, td..2td-1 the score terms): registers stay free for the particle arithmetic
+    for (int d = 0; d < 2 * td; ++d) tsum[d][tid] = (R)0;
+    auto ga = [&](int d) -> R& { return tsum[d][tid]; };
+    auto gs = [&](int d) -> R& { return tsum[td + d][tid]; };
     for (int i = tid; i < M; i += blockDim.x) {
         const int g = k * M + i;
         const R wi = (lsm[i] > (R)(-INFINITY)) ? exp(lsm[i] - mx) * inv_sum : (R)0;
@@ -388,40 +387,40 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
             const R zz = (x[0] - mu[0]) / sv;
             const R dsw = (R)(-1) / sw + e * e / (sw * sw * sw);
             xhat[0] += lhat * e / (sw * sw);
-            ga[0] += xhat[0] * xp[0];
-            ga[1] += xhat[0] * zz;
-            ga[2] += lhat * dsw;
+            ga(0) += xhat[0] * xp[0];
+            ga(1) += xhat[0] * zz;
+            ga(2) += lhat * dsw;
             v[0] = a * xhat[0];
-            gs[0] += delta * zz * xp[0] / sv;
-            gs[1] += delta * (zz * zz - (R)1) / sv;
-            gs[2] += delta * dsw;
+            gs(0) += delta * zz * xp[0] / sv;
+            gs(1) += delta * (zz * zz - (R)1) / sv;
+            gs(2) += delta * dsw;
             if (t == 1) {                          // x_0 = sigma_0 z_0
                 const R x0 = xp[0];
-                ga[3] += v[0] * x0 / s0;
-                gs[3] += delta * (x0 * x0 / (s0 * s0) - (R)1) / s0;
+                ga(3) += v[0] * x0 / s0;
+                gs(3) += delta * (x0 * x0 / (s0 * s0) - (R)1) / s0;
             }
         } else if (MODEL == SV) {
             // x = mu + phi (parent - mu) + sigma z;  l = -x/2 - y^2 e^-x / 2 + const
             const R mu_ = mp.th[0], phi = mp.th[1], sg = mp.th[2];
             const R zz = (x[0] - mu[0]) / sg;
             xhat[0] += lhat * ((R)(-0.5) + (R)0.5 * yv[0] * yv[0] * exp(-x[0]));
-            ga[0] += xhat[0] * ((R)1 - phi);
-            ga[1] += xhat[0] * (xp[0] - mu_);
-            ga[2] += xhat[0] * zz;
+            ga(0) += xhat[0] * ((R)1 - phi);
+            ga(1) += xhat[0] * (xp[0] - mu_);
+            ga(2) += xhat[0] * zz;
             v[0] = phi * xhat[0];
-            gs[0] += delta * zz * ((R)1 - phi) / sg;
-            gs[1] += delta * zz * (xp[0] - mu_) / sg;
-            gs[2] += delta * (zz * zz - (R)1) / sg;
+            gs(0) += delta * zz * ((R)1 - phi) / sg;
+            gs(1) += delta * zz * (xp[0] - mu_) / sg;
+            gs(2) += delta * (zz * zz - (R)1) / sg;
             if (t == 1) {                          // x_0 = mu + sigma (1 - phi^2)^-1/2 z_0
                 const R om = (R)1 - phi * phi;
                 const R sd0 = sg / sqrt(om);
                 const R z0 = (xp[0] - mu_) / sd0;
-                ga[0] += v[0];
-                ga[1] += v[0] * z0 * sd0 * phi / om;
-                ga[2] += v[0] * z0 * sd0 / sg;
-                gs[0] += delta * z0 / sd0;
-                gs[1] += delta * (z0 * z0 - (R)1) * phi / om;
-                gs[2] += delta * (z0 * z0 - (R)1) / sg;
+                ga(0) += v[0];
+                ga(1) += v[0] * z0 * sd0 * phi / om;
+                ga(2) += v[0] * z0 * sd0 / sg;
+                gs(0) += delta * z0 / sd0;
+                gs(1) += delta * (z0 * z0 - (R)1) * phi / om;
+                gs(2) += delta * (z0 * z0 - (R)1) / sg;
             }
         } else if (MODEL == NGM) {
             // x = p/2 + 25 p / (1 + p^2) + drift + sqrt(q) z;  l = -log(2 pi r)/2 - (y - x^2/20)^2 / (2 r)
@@ -431,17 +430,17 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
             const R e = yv[0] - x[0] * x[0] / (R)20;
             const R dlr = (R)(-0.5) / r + e * e / ((R)2 * r * r);
             xhat[0] += lhat * e * (x[0] / (R)10) / r;
-            ga[0] += xhat[0] * zz / ((R)2 * sq);
-            ga[1] += lhat * dlr;
+            ga(0) += xhat[0] * zz / ((R)2 * sq);
+            ga(1) += lhat * dlr;
             const R pv = xp[0], den = (R)1 + pv * pv;
             v[0] = xhat[0] * ((R)0.5 + (R)25 * ((R)1 - pv * pv) / (den * den));
-            gs[0] += delta * (zz * zz - (R)1) / ((R)2 * q);
-            gs[1] += delta * dlr;
+            gs(0) += delta * (zz * zz - (R)1) / ((R)2 * q);
+            gs(1) += delta * dlr;
             if (t == 1) {                          // x_0 = sqrt(p0) z_0
                 const R sp0 = sqrt(p0);
                 const R z0 = pv / sp0;
-                ga[2] += v[0] * z0 / ((R)2 * sp0);
-                gs[2] += delta * (z0 * z0 - (R)1) / ((R)2 * p0);
+                ga(2) += v[0] * z0 / ((R)2 * sp0);
+                gs(2) += delta * (z0 * z0 - (R)1) / ((R)2 * p0);
             }
         } else {
             const R inv_r = (R)2 * mp.c1;          // c1 = 1/(2r)
@@ -470,9 +469,9 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
                         if (o < dy) dl += mm.C[o * kMaxDx + d] * ee[o];
                     xhat[d] += lhat * dl * inv_r;
                     const R zd = (x[d] - mu[d]) * inv_s;
-                    ga[d] += xhat[d] * xp[d];                   // A_dd
+                    ga(d) += xhat[d] * xp[d];                   // A_dd
                     qsum += xhat[d] * (R)0.5 * s * zd;           // log q
-                    gs[d] += delta * zd * xp[d] * inv_s;
+                    gs(d) += delta * zd * xp[d] * inv_s;
                     zn += zd * zd;
                 }
             }
@@ -480,12 +479,12 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
 #pragma unroll
             for (int d = 0; d < kMaxTheta; ++d) {
                 if (d == dx) {
-                    ga[d] += qsum;
-                    gs[d] += delta * (R)0.5 * (zn - (R)dx);
+                    ga(d) += qsum;
+                    gs(d) += delta * (R)0.5 * (zn - (R)dx);
                 }
                 if (d == dx + 1) {
-                    ga[d] += lhat * dlr;
-                    gs[d] += delta * dlr;
+                    ga(d) += lhat * dlr;
+                    gs(d) += delta * dlr;
                 }
             }
 #pragma unroll
@@ -522,13 +521,6 @@ __global__ void __launch_bounds__(kGradThreads) grad_island_kernel(StepParams p,
     // (this CTA alone updates row k of gacc: no atomics; the final sum over the islands
     // runs in island order)
     const int nt = 2 * td;
-#pragma unroll
-    for (int d = 0; d < kMaxTheta; ++d) {
-        if (d < td) {
-            tsum[d][tid] = ga[d];
-            tsum[td + d][tid] = gs[d];
-        }
-    }
     __syncthreads();
     const int nseg = blockDim.x / nt;              // segments per term (at least 1: nt <= 20 < 128)
     const int seglen = (blockDim.x + nseg - 1) / nseg;
