@@ -140,28 +140,35 @@ __device__ __forceinline__ R logg_mm(const ModelPar<R>& mp, const R* y, int dx, 
 }
 
 // x_t of the particles between checkpoints: x_t(g) = f(x_{t-1}(parent), z_t(g))
+// Launched dependently on the kernel before it (the previous step's recompute): the
+// noise is drawn before the wait, the parent states (that kernel's output) read after.
 template <typename R, int MODEL, int DX>
 __global__ void __launch_bounds__(256) grad_recompute_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
                                                               int t)
 {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int c = blockIdx.y;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= p.N) return;
     ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
     if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
     const RunParams run = *p.run;
     const Stream st{p.seed_lo, p.seed_hi, run.iter, (run.chain0 + (uint32_t)c) << 8};
-    const int dx = p.dx, N = p.N;
+    const int dx = p.dx;
+    const bool has = g < p.N;
+    R xp[DX], x[DX], z[DX > 1 ? DX : 1];
+    uint32_t w0 = 0, w2 = 0;
+    int par = 0;
+    if (has) {
+        model_step_noise<R, MODEL, DX>(mp, st, (uint32_t)g, (uint32_t)t, dx, z, w0, w2);
+        par = parent_of(p, c, t, g);                 // the forward pass's lineage
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (!has) return;
     const R* xprev = xstate<R, DX>(p, c, t - 1);
     R* xt = xstate<R, DX>(p, c, t);
-    const int par = parent_of(p, c, t, g);
-    R xp[DX], x[DX], z[DX > 1 ? DX : 1];
     load_state<R, DX>(xprev, (size_t)par, dx, xp);
-    uint32_t w0, w2;
-    model_step_noise<R, MODEL, DX>(mp, st, (uint32_t)g, (uint32_t)t, dx, z, w0, w2);
     transition_mm<R, MODEL, DX>(mp, dx, xp, x, mm, z);
     store_state<R, DX>(xt, (size_t)g, dx, x);
-    (void)N;
 }
 
 // pi_T(k) = W^k_{T,1} / sum_j W^j_{T,1}: one CTA per filter
@@ -224,8 +231,12 @@ __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, c
 // Step t of the backward pass: one CTA per island.
 template <typename R, int MODEL, int DX>
 __global__ void __launch_bounds__(kGradThreads, 6) grad_island_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
-                                                                   int t)
+                                                                   int t, int dep)
 {
+    // launched dependently on step t+1's kernel (programmatic dependent launch): the
+    // next kernel may start once every CTA of this one has, and this one reads step
+    // t+1's outputs (adjoints, descendant weights, pi_{t+1}) only after the wait below
+    if (dep) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned char gsm[];
     __shared__ R yv[kMaxDy];
     __shared__ R tsum[2 * kMaxTheta][kGradThreads + 1];   // the threads' theta terms, a row per term
@@ -256,17 +267,56 @@ __global__ void __launch_bounds__(kGradThreads, 6) grad_island_kernel(StepParams
     R x0[DX], xp0[DX], xh0[DX], dh0 = (R)0;
 #pragma unroll
     for (int d = 0; d < DX; ++d) x0[d] = xp0[d] = xh0[d] = (R)0;
+    // (the states, the lineage, y and the forward pass's records are earlier kernels' outputs)
     if (pre) {
         par0 = parent_of(p, c, t, g0);
         load_state<R, DX>(xt, (size_t)g0, dx, x0);
-        load_state<R, DX>(xh_in, (size_t)g0, dx, xh0);
-        if (t < p.T) dh0 = dh_in[g0];
         load_state<R, DX>(xprev, (size_t)par0, dx, xp0);
     }
     for (int o = tid; o < dy; o += blockDim.x) yv[o] = (R)p.y[(size_t)(t - 1) * dy + o];
     __syncthreads();
     ModelPar<R> mp = reinterpret_cast<const ModelPar<R>*>(p.mpar)[c];
     if (MODEL == NGM) mp.drift = reinterpret_cast<const R*>(p.drift)[t - 1];
+
+    // island softmax of the log-weights
+    R mx = (R)(-INFINITY);
+    for (int i = tid; i < M; i += blockDim.x) {
+        const int g = k * M + i;
+        R x[DX];
+        if (i == tid) {
+#pragma unroll
+            for (int d = 0; d < DX; ++d) x[d] = x0[d];
+        } else {
+            load_state<R, DX>(xt, (size_t)g, dx, x);
+        }
+        const R l = logg_mm<R, MODEL, DX>(mp, yv, dx, dy, x, mm);
+        lsm[i] = l;
+        mx = l > mx ? l : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const R v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    if (lane == 0) rmx[warp] = mx;
+    __syncthreads();
+    mx = rmx[0];
+    for (int w = 1; w < nw; ++w) mx = rmx[w] > mx ? rmx[w] : mx;
+    R sum = 0;
+    if (mx > (R)(-INFINITY))
+        for (int i = tid; i < M; i += blockDim.x) sum += exp(lsm[i] - mx);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) rsum[warp] = sum;
+    __syncthreads();
+    sum = 0;
+    for (int w = 0; w < nw; ++w) sum += rsum[w];
+    const R inv_sum = sum > (R)0 ? (R)1 / sum : (R)0;
+
+    // step t+1's outputs from here on
+    if (dep) asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (pre) {
+        load_state<R, DX>(xh_in, (size_t)g0, dx, xh0);
+        if (t < p.T) dh0 = dh_in[g0];
+    }
     // pi_t(k): at t = T from grad_pi_final_kernel; before, from pi_{t+1} of the block of
     // r^(s*_t - 1) = 2^lvl islands holding k (r = 2^rb the radix), whose pi_{t+1} mass
     // the block hands to its members in proportion to W_{t,1} (the averaging of the
@@ -317,39 +367,6 @@ __global__ void __launch_bounds__(kGradThreads, 6) grad_island_kernel(StepParams
         if (tid == 0) p.gpi[t & 1][(size_t)c * p.m + k] = pik;
     }
     const R pik_r = (R)pik;
-
-    // island softmax of the log-weights
-    R mx = (R)(-INFINITY);
-    for (int i = tid; i < M; i += blockDim.x) {
-        const int g = k * M + i;
-        R x[DX];
-        if (i == tid) {
-#pragma unroll
-            for (int d = 0; d < DX; ++d) x[d] = x0[d];
-        } else {
-            load_state<R, DX>(xt, (size_t)g, dx, x);
-        }
-        const R l = logg_mm<R, MODEL, DX>(mp, yv, dx, dy, x, mm);
-        lsm[i] = l;
-        mx = l > mx ? l : mx;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const R v = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = v > mx ? v : mx;
-    }
-    if (lane == 0) rmx[warp] = mx;
-    __syncthreads();
-    mx = rmx[0];
-    for (int w = 1; w < nw; ++w) mx = rmx[w] > mx ? rmx[w] : mx;
-    R sum = 0;
-    if (mx > (R)(-INFINITY))
-        for (int i = tid; i < M; i += blockDim.x) sum += exp(lsm[i] - mx);
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) rsum[warp] = sum;
-    __syncthreads();
-    sum = 0;
-    for (int w = 0; w < nw; ++w) sum += rsum[w];
-    const R inv_sum = sum > (R)0 ? (R)1 / sum : (R)0;
 
     // per-thread sums in the pass's precision (a thread holds few particles),
     // the CTA and grid reductions in double
@@ -601,10 +618,35 @@ cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStrea
     const int nb = (p.T + K - 1) / K;
     for (int b = nb - 1; b >= 0 && e == cudaSuccess; --b) {
         const int lo = b * K + 1, hi = (b + 1) * K < p.T ? (b + 1) * K : p.T;
-        for (int t = lo; t <= hi; ++t)
-            if (t % K != 0 && t != p.T) grad_recompute_kernel<R, MODEL, DX><<<pgrid, 256, 0, stream>>>(p, mm, t);
+        for (int t = lo; t <= hi && e == cudaSuccess; ++t) {
+            if (t % K == 0 || t == p.T) continue;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = pgrid;
+            cfg.blockDim = dim3(256);
+            cfg.stream = stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            e = cudaLaunchKernelEx(&cfg, grad_recompute_kernel<R, MODEL, DX>, p, mm, t);
+        }
         for (int t = hi; t >= lo; --t) {
-            grad_island_kernel<R, MODEL, DX><<<igrid, kGradThreads, smem, stream>>>(p, mm, t);
+            // the first step of a block follows the recompute kernels in plain stream order;
+            // the others start while the step before them finishes
+            const int dep = t < hi ? 1 : 0;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = igrid;
+            cfg.blockDim = dim3(kGradThreads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = dep;
+            e = cudaLaunchKernelEx(&cfg, grad_island_kernel<R, MODEL, DX>, p, mm, t, dep);
+            if (e != cudaSuccess) break;
         }
         e = cudaGetLastError();
     }
