@@ -198,6 +198,57 @@ airpf_status airpf_run(airpf_ctx* ctx, const double* d_theta, const double* d_y,
 airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y,
                             uint32_t chain0, uint32_t iter, double* log_z);
 
+/* Stepwise passes: the caller drives the steps of one pass, so that the islands of one
+ * filter can be split over G processes, one GPU each (Section 2 lets the m islands of a
+ * filter run in parallel; the interaction stages are the only coupling): every process
+ * holds the whole filter's buffers, runs the island work of its own contiguous range of
+ * CTAs (m/G islands), exchanges the step's CTA records and particle rows with the others
+ * (an all-gather of airpf_step_regions), and runs the step's cascade over all records,
+ * which every process then holds identically.  For one filter (B = 1), without records or
+ * adaptive internal resampling, with per-step launches (AIRPF_LAUNCH_STEPS or
+ * AIRPF_LAUNCH_STEPS_SPLIT); otherwise AIRPF_ERR_UNSUPPORTED.  Asynchronous on the context's
+ * stream.  A pass:
+ *   airpf_step_begin; for t = 1..T: airpf_step_islands(t, own range), exchange,
+ *   airpf_step_cascade(t); airpf_step_end.
+ * The result equals airpf_run's for the same (chain0, iter).  Split steps may defer the
+ * exchange of the particle rows until after the cascade and skip it when the step's
+ * interacting stages all lie inside one process's islands (airpf_step_levels): with
+ * contiguous ranges of m/G islands, stage s pairs islands 2^(s-1) apart, so only the
+ * top log2 G binary stages cross processes. */
+
+/* Copies theta (d_theta_dim doubles) and y (T*dy) in and runs the pass's prologue. */
+airpf_status airpf_step_begin(airpf_ctx* ctx, const double* d_theta, const double* d_y,
+                              uint32_t chain0, uint32_t iter);
+
+/* Island work of step t (1..T, Algorithm 1's weighting, internal resampling and mutation of
+ * step t, and the cascade of step t-1 in fused steps) for CTAs cta0 .. cta0+ncta-1 of the
+ * filter: ncta a power of 2 dividing cta0 (0: all CTAs).  The filter has m/G CTAs of G
+ * islands (airpf_step_regions gives their records' sizes). */
+airpf_status airpf_step_islands(airpf_ctx* ctx, int32_t t, int32_t cta0, int32_t ncta);
+
+/* The cascade of step t (interaction stages, s*, log Z) over all CTA records: the cascade
+ * kernel of split steps; fused steps run it at the next island launch (and, for t = T, in a
+ * launch of their own here). */
+airpf_status airpf_step_cascade(airpf_ctx* ctx, int32_t t);
+
+/* Copies log Z^N_T (one double) to d_log_z. */
+airpf_status airpf_step_end(airpf_ctx* ctx, double* d_log_z);
+
+/* The device regions that step t's island launch writes and the other processes need, as
+ * byte offsets into the context's workspace and sizes: the CTA records (exponents, block-sum
+ * subtrees, sums of squares) and the particle rows of each state dimension.  Each region is
+ * laid out by CTA (or island) in order, so CTA range [j n, (j+1) n) owns the j-th of
+ * (regions bytes / n CTAs) equal parts.  offsets, bytes: arrays of at least 3 + dx entries;
+ * *count receives the number of regions. */
+airpf_status airpf_step_regions(airpf_ctx* ctx, int32_t t, size_t* offsets, size_t* bytes, int32_t* count);
+
+/* Split steps: waits for the stream, then gives the number of binary interaction levels
+ * of the last cascade (s* - 1 in binary stages; 0 if no stage interacted, log2 m if all
+ * did).  The island CTAs of the next step read particle rows of islands at most
+ * 2^levels - 1 apart.  Fused steps: AIRPF_ERR_UNSUPPORTED (their cascade runs inside the
+ * next island launch, so the rows are exchanged every step). */
+airpf_status airpf_step_levels(airpf_ctx* ctx, int32_t* levels);
+
 /* Size of the device scratch of airpf_run_static: a fixed device array inside
  * the library, which CUDA allocates when the library's module loads on a device. */
 #define AIRPF_STATIC_SCRATCH_BYTES ((size_t)32 << 20)

@@ -107,6 +107,51 @@ class AIRPF:
                                                lz.ctypes.data_as(ctypes.c_void_p)), self.ctx)
         return lz
 
+    # -- stepwise passes (the islands of one filter split over processes) -----------------
+    def step_begin(self, theta, y, *, chain0: int = 0, iter: int = 0):
+        """Copies theta and y in and runs the pass's prologue (airpf_step_begin)."""
+        torch = self._torch
+        theta = theta.reshape(self.B, self.theta_dim).to(device="cuda", dtype=torch.float64).contiguous()
+        y = y.reshape(-1).to(device="cuda", dtype=torch.float64).contiguous()
+        self._keep = (theta, y)
+        _binding.check(self.lib.airpf_step_begin(self.ctx, _ptr(theta), _ptr(y), chain0, iter), self.ctx)
+
+    def step_islands(self, t: int, cta0: int = 0, ncta: int = 0):
+        """Island work of step t for CTAs cta0 .. cta0+ncta-1 (0: all) (airpf_step_islands)."""
+        _binding.check(self.lib.airpf_step_islands(self.ctx, t, cta0, ncta), self.ctx)
+
+    def step_cascade(self, t: int):
+        """The cascade of step t over all CTA records (airpf_step_cascade)."""
+        _binding.check(self.lib.airpf_step_cascade(self.ctx, t), self.ctx)
+
+    def step_end(self):
+        """Returns log Z^N_T as a [1] float64 CUDA tensor (airpf_step_end)."""
+        out = self._torch.empty(1, dtype=self._torch.float64, device="cuda")
+        _binding.check(self.lib.airpf_step_end(self.ctx, _ptr(out)), self.ctx)
+        return out
+
+    def step_regions(self, t: int):
+        """Views of the workspace that step t's island launch writes, one uint8 tensor a
+        region: CTA exponents, CTA block-sum subtrees, CTA sums of squares, then the particle
+        rows of each state dimension (airpf_step_regions).  Each is ordered by CTA, so CTA
+        range j of G equal ranges owns part j of G equal parts of every region."""
+        n = 8 + self.dx
+        offs, nb, cnt = (ctypes.c_size_t * n)(), (ctypes.c_size_t * n)(), ctypes.c_int32()
+        _binding.check(self.lib.airpf_step_regions(self.ctx, t, offs, nb, ctypes.byref(cnt)), self.ctx)
+        return [self.workspace[offs[i]:offs[i] + nb[i]] for i in range(cnt.value)]
+
+    @property
+    def ctas(self) -> int:
+        """CTAs of one filter's island launch (one int32 exponent record each)."""
+        return self.step_regions(0)[0].numel() // 4
+
+    def step_levels(self) -> int:
+        """Split steps: the binary interaction levels of the last cascade (airpf_step_levels;
+        synchronises the stream)."""
+        lv = ctypes.c_int32()
+        _binding.check(self.lib.airpf_step_levels(self.ctx, ctypes.byref(lv)), self.ctx)
+        return int(lv.value)
+
     def pmmh(self, y, state_theta, state_logz, *, step, lo, hi, iters: int, chain0: int = 0,
              iter0: int = 0, n_accept=None, record: bool = True):
         """Random-walk PMMH, one chain per filter, entirely on the device (airpf_pmmh).

@@ -52,6 +52,13 @@ SIGNATURES = {
     "airpf_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint32, c_void_p, c_void_p, c_void_p]),
     "airpf_pmmh_langevin": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_uint32, c_uint32, c_int32, c_void_p, c_void_p, c_void_p]),
+    "airpf_step_begin": (c_int32, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint32]),
+    "airpf_step_islands": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
+    "airpf_step_cascade": (c_int32, [c_void_p, c_int32]),
+    "airpf_step_end": (c_int32, [c_void_p, c_void_p]),
+    "airpf_step_regions": (c_int32, [c_void_p, c_int32, ctypes.POINTER(c_size_t), ctypes.POINTER(c_size_t),
+                                     ctypes.POINTER(c_int32)]),
+    "airpf_step_levels": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
     "airpf_sync": (c_int32, [c_void_p]),
     "airpf_launch_mode": (c_int32, [c_void_p]),
     "airpf_moments": (c_int32, [c_void_p, c_void_p]),

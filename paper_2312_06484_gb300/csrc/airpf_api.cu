@@ -680,6 +680,144 @@ airpf_status airpf_run_host(airpf_ctx* ctx, const double* theta, const double* y
     return airpf_sync(ctx);
 }
 
+// ---------------------------------------------------------------------------
+// Stepwise passes: the caller drives the steps, so that the islands of one filter
+// can be split over several processes (one GPU each) with an exchange of the step's
+// CTA records and particle rows between the island launch and the cascade.
+// ---------------------------------------------------------------------------
+static airpf_status step_check(airpf_ctx* ctx)
+{
+    if (!ctx) return AIRPF_ERR_ARG;
+    if (!is_steps(ctx->launch)) {
+        set_err(ctx, "stepwise passes need per-step launches (AIRPF_LAUNCH_STEPS or AIRPF_LAUNCH_STEPS_SPLIT)");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    if (ctx->cfg.record != 0 || ctx->cfg.B != 1 || ctx->cfg.tau_int > 0.0) {
+        set_err(ctx, "stepwise passes run one filter (B = 1) without records or adaptive internal resampling");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    return AIRPF_OK;
+}
+
+airpf_status airpf_step_begin(airpf_ctx* ctx, const double* d_theta, const double* d_y, uint32_t chain0, uint32_t iter)
+{
+    airpf_status s = step_check(ctx);
+    if (s != AIRPF_OK) return s;
+    if (!d_theta || !d_y) {
+        set_err(ctx, "theta and y are required");
+        return AIRPF_ERR_ARG;
+    }
+    if ((uint64_t)chain0 + 1u > (1u << 24)) {
+        set_err(ctx, "chain0 must be below 2^24");
+        return AIRPF_ERR_ARG;
+    }
+    const airpf_config& c = ctx->cfg;
+    if ((s = copy_async(ctx, at<void>(ctx, ctx->L.theta), d_theta, sizeof(double) * ctx->theta_dim))) return s;
+    if ((s = copy_async(ctx, at<void>(ctx, ctx->L.y), d_y, sizeof(double) * (size_t)c.T * c.dy))) return s;
+    cudaError_t e = airpf::launch_set_run(at<RunParams>(ctx, ctx->L.run), iter, chain0, ctx->stream);
+    if (e == cudaSuccess) e = airpf::prepare_step(ctx->sp);
+    StepParams q = ctx->sp;
+    q.pdl = 0;
+    if (e == cudaSuccess) e = airpf::launch_step(q, 0, ctx->stream);      // the prologue
+    return e == cudaSuccess ? AIRPF_OK : cuda_fail(ctx, e, "airpf_step_begin");
+}
+
+airpf_status airpf_step_islands(airpf_ctx* ctx, int32_t t, int32_t cta0, int32_t ncta)
+{
+    airpf_status s = step_check(ctx);
+    if (s != AIRPF_OK) return s;
+    const int P = ctx->sp.P;
+    if (t < 1 || t > ctx->cfg.T) {
+        set_err(ctx, "step %d outside 1 .. T = %d", t, ctx->cfg.T);
+        return AIRPF_ERR_ARG;
+    }
+    if (ncta == 0) ncta = P;
+    if (cta0 < 0 || ncta < 1 || (ncta & (ncta - 1)) || cta0 % ncta != 0 || cta0 + ncta > P) {
+        set_err(ctx, "CTA range [%d, %d) must be an aligned power-of-2 range within the %d CTAs", cta0, cta0 + ncta, P);
+        return AIRPF_ERR_ARG;
+    }
+    StepParams q = ctx->sp;
+    q.pdl = 0;
+    q.cta0 = cta0;
+    q.ncta = ncta;
+    q.lg_ncta = ilog2_exact(ncta);
+    cudaError_t e = airpf::launch_step(q, t, ctx->stream);
+    return e == cudaSuccess ? AIRPF_OK : cuda_fail(ctx, e, "airpf_step_islands");
+}
+
+airpf_status airpf_step_cascade(airpf_ctx* ctx, int32_t t)
+{
+    airpf_status s = step_check(ctx);
+    if (s != AIRPF_OK) return s;
+    if (t < 1 || t > ctx->cfg.T) {
+        set_err(ctx, "step %d outside 1 .. T = %d", t, ctx->cfg.T);
+        return AIRPF_ERR_ARG;
+    }
+    if (ctx->sp.fused && t < ctx->cfg.T) return AIRPF_OK;     // the next island launch runs it in every CTA
+    StepParams q = ctx->sp;
+    q.pdl = 0;
+    cudaError_t e;
+    if (ctx->sp.fused) {
+        // the last step's cascade (log Z): the lineage launch of step T+1 runs it
+        e = airpf::launch_step(q, t + 1, ctx->stream);
+    } else {
+        e = airpf::launch_cascade(q, t, ctx->stream);
+    }
+    return e == cudaSuccess ? AIRPF_OK : cuda_fail(ctx, e, "airpf_step_cascade");
+}
+
+airpf_status airpf_step_end(airpf_ctx* ctx, double* d_log_z)
+{
+    airpf_status s = step_check(ctx);
+    if (s != AIRPF_OK) return s;
+    if (!d_log_z) {
+        set_err(ctx, "log_z is required");
+        return AIRPF_ERR_ARG;
+    }
+    return copy_async(ctx, d_log_z, at<void>(ctx, ctx->L.logz), sizeof(double));
+}
+
+airpf_status airpf_step_regions(airpf_ctx* ctx, int32_t t, size_t* offsets, size_t* bytes, int32_t* count)
+{
+    airpf_status s = step_check(ctx);
+    if (s != AIRPF_OK) return s;
+    if (!offsets || !bytes || !count || t < 0) return AIRPF_ERR_ARG;
+    const airpf_config& c = ctx->cfg;
+    const size_t P = (size_t)ctx->sp.P, G = (size_t)ctx->sp.G, N = (size_t)ctx->N;
+    const size_t rsz = c.precision == AIRPF_FP64 ? 8 : 4;
+    const int par = t & 1;
+    int n = 0;
+    offsets[n] = ctx->L.pe[par];
+    bytes[n++] = sizeof(int) * P;
+    offsets[n] = ctx->L.pt[par];
+    bytes[n++] = sizeof(double) * 2 * G * P;
+    offsets[n] = ctx->L.pq[par];
+    bytes[n++] = rsz * 8 * P;
+    for (int d = 0; d < c.dx; ++d) {
+        offsets[n] = ctx->L.X[par] + rsz * (size_t)d * N;
+        bytes[n++] = rsz * N;
+    }
+    *count = n;
+    return AIRPF_OK;
+}
+
+airpf_status airpf_step_levels(airpf_ctx* ctx, int32_t* levels)
+{
+    airpf_status s = step_check(ctx);
+    if (s != AIRPF_OK) return s;
+    if (!levels) return AIRPF_ERR_ARG;
+    if (ctx->sp.fused) {
+        set_err(ctx, "fused steps run a step's cascade inside the next island launch");
+        return AIRPF_ERR_UNSUPPORTED;
+    }
+    int ss = 0;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&ss, ctx->sp.csum, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "airpf_step_levels");
+    *levels = ss - 1;                 // binary levels below the first quiet one
+    return AIRPF_OK;
+}
+
 airpf_status airpf_sync(airpf_ctx* ctx)
 {
     if (!ctx) return AIRPF_ERR_ARG;

@@ -36,6 +36,7 @@ struct StepParams {
     int cdf_bits;                 // 31 - ceil(log2 M)
     int G, tpi, ppt;              // islands per CTA, threads per island, particles per thread
     int lg_tpi;                   // log2 tpi
+    int cta0, ncta, lg_ncta;      // island launches over CTAs cta0 .. cta0+ncta-1 of each filter (ncta 0: all)
     int theta_dim;
     uint32_t seed_lo, seed_hi;
     const RunParams* run;

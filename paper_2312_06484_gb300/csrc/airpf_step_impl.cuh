@@ -1887,8 +1887,14 @@ __global__ void __launch_bounds__(kMaxThreads, LV == 3 ? 1 : kMinCtasPerSm) airp
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int cpf = p.P;                       // CTAs per filter (a power of 2)
-    const int c = blockIdx.x >> (p.S - p.g);
-    const int k0 = (blockIdx.x - c * cpf) * p.G;
+    int c, k0;
+    if (p.ncta > 0) {                          // a range of each filter's CTAs (sharded passes)
+        c = blockIdx.x >> p.lg_ncta;
+        k0 = (p.cta0 + (int)(blockIdx.x - (c << p.lg_ncta))) * p.G;
+    } else {
+        c = blockIdx.x >> (p.S - p.g);
+        k0 = (blockIdx.x - c * cpf) * p.G;
+    }
     if (p.active != nullptr && p.active[c] == 0) return;   // uniform over the CTA
     step_body<R, MODEL, DX, PPT, REC, LV>(p, t, c, k0, smem, p.pdl != 0);
 }
@@ -1996,7 +2002,7 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
 {
     const size_t smem = step_smem_bytes(p);
     const int block = p.G * p.tpi;
-    const int grid = p.B * (p.m / p.G);
+    const int grid = p.B * (p.ncta > 0 ? p.ncta : p.m / p.G);
     const int want = smem > 48 * 1024 ? (int)smem : 48 * 1024;
     if (op == OP_PREPARE) {
         // opt in to more than 48 KB of dynamic shared memory (outside any capture)
