@@ -228,9 +228,14 @@ __device__ __forceinline__ void transition_mean(const ModelPar<R>& mp, int dx, c
     }
 }
 
-// Step t of the backward pass: one CTA per island.
+// Step t of the backward pass: one CTA per island.  Resident CTAs a SM: 7 in FP32 (at
+// most 72 registers; m = 2048 islands then take two waves of the 152 SMs instead of
+// 2.25), 6 in FP64 (which would spill heavily at 72).
+template <typename R>
+constexpr int grad_island_min_ctas() { return sizeof(R) == 4 ? 7 : 6; }
+
 template <typename R, int MODEL, int DX>
-__global__ void __launch_bounds__(kGradThreads, 6) grad_island_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
+__global__ void __launch_bounds__(kGradThreads, grad_island_min_ctas<R>()) grad_island_kernel(StepParams p, const __grid_constant__ ModelMat<R> mm,
                                                                    int t, int dep)
 {
     // launched dependently on step t+1's kernel (programmatic dependent launch): the
