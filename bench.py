@@ -62,12 +62,13 @@ def ops_per_particle_step(model: str) -> float:
 # Figures from the committed ncu captures of the kernels named (set to None when the kernel
 # changes, until it is captured again): DRAM read + write per launch, issue-active fraction.
 NCU = {
-    "ngm_island_step": {"dram_bytes_per_launch": None, "issue_active": None,
-                        "source": "ncu capture of airpf_step_kernel<float, NGM, 1, 4, false, 2> pending"},
-    "sv_fused_step": {"dram_bytes_per_launch": 1159680, "issue_active": 0.258,
+    "ngm_island_step": {"dram_bytes_per_launch": 93837312, "issue_active": 0.685,
+                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, "
+                                  "airpf_step_kernel<float, NGM, 1, 4, false, 2> at steps 5 and 6, caches flushed"},
+    "sv_fused_step": {"dram_bytes_per_launch": 1163264, "issue_active": 0.219,
                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, one "
-                                "launch of airpf_step_kernel<float, SV, 1, 4, false, 3>, cold cache"},
-    "fp64_ngm_island_step": {"fp64_pipe": 0.857, "issue_active": 0.111,
+                                "launch of airpf_step_kernel<float, SV, 1, 4, false, 3>, caches flushed"},
+    "fp64_ngm_island_step": {"fp64_pipe": 0.857, "issue_active": 0.116,
                              "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
                                        "airpf_step_kernel<double, NGM, 1, 4, false, 2>"},
     "fp64_sv_fused_step": {"fp64_pipe": 0.761, "issue_active": 0.103,
@@ -501,7 +502,7 @@ def run_gpu(args) -> None:
                  seed=1, launch=args.launch, **tile)
     launch_name = {1: "fused steps: one kernel per step (CUDA graph, programmatic dependent launch)",
                    2: "persistent, CTA per filter", 3: "persistent cooperative grid",
-                   4: "split steps: one island kernel per step, the cascade in the tail of its last CTAs "
+                   4: "split steps: an island kernel and a group-cascade kernel per step "
                       "(CUDA graph, programmatic dependent launch)"}[f.launch_mode]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = f.stream
@@ -596,12 +597,13 @@ def run_gpu(args) -> None:
     changepoint = None if args.no_changepoint else changepoint_leg(gp, torch, ws)
 
     ms_step = tot_ms / args.steps
-    step_us = 1e3 * ms_step / T_OBS           # one time step: the island kernel (with its tail cascade) and gaps
+    step_us = 1e3 * ms_step / T_OBS           # one time step: the island kernel, the cascade kernel and gaps
     roof = alu_roofline("NGM", N, step_us, sms, peaks, peak_src)
     roof.update({
-        "kernel": "airpf_step_kernel<float, NGM, 1, 4, false, 2> (split step: island work, then the cascade in "
-                  "the tail of the last CTAs)" if f.launch_mode == 4 else "airpf_step_kernel (one time step)",
-        "launch_avg_source": "timed region: pass time / T (the step's kernel and the gap to the next)",
+        "kernel": "airpf_step_kernel<float, NGM, 1, 4, false, 2> (split step: the island launch, then "
+                  "airpf_group_cascade_kernel<float>)" if f.launch_mode == 4 else "airpf_step_kernel (one time step)",
+        "launch_avg_source": "timed region: pass time / T (a step's island and cascade kernels and the gaps, so "
+                             "the island kernel's own fraction is higher by its share of the step)",
         "algorithmic_bytes_per_launch": 8 * N,
         "traffic": NCU["ngm_island_step"]["dram_bytes_per_launch"],
         "ncu_issue_active": NCU["ngm_island_step"]["issue_active"],
@@ -673,7 +675,8 @@ def run_profile_case(args) -> None:
         run = lambda j: f.run(th, y, iter=j)
     elif args.profile_case in ("sv", "sv_fp64"):
         prec = "fp64" if args.profile_case.endswith("fp64") else "fp32"
-        f = gp.AIRPF(synth.MODEL_SV, m=M_ISL, M=M_PART, T=T, B=1, mode="adaptive", tau=TAU, precision=prec, seed=1)
+        f = gp.AIRPF(synth.MODEL_SV, m=SV_M_ISL, M=SV_M_PART, T=T, B=1, mode="adaptive", tau=TAU, precision=prec,
+                     seed=1)
         y = torch.tensor(synth.sv_observations(T, seed=2), device="cuda")
         th = torch.tensor(synth.SV_THETA[None, :], device="cuda")
         run = lambda j: f.run(th, y, iter=j)
