@@ -62,6 +62,9 @@ struct airpf_ctx {
     bool graph_pm_ready;
     cudaGraphExec_t graph_bwd;  // the backward pass of the gradient
     bool graph_bwd_ready;
+    cudaStream_t bwd_aux;       // the backward pass's second capture stream (recomputation)
+    cudaEvent_t bwd_ev[airpf::kGradEvents];
+    bool bwd_aux_ready;
     int launch;               // resolved airpf_launch
     StepParams sp;
     StepParams sp_pm;
@@ -190,7 +193,7 @@ WsLayout make_ws_layout(const airpf_config* c)
         const size_t nck = T / K + 1 + (T % K != 0 ? 1 : 0);
         const size_t dxs = c->model == AIRPF_MODEL_LGSSM ? 8 : (size_t)c->dx;   // states [N][dx padded]
         L.xck = take(rsz * B * nck * dxs * N);
-        L.xblk = take(rsz * B * K * dxs * N);
+        L.xblk = take(rsz * 2 * B * K * dxs * N);     // two blocks: one recomputed while the other is used
         L.logw = take(sizeof(double) * B * T * c->m);
         for (int i = 0; i < 2; ++i) L.gpi[i] = take(sizeof(double) * B * c->m);
         const size_t dxp = c->model == AIRPF_MODEL_LGSSM ? 8 : (size_t)c->dx;   // adjoints padded per particle
@@ -620,6 +623,10 @@ airpf_status airpf_destroy(airpf_ctx* ctx)
     if (ctx->graph_ready) cudaGraphExecDestroy(ctx->graph);
     if (ctx->graph_pm_ready) cudaGraphExecDestroy(ctx->graph_pm);
     if (ctx->graph_bwd_ready) cudaGraphExecDestroy(ctx->graph_bwd);
+    if (ctx->bwd_aux_ready) {
+        for (int i = 0; i < airpf::kGradEvents; ++i) cudaEventDestroy(ctx->bwd_ev[i]);
+        cudaStreamDestroy(ctx->bwd_aux);
+    }
     if (ctx->ev) {
         for (int i = 0; i < ctx->n_ev; ++i) cudaEventDestroy(ctx->ev[i]);
         delete[] ctx->ev;
@@ -848,9 +855,25 @@ airpf_status airpf_grad(airpf_ctx* ctx, const double* d_theta, const double* d_y
     if (s != AIRPF_OK) return s;
     const int64_t fwd = ctx->launches;
     if (!ctx->graph_bwd_ready) {
+        if (!ctx->bwd_aux_ready) {
+            cudaError_t e = cudaStreamCreateWithFlags(&ctx->bwd_aux, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "backward-pass stream");
+            int made = 0;
+            while (made < airpf::kGradEvents && e == cudaSuccess) {
+                e = cudaEventCreateWithFlags(&ctx->bwd_ev[made], cudaEventDisableTiming);
+                if (e == cudaSuccess) ++made;
+            }
+            if (e != cudaSuccess) {
+                for (int i = 0; i < made; ++i) cudaEventDestroy(ctx->bwd_ev[i]);
+                cudaStreamDestroy(ctx->bwd_aux);
+                return cuda_fail(ctx, e, "backward-pass events");
+            }
+            ctx->bwd_aux_ready = true;
+        }
         cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
-        cudaError_t le = airpf::launch_grad_backward(ctx->sp, ctx->md_host, ctx->cap_stream);
+        cudaError_t le = airpf::launch_grad_backward(ctx->sp, ctx->md_host, ctx->cap_stream, ctx->bwd_aux,
+                                                     ctx->bwd_ev);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (le != cudaSuccess) {

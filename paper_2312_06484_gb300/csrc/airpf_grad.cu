@@ -37,7 +37,8 @@ namespace {
 constexpr int kGradThreads = 128;
 
 // time-t particles [N][DX] of filter c (a particle's DX components together):
-// a checkpoint slot or the recomputed block
+// a checkpoint slot, or the recomputed states of block t / ckpt (two block buffers,
+// by the block's parity: one is recomputed while the adjoint steps use the other)
 template <typename R, int DX>
 __device__ __forceinline__ R* xstate(const StepParams& p, int c, int t)
 {
@@ -47,7 +48,8 @@ __device__ __forceinline__ R* xstate(const StepParams& p, int c, int t)
     else if (t % p.ckpt == 0) slot = t / p.ckpt;
     else if (t == p.T) slot = p.nck - 1;
     if (slot >= 0) return reinterpret_cast<R*>(p.xck) + ((size_t)c * p.nck + slot) * per;
-    return reinterpret_cast<R*>(p.xblk) + ((size_t)c * p.ckpt + (t % p.ckpt)) * per;
+    const size_t buf = (size_t)((t / p.ckpt) & 1);
+    return reinterpret_cast<R*>(p.xblk) + ((buf * p.B + c) * p.ckpt + (t % p.ckpt)) * per;
 }
 
 // a particle's DX components from/to the [N][DX] layout (two 16-byte accesses for 8 floats)
@@ -598,7 +600,8 @@ __global__ void __launch_bounds__(256) grad_sum_kernel(StepParams p)
 }
 
 template <typename R, int MODEL, int DX>
-cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStream_t stream)
+cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStream_t stream, cudaStream_t aux,
+                           cudaEvent_t* ev)
 {
     ModelMat<R> mm;
     for (int i = 0; i < kMaxDx * kMaxDx; ++i) mm.A[i] = (R)0;
@@ -621,23 +624,40 @@ cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStrea
     const dim3 pgrid((p.N + 255) / 256, p.B), igrid(p.m, p.B);
     const int K = p.ckpt;
     const int nb = (p.T + K - 1) / K;
-    for (int b = nb - 1; b >= 0 && e == cudaSuccess; --b) {
-        const int lo = b * K + 1, hi = (b + 1) * K < p.T ? (b + 1) * K : p.T;
-        for (int t = lo; t <= hi && e == cudaSuccess; ++t) {
+    auto steps = [&](int b, int* lo, int* hi) {
+        *lo = b * K + 1;
+        *hi = (b + 1) * K < p.T ? (b + 1) * K : p.T;
+    };
+    // the states of block b's steps that are not checkpoints, on the second stream
+    // (each recompute launched dependently on the one before it in the block)
+    auto recompute = [&](int b) -> cudaError_t {
+        int lo, hi;
+        steps(b, &lo, &hi);
+        cudaError_t r = cudaSuccess;
+        bool first = true;
+        for (int t = lo; t <= hi && r == cudaSuccess; ++t) {
             if (t % K == 0 || t == p.T) continue;
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = pgrid;
             cfg.blockDim = dim3(256);
-            cfg.stream = stream;
+            cfg.stream = aux;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            e = cudaLaunchKernelEx(&cfg, grad_recompute_kernel<R, MODEL, DX>, p, mm, t);
+            cfg.numAttrs = first ? 0 : 1;
+            r = cudaLaunchKernelEx(&cfg, grad_recompute_kernel<R, MODEL, DX>, p, mm, t);
+            first = false;
         }
-        for (int t = hi; t >= lo; --t) {
-            // the first step of a block follows the recompute kernels in plain stream order;
+        return r == cudaSuccess ? cudaEventRecord(ev[1 + (b & 1)], aux) : r;
+    };
+    // block b's adjoint steps, last step first, once its states are recomputed
+    auto adjoint = [&](int b) -> cudaError_t {
+        int lo, hi;
+        steps(b, &lo, &hi);
+        cudaError_t r = cudaStreamWaitEvent(stream, ev[1 + (b & 1)], 0);
+        for (int t = hi; t >= lo && r == cudaSuccess; --t) {
+            // the first step of a block follows the recomputation in plain stream order;
             // the others start while the step before them finishes
             const int dep = t < hi ? 1 : 0;
             cudaLaunchConfig_t cfg = {};
@@ -650,22 +670,35 @@ cudaError_t backward_typed(const StepParams& p, const double* host_md, cudaStrea
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = dep;
-            e = cudaLaunchKernelEx(&cfg, grad_island_kernel<R, MODEL, DX>, p, mm, t, dep);
-            if (e != cudaSuccess) break;
+            r = cudaLaunchKernelEx(&cfg, grad_island_kernel<R, MODEL, DX>, p, mm, t, dep);
         }
-        e = cudaGetLastError();
+        return r == cudaSuccess ? cudaEventRecord(ev[3 + (b & 1)], stream) : r;
+    };
+    // fork: block b-1 is recomputed while block b's adjoint steps run; its buffer was
+    // last read by block b+1's adjoint steps
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[0], 0);
+    if (e == cudaSuccess) e = recompute(nb - 1);
+    for (int b = nb - 1; b >= 0 && e == cudaSuccess; --b) {
+        if (b >= 1) {
+            if (b + 1 <= nb - 1) e = cudaStreamWaitEvent(aux, ev[3 + ((b + 1) & 1)], 0);
+            if (e == cudaSuccess) e = recompute(b - 1);
+        }
+        if (e == cudaSuccess) e = adjoint(b);      // joins the second stream back (block 0 last)
     }
     if (e == cudaSuccess) grad_sum_kernel<<<p.B, 256, 0, stream>>>(p);
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 template <typename R>
-cudaError_t backward_r(const StepParams& p, const double* host_md, cudaStream_t stream)
+cudaError_t backward_r(const StepParams& p, const double* host_md, cudaStream_t stream, cudaStream_t aux,
+                       cudaEvent_t* ev)
 {
-    if (p.model == AR1) return backward_typed<R, AR1, 1>(p, host_md, stream);
-    if (p.model == SV) return backward_typed<R, SV, 1>(p, host_md, stream);
-    if (p.model == NGM) return backward_typed<R, NGM, 1>(p, host_md, stream);
-    if (p.model == LGSSM) return backward_typed<R, LGSSM, kMaxDx>(p, host_md, stream);
+    if (p.model == AR1) return backward_typed<R, AR1, 1>(p, host_md, stream, aux, ev);
+    if (p.model == SV) return backward_typed<R, SV, 1>(p, host_md, stream, aux, ev);
+    if (p.model == NGM) return backward_typed<R, NGM, 1>(p, host_md, stream, aux, ev);
+    if (p.model == LGSSM) return backward_typed<R, LGSSM, kMaxDx>(p, host_md, stream, aux, ev);
     return cudaErrorInvalidValue;
 }
 
@@ -673,10 +706,11 @@ cudaError_t backward_r(const StepParams& p, const double* host_md, cudaStream_t 
 
 bool grad_supported(int model) { return model == AR1 || model == SV || model == NGM || model == LGSSM; }
 
-cudaError_t launch_grad_backward(const StepParams& p, const double* host_md, cudaStream_t stream)
+cudaError_t launch_grad_backward(const StepParams& p, const double* host_md, cudaStream_t stream, cudaStream_t aux,
+                                 cudaEvent_t* ev)
 {
     if (p.M * (p.fp64 ? 8 : 4) > 48 * 1024) return cudaErrorInvalidValue;
-    return p.fp64 ? backward_r<double>(p, host_md, stream) : backward_r<float>(p, host_md, stream);
+    return p.fp64 ? backward_r<double>(p, host_md, stream, aux, ev) : backward_r<float>(p, host_md, stream, aux, ev);
 }
 
 }  // namespace airpf

@@ -70,7 +70,7 @@ struct StepParams {
     // (three rotating buffers each), and the two results
     int grad, ckpt, nck;
     void* xck;                    // [B][nck][dx][N]
-    void* xblk;                   // [B][ckpt][dx][N]
+    void* xblk;                   // [2][B][ckpt][N][dx]: blocks of even and odd index
     double* logw;                 // [B][T][m]
     // output measures (record AIRPF_RECORD_MOMENTS): per island and step, log W_{t,0} and
     // log W_{t,1}, and every warp's sums of x_d and x_d^2 over its mutated and its
@@ -143,7 +143,12 @@ int max_cta_threads();
 // on `stream`: every model but TOY (host_md: the LGSSM's A then C, row-major).
 // Zeroes its accumulators first.
 constexpr int kModelDataMax = 8 * 8 + 8 * 8;
-cudaError_t launch_grad_backward(const StepParams& p, const double* host_md, cudaStream_t stream);
+// The backward pass, recorded into the capture of `stream`: the recomputation of the
+// states of each block of ckpt steps runs on `aux` (forked from and joined back to
+// `stream` through the kGradEvents events), one block ahead of the adjoint steps.
+constexpr int kGradEvents = 5;
+cudaError_t launch_grad_backward(const StepParams& p, const double* host_md, cudaStream_t stream, cudaStream_t aux,
+                                 cudaEvent_t* ev);
 bool grad_supported(int model);
 
 // Writes the run parameters (one thread).
