@@ -1356,12 +1356,21 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         }
     }
 
-    // ---- 2. everything below reads what earlier kernels of the pass wrote ----
-    if (dep) {
-        dependency_wait();
-        allow_dependents();
+    // Split steps: the island kernel of step t-1 has completed before this one starts
+    // (the cascade kernel between them lets this kernel launch only after its own wait
+    // on that kernel), so the rows and CTA records of step t-1 may be read before the
+    // wait; only the cascade's outputs need it.  Fused steps launch directly after the
+    // previous island kernel and must wait first.
+    constexpr bool kSplitOnly = (LV == 2);
+    const bool split_path = kSplitOnly || (LV == 0 && p.split);
+    typename Casc<FX>::V own_top = 0;       // the own CTA record's island node (level 0)
+    int own_ex = INT_MIN;
+    if (kSplitOnly && t >= 2 && t <= p.T && p.g >= 1 && tid < p.G) {
+        own_ex = __ldcg(&p.pe[(t - 1) & 1][(size_t)c * p.P + jo]);
+        own_top = __ldcg(&reinterpret_cast<const typename Casc<FX>::V*>(p.pt[(t - 1) & 1])
+                             [((size_t)c * p.P + jo) * 2 * p.G + tree_off(p.G, 0) + tid]);
     }
-    if (t >= 2 && t <= p.T) {           // the own block (the parents when the island keeps it)
+    auto load_own_block = [&]() {           // the own block (the parents when the island keeps it)
         if (vec && li * PPT < M) {
 #pragma unroll
             for (int d = 0; d < DX; ++d) {
@@ -1383,7 +1392,15 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
                 }
             }
         }
+    };
+    if (kSplitOnly && t >= 2 && t <= p.T) load_own_block();
+
+    // ---- 2. everything below reads what earlier kernels of the pass wrote ----
+    if (dep) {
+        dependency_wait();
+        allow_dependents();
     }
+    if (!kSplitOnly && t >= 2 && t <= p.T) load_own_block();
 
     // the own islands' weight and source block (written by the cascade of step t-1)
     if (t == 1) {
@@ -1399,16 +1416,29 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         // the filter (the first CTA also writes log Z and the run's records)
         const CascadeOwn own{k0, own_w, own_we, own_src};
         cascade_all<FX, true>(p, c, t - 1, st, tree, &own, designated);
-    } else if (LV == 2 || (LV == 0 && p.split)) {
-        // the cascade kernels of step t-1 left s*, the largest exponent, the group
-        // records and the top tree; this CTA derives its islands' weights and walks
-        int* csum_sh = reinterpret_cast<int*>(scal) + 4;
-        if (tid < 2) csum_sh[tid] = __ldcg(&p.csum[(size_t)c * 4 + tid]);
-        __syncthreads();
-        const CascadeOwn own{k0, own_w, own_we, own_src};
-        const BlockSums<FX> bs{p, c, t - 1, csum_sh[1],
-                               reinterpret_cast<const typename Casc<FX>::V*>(p.utg) + (size_t)c * 2 * p.P, true, true};
-        own_outputs<FX>(bs, st, csum_sh[0], own);
+    } else if (split_path) {
+        // the cascade kernel of step t-1 left s*, the largest exponent, the group
+        // records and the top tree; this CTA derives its islands' weights and walks.
+        // Every thread reads the summary itself (a broadcast load, no barrier).
+        const int ss = __ldcg(&p.csum[(size_t)c * 4 + 0]);
+        const int emax = __ldcg(&p.csum[(size_t)c * 4 + 1]);
+        if (kSplitOnly && ss == 1 && p.g >= 1) {
+            // no stage interacted: each island keeps its block and its weight, level 0
+            // of the own CTA record (loaded before the wait)
+            if (tid < p.G) {
+                XW w{0ull, 0};
+                if (emax != INT_MIN && own_ex != INT_MIN) w = Casc<FX>::weight(own_top, own_ex - Casc<FX>::frac(p));
+                own_w[tid] = w.bits;
+                own_we[tid] = w.e;
+                own_src[tid] = k0 + tid;
+            }
+        } else {
+            const CascadeOwn own{k0, own_w, own_we, own_src};
+            const BlockSums<FX> bs{p, c, t - 1, emax,
+                                   reinterpret_cast<const typename Casc<FX>::V*>(p.utg) + (size_t)c * 2 * p.P, true,
+                                   true};
+            own_outputs<FX>(bs, st, ss, own);
+        }
     } else {
         // the cascade's summary of step t-1, this CTA's record of step t-1 and
         // (used only if some stage interacted) the inherited blocks
@@ -1462,10 +1492,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     R* mxr_all = reinterpret_cast<R*>(smem + L.island + L.mxr);
     const int nwi = (p.tpi + 31) >> 5;
 
-    R* Am = mshared;                 // filled before the dependency wait
+    R* Am = mshared;                 // filled before the dependency wait (ordered by the barrier above)
     R* Cm = mshared + dx * dx;
     R* yv = Cm + p.dy * dx;
-    __syncthreads();     // orders those writes, and the cascade's smem reads before the island work reuses it
 
     const int par = own_src[g];
     Cdf* cdf = cdf_all + (size_t)g * M;
