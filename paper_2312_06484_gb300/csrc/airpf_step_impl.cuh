@@ -1278,15 +1278,23 @@ __global__ void airpf_prologue_kernel(StepParams p)
 // thread of the CTA; all barriers inside are CTA-uniform.
 // ---------------------------------------------------------------------------
 // LV: which launch the body serves, fixed at compile time for the per-step
-// kernels (1 fused steps, 2 split steps) or chosen at run time (0)
-template <typename R, int MODEL, int DX, int PPT, bool REC = true, int LV = 0>
+// kernels (1 fused steps, 2 split steps) or chosen at run time (0).  MC: the island
+// size M fixed at compile time (0: read at run time), with TPI = MC / PPT threads an
+// island; the loops over an island's particles, the search and the CDF layout then
+// unroll and fold (about 13% fewer issue cycles on the m = 65536 x M = 256 workload).
+template <typename R, int MODEL, int DX, int PPT, bool REC = true, int LV = 0, int MC = 0>
 __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int k0, unsigned char* smem,
                                           bool dep = false)
 {
     using Cdf = typename CdfType<R>::T;
     constexpr bool FX = sizeof(R) == 4;
+    constexpr int TPI = MC > 0 ? MC / PPT : 0;
+    static_assert(MC == 0 || (TPI >= 32 && (TPI & (TPI - 1)) == 0 && TPI * PPT == MC), "MC = PPT x 2^k, 2^k >= 32");
     const int tid = threadIdx.x;
-    const int N = p.N, M = p.M, dx = p.dx;
+    const int N = p.N, M = MC > 0 ? MC : p.M, dx = p.dx;
+    const int tpi = TPI > 0 ? TPI : p.tpi;
+    constexpr int LG_TPI = TPI >= 512 ? 9 : TPI >= 256 ? 8 : TPI >= 128 ? 7 : TPI >= 64 ? 6 : 5;
+    const int lg_tpi = TPI > 0 ? LG_TPI : p.lg_tpi;
     const int jo = k0 >> p.g;                  // G, tpi and m/G are powers of 2: shifts, not divisions
     const Layout L = make_layout(p);
     double* tree = reinterpret_cast<double*>(smem + L.tree);
@@ -1305,7 +1313,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     // ---- 1. before any dependency: the step's noise (and at t = 1 the prior
     //      draw), from the run parameters and model constants only, which the
     //      kernels of this pass never write ----
-    const int g = tid >> p.lg_tpi, li = tid & (p.tpi - 1);
+    const int g = tid >> lg_tpi, li = tid & (tpi - 1);
     const int lane = tid & 31, wi = li >> 5;   // warp index within the island
     const int k = k0 + g;
     const R* Xp = reinterpret_cast<const R*>(p.X[(t - 1) & 1]);
@@ -1490,7 +1498,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     R* xs_all = reinterpret_cast<R*>(smem + L.island + L.xs);
     Cdf* red_all = reinterpret_cast<Cdf*>(smem + L.island + L.red);
     R* mxr_all = reinterpret_cast<R*>(smem + L.island + L.mxr);
-    const int nwi = (p.tpi + 31) >> 5;
+    const int nwi = (tpi + 31) >> 5;
 
     R* Am = mshared;                 // filled before the dependency wait (ordered by the barrier above)
     R* Cm = mshared + dx * dx;
@@ -1594,7 +1602,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     // an island of several warps (then G <= 8) syncs on its own barrier 1 + g
     if (nwi > 1) {
         if (lane == 0) mxr[wi] = mx;
-        named_sync(1 + g, p.tpi);
+        named_sync(1 + g, tpi);
         R v = mxr[0];
         for (int w = 1; w < nwi; ++w) v = (mxr[w] > v) ? mxr[w] : v;
         mx = v;
@@ -1646,7 +1654,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     if (nwi > 1) {
         if (lane == 31) red[wi] = incl;
         if (air && lane == 0) sqr[wi] = sq;
-        named_sync(1 + g, p.tpi);
+        named_sync(1 + g, tpi);
         Cdf off = 0;
         for (int w = 0; w < wi; ++w) off += red[w];
         excl += off;
@@ -1665,7 +1673,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
                 if (d < dx) xs[(size_t)d * M + i] = xv[r][d];
         }
     }
-    if (nwi > 1) named_sync(1 + g, p.tpi);    // an island of one warp needs only the warp
+    if (nwi > 1) named_sync(1 + g, tpi);    // an island of one warp needs only the warp
     else __syncwarp();
     const Cdf total = cdf[eyt ? 0 : cdf_ix(M - 1)];
 
@@ -1911,7 +1919,7 @@ static __device__ bool grid_barrier(unsigned* bar, unsigned* err)
 // steps, 2 split steps, 0 either (and the recording passes); 3 fused steps
 // with up to 128 registers a thread instead of 64 (no spills, half the resident
 // CTAs: for grids that are one wave either way)
-template <typename R, int MODEL, int DX, int PPT, bool REC, int LV>
+template <typename R, int MODEL, int DX, int PPT, bool REC, int LV, int MC = 0>
 __global__ void __launch_bounds__(kMaxThreads, LV == 3 ? 1 : kMinCtasPerSm) airpf_step_kernel(StepParams p, int t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1925,7 +1933,7 @@ __global__ void __launch_bounds__(kMaxThreads, LV == 3 ? 1 : kMinCtasPerSm) airp
         k0 = (blockIdx.x - c * cpf) * p.G;
     }
     if (p.active != nullptr && p.active[c] == 0) return;   // uniform over the CTA
-    step_body<R, MODEL, DX, PPT, REC, LV>(p, t, c, k0, smem, p.pdl != 0);
+    step_body<R, MODEL, DX, PPT, REC, LV, MC>(p, t, c, k0, smem, p.pdl != 0);
 }
 
 // The cascade of step t: one CTA per filter.
@@ -2026,6 +2034,12 @@ static cudaError_t launch_dependent(K kernel, dim3 grid, dim3 block, size_t smem
     return cudaLaunchKernelEx(&cfg, kernel, p, t);
 }
 
+// The lean step kernels also come with the island size fixed at compile time for
+// the size of the workloads this library is tuned for: M = 256 particles, 4 a thread
+// (64 threads an island).
+constexpr int kFixedM = 256, kFixedPpt = 4;
+__host__ inline bool fixed_island(const StepParams& p) { return p.M == kFixedM && p.tpi == kFixedM / kFixedPpt; }
+
 template <typename R, int MODEL, int DX, int PPT>
 static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
 {
@@ -2046,6 +2060,17 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 3>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if constexpr (PPT == kFixedPpt) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 1, kFixedM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 2, kFixedM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 3, kFixedM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        }
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -2073,7 +2098,15 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         int dev = 0, sms = 0, per_sm = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
+        bool fixed_done = false;
+        if constexpr (PPT == kFixedPpt) {
+            if (e == cudaSuccess && fixed_island(p)) {
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, airpf_step_kernel<R, MODEL, DX, PPT, false, 3, kFixedM>, block, smem);
+                fixed_done = true;
+            }
+        }
+        if (e == cudaSuccess && !fixed_done)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, airpf_step_kernel<R, MODEL, DX, PPT, false, 3>,
                                                               block, smem);
         *fits = (e == cudaSuccess && (long long)per_sm * sms >= grid) ? 1 : 0;
@@ -2118,6 +2151,14 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         kernel<<<grid, block, smem, stream>>>(p, t);
         return cudaGetLastError();
     };
+    if constexpr (PPT == kFixedPpt) {
+        if (!rec && fixed_island(p)) {       // islands of kFixedM particles: the compile-time size
+            if (p.fused)
+                return p.wide ? go(airpf_step_kernel<R, MODEL, DX, PPT, false, 3, kFixedM>)
+                              : go(airpf_step_kernel<R, MODEL, DX, PPT, false, 1, kFixedM>);
+            if (p.split) return go(airpf_step_kernel<R, MODEL, DX, PPT, false, 2, kFixedM>);
+        }
+    }
     if (!rec && p.fused)
         return p.wide ? go(airpf_step_kernel<R, MODEL, DX, PPT, false, 3>) : go(airpf_step_kernel<R, MODEL, DX, PPT, false, 1>);
     if (!rec && p.split) return go(airpf_step_kernel<R, MODEL, DX, PPT, false, 2>);

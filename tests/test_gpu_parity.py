@@ -159,6 +159,11 @@ def test_ngm_m65536_full_size_fp64():
     o = oracle.airpf(synth.MODEL_NGM, synth.NGM_THETA, y, m=m, M=M, mode=oracle.MODE_ADAPTIVE, tau=0.3, seed=1)
     upto = compare_filter(g, 0, o, m=m, what="NGM m=65536")
     assert upto >= 1
+    # the pass that records nothing runs the lean split kernel with M = 256 fixed at
+    # compile time (the bench's kernel): the same log Z, bit for bit
+    lean = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, m=m, M=M, B=1, mode="adaptive", tau=0.3, seed=1, record=0)
+    assert lean["launch_mode"] == 4
+    np.testing.assert_array_equal(lean["log_z"], g["log_z"])
 
 
 @pytest.mark.parametrize("launch,B", [("steps", 1), ("steps", 3), ("split", 1)])
@@ -181,3 +186,6 @@ def test_lean_passes_match_oracle(gpu_lib, launch, B):
     f32_one = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, B=1, record=0, precision="fp32", **kw)
     f32_many = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, B=3, record=0, precision="fp32", **kw)
     assert f32_one["log_z"][0] == f32_many["log_z"][0]
+    # FP32 too: the lean kernels (M = 256 fixed at compile time) give the recording kernel's bits
+    f32_rec = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, B=3, record=7, precision="fp32", **kw)
+    np.testing.assert_array_equal(f32_many["log_z"], f32_rec["log_z"])
