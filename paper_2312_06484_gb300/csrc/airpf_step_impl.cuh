@@ -215,9 +215,9 @@ __device__ __forceinline__ V warp_incl_scan(V v, int lane)
 
 // max / sum over the whole CTA (blockDim a multiple of 32); sh: kMaxWarps slots
 template <typename V>
-__device__ __forceinline__ V block_max(V v, V* sh)
+__device__ __forceinline__ V block_max(V v, V* sh, int nw)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_max(v);
     __syncthreads();
     if (lane == 0) sh[warp] = v;
@@ -225,6 +225,12 @@ __device__ __forceinline__ V block_max(V v, V* sh)
     V r = sh[0];
     for (int w = 1; w < nw; ++w) r = sh[w] > r ? sh[w] : r;
     return r;
+}
+
+template <typename V>
+__device__ __forceinline__ V block_max(V v, V* sh)
+{
+    return block_max(v, sh, (int)(blockDim.x >> 5));
 }
 
 // Programmatic dependent launch: wait until the previous kernel of the stream
@@ -1004,13 +1010,13 @@ __device__ __forceinline__ void block_sum_slots(const Qt (&part)[kGroupQ], int n
 // layout), and the sums of squares of the nodes of levels 0 .. ln-1 into
 // Q[q0 + l].  Warp shuffles for the levels inside a warp, warp 0 above them.
 template <bool FX>
-__device__ void leaf_tree(typename Casc<FX>::V v, int ln, typename Casc<FX>::V* nd, typename Casc<FX>::Qt* qw,
-                          typename Casc<FX>::Qt* Q, int q0)
+__device__ __forceinline__ void leaf_tree(typename Casc<FX>::V v, int ln, typename Casc<FX>::V* nd,
+                                          typename Casc<FX>::Qt* qw, typename Casc<FX>::Qt* Q, int q0, int nw)
 {
     using C = Casc<FX>;
     using V = typename C::V;
     using Qt = typename C::Qt;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = 1 << ln;
     const bool has = tid < n;
     auto wsum = [&](Qt x, int l) {
@@ -1080,14 +1086,33 @@ __device__ void leaf_tree(typename Casc<FX>::V v, int ln, typename Casc<FX>::V* 
 // cascade in every island CTA, much slower on that workload, where stage 1
 // interacts on a third to a half of the steps and every CTA then built the top
 // tree.)
-template <bool FX>
+// The split cascade's shape: CTA-record levels g, group levels gs, groups NG, binary
+// stages S and the cascade CTA's warps, read at run time (FIX = 0) or fixed at compile
+// time (FIX = 1) for the m = 65536-island filter of 4-island CTAs (16384 CTA records,
+// 128 groups of 128, 128-thread CTAs), whose loops then unroll.
+template <int FIX> struct SplitShape {
+    int g, gs, NG, S, nw;
+    __device__ explicit SplitShape(const StepParams& p)
+        : g(p.g), gs(p.gs), NG(p.NG), S(p.S), nw((int)(blockDim.x >> 5)) {}
+};
+template <> struct SplitShape<1> {
+    static constexpr int g = 2, gs = 7, NG = 128, S = 16, nw = 4;
+    __device__ explicit SplitShape(const StepParams&) {}
+};
+__host__ inline bool split_shape_fixed(const StepParams& p, int threads)
+{
+    return p.g == 2 && p.gs == 7 && p.NG == 128 && p.S == 16 && threads == 128;
+}
+
+template <bool FX, int FIX>
 __device__ void group_cascade(const StepParams& p, int c, int tp, int grp, unsigned char* sm)
 {
     using C = Casc<FX>;
     using V = typename C::V;
     using Qt = typename C::Qt;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int G = p.G, g = p.g, P = p.P, NG = p.NG, gs = p.gs, GS = 1 << gs;
+    const SplitShape<FIX> sp(p);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = sp.nw;
+    const int g = sp.g, G = 1 << g, NG = sp.NG, gs = sp.gs, GS = 1 << gs, P = NG << gs;
     const int h = g + gs;                    // level of the group root
     const int par = tp & 1;
     V* nd = reinterpret_cast<V*>(sm);                                             // [2 GS] tree nodes
@@ -1111,7 +1136,7 @@ __device__ void group_cascade(const StepParams& p, int c, int tp, int grp, unsig
             if (l < g) q[l] = __ldcg(&reinterpret_cast<const Qt*>(p.pq[par])[(r0 + tid) * 8 + l]);
     }
     const bool ok = has && pos_v(top) && e != INT_MIN;
-    const int em = block_max(ok ? e : INT_MIN, red);
+    const int em = block_max(ok ? e : INT_MIN, red, nw);
     const int sh = ok ? em - e : 0;
     // the records' levels below g, rescaled to 2^em
 #pragma unroll
@@ -1121,7 +1146,7 @@ __device__ void group_cascade(const StepParams& p, int c, int tp, int grp, unsig
             if (lane == 0) qr[warp * 4 + l] = x;
         }
     }
-    leaf_tree<FX>(ok ? C::rescale(top, sh) : (V)0, gs, nd, qw, Q, g);
+    leaf_tree<FX>(ok ? C::rescale(top, sh) : (V)0, gs, nd, qw, Q, g, nw);
     if (tid < g) {
         Qt acc = (Qt)0;
         for (int w = 0; w < nw; ++w) acc += qr[w * 4 + tid];
@@ -1129,7 +1154,7 @@ __device__ void group_cascade(const StepParams& p, int c, int tp, int grp, unsig
     }
     __syncthreads();
     V* gt = reinterpret_cast<V*>(p.gtr[par]) + ((size_t)c * NG + grp) * 2 * GS;
-    for (int i = tid; i < 2 * GS - 1; i += blockDim.x) gt[i] = nd[i];
+    for (int i = tid; i < 2 * GS - 1; i += 32 * nw) gt[i] = nd[i];
     Qt* gq = reinterpret_cast<Qt*>(p.gqs[par]) + ((size_t)c * NG + grp) * kGroupQ;
     if (tid < h) gq[tid] = Q[tid];
     if (tid == 0) p.ge[par][(size_t)c * NG + grp] = em;
@@ -1144,14 +1169,15 @@ __host__ __device__ inline size_t split_cascade_smem_bytes(const StepParams& p)
            + align16(sizeof(double) * (kMaxWarps * kGroupQ + kMaxStages + kMaxWarps + kMaxWarps * kGroupQ + 4));
 }
 
-template <bool FX>
+template <bool FX, int FIX>
 __device__ void top_cascade(const StepParams& p, int c, int tp, unsigned char* sm)
 {
     using C = Casc<FX>;
     using V = typename C::V;
     using Qt = typename C::Qt;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int g = p.g, P = p.P, NG = p.NG, gs = p.gs, GS = 1 << gs, S = p.S, m = p.m;
+    const SplitShape<FIX> sp(p);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = sp.nw;
+    const int g = sp.g, NG = sp.NG, gs = sp.gs, GS = 1 << gs, P = NG << gs, S = sp.S, m = 1 << S;
     const int h = g + gs, par = tp & 1;
     V* nd = reinterpret_cast<V*>(sm);                                             // [2 NG]
     double* rs = reinterpret_cast<double*>(sm + align16(sizeof(double) * 2 * NG));
@@ -1173,7 +1199,7 @@ __device__ void top_cascade(const StepParams& p, int c, int tp, unsigned char* s
 #pragma unroll
     for (int l = 0; l < kGroupQ; ++l) qg[l] = (has && l < h) ? __ldcg(&gq[l]) : (Qt)0;
     const bool ok = has && pos_v(r) && e != INT_MIN;
-    const int emax = block_max(ok ? e : INT_MIN, red);
+    const int emax = block_max(ok ? e : INT_MIN, red, nw);
     const int sh = ok ? emax - e : 0;
     const V leaf = ok ? C::rescale(r, sh) : (V)0;
     // stage 1 first: it needs only the total and level 0's sum of squares (ENF_1 =
@@ -1214,7 +1240,7 @@ __device__ void top_cascade(const StepParams& p, int c, int tp, unsigned char* s
             if (lane == 0) qr[warp * kGroupQ + l] = x;
         }
     }
-    leaf_tree<FX>(leaf, S - h, nd, qw, Q, h);
+    leaf_tree<FX>(leaf, S - h, nd, qw, Q, h, nw);
     if (tid < h) {
         Qt acc = (Qt)0;
         for (int w = 0; w < nw; ++w) acc += qr[w * kGroupQ + tid];
@@ -1241,7 +1267,7 @@ __device__ void top_cascade(const StepParams& p, int c, int tp, unsigned char* s
         }
     }
     V* ut = reinterpret_cast<V*>(p.utg) + (size_t)c * 2 * P;
-    for (int i = tid; i < 2 * NG - 1; i += blockDim.x) ut[i] = nd[i];
+    for (int i = tid; i < 2 * NG - 1; i += 32 * nw) ut[i] = nd[i];
 }
 
 enum { OP_STEP = 0, OP_PREPARE = 1, OP_FITS = 2, OP_PERSIST_GRID = 3, OP_PERSIST_CTA = 4, OP_CASCADE = 5,
@@ -1957,27 +1983,28 @@ __global__ void __launch_bounds__(kCascadeThreads) airpf_cascade_kernel(StepPara
 // Publication: every thread's stores, a CTA barrier, one thread's device-scope fence
 // and ticket; the last arrival fences before it reads.  The ticket wraps to zero by
 // itself (atomicInc) and the prologue clears it.
-template <typename R>
+template <typename R, int FIX = 0>
 __global__ void __launch_bounds__(512) airpf_group_cascade_kernel(StepParams p, int t)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int last;
-    const int c = blockIdx.x >> (p.S - p.g - p.gs), grp = blockIdx.x & (p.NG - 1);
+    const SplitShape<FIX> sp(p);
+    const int c = blockIdx.x >> (sp.S - sp.g - sp.gs), grp = blockIdx.x & (sp.NG - 1);
     if (p.active != nullptr && p.active[c] == 0) return;
     if (p.pdl) {                  // the records are the island-step kernel's output
         dependency_wait();
         allow_dependents();
     }
-    group_cascade<sizeof(R) == 4>(p, c, t, grp, smem);
+    group_cascade<sizeof(R) == 4, FIX>(p, c, t, grp, smem);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicInc(&p.tick[c], (unsigned)(p.NG - 1)) == (unsigned)(p.NG - 1);
+        last = atomicInc(&p.tick[c], (unsigned)(sp.NG - 1)) == (unsigned)(sp.NG - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    top_cascade<sizeof(R) == 4>(p, c, t, smem);
+    top_cascade<sizeof(R) == 4, FIX>(p, c, t, smem);
 }
 
 // All T+1 steps in one launch.  GRID: the filter spans several co-resident CTAs
@@ -2127,6 +2154,12 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         const size_t cs = split_cascade_smem_bytes(p);
         int tg = (1 << p.gs) > p.NG ? (1 << p.gs) : p.NG;
         if (tg < 32) tg = 32;
+        if (split_shape_fixed(p, tg)) {
+            if (p.pdl)
+                return launch_dependent(airpf_group_cascade_kernel<R, 1>, dim3(p.NG * p.B), dim3(tg), cs, stream, p, t);
+            airpf_group_cascade_kernel<R, 1><<<p.NG * p.B, tg, cs, stream>>>(p, t);
+            return cudaGetLastError();
+        }
         if (p.pdl) return launch_dependent(airpf_group_cascade_kernel<R>, dim3(p.NG * p.B), dim3(tg), cs, stream, p, t);
         airpf_group_cascade_kernel<R><<<p.NG * p.B, tg, cs, stream>>>(p, t);
         return cudaGetLastError();
