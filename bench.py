@@ -62,18 +62,19 @@ def ops_per_particle_step(model: str) -> float:
 # Figures from the committed ncu captures of the kernels named (set to None when the kernel
 # changes, until it is captured again): DRAM read + write per launch, issue-active fraction.
 NCU = {
-    "ngm_island_step": {"dram_bytes_per_launch": 93837312, "issue_active": 0.685,
+    "ngm_island_step": {"dram_bytes_per_launch": 94348032, "issue_active": 0.737,
                         "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, "
-                                  "airpf_step_kernel<float, NGM, 1, 4, false, 2> at steps 5 and 6, caches flushed"},
-    "sv_fused_step": {"dram_bytes_per_launch": 1163264, "issue_active": 0.219,
-                      "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, one "
-                                "launch of airpf_step_kernel<float, SV, 1, 4, false, 3>, caches flushed"},
-    "fp64_ngm_island_step": {"fp64_pipe": 0.857, "issue_active": 0.116,
+                                  "airpf_step_kernel<float, NGM, 1, 4, false, 2, 256> at steps 5 and 6, caches flushed"},
+    "sv_fused_step": {"dram_bytes_per_launch": 1155840, "issue_active": 0.437,
+                      "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum (caches flushed) and "
+                                "smsp__issue_active (warm caches, as in a pass), "
+                                "airpf_step_kernel<float, SV, 1, 4, false, 3, 256>"},
+    "fp64_ngm_island_step": {"fp64_pipe": 0.857, "issue_active": 0.104,
                              "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
-                                       "airpf_step_kernel<double, NGM, 1, 4, false, 2>"},
-    "fp64_sv_fused_step": {"fp64_pipe": 0.761, "issue_active": 0.103,
+                                       "airpf_step_kernel<double, NGM, 1, 4, false, 2, 256>"},
+    "fp64_sv_fused_step": {"fp64_pipe": 0.781, "issue_active": 0.098,
                            "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
-                                     "airpf_step_kernel<double, SV, 1, 4, false, 3>"},
+                                     "airpf_step_kernel<double, SV, 1, 4, false, 3, 256>"},
 }
 
 
@@ -428,14 +429,14 @@ def sv_leg(gp, torch, ws, chain, flush, peaks, peak_src, sms, n_fp32=20, n_fp64=
                                        prec="fp32", passes=5, flush=flush, chain=chain, launch="steps")
     step_us = 1e3 * res["fp32"]["ms_per_pass"] / T_OBS
     rf = alu_roofline("SV", N, step_us, sms, peaks, peak_src)
-    rf.update({"kernel": "airpf_step_kernel<float, SV, 1, 4, false, 3> (fused step: cascade + island work)",
+    rf.update({"kernel": "airpf_step_kernel<float, SV, 1, 4, false, 3, 256> (fused step: cascade + island work)",
                "launch_avg_source": "timed passes: pass time / T (one kernel per step and the gaps)",
                "algorithmic_bytes_per_launch": 8 * N,
                "traffic": NCU["sv_fused_step"]["dram_bytes_per_launch"],
                "ncu_issue_active": NCU["sv_fused_step"]["issue_active"], "ncu_source": NCU["sv_fused_step"]["source"],
                "event_nodes": {"step_kernel_us": isl, "ms_per_pass_with_event_nodes": pms}})
     res["roofline"] = rf
-    res["fp64"]["roofline"] = {"bound": "fp64", "kernel": "airpf_step_kernel<double, SV, 1, 4, false, 3>",
+    res["fp64"]["roofline"] = {"bound": "fp64", "kernel": "airpf_step_kernel<double, SV, 1, 4, false, 3, 256>",
                                "fp64_pipe_frac_ncu": NCU["fp64_sv_fused_step"]["fp64_pipe"],
                                "ncu_issue_active": NCU["fp64_sv_fused_step"]["issue_active"],
                                "ncu_source": NCU["fp64_sv_fused_step"]["source"],
@@ -579,7 +580,7 @@ def run_gpu(args) -> None:
                 "log_z_fp64": lz64.tolist(), "log_z_fp32_same_streams": lz32[:n64].tolist(),
                 "log_z_abs_diff_mean": float(np.mean(np.abs(lz32[:n64] - lz64))),
                 "log_z_fp32_sd_over_passes": float(lz32.std(ddof=1)) if lz32.size > 1 else None,
-                "roofline": {"bound": "fp64", "kernel": "airpf_step_kernel<double, NGM, 1, 4, false, 2>",
+                "roofline": {"bound": "fp64", "kernel": "airpf_step_kernel<double, NGM, 1, 4, false, 2, 256>",
                              "fp64_pipe_frac_ncu": NCU["fp64_ngm_island_step"]["fp64_pipe"],
                              "ncu_issue_active": NCU["fp64_ngm_island_step"]["issue_active"],
                              "ncu_source": NCU["fp64_ngm_island_step"]["source"]}}
@@ -600,8 +601,8 @@ def run_gpu(args) -> None:
     step_us = 1e3 * ms_step / T_OBS           # one time step: the island kernel, the cascade kernel and gaps
     roof = alu_roofline("NGM", N, step_us, sms, peaks, peak_src)
     roof.update({
-        "kernel": "airpf_step_kernel<float, NGM, 1, 4, false, 2> (split step: the island launch, then "
-                  "airpf_group_cascade_kernel<float>)" if f.launch_mode == 4 else "airpf_step_kernel (one time step)",
+        "kernel": "airpf_step_kernel<float, NGM, 1, 4, false, 2, 256> (split step: the island launch, then "
+                  "airpf_group_cascade_kernel<float, 1>)" if f.launch_mode == 4 else "airpf_step_kernel (one time step)",
         "launch_avg_source": "timed region: pass time / T (a step's island and cascade kernels and the gaps, so "
                              "the island kernel's own fraction is higher by its share of the step)",
         "algorithmic_bytes_per_launch": 8 * N,
