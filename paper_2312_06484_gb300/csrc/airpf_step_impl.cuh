@@ -2061,11 +2061,35 @@ static cudaError_t launch_dependent(K kernel, dim3 grid, dim3 block, size_t smem
     return cudaLaunchKernelEx(&cfg, kernel, p, t);
 }
 
-// The lean step kernels also come with the island size fixed at compile time for
-// the size of the workloads this library is tuned for: M = 256 particles, 4 a thread
-// (64 threads an island).
+// The lean step kernels also come with the island size fixed at compile time, for
+// islands of 4 particles a thread: M = 256 (64 threads an island) in both precisions and
+// every lean launch form; in FP32 also M = 128, 512 and 1024 (32, 128 and 256 threads)
+// for the fused (64-register) and split forms.  The FP64 steps are bound by the FP64
+// pipe, which the compile-time size does not relieve.
 constexpr int kFixedM = 256, kFixedPpt = 4;
-__host__ inline bool fixed_island(const StepParams& p) { return p.M == kFixedM && p.tpi == kFixedM / kFixedPpt; }
+__host__ inline bool fixed_island(const StepParams& p, int M)
+{
+    return p.M == M && p.tpi == (M / kFixedPpt < 32 ? 32 : M / kFixedPpt);
+}
+__host__ inline bool fixed_island(const StepParams& p) { return fixed_island(p, kFixedM); }
+
+// apply(kernel) to the fixed-size kernel of launch form LV for this context's island
+// size, if there is one (returns false otherwise)
+template <typename R, int MODEL, int DX, int PPT, int LV, typename F>
+__host__ bool with_fixed_kernel(const StepParams& p, F&& apply)
+{
+    if constexpr (PPT != kFixedPpt) {
+        return false;
+    } else {
+        if (fixed_island(p, 256)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 256>), true;
+        if constexpr (sizeof(R) == 4 && LV != 3) {
+            if (fixed_island(p, 128)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 128>), true;
+            if (fixed_island(p, 512)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 512>), true;
+            if (fixed_island(p, 1024)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 1024>), true;
+        }
+        return false;
+    }
+}
 
 template <typename R, int MODEL, int DX, int PPT>
 static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream, int op, int* fits)
@@ -2087,17 +2111,12 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 3>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-        if constexpr (PPT == kFixedPpt) {
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 1, kFixedM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 2, kFixedM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(airpf_step_kernel<R, MODEL, DX, PPT, false, 3, kFixedM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-        }
+        auto set_smem = [&](auto kernel) {
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        };
+        with_fixed_kernel<R, MODEL, DX, PPT, 1>(p, set_smem);
+        with_fixed_kernel<R, MODEL, DX, PPT, 2>(p, set_smem);
+        with_fixed_kernel<R, MODEL, DX, PPT, 3>(p, set_smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(airpf_persistent_kernel<R, MODEL, DX, PPT, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -2126,13 +2145,10 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         bool fixed_done = false;
-        if constexpr (PPT == kFixedPpt) {
-            if (e == cudaSuccess && fixed_island(p)) {
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per_sm, airpf_step_kernel<R, MODEL, DX, PPT, false, 3, kFixedM>, block, smem);
-                fixed_done = true;
-            }
-        }
+        if (e == cudaSuccess)
+            fixed_done = with_fixed_kernel<R, MODEL, DX, PPT, 3>(p, [&](auto kernel) {
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+            });
         if (e == cudaSuccess && !fixed_done)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, airpf_step_kernel<R, MODEL, DX, PPT, false, 3>,
                                                               block, smem);
@@ -2184,13 +2200,12 @@ static cudaError_t launch_typed(const StepParams& p, int t, cudaStream_t stream,
         kernel<<<grid, block, smem, stream>>>(p, t);
         return cudaGetLastError();
     };
-    if constexpr (PPT == kFixedPpt) {
-        if (!rec && fixed_island(p)) {       // islands of kFixedM particles: the compile-time size
-            if (p.fused)
-                return p.wide ? go(airpf_step_kernel<R, MODEL, DX, PPT, false, 3, kFixedM>)
-                              : go(airpf_step_kernel<R, MODEL, DX, PPT, false, 1, kFixedM>);
-            if (p.split) return go(airpf_step_kernel<R, MODEL, DX, PPT, false, 2, kFixedM>);
-        }
+    if (!rec) {                               // the compile-time island size, where there is one
+        cudaError_t r = cudaSuccess;
+        auto run = [&](auto kernel) { r = go(kernel); };
+        if (p.fused && p.wide && with_fixed_kernel<R, MODEL, DX, PPT, 3>(p, run)) return r;
+        if (p.fused && !p.wide && with_fixed_kernel<R, MODEL, DX, PPT, 1>(p, run)) return r;
+        if (p.split && with_fixed_kernel<R, MODEL, DX, PPT, 2>(p, run)) return r;
     }
     if (!rec && p.fused)
         return p.wide ? go(airpf_step_kernel<R, MODEL, DX, PPT, false, 3>) : go(airpf_step_kernel<R, MODEL, DX, PPT, false, 1>);

@@ -19,6 +19,9 @@ CASES = [  # model, theta, observations, m, M, launch, mode
     (synth.MODEL_NGM, synth.NGM_THETA, synth.ngm_observations(24, seed=5), 2048, 32, "split", "adaptive"),
     (synth.MODEL_NGM, synth.NGM_THETA, synth.ngm_observations(16, seed=5), 1024, 64, "split", "always"),
     (synth.MODEL_SV, synth.SV_THETA, synth.sv_observations(20, seed=2), 256, 64, "steps", "adaptive"),
+    # M = 256: the lean kernels with the island size fixed at compile time
+    (synth.MODEL_NGM, synth.NGM_THETA, synth.ngm_observations(12, seed=5), 2048, 256, "split", "adaptive"),
+    (synth.MODEL_SV, synth.SV_THETA, synth.sv_observations(12, seed=2), 512, 256, "steps", "always"),
 ]
 
 
