@@ -312,8 +312,8 @@ def grad_leg(gp, torch, ws: int, passes: int = 2) -> dict:
            "forward_ms": ms_fwd, "backward_over_forward": (ms - ms_fwd) / ms_fwd, "ckpt": 10,
            "roofline": {"bound": "latency", "kernel": "grad_island_kernel<float, LGSSM, 8>",
                         "backward_ms_per_step": (ms - ms_fwd) / T, "frac": None,
-                        "note": "latency and atomics: issue active 37-38%, long and short scoreboard stalls "
-                                "(ncu capture of the backward island kernel)"},
+                        "note": "latency: issue active 59-60%, long_scoreboard the top stall (gathers by parent, "
+                                "vector atomics to the parents), ncu metrics of grad_island_kernel<float, LGSSM, 8>"},
            "precision": "fp32", "score_norm": float(out["score"].norm()), "grad_norm": float(out["grad"].norm())}
     f.close()
     return res
