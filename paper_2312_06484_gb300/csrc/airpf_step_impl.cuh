@@ -1666,7 +1666,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
     for (int r = 0; r < PPT; ++r) {
         Cdf w = 0;
         if (alive && lv[r] > (R)(-INFINITY)) {
-            if constexpr (!FX) w = exp(lv[r] - mx);
+            if constexpr (!FX) w = exp_tab(lv[r] - mx);
             else w = __float2uint_rn(__expf(lv[r] - mx) * p.cdf_scale);
         }
         run_sum += w;
