@@ -91,8 +91,11 @@ __device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, float& z0,
 __device__ __forceinline__ double exp_tab(double x)
 {
     if (!(fabs(x) <= 708.0)) return exp(x);
-    const int n = __double2int_rn(x * kExpInvLn2x64);
-    const double dn = (double)n;
+    // n = nearest integer to 64 x / ln 2, in the low bits of a sum with 1.5 2^52 (one
+    // rounding, no conversion instructions)
+    const double t = fma(x, kExpInvLn2x64, 0x1.8p52);
+    const double dn = t - 0x1.8p52;
+    const int n = __double2loint(t);
     double r = fma(-dn, kExpLn2d64Hi, x);
     r = fma(-dn, kExpLn2d64Lo, r);
     double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
