@@ -431,11 +431,11 @@ int32_t airpf_launch_mode(const airpf_ctx* ctx);
  * AIRPF_ERR_UNSUPPORTED for other launch modes. */
 airpf_status airpf_debug_inject(airpf_ctx* ctx, int32_t what);
 
-/* Test hook, no counterpart in the paper: d_y[i] = the exponential of d_x[i] as the FP64 path
- * computes it (a table-driven double exponential), for i < n; device arrays of n doubles,
- * asynchronous on `stream` (a cudaStream_t, NULL for the default stream).  AIRPF_ERR_ARG for
- * n < 0 or a NULL array with n > 0. */
-airpf_status airpf_debug_exp(const double* d_x, double* d_y, int64_t n, void* stream);
+/* Test hook, no counterpart in the paper: d_y[i] = f(d_x[i]) for i < n as the FP64 path
+ * computes f (table-driven double functions): fn = 0 the exponential, fn = 1 the natural
+ * logarithm.  Device arrays of n doubles, asynchronous on `stream` (a cudaStream_t, NULL for
+ * the default stream).  AIRPF_ERR_ARG for another fn, n < 0 or a NULL array with n > 0. */
+airpf_status airpf_debug_math(int32_t fn, const double* d_x, double* d_y, int64_t n, void* stream);
 
 /* Number of model parameters for (model, dx); 0 for an unknown model. */
 int32_t airpf_theta_dim(int32_t model, int32_t dx);

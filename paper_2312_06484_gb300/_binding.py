@@ -64,7 +64,7 @@ SIGNATURES = {
     "airpf_moments": (c_int32, [c_void_p, c_void_p]),
     "airpf_kernel_times": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "airpf_debug_inject": (c_int32, [c_void_p, c_int32]),
-    "airpf_debug_exp": (c_int32, [c_void_p, c_void_p, ctypes.c_int64, c_void_p]),
+    "airpf_debug_math": (c_int32, [c_int32, c_void_p, c_void_p, ctypes.c_int64, c_void_p]),
     "airpf_theta_dim": (c_int32, [c_int32, c_int32]),
     "airpf_last_launch_count": (c_int64, [c_void_p]),
     "airpf_last_error": (ctypes.c_char_p, [c_void_p]),

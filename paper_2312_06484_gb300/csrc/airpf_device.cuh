@@ -8,6 +8,7 @@
 #pragma once
 #include <cstdint>
 #include "airpf_exp_table.h"
+#include "airpf_log_table.h"
 #include <cmath>
 
 namespace airpf {
@@ -58,30 +59,6 @@ struct Stream {
 
 __device__ __forceinline__ double unif_f64(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
 
-// Box-Muller pair from two words: r = sqrt(-2 ln u0), angle 2 pi u1.
-__device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, double& z0, double& z1)
-{
-    const double rad = sqrt(-2.0 * log(unif_f64(w0)));
-    const double ang = (2.0 * 3.141592653589793) * unif_f64(w1);
-    double s, c;
-    sincos(ang, &s, &c);
-    z0 = rad * c;
-    z1 = rad * s;
-}
-
-// float version on the SFU: cos(2 pi u) = -cos(pi (2u - 1)), same for sin.
-__device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, float& z0, float& z1)
-{
-    const float u0 = fmaf((float)w0, 0x1p-32f, 0x1p-33f);
-    const float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
-    const float rad = r2 * rsqrtf(r2);
-    const float a = fmaf((float)w1, 0x1p-31f, 0x1p-32f) - 1.0f;
-    float s, c;
-    __sincosf(3.14159265358979f * a, &s, &c);
-    z0 = -rad * c;
-    z1 = -rad * s;
-}
-
 // The double exponential of the FP64 path, table-driven (Tang, ACM TOMS 15(2), 1989):
 // x = (64 k + j) ln 2 / 64 + r with |r| <= ln 2 / 128, exp(x) = 2^k 2^(j/64) e^r, e^r - 1 by
 // its Taylor polynomial through r^5 (the next term is below 0.2 ulp at |r| <= ln 2 / 128).
@@ -107,11 +84,63 @@ __device__ __forceinline__ double exp_tab(double x)
     return __longlong_as_double(__double_as_longlong(v) + ((long long)(n >> 6) << 52));
 }
 
+// The double logarithm of the FP64 path, table-driven (Tang, ACM TOMS 16(4), 1990): x = 2^e m,
+// m in [1, 2), F = 1 + j/128 the nearest 128th to m, f = m - F (exact), s = f / F taken as
+// f (1/F) with the reciprocal from the table, log x = e ln 2 + log F + log(1 + s) with
+// log(1 + s) by its Taylor polynomial through s^7 (|s| <= 2^-8), e ln 2 + log F summed
+// exactly from parts on a common grid.  At most about 1 ulp from the exact value; zero,
+// negative, subnormal and non-finite arguments defer to the library function.
+__device__ __forceinline__ double log_tab(double x)
+{
+    if (!(x >= 0x1p-1022 && x <= 0x1.fffffffffffffp+1023)) return log(x);
+    const long long b = __double_as_longlong(x);
+    const int e = (int)(b >> 52) - 1023;
+    const long long mb = b & 0x000FFFFFFFFFFFFFLL;
+    const double m = __longlong_as_double(mb | 0x3FF0000000000000LL);
+    const int j = (int)(((mb >> 44) + 1) >> 1);                   // nearest 128th: 0 .. 128
+    const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 45));
+    const double s = (m - F) * __ldg(&kLogInvF[j]);
+    double q = fma(s, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(s, q, 0.2);
+    q = fma(s, q, -0.25);
+    q = fma(s, q, 1.0 / 3.0);
+    q = fma(s, q, -0.5);
+    const double p = fma(s * s, q, s);
+    const double de = (double)e;
+    const double hi = fma(de, kLogLn2Hi, __ldg(&kLogFHi[j]));       // exact
+    const double lo = fma(de, kLogLn2Lo, __ldg(&kLogFLo[j]));
+    return hi + (lo + p);
+}
+
+// Box-Muller pair from two words: r = sqrt(-2 ln u0), angle 2 pi u1.
+__device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, double& z0, double& z1)
+{
+    const double rad = sqrt(-2.0 * log_tab(unif_f64(w0)));
+    const double ang = (2.0 * 3.141592653589793) * unif_f64(w1);
+    double s, c;
+    sincos(ang, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+
+// float version on the SFU: cos(2 pi u) = -cos(pi (2u - 1)), same for sin.
+__device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, float& z0, float& z1)
+{
+    const float u0 = fmaf((float)w0, 0x1p-32f, 0x1p-33f);
+    const float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
+    const float rad = r2 * rsqrtf(r2);
+    const float a = fmaf((float)w1, 0x1p-31f, 0x1p-32f) - 1.0f;
+    float s, c;
+    __sincosf(3.14159265358979f * a, &s, &c);
+    z0 = -rad * c;
+    z1 = -rad * s;
+}
+
 template <typename R> __device__ __forceinline__ R fexp(R v);
 template <> __device__ __forceinline__ double fexp<double>(double v) { return exp_tab(v); }
 template <> __device__ __forceinline__ float fexp<float>(float v) { return __expf(v); }
 template <typename R> __device__ __forceinline__ R flog(R v);
-template <> __device__ __forceinline__ double flog<double>(double v) { return log(v); }
+template <> __device__ __forceinline__ double flog<double>(double v) { return log_tab(v); }
 template <> __device__ __forceinline__ float flog<float>(float v) { return __logf(v); }
 template <typename R> __device__ __forceinline__ R fsqrt(R v);
 template <> __device__ __forceinline__ double fsqrt<double>(double v) { return sqrt(v); }

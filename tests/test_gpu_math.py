@@ -1,0 +1,69 @@
+"""The FP64 path's table-driven double exponential and logarithm (airpf_debug_math) against the
+host library's (numpy) and the device library's (torch on CUDA): within 2 ulp where the tables
+are used, and the library's values outside that range (infinities, NaN, zero, subnormals)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+EXP, LOG = 0, 1
+
+
+def _tab(fn: int, x: np.ndarray) -> np.ndarray:
+    from paper_2312_06484_gb300 import _binding
+    lib = _binding.load()
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(xd)
+    _binding.check(lib.airpf_debug_math(fn, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()),
+                                        xd.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+def _ulps(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Distance in units in the last place (same-sign values)."""
+    return np.abs(a.view(np.int64) - b.view(np.int64))
+
+
+def test_exp_within_two_ulp_of_the_library_exponentials(gpu_lib):
+    rng = np.random.default_rng(7)
+    ln2_64 = np.log(2.0) / 64
+    x = np.concatenate([rng.uniform(-708.0, 708.0, 2_000_000), rng.uniform(-1.0, 1.0, 1_000_000),
+                        rng.uniform(-40.0, 0.0, 1_000_000),            # the weights' range
+                        np.arange(-20000, 20000) * ln2_64,             # table boundaries
+                        np.arange(-20000, 20000) * ln2_64 + ln2_64 / 2,
+                        [0.0, -0.0, 1e-300, -1e-300, 708.0, -708.0]])
+    got = _tab(EXP, x)
+    assert _ulps(got, np.exp(x)).max() <= 2
+    assert _ulps(got, torch.exp(torch.tensor(x, device="cuda")).cpu().numpy()).max() <= 2
+
+
+def test_log_within_two_ulp_of_the_library_logarithms(gpu_lib):
+    rng = np.random.default_rng(8)
+    w = rng.integers(0, 2 ** 32, 2_000_000, dtype=np.uint64)
+    u = (w.astype(np.float64) + 0.5) * 2.0 ** -32                       # the Box-Muller words
+    edge = (np.array([0, 1, 2, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 2, 2 ** 32 - 1], dtype=np.float64) + 0.5) * 2.0 ** -32
+    near1 = 1.0 + rng.uniform(-1e-3, 1e-3, 500_000)
+    wide = np.exp(rng.uniform(-700.0, 700.0, 1_000_000))
+    grid = 1.0 + np.arange(0, 257) / 256.0                              # the table points and midpoints
+    x = np.concatenate([u, edge, near1, wide, grid, grid / 2, [1.0, 2.0, 0.5, np.e, 2.2250738585072014e-308]])
+    got = _tab(LOG, x)
+    host = np.log(x)
+    dev = torch.log(torch.tensor(x, device="cuda")).cpu().numpy()
+    pos, neg = host > 0, host < 0                                       # compare same-sign values
+    for ref in (host, dev):
+        assert _ulps(got[pos], ref[pos]).max() <= 2 and _ulps(-got[neg], -ref[neg]).max() <= 2
+    assert np.all(got[host == 0] == 0)
+
+
+def test_outside_the_table_ranges_they_are_the_library_functions(gpu_lib):
+    x = np.array([709.5, 710.0, 1e6, np.inf, -709.0, -740.0, -745.2, -746.0, -1e6, -np.inf, np.nan])
+    got = _tab(EXP, x)
+    np.testing.assert_array_equal(got, torch.exp(torch.tensor(x, device="cuda")).cpu().numpy())
+    assert np.isnan(got[-1]) and got[3] == np.inf and got[9] == 0.0
+    x = np.array([0.0, -0.0, -1.0, 1e-310, 5e-324, np.inf, np.nan])
+    got = _tab(LOG, x)
+    np.testing.assert_array_equal(got, torch.log(torch.tensor(x, device="cuda")).cpu().numpy())
+    assert got[0] == -np.inf and np.isnan(got[2]) and got[5] == np.inf
