@@ -69,10 +69,10 @@ NCU = {
                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum (caches flushed) and "
                                 "smsp__issue_active (warm caches, as in a pass), "
                                 "airpf_step_kernel<float, SV, 1, 4, false, 3, 256>"},
-    "fp64_ngm_island_step": {"fp64_pipe": 0.857, "issue_active": 0.104,
+    "fp64_ngm_island_step": {"fp64_pipe": 0.858, "issue_active": 0.107,
                              "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
                                        "airpf_step_kernel<double, NGM, 1, 4, false, 2, 256>"},
-    "fp64_sv_fused_step": {"fp64_pipe": 0.781, "issue_active": 0.098,
+    "fp64_sv_fused_step": {"fp64_pipe": 0.761, "issue_active": 0.103,
                            "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
                                      "airpf_step_kernel<double, SV, 1, 4, false, 3, 256>"},
 }
