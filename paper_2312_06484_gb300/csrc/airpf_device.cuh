@@ -9,6 +9,7 @@
 #include <cstdint>
 #include "airpf_exp_table.h"
 #include "airpf_log_table.h"
+#include "airpf_sincos_table.h"
 #include <cmath>
 
 namespace airpf {
@@ -112,13 +113,36 @@ __device__ __forceinline__ double log_tab(double x)
     return hi + (lo + p);
 }
 
+// sin(2 pi v) and cos(2 pi v) for v in [0, 1], table-driven: 2 pi v = 2 pi j / 256 + x with
+// j the nearest 256th (exact reduction: v has at most 33 significant bits here) and
+// |x| <= pi / 256, the angle-addition formulas with the table's sin and cos of 2 pi j / 256
+// and Taylor polynomials of sin x through x^7 and cos x through x^6 (the next terms are below
+// 1e-19).  Within a few 1e-16 of the exact values; other v defer to the library's sincos.
+__device__ __forceinline__ void sincos2pi_tab(double v, double* s, double* c)
+{
+    if (!(v >= 0.0 && v <= 1.0)) {
+        sincos(6.283185307179586 * v, s, c);
+        return;
+    }
+    const double t = v * 256.0;
+    const double tj = fma(1.0, t, 0x1.8p52);                        // nearest integer in the low bits
+    const double f = t - (tj - 0x1.8p52);
+    const int j = __double2loint(tj) & 255;
+    const double x = f * kTwoPiDiv256;
+    const double x2 = x * x;
+    const double cx = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    const double sx = fma(x * x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), x);
+    const double sj = __ldg(&kSin256[j]), cj = __ldg(&kCos256[j]);
+    *s = fma(sj, cx, cj * sx);
+    *c = fma(cj, cx, -(sj * sx));
+}
+
 // Box-Muller pair from two words: r = sqrt(-2 ln u0), angle 2 pi u1.
 __device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, double& z0, double& z1)
 {
     const double rad = sqrt(-2.0 * log_tab(unif_f64(w0)));
-    const double ang = (2.0 * 3.141592653589793) * unif_f64(w1);
     double s, c;
-    sincos(ang, &s, &c);
+    sincos2pi_tab(unif_f64(w1), &s, &c);
     z0 = rad * c;
     z1 = rad * s;
 }

@@ -204,18 +204,27 @@ cudaError_t launch_set_run(RunParams* d_run, uint32_t iter, uint32_t chain0, cud
     return cudaGetLastError();
 }
 
-// the FP64 path's double functions over an array (a test hook): 0 exp, 1 log
+// the FP64 path's double functions over an array (a test hook): 0 exp, 1 log,
+// 2 sin(2 pi x), 3 cos(2 pi x)
 __global__ void math_tab_kernel(int fn, const double* x, double* y, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = fn == 0 ? exp_tab(x[i]) : log_tab(x[i]);
+    {
+        if (fn == 0) y[i] = exp_tab(x[i]);
+        else if (fn == 1) y[i] = log_tab(x[i]);
+        else {
+            double sv, cv;
+            sincos2pi_tab(x[i], &sv, &cv);
+            y[i] = fn == 2 ? sv : cv;
+        }
+    }
 }
 
 }  // namespace airpf
 
 extern "C" airpf_status airpf_debug_math(int32_t fn, const double* d_x, double* d_y, int64_t n, void* stream)
 {
-    if ((fn != 0 && fn != 1) || n < 0 || (n > 0 && (!d_x || !d_y))) return AIRPF_ERR_ARG;
+    if (fn < 0 || fn > 3 || n < 0 || (n > 0 && (!d_x || !d_y))) return AIRPF_ERR_ARG;
     if (n == 0) return AIRPF_OK;
     const int64_t blocks64 = (n + 255) / 256;
     const int blocks = (int)(blocks64 < 4096 ? blocks64 : 4096);

@@ -1,6 +1,9 @@
-"""The FP64 path's table-driven double exponential and logarithm (airpf_debug_math) against the
-host library's (numpy) and the device library's (torch on CUDA): within 2 ulp where the tables
-are used, and the library's values outside that range (infinities, NaN, zero, subnormals)."""
+"""The FP64 path's table-driven double exponential, logarithm and Box-Muller sine and cosine
+(airpf_debug_math) against the host library's (numpy) and the device library's (torch on
+CUDA): the exponential and logarithm within 2 ulp where the tables are used and the library's
+values outside that range (infinities, NaN, zero, subnormals); sin and cos of 2 pi v within a
+few 1e-16 of an extended-precision reference (2 ulp where |value| >= 1/4), exact at the
+quarter turns."""
 import ctypes
 
 import numpy as np
@@ -8,7 +11,7 @@ import pytest
 import torch
 
 pytestmark = pytest.mark.gpu
-EXP, LOG = 0, 1
+EXP, LOG, SIN2PI, COS2PI = 0, 1, 2, 3
 
 
 def _tab(fn: int, x: np.ndarray) -> np.ndarray:
@@ -67,3 +70,25 @@ def test_outside_the_table_ranges_they_are_the_library_functions(gpu_lib):
     got = _tab(LOG, x)
     np.testing.assert_array_equal(got, torch.log(torch.tensor(x, device="cuda")).cpu().numpy())
     assert got[0] == -np.inf and np.isnan(got[2]) and got[5] == np.inf
+
+
+def test_sin_cos_of_two_pi_v(gpu_lib):
+    rng = np.random.default_rng(9)
+    w = rng.integers(0, 2 ** 32, 1_000_000, dtype=np.uint64)
+    v = (w.astype(np.float64) + 0.5) * 2.0 ** -32                       # the Box-Muller words
+    grid = np.arange(0, 513) / 512.0                                    # table points and midpoints
+    v = np.concatenate([v, grid, [2.0 ** -33, 1 - 2.0 ** -33]])
+    # reference in extended precision: 2 pi as a double-double, the product and sine in long double
+    two_pi = np.longdouble(6.283185307179586) + np.longdouble(2.4492935982947064e-16)
+    ang = v.astype(np.longdouble) * two_pi
+    s, c = _tab(SIN2PI, v), _tab(COS2PI, v)
+    for got, ref in ((s, np.sin(ang)), (c, np.cos(ang))):
+        err = np.abs(got.astype(np.longdouble) - ref).astype(np.float64)
+        assert err.max() <= 3.4e-16                                     # a few 1e-16 absolute
+        big = np.abs(ref) >= 0.25
+        assert np.all(err[big] <= 2 * np.spacing(np.abs(ref[big]).astype(np.float64)))   # 2 ulp
+    # and near the host library's values (whose argument 2 pi v is itself rounded)
+    assert np.abs(s - np.sin(2 * np.pi * v)).max() <= 1e-15 and np.abs(c - np.cos(2 * np.pi * v)).max() <= 1e-15
+    x = np.array([0.0, 0.25, 0.5, 0.75, 1.0])
+    np.testing.assert_array_equal(_tab(SIN2PI, x), [0.0, 1.0, 0.0, -1.0, 0.0])
+    np.testing.assert_array_equal(_tab(COS2PI, x), [1.0, 0.0, -1.0, 0.0, 1.0])

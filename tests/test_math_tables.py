@@ -2,7 +2,8 @@
 are what their generators write; the exponential's table holds 2^(j/64) to the nearest double
 and its split of ln 2 / 64 is exact when multiplied by any |n| < 2^17; the logarithm's table
 holds 1/F_j to the nearest double and log F_j as an exact sum of a part on the grid 2^-42 and
-the rest, with F_128 = 2 split like ln 2."""
+the rest, with F_128 = 2 split like ln 2; the sine and cosine tables hold sin and cos of
+2 pi j / 256, exact at the multiples of pi / 2."""
 import os
 import subprocess
 import sys
@@ -89,3 +90,25 @@ def test_log_tables():
     assert t["kLogFHi"][0] == 0.0 and t["kLogFLo"][0] == 0.0
     assert (Fraction(t["kLogLn2Hi"]) / grid).denominator == 1
     assert abs(t["kLogLn2Hi"] + t["kLogLn2Lo"] - np.log(2.0)) < 1e-17
+
+
+def test_sincos_header_is_the_generator_output():
+    pytest.importorskip("mpmath")
+    out = subprocess.run([sys.executable, "gen_sincos_table.py"], cwd=CSRC, capture_output=True, text=True,
+                         check=True)
+    assert out.stdout == open(os.path.join(CSRC, "airpf_sincos_table.h")).read()
+
+
+def test_sincos_tables():
+    text = open(os.path.join(CSRC, "airpf_sincos_table.h")).read()
+    tabs = {}
+    for name in ("kSin256", "kCos256"):
+        start = text.index("{", text.index(name + "[256]")) + 1
+        body = " ".join(ln.split("//")[0] for ln in text[start:text.index("}", start)].splitlines())
+        tabs[name] = np.array([float.fromhex(t) for t in body.split(",") if t.strip()])
+    j = np.arange(256)
+    assert np.abs(tabs["kSin256"] - np.sin(2 * np.pi * j / 256)).max() < 1e-15   # numpy rounds the angle
+    assert np.abs(tabs["kCos256"] - np.cos(2 * np.pi * j / 256)).max() < 1e-15
+    assert tabs["kSin256"][0] == 0 and tabs["kSin256"][128] == 0 and tabs["kSin256"][64] == 1
+    assert tabs["kCos256"][64] == 0 and tabs["kCos256"][192] == 0 and tabs["kCos256"][128] == -1
+    assert np.all(tabs["kSin256"][1:128] > 0) and np.all(tabs["kSin256"][129:] < 0)
