@@ -69,10 +69,10 @@ NCU = {
                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum (caches flushed) and "
                                 "smsp__issue_active (warm caches, as in a pass), "
                                 "airpf_step_kernel<float, SV, 1, 4, false, 3, 256>"},
-    "fp64_ngm_island_step": {"fp64_pipe": 0.858, "issue_active": 0.107,
+    "fp64_ngm_island_step": {"fp64_pipe": 0.860, "issue_active": 0.107,
                              "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
                                        "airpf_step_kernel<double, NGM, 1, 4, false, 2, 256>"},
-    "fp64_sv_fused_step": {"fp64_pipe": 0.761, "issue_active": 0.103,
+    "fp64_sv_fused_step": {"fp64_pipe": 0.749, "issue_active": 0.102,
                            "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
                                      "airpf_step_kernel<double, SV, 1, 4, false, 3, 256>"},
 }
@@ -660,6 +660,45 @@ def run_gpu(args) -> None:
         dist.destroy_process_group()
 
 
+def run_stepwise_times() -> None:
+    """The m = 65536 x M = 256 NGM pass on a T = 200 series, once from its CUDA graph and once
+    step by step through the stepwise ABI with CUDA events around each island and cascade
+    launch (plain stream order): how much of the cascade the graph hides."""
+    import torch
+    import paper_2312_06484_gb300 as gp
+    T = 200
+    y = torch.tensor(synth.ngm_observations(T, seed=5), device="cuda")
+    th = torch.tensor(synth.NGM_THETA[None, :], device="cuda")
+    f = gp.AIRPF(synth.MODEL_NGM, m=M_ISL, M=M_PART, T=T, B=1, mode="adaptive", tau=TAU, precision="fp32", seed=1)
+    for w in range(2):
+        f.run(th, y, iter=w)
+    f.sync()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0, e1 = ev(), ev()
+    e0.record(f.stream)
+    f.run(th, y, iter=7)
+    e1.record(f.stream)
+    f.sync()
+    f.step_begin(th, y, iter=7)
+    marks = []
+    for t in range(1, T + 1):
+        a, b, c = ev(), ev(), ev()
+        a.record(f.stream)
+        f.step_islands(t)
+        b.record(f.stream)
+        f.step_cascade(t)
+        c.record(f.stream)
+        marks.append((a, b, c))
+    f.step_end()
+    f.sync()
+    isl = [a.elapsed_time(b) * 1e3 for a, b, _ in marks[1:]]          # steps 2..T
+    cas = [b.elapsed_time(c) * 1e3 for _, b, c in marks[1:-1]]
+    print(json.dumps({"profile_case": "ngm_stepwise", "T": T, "graph_us_per_step": e0.elapsed_time(e1) * 1e3 / T,
+                      "island_us_mean": sum(isl) / len(isl), "island_us_min": min(isl),
+                      "cascade_us_mean": sum(cas) / len(cas), "cascade_us_min": min(cas)}), flush=True)
+    f.close()
+
+
 def run_profile_case(args) -> None:
     """One workload for a profiler capture (T = 20): the m = 65536 x M = 256 NGM pass (split
     steps; FP32 or FP64), the m = 1024 x M = 256 SV pass (fused steps; FP32 or FP64), or the
@@ -715,7 +754,8 @@ def main():
     ap.add_argument("--no-ngm", action="store_true", help="skip the NGM particle-count sweep")
     ap.add_argument("--no-sv", action="store_true", help="skip the stochastic-volatility leg")
     ap.add_argument("--no-changepoint", action="store_true", help="skip the change-point PMMH leg")
-    ap.add_argument("--profile-case", choices=["ngm256", "ngm256_fp64", "sv", "sv_fp64", "grad"], default=None,
+    ap.add_argument("--profile-case", choices=["ngm256", "ngm256_fp64", "sv", "sv_fp64", "grad", "ngm_stepwise"],
+                    default=None,
                     help="run one small workload for a profiler capture instead of the bench line")
     ap.add_argument("--launch", default="auto", choices=["auto", "steps", "split", "grid"])
     ap.add_argument("--ppt", type=int, default=0, help="particles per thread (0: automatic)")
@@ -725,6 +765,8 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile_case == "ngm_stepwise":
+        run_stepwise_times()
     elif args.profile_case:
         run_profile_case(args)
     else:
