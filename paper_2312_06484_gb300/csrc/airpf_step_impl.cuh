@@ -575,15 +575,19 @@ __device__ void own_outputs(const BlockSums<FX>& bs, const Stream& st, int ss, c
 
 // OWN: the result goes to the calling CTA's own islands (fused steps), so the
 // code that writes it for the next step's CTAs is compiled out
-template <bool FX, bool OWN = false>
+// FP: the filter's shape fixed at compile time (FP = 1: m = 1024 islands in 256 CTAs of
+// 4 islands and 256 threads, the fused shape of the 1024 x 256 workload) or read at run
+// time (FP = 0); the loops over the records then unroll.
+template <bool FX, bool OWN = false, int FP = 0>
 __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st, double* raw,
                             const CascadeOwn* own = nullptr, bool records = true)
 {
     using C = Casc<FX>;
     using V = typename C::V;
     using Qt = typename C::Qt;
-    const int m = p.m, S = p.S, P = p.P, G = p.G, g = p.g, SU = S - g;
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    const int m = FP ? 1024 : p.m, S = FP ? 10 : p.S, P = FP ? 256 : p.P, G = FP ? 4 : p.G, g = FP ? 2 : p.g;
+    const int SU = S - g;
+    const int tid = threadIdx.x, nthr = FP ? 256 : (int)blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
     const int* pe = p.pe[tp & 1] + (size_t)c * P;
     const V* pt = reinterpret_cast<const V*>(p.pt[tp & 1]) + (size_t)c * P * 2 * G;
     const Qt* pq = reinterpret_cast<const Qt*>(p.pq[tp & 1]) + (size_t)c * P * 8;
@@ -1449,7 +1453,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         // this CTA runs the cascade of step t-1 itself, from every CTA record of
         // the filter (the first CTA also writes log Z and the run's records)
         const CascadeOwn own{k0, own_w, own_we, own_src};
-        cascade_all<FX, true>(p, c, t - 1, st, tree, &own, designated);
+        if (MC == 256 && p.m == 1024 && p.G == 4 && blockDim.x == 256)   // the fixed shape (uniform)
+            cascade_all<FX, true, 1>(p, c, t - 1, st, tree, &own, designated);
+        else
+            cascade_all<FX, true>(p, c, t - 1, st, tree, &own, designated);
     } else if (split_path) {
         // the cascade kernel of step t-1 left s*, the largest exponent, the group
         // records and the top tree; this CTA derives its islands' weights and walks.
