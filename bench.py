@@ -65,7 +65,7 @@ NCU = {
     "ngm_island_step": {"dram_bytes_per_launch": 94348032, "issue_active": 0.737,
                         "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, "
                                   "airpf_step_kernel<float, NGM, 1, 4, false, 2, 256> at steps 5 and 6, caches flushed"},
-    "sv_fused_step": {"dram_bytes_per_launch": 1155840, "issue_active": 0.437,
+    "sv_fused_step": {"dram_bytes_per_launch": 1156352, "issue_active": 0.397,
                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum (caches flushed) and "
                                 "smsp__issue_active (warm caches, as in a pass), "
                                 "airpf_step_kernel<float, SV, 1, 4, false, 3, 256>"},

@@ -61,28 +61,26 @@ struct Stream {
 __device__ __forceinline__ double unif_f64(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
 
 // The double exponential of the FP64 path, table-driven (Tang, ACM TOMS 15(2), 1989):
-// x = (64 k + j) ln 2 / 64 + r with |r| <= ln 2 / 128, exp(x) = 2^k 2^(j/64) e^r, e^r - 1 by
-// its Taylor polynomial through r^5 (the next term is below 0.2 ulp at |r| <= ln 2 / 128).
-// About half the FP64-pipe instructions of the library function, at most about 1 ulp from
-// the exact value; outside |x| <= 708 (overflow, subnormal results, infinities, NaN) it
-// defers to the library function.
+// x = (256 k + j) ln 2 / 256 + r with |r| <= ln 2 / 512, exp(x) = 2^k 2^(j/256) e^r, e^r - 1
+// by its Taylor polynomial through r^4 (the next term is below 0.2 ulp at |r| <= ln 2 / 512).
+// At most about 1 ulp from the exact value; outside |x| <= 708 (overflow, subnormal results,
+// infinities, NaN) it defers to the library function.
 __device__ __forceinline__ double exp_tab(double x)
 {
     if (!(fabs(x) <= 708.0)) return exp(x);
-    // n = nearest integer to 64 x / ln 2, in the low bits of a sum with 1.5 2^52 (one
+    // n = nearest integer to 256 x / ln 2, in the low bits of a sum with 1.5 2^52 (one
     // rounding, no conversion instructions)
-    const double t = fma(x, kExpInvLn2x64, 0x1.8p52);
+    const double t = fma(x, kExpInvLn2xN, 0x1.8p52);
     const double dn = t - 0x1.8p52;
     const int n = __double2loint(t);
-    double r = fma(-dn, kExpLn2d64Hi, x);
-    r = fma(-dn, kExpLn2d64Lo, r);
-    double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    q = fma(r, q, 1.0 / 6.0);
+    double r = fma(-dn, kExpLn2dNHi, x);
+    r = fma(-dn, kExpLn2dNLo, r);
+    double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     q = fma(r, q, 0.5);
     const double p = fma(r * r, q, r);
-    const double tj = __ldg(&kExp2Table[n & 63]);
+    const double tj = __ldg(&kExp2Table[n & 255]);
     const double v = fma(tj, p, tj);
-    return __longlong_as_double(__double_as_longlong(v) + ((long long)(n >> 6) << 52));
+    return __longlong_as_double(__double_as_longlong(v) + ((long long)(n >> 8) << 52));
 }
 
 // The double logarithm of the FP64 path, table-driven (Tang, ACM TOMS 16(4), 1990): x = 2^e m,

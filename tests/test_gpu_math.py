@@ -32,11 +32,11 @@ def _ulps(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def test_exp_within_two_ulp_of_the_library_exponentials(gpu_lib):
     rng = np.random.default_rng(7)
-    ln2_64 = np.log(2.0) / 64
+    ln2_n = np.log(2.0) / 256
     x = np.concatenate([rng.uniform(-708.0, 708.0, 2_000_000), rng.uniform(-1.0, 1.0, 1_000_000),
                         rng.uniform(-40.0, 0.0, 1_000_000),            # the weights' range
-                        np.arange(-20000, 20000) * ln2_64,             # table boundaries
-                        np.arange(-20000, 20000) * ln2_64 + ln2_64 / 2,
+                        np.arange(-100000, 100000) * ln2_n,            # table points
+                        np.arange(-100000, 100000) * ln2_n + ln2_n / 2,   # and reduction boundaries
                         [0.0, -0.0, 1e-300, -1e-300, 708.0, -708.0]])
     got = _tab(EXP, x)
     assert _ulps(got, np.exp(x)).max() <= 2

@@ -1,6 +1,6 @@
 """The constants of the FP64 path's table-driven exponential and logarithm: the committed headers
-are what their generators write; the exponential's table holds 2^(j/64) to the nearest double
-and its split of ln 2 / 64 is exact when multiplied by any |n| < 2^17; the logarithm's table
+are what their generators write; the exponential's table holds 2^(j/256) to the nearest double
+and its split of ln 2 / 256 is exact when multiplied by any |n| < 2^19; the logarithm's table
 holds 1/F_j to the nearest double and log F_j as an exact sum of a part on the grid 2^-42 and
 the rest, with F_128 = 2 split like ln 2; the sine and cosine tables hold sin and cos of
 2 pi j / 256, exact at the multiples of pi / 2."""
@@ -39,18 +39,16 @@ def test_header_is_the_generator_output():
 
 def test_table_and_split_constants():
     vals, table = _consts(_header())
-    assert len(table) == 64
+    assert len(table) == 256
     for j, v in enumerate(table):
-        # the nearest double: within half an ulp of 2^(j/64) (checked against a long-double-free
-        # bound: 2^(j/64) computed as exp2 in double is itself within 1 ulp)
-        assert abs(v - np.exp2(j / 64)) <= np.spacing(v)
-        assert (v ** 64 / 2 ** j - 1) < 64 * 2.3e-16
-    hi, lo = vals["kExpLn2d64Hi"], vals["kExpLn2d64Lo"]
-    assert Fraction(hi).denominator.bit_length() <= 7 + 36 + 1        # 36 significant bits
-    assert abs(hi + lo - np.log(2) / 64) < 1e-18
-    n = 2 ** 17 - 1
+        # within an ulp of 2^(j/256) as exp2 gives it in double (itself within an ulp)
+        assert abs(v - np.exp2(j / 256)) <= np.spacing(v)
+    hi, lo = vals["kExpLn2dNHi"], vals["kExpLn2dNLo"]
+    assert Fraction(hi).denominator.bit_length() <= 9 + 34 + 1        # 34 significant bits
+    assert abs(hi + lo - np.log(2) / 256) < 1e-19
+    n = 2 ** 19 - 1
     assert Fraction(n) * Fraction(hi) == Fraction(n * hi)               # n hi exact in double
-    assert abs(vals["kExpInvLn2x64"] * np.log(2) / 64 - 1) < 3e-16
+    assert abs(vals["kExpInvLn2xN"] * np.log(2) / 256 - 1) < 3e-16
 
 
 def _log_header():
