@@ -433,7 +433,10 @@ airpf_status airpf_debug_inject(airpf_ctx* ctx, int32_t what);
 
 /* Test hook, no counterpart in the paper: d_y[i] = f(d_x[i]) for i < n as the FP64 path
  * computes f (table-driven double functions): fn = 0 the exponential, fn = 1 the natural
- * logarithm, fn = 2 and 3 sin(2 pi x) and cos(2 pi x) (the Box-Muller angle).  Device arrays of n doubles, asynchronous on `stream` (a cudaStream_t, NULL for
+ * logarithm, fn = 2 and 3 sin(2 pi x) and cos(2 pi x) (the Box-Muller angle); of a 32-bit
+ * word w = x (an integer 0 .. 2^32 - 1 given as a double): fn = 4 the uniform (w + 1/2) 2^-32,
+ * fn = 5 its logarithm, fn = 6 and 7 the sine and cosine of 2 pi times it (the forms the
+ * Box-Muller pairs use, reduced in integers).  Device arrays of n doubles, asynchronous on `stream` (a cudaStream_t, NULL for
  * the default stream).  AIRPF_ERR_ARG for another fn, n < 0 or a NULL array with n > 0. */
 airpf_status airpf_debug_math(int32_t fn, const double* d_x, double* d_y, int64_t n, void* stream);
 

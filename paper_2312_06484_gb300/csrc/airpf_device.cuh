@@ -58,7 +58,31 @@ struct Stream {
     }
 };
 
-__device__ __forceinline__ double unif_f64(uint32_t w) { return ((double)w + 0.5) * 0x1p-32; }
+// (w + 1/2) 2^-32, exactly: 1 + (w + 1/2) 2^-32 assembled from its bits (w in mantissa bits
+// 51..20, the half in bit 19), less 1 (exact for a value in [1, 2)); one FP64 instruction
+__device__ __forceinline__ double unif_f64(uint32_t w)
+{
+    return __hiloint2double((int)(0x3FF00000u | (w >> 12)), (int)((w << 20) | (1u << 19))) - 1.0;
+}
+
+// x > -inf (false for NaN), decided on the bit pattern by the integer pipe
+__device__ __forceinline__ bool above_neg_inf(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x7FFFFFFFFFFFFFFFull) <= 0x7FF0000000000000ull && b != 0xFFF0000000000000ull;
+}
+
+// A signed 64-bit integer in the order of the double x (not NaN): the bit pattern, with the
+// magnitude bits of negative values flipped.  The map is its own inverse.
+__device__ __forceinline__ long long order_key(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ __forceinline__ double from_order_key(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFll));
+}
 
 // The double exponential of the FP64 path, table-driven (Tang, ACM TOMS 15(2), 1989):
 // x = (256 k + j) ln 2 / 256 + r with |r| <= ln 2 / 512, exp(x) = 2^k 2^(j/256) e^r, e^r - 1
@@ -67,7 +91,9 @@ __device__ __forceinline__ double unif_f64(uint32_t w) { return ((double)w + 0.5
 // infinities, NaN) it defers to the library function.
 __device__ __forceinline__ double exp_tab(double x)
 {
-    if (!(fabs(x) <= 708.0)) return exp(x);
+    // |x| <= 708 (false for NaN) on the bit pattern: 0x40862... is 708.0
+    if (!(((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) <= 0x4086200000000000ull))
+        return exp(x);
     // n = nearest integer to 256 x / ln 2, in the low bits of a sum with 1.5 2^52 (one
     // rounding, no conversion instructions)
     const double t = fma(x, kExpInvLn2xN, 0x1.8p52);
@@ -87,14 +113,10 @@ __device__ __forceinline__ double exp_tab(double x)
 // m in [1, 2), F = 1 + j/128 the nearest 128th to m, f = m - F (exact), s = f / F taken as
 // f (1/F) with the reciprocal from the table, log x = e ln 2 + log F + log(1 + s) with
 // log(1 + s) by its Taylor polynomial through s^7 (|s| <= 2^-8), e ln 2 + log F summed
-// exactly from parts on a common grid.  At most about 1 ulp from the exact value; zero,
-// negative, subnormal and non-finite arguments defer to the library function.
-__device__ __forceinline__ double log_tab(double x)
+// exactly from parts on a common grid.  At most about 1 ulp from the exact value.
+// log_parts takes e and the 52 fraction bits of m.
+__device__ __forceinline__ double log_parts(int e, long long mb)
 {
-    if (!(x >= 0x1p-1022 && x <= 0x1.fffffffffffffp+1023)) return log(x);
-    const long long b = __double_as_longlong(x);
-    const int e = (int)(b >> 52) - 1023;
-    const long long mb = b & 0x000FFFFFFFFFFFFFLL;
     const double m = __longlong_as_double(mb | 0x3FF0000000000000LL);
     const int j = (int)(((mb >> 44) + 1) >> 1);                   // nearest 128th: 0 .. 128
     const double F = __longlong_as_double(0x3FF0000000000000LL + ((long long)j << 45));
@@ -111,22 +133,31 @@ __device__ __forceinline__ double log_tab(double x)
     return hi + (lo + p);
 }
 
-// sin(2 pi v) and cos(2 pi v) for v in [0, 1], table-driven: 2 pi v = 2 pi j / 256 + x with
-// j the nearest 256th (exact reduction: v has at most 33 significant bits here) and
-// |x| <= pi / 256, the angle-addition formulas with the table's sin and cos of 2 pi j / 256
-// and Taylor polynomials of sin x through x^7 and cos x through x^6 (the next terms are below
-// 1e-19).  Within a few 1e-16 of the exact values; other v defer to the library's sincos.
-__device__ __forceinline__ void sincos2pi_tab(double v, double* s, double* c)
+// log x; zero, negative, subnormal and non-finite arguments (told apart on the bit pattern)
+// defer to the library function
+__device__ __forceinline__ double log_tab(double x)
 {
-    if (!(v >= 0.0 && v <= 1.0)) {
-        sincos(6.283185307179586 * v, s, c);
-        return;
-    }
-    const double t = v * 256.0;
-    const double tj = fma(1.0, t, 0x1.8p52);                        // nearest integer in the low bits
-    const double f = t - (tj - 0x1.8p52);
-    const int j = __double2loint(tj) & 255;
-    const double x = f * kTwoPiDiv256;
+    const long long b = __double_as_longlong(x);
+    if (!(b >= 0x0010000000000000LL && b <= 0x7FEFFFFFFFFFFFFFLL)) return log(x);
+    return log_parts((int)(b >> 52) - 1023, b & 0x000FFFFFFFFFFFFFLL);
+}
+
+// log of the uniform (w + 1/2) 2^-32 = v 2^-33, v = 2w + 1: the exponent and the fraction
+// bits from the integer v (no conversion, no range test: the value is normal, in (0, 1));
+// the same value as log_tab(unif_f64(w))
+__device__ __forceinline__ double log_unif(uint32_t w)
+{
+    const unsigned long long v = 2ull * w + 1ull;                 // 1 .. 2^33 - 1
+    const int msb = 63 - __clzll((long long)v);                   // 0 .. 32
+    return log_parts(msb - 33, (long long)((v << (52 - msb)) & 0x000FFFFFFFFFFFFFull));
+}
+
+// sin(2 pi v) and cos(2 pi v), table-driven: 2 pi v = 2 pi j / 256 + x with j the nearest
+// 256th and |x| <= pi / 256, the angle-addition formulas with the table's sin and cos of
+// 2 pi j / 256 and Taylor polynomials of sin x through x^7 and cos x through x^6 (the next
+// terms are below 1e-19).  Within a few 1e-16 of the exact values.
+__device__ __forceinline__ void sincos2pi_parts(int j, double x, double* s, double* c)
+{
     const double x2 = x * x;
     const double cx = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
     const double sx = fma(x * x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), x);
@@ -135,12 +166,38 @@ __device__ __forceinline__ void sincos2pi_tab(double v, double* s, double* c)
     *c = fma(cj, cx, -(sj * sx));
 }
 
+// v in [0, 1] (told apart on the bit pattern; other v defer to the library's sincos): the
+// reduction is exact when v has at most 33 significant bits
+__device__ __forceinline__ void sincos2pi_tab(double v, double* s, double* c)
+{
+    const long long b = __double_as_longlong(v);
+    if (!(b >= 0 && b <= 0x3FF0000000000000LL)) {
+        sincos(6.283185307179586 * v, s, c);
+        return;
+    }
+    const double t = v * 256.0;
+    const double tj = fma(1.0, t, 0x1.8p52);                        // nearest integer in the low bits
+    const double f = t - (tj - 0x1.8p52);
+    sincos2pi_parts(__double2loint(tj) & 255, f * kTwoPiDiv256, s, c);
+}
+
+// sin and cos of 2 pi (w + 1/2) 2^-32, reduced in integers: j = the nearest 256th, and
+// 256 v - j = (2 (w - j 2^24) + 1) 2^-25 with the odd integer below 2^24 in magnitude
+// (32-bit wrap-around gives the signed remainder for j = 256 too); the same values as
+// sincos2pi_tab(unif_f64(w))
+__device__ __forceinline__ void sincos2pi_unif(uint32_t w, double* s, double* c)
+{
+    const uint32_t j = ((w >> 23) + 1u) >> 1;                       // 0 .. 256
+    const int r = (int)((w - (j << 24)) * 2u + 1u);
+    sincos2pi_parts((int)(j & 255u), (double)r * (kTwoPiDiv256 * 0x1p-25), s, c);
+}
+
 // Box-Muller pair from two words: r = sqrt(-2 ln u0), angle 2 pi u1.
 __device__ __forceinline__ void normal_pair(uint32_t w0, uint32_t w1, double& z0, double& z1)
 {
-    const double rad = sqrt(-2.0 * log_tab(unif_f64(w0)));
+    const double rad = sqrt(-2.0 * log_unif(w0));
     double s, c;
-    sincos2pi_tab(unif_f64(w1), &s, &c);
+    sincos2pi_unif(w1, &s, &c);
     z0 = rad * c;
     z1 = rad * s;
 }
@@ -446,7 +503,8 @@ __device__ __forceinline__ R model_logg(const ModelPar<R>& p, const R* y, int dx
         }
         l = p.c2 - ss * p.c1;
     }
-    return (l > -INFINITY) ? l : (R)(-INFINITY);
+    if constexpr (sizeof(R) == 8) return above_neg_inf((double)l) ? l : (R)(-INFINITY);
+    else return (l > -INFINITY) ? l : (R)(-INFINITY);
 }
 
 }  // namespace airpf

@@ -212,10 +212,19 @@ __global__ void math_tab_kernel(int fn, const double* x, double* y, int64_t n)
     {
         if (fn == 0) y[i] = exp_tab(x[i]);
         else if (fn == 1) y[i] = log_tab(x[i]);
-        else {
+        else if (fn == 2 || fn == 3) {
             double sv, cv;
             sincos2pi_tab(x[i], &sv, &cv);
             y[i] = fn == 2 ? sv : cv;
+        } else {                       // functions of a 32-bit word w (given as a double)
+            const uint32_t w = (uint32_t)x[i];
+            if (fn == 4) y[i] = unif_f64(w);
+            else if (fn == 5) y[i] = log_unif(w);
+            else {
+                double sv, cv;
+                sincos2pi_unif(w, &sv, &cv);
+                y[i] = fn == 6 ? sv : cv;
+            }
         }
     }
 }
@@ -224,7 +233,7 @@ __global__ void math_tab_kernel(int fn, const double* x, double* y, int64_t n)
 
 extern "C" airpf_status airpf_debug_math(int32_t fn, const double* d_x, double* d_y, int64_t n, void* stream)
 {
-    if (fn < 0 || fn > 3 || n < 0 || (n > 0 && (!d_x || !d_y))) return AIRPF_ERR_ARG;
+    if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!d_x || !d_y))) return AIRPF_ERR_ARG;
     if (n == 0) return AIRPF_OK;
     const int64_t blocks64 = (n + 255) / 256;
     const int blocks = (int)(blocks64 < 4096 ? blocks64 : 4096);

@@ -202,6 +202,27 @@ __device__ __forceinline__ V group_sum(V v, int n)
     return v;
 }
 
+// Warp sums of eight doubles at once (a reduce-scatter butterfly: at each of the first three
+// levels a lane keeps half of its values and adds the partner's copy of that half; 7 + 2
+// additions a lane instead of 8 x 5).  Returns at every lane the warp total of value
+// (lane >> 2) & 7.
+__device__ __forceinline__ double warp_reduce_scatter8(const double (&v)[8], int lane)
+{
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+    double h4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        h4[i] = (b4 ? v[i + 4] : v[i]) + __shfl_xor_sync(0xffffffffu, b4 ? v[i] : v[i + 4], 16);
+    double h2[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        h2[i] = (b3 ? h4[i + 2] : h4[i]) + __shfl_xor_sync(0xffffffffu, b3 ? h4[i] : h4[i + 2], 8);
+    double h = (b2 ? h2[1] : h2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? h2[0] : h2[1], 4);
+    h += __shfl_xor_sync(0xffffffffu, h, 2);
+    h += __shfl_xor_sync(0xffffffffu, h, 1);
+    return h;
+}
+
 template <typename V>
 __device__ __forceinline__ V warp_incl_scan(V v, int lane)
 {
@@ -330,6 +351,17 @@ __device__ __forceinline__ XW xw_from_u64(u64 v, int e_add)
 }
 
 // Arithmetic of the cascade for each precision (see file comment).
+// v 2^-sh for v >= 0 and sh >= 0: the exponent field lowered by sh on the integer pipe when
+// the result stays normal (exact, as ldexp); ldexp itself for a zero, subnormal or
+// non-finite v, or a result that would be subnormal
+__device__ __forceinline__ double scale_down(double v, int sh)
+{
+    const long long b = __double_as_longlong(v);
+    const int ex = (int)(b >> 52);                    // biased exponent of a non-negative v
+    if ((unsigned)sh < (unsigned)ex && ex < 0x7FF) return __longlong_as_double(b - ((long long)sh << 52));
+    return ldexp(v, -sh);
+}
+
 template <bool FX> struct Casc;
 template <> struct Casc<false> {
     using V = double;
@@ -338,8 +370,8 @@ template <> struct Casc<false> {
     __device__ static int frac(const StepParams&) { return 0; }
     __device__ static bool positive(u64 b) { return (long long)b > 0; }
     __device__ static V leaf(u64 b, int de, int) { return ldexp(__longlong_as_double((long long)b), de); }
-    __device__ static V rescale(V v, int sh) { return ldexp(v, -sh); }
-    __device__ static Qt qscale(Qt q, int sh2) { return ldexp(q, -sh2); }
+    __device__ static V rescale(V v, int sh) { return scale_down(v, sh); }
+    __device__ static Qt qscale(Qt q, int sh2) { return scale_down(q, sh2); }
     __device__ static Qt qv(V v) { return v; }
     __device__ static double to_d(V v) { return v; }
     __device__ static XW weight(V bsum, int e_add) { return xw_from_double(bsum, e_add); }
@@ -377,6 +409,8 @@ template <> struct Casc<true> {
 };
 
 template <typename V> __device__ __forceinline__ bool pos_v(V v) { return v > (V)0; }
+// a sum of non-negative weights (never NaN) is positive iff its bit pattern is
+template <> __device__ __forceinline__ bool pos_v<double>(double v) { return __double_as_longlong(v) > 0; }
 
 // ---------------------------------------------------------------------------
 // Cascade of step tp for filter c (see file comment), run by one CTA: the
@@ -697,9 +731,27 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
         __syncthreads();
         V tot = (V)0;
         Qt q0 = (Qt)0;
-        for (int w = 0; w < nw; ++w) {
-            tot += w_tot[w];
-            q0 += w_q0[w];
+        if constexpr (!FX) {
+            // FP64: the warps' partials summed by a butterfly over the first nw lanes
+            // (log2 nw additions a thread instead of nw), lane 0's sum broadcast
+            if (lane < nw) {
+                tot = w_tot[lane];
+                q0 = w_q0[lane];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                if (o < nw) {
+                    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                    q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+                }
+            }
+            tot = __shfl_sync(0xffffffffu, tot, 0);
+            q0 = __shfl_sync(0xffffffffu, q0, 0);
+        } else {
+            for (int w = 0; w < nw; ++w) {
+                tot += w_tot[w];
+                q0 += w_q0[w];
+            }
         }
         const Qt tq = C::qv(tot);
         const bool quiet1 = p.mode == 0 || (pos_v(tot) && !(tq * tq < C::tau(p) * (Qt)m * q0));
@@ -795,18 +847,25 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
             }
         }
     }
+    if constexpr (!FX && FP == 1) {
+        // FP64, fixed shape (g = 2, L5 = 5): the eight per-level partial sums reduced together
+        double vals[8] = {qlow[0], qlow[1], qu[0], qu[1], qu[2], qu[3], qu[4], qu[5]};
+        const double s = warp_reduce_scatter8(vals, lane);
+        if ((lane & 3) == 0) Qw[warp * kQw + (lane >> 2)] = s;
+    } else {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        if (l < g) {
-            const Qt s = warp_sum(qlow[l]);
-            if (lane == 0) Qw[warp * kQw + l] = s;
+        for (int l = 0; l < 4; ++l) {
+            if (l < g) {
+                const Qt s = warp_sum(qlow[l]);
+                if (lane == 0) Qw[warp * kQw + l] = s;
+            }
         }
-    }
 #pragma unroll
-    for (int u = 0; u <= kShuffleLevels; ++u) {
-        if (u <= L5) {
-            const Qt s = warp_sum(qu[u]);
-            if (lane == 0) Qw[warp * kQw + g + u] = s;
+        for (int u = 0; u <= kShuffleLevels; ++u) {
+            if (u <= L5) {
+                const Qt s = warp_sum(qu[u]);
+                if (lane == 0) Qw[warp * kQw + g + u] = s;
+            }
         }
     }
     __syncthreads();
@@ -1627,11 +1686,23 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         moment_sums<R, DX>(p, c, t, k, wi, lane, dx, 0, s1, s2);
     }
 
-    // island maximum of the log-weights
-    R mx = lv[0];
+    // island maximum of the log-weights (no NaN among them); FP64: taken on their order keys
+    // by the integer pipe
+    R mx;
+    if constexpr (!FX) {
+        long long km = order_key(lv[0]);
 #pragma unroll
-    for (int r = 1; r < PPT; ++r) mx = (lv[r] > mx) ? lv[r] : mx;
-    mx = warp_max(mx);
+        for (int r = 1; r < PPT; ++r) {
+            const long long kr = order_key(lv[r]);
+            km = kr > km ? kr : km;
+        }
+        mx = from_order_key(warp_max(km));
+    } else {
+        mx = lv[0];
+#pragma unroll
+        for (int r = 1; r < PPT; ++r) mx = (lv[r] > mx) ? lv[r] : mx;
+        mx = warp_max(mx);
+    }
     // an island of several warps (then G <= 8) syncs on its own barrier 1 + g
     if (nwi > 1) {
         if (lane == 0) mxr[wi] = mx;
@@ -1640,7 +1711,9 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
         for (int w = 1; w < nwi; ++w) v = (mxr[w] > v) ? mxr[w] : v;
         mx = v;
     }
-    const bool alive = (mx > (R)(-INFINITY));
+    bool alive;
+    if constexpr (!FX) alive = above_neg_inf(mx);
+    else alive = (mx > (R)(-INFINITY));
 
     // The CDF in shared memory, each 128-byte row of it XOR-swizzled by its row
     // index: the binary search's probes at one depth share their low address
@@ -1672,7 +1745,7 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
         Cdf w = 0;
-        if (alive && lv[r] > (R)(-INFINITY)) {
+        if (alive && (FX ? lv[r] > (R)(-INFINITY) : above_neg_inf((double)lv[r]))) {
             if constexpr (!FX) w = exp_tab(lv[r] - mx);
             else w = __float2uint_rn(__expf(lv[r] - mx) * p.cdf_scale);
         }

@@ -3,7 +3,9 @@
 CUDA): the exponential and logarithm within 2 ulp where the tables are used and the library's
 values outside that range (infinities, NaN, zero, subnormals); sin and cos of 2 pi v within a
 few 1e-16 of an extended-precision reference (2 ulp where |value| >= 1/4), exact at the
-quarter turns."""
+quarter turns; and the Box-Muller forms of a 32-bit word (the uniform assembled from its bits,
+its logarithm and the angle reduced in integers) bit for bit equal to the generic functions of
+that uniform."""
 import ctypes
 
 import numpy as np
@@ -12,6 +14,7 @@ import torch
 
 pytestmark = pytest.mark.gpu
 EXP, LOG, SIN2PI, COS2PI = 0, 1, 2, 3
+UNIF_W, LOG_W, SIN2PI_W, COS2PI_W = 4, 5, 6, 7
 
 
 def _tab(fn: int, x: np.ndarray) -> np.ndarray:
@@ -92,3 +95,18 @@ def test_sin_cos_of_two_pi_v(gpu_lib):
     x = np.array([0.0, 0.25, 0.5, 0.75, 1.0])
     np.testing.assert_array_equal(_tab(SIN2PI, x), [0.0, 1.0, 0.0, -1.0, 0.0])
     np.testing.assert_array_equal(_tab(COS2PI, x), [1.0, 0.0, -1.0, 0.0, 1.0])
+
+
+def test_word_forms_equal_the_generic_functions_of_the_uniform(gpu_lib):
+    rng = np.random.default_rng(10)
+    w = np.concatenate([rng.integers(0, 2 ** 32, 1_000_000, dtype=np.uint64),
+                        np.arange(0, 4096, dtype=np.uint64),                    # small words: e down to -33
+                        2 ** 32 - 1 - np.arange(0, 4096, dtype=np.uint64),      # the top: j = 256
+                        (np.arange(0, 512, dtype=np.uint64) << 23),             # 512th boundaries
+                        (np.arange(1, 513, dtype=np.uint64) << 23) - 1,
+                        np.uint64(1) << np.arange(0, 32, dtype=np.uint64)])     # every exponent
+    wd = w.astype(np.float64)
+    u = _tab(UNIF_W, wd)
+    np.testing.assert_array_equal(u, (wd + 0.5) * 2.0 ** -32)                   # exact
+    for fw, fu in ((LOG_W, LOG), (SIN2PI_W, SIN2PI), (COS2PI_W, COS2PI)):
+        np.testing.assert_array_equal(_tab(fw, wd).view(np.int64), _tab(fu, u).view(np.int64))
