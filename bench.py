@@ -62,17 +62,17 @@ def ops_per_particle_step(model: str) -> float:
 # Figures from the committed ncu captures of the kernels named (set to None when the kernel
 # changes, until it is captured again): DRAM read + write per launch, issue-active fraction.
 NCU = {
-    "ngm_island_step": {"dram_bytes_per_launch": 94348032, "issue_active": 0.737,
+    "ngm_island_step": {"dram_bytes_per_launch": 94030080, "issue_active": 0.727,
                         "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, "
                                   "airpf_step_kernel<float, NGM, 1, 4, false, 2, 256> at steps 5 and 6, caches flushed"},
     "sv_fused_step": {"dram_bytes_per_launch": 1156352, "issue_active": 0.397,
                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum (caches flushed) and "
                                 "smsp__issue_active (warm caches, as in a pass), "
                                 "airpf_step_kernel<float, SV, 1, 4, false, 3, 256>"},
-    "fp64_ngm_island_step": {"fp64_pipe": 0.860, "issue_active": 0.107,
+    "fp64_ngm_island_step": {"fp64_pipe": 0.858, "issue_active": 0.122,
                              "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
                                        "airpf_step_kernel<double, NGM, 1, 4, false, 2, 256>"},
-    "fp64_sv_fused_step": {"fp64_pipe": 0.749, "issue_active": 0.102,
+    "fp64_sv_fused_step": {"fp64_pipe": 0.736, "issue_active": 0.110,
                            "source": "ncu sm__inst_executed_pipe_fp64 (pct of peak, active cycles), "
                                      "airpf_step_kernel<double, SV, 1, 4, false, 3, 256>"},
 }

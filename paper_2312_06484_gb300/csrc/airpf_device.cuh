@@ -328,6 +328,13 @@ template <typename R> __device__ __forceinline__ R fdiv(R a, R b);
 template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
 template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
 
+// x^2 / 20 (the growth model's observation mean) as two rounded products, x x and then 1/20
+// rounded to R, not contracted into the subtraction that follows: within about 1 ulp of the
+// quotient, at the cost of two multiplications instead of a division
+template <typename R> __device__ __forceinline__ R ngm_obs_mean(R x);
+template <> __device__ __forceinline__ double ngm_obs_mean<double>(double x) { return __dmul_rn(__dmul_rn(x, x), 0.05); }
+template <> __device__ __forceinline__ float ngm_obs_mean<float>(float x) { return __fmul_rn(__fmul_rn(x, x), 0.05f); }
+
 template <typename R> __device__ __forceinline__ R unif_r(uint32_t w);
 template <> __device__ __forceinline__ double unif_r<double>(uint32_t w) { return unif_f64(w); }
 template <> __device__ __forceinline__ float unif_r<float>(uint32_t w) { return fmaf((float)w, 0x1p-32f, 0x1p-33f); }
@@ -480,7 +487,7 @@ __device__ __forceinline__ R model_logg(const ModelPar<R>& p, const R* y, int dx
     } else if (MODEL == SV) {
         l = p.c1 - (R)0.5 * x[0] - (R)0.5 * y[0] * y[0] * fexp<R>(-x[0]);
     } else if (MODEL == NGM) {
-        const R e = y[0] - x[0] * x[0] / (R)20;
+        const R e = y[0] - ngm_obs_mean<R>(x[0]);
         l = p.c1 - e * e * p.c2;
     } else if (MODEL == TOY) {
         l = (y[0] == x[0]) ? p.c1 : p.c2;

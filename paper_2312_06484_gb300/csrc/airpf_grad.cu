@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kGradThreads, grad_island_min_ctas<R>()) grad_
             const R q = mp.th[0], r = mp.th[1], p0 = mp.th[2];
             const R sq = mp.c0;
             const R zz = (x[0] - mu[0]) / sq;
-            const R e = yv[0] - x[0] * x[0] / (R)20;
+            const R e = yv[0] - ngm_obs_mean<R>(x[0]);
             const R dlr = (R)(-0.5) / r + e * e / ((R)2 * r * r);
             xhat[0] += lhat * e * (x[0] / (R)10) / r;
             ga(0) += xhat[0] * zz / ((R)2 * sq);

@@ -722,32 +722,36 @@ __device__ void cascade_all(const StepParams& p, int c, int tp, const Stream& st
                 }
             }
         }
-        tpart = warp_sum(tpart);
-        qpart = warp_sum(qpart);
-        if (lane == 0) {
-            w_tot[warp] = tpart;
-            w_q0[warp] = qpart;
-        }
-        __syncthreads();
         V tot = (V)0;
         Qt q0 = (Qt)0;
-        if constexpr (!FX) {
-            // FP64: the warps' partials summed by a butterfly over the first nw lanes
-            // (log2 nw additions a thread instead of nw), lane 0's sum broadcast
-            if (lane < nw) {
-                tot = w_tot[lane];
-                q0 = w_q0[lane];
-            }
+        if (!FX && nw <= 16) {
+            // FP64: the two sums in the two half-warps after one exchange (lanes 0-15 the
+            // weights, 16-31 the squares: 5 additions a thread instead of 10); then the
+            // warps' partials the same way over lanes 0 .. nw-1 and 16 .. 16+nw-1
+            const bool hi = (lane & 16) != 0;
+            double h = (double)(hi ? qpart : tpart) +
+                       __shfl_xor_sync(0xffffffffu, (double)(hi ? tpart : qpart), 16);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                if (o < nw) {
-                    tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                    q0 += __shfl_xor_sync(0xffffffffu, q0, o);
-                }
-            }
-            tot = __shfl_sync(0xffffffffu, tot, 0);
-            q0 = __shfl_sync(0xffffffffu, q0, 0);
+            for (int o = 8; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+            if (lane == 0) w_tot[warp] = (V)h;
+            if (lane == 16) w_q0[warp] = (Qt)h;
+            __syncthreads();
+            const int lw = lane & 15;
+            double v = 0.0;
+            if (lw < nw) v = hi ? (double)w_q0[lw] : (double)w_tot[lw];
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1)
+                if (o < nw) v += __shfl_xor_sync(0xffffffffu, v, o);
+            tot = (V)__shfl_sync(0xffffffffu, v, 0);
+            q0 = (Qt)__shfl_sync(0xffffffffu, v, 16);
         } else {
+            tpart = warp_sum(tpart);
+            qpart = warp_sum(qpart);
+            if (lane == 0) {
+                w_tot[warp] = tpart;
+                w_q0[warp] = qpart;
+            }
+            __syncthreads();
             for (int w = 0; w < nw; ++w) {
                 tot += w_tot[w];
                 q0 += w_q0[w];
