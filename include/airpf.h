@@ -130,7 +130,9 @@ typedef struct {
     uint64_t seed;
     int32_t launch;         /* airpf_launch (a requested mode that cannot run: AIRPF_ERR_UNSUPPORTED) */
     int32_t reserved;       /* must be 0 */
-    int32_t ppt;            /* particles per thread: 2 or 4, 0 = automatic */
+    int32_t ppt;            /* particles per thread: 2, 4 or 8 (8: FP32 SV and NGM only), 0 =
+                             * automatic (8 for FP32 SV and NGM split steps with M = 256, else 4
+                             * above M = 64 and 2 up to it) */
     int32_t islands_per_cta;/* islands per CTA: a power of 2, 0 = automatic (capped at 512 threads) */
     int32_t ckpt;           /* AIRPF_RECORD_GRAD: states kept every ckpt steps, recomputed in
                                between during the backward pass (0 = every step) */
@@ -423,6 +425,12 @@ airpf_status airpf_kernel_times(airpf_ctx* ctx, double* step_ms, double* cascade
 airpf_status airpf_moments(airpf_ctx* ctx, double* d_moments);
 
 int32_t airpf_launch_mode(const airpf_ctx* ctx);
+
+/* The context's island-to-thread mapping (no counterpart in the paper): threads per island,
+ * particles per thread and islands per CTA, written to the three host int32 pointers.
+ * AIRPF_ERR_ARG for a NULL context or pointer. */
+airpf_status airpf_tiling(const airpf_ctx* ctx, int32_t* threads_per_island, int32_t* particles_per_thread,
+                          int32_t* islands_per_cta);
 
 /* Fault injection for tests of the failure path, no counterpart in the paper.
  * what = 1: in the next PERSISTENT_GRID pass, CTA 0 leaves before the first

@@ -240,6 +240,14 @@ class AIRPF:
     def launch_mode(self) -> int:
         return int(self.lib.airpf_launch_mode(self.ctx))
 
+    @property
+    def tiling(self) -> dict:
+        """The island-to-thread mapping: threads per island, particles per thread, islands
+        per CTA (airpf_tiling)."""
+        v = (ctypes.c_int32 * 3)()
+        _binding.check(self.lib.airpf_tiling(self.ctx, ctypes.byref(v, 0), ctypes.byref(v, 4), ctypes.byref(v, 8)))
+        return {"threads_per_island": v[0], "particles_per_thread": v[1], "islands_per_cta": v[2]}
+
     def sync(self):
         """Wait for the stream; raises AirpfError (AIRPF_ERR_TIMEOUT) if a bounded device wait ran out."""
         _binding.check(self.lib.airpf_sync(self.ctx), self.ctx)

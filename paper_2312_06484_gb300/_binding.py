@@ -61,6 +61,7 @@ SIGNATURES = {
     "airpf_step_levels": (c_int32, [c_void_p, ctypes.POINTER(c_int32)]),
     "airpf_sync": (c_int32, [c_void_p]),
     "airpf_launch_mode": (c_int32, [c_void_p]),
+    "airpf_tiling": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "airpf_moments": (c_int32, [c_void_p, c_void_p]),
     "airpf_kernel_times": (c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "airpf_debug_inject": (c_int32, [c_void_p, c_int32]),

@@ -18,7 +18,7 @@ SOURCES = ["airpf_step.cu", "airpf_api.cu", "airpf_pmmh.cu", "airpf_static.cu", 
 # particles per thread
 INST_SOURCE = "airpf_launch_inst.cu"
 INST_UNITS = [(r, model, ppt) for r in ("float", "double") for model in ("AR1", "SV", "NGM", "LGSSM", "TOY", "CP")
-              for ppt in (2, 4)]
+              for ppt in (2, 4)] + [("float", "SV", 8), ("float", "NGM", 8)]
 HEADERS = ["airpf_device.cuh", "airpf_exp_table.h", "airpf_log_table.h", "airpf_sincos_table.h", "airpf_internal.h", "airpf_step_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

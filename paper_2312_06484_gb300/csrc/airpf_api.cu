@@ -120,7 +120,9 @@ const char* check_config(const airpf_config* c)
     }
     if (c->launch < 0 || c->launch > 4) return "unknown launch mode";
     if (c->reserved != 0) return "reserved must be 0";
-    if (c->ppt != 0 && c->ppt != 2 && c->ppt != 4) return "ppt must be 0, 2 or 4";
+    if (c->ppt != 0 && c->ppt != 2 && c->ppt != 4 && c->ppt != 8) return "ppt must be 0, 2, 4 or 8";
+    if (c->ppt == 8 && !(c->precision == AIRPF_FP32_MIXED && (c->model == AIRPF_MODEL_SV || c->model == AIRPF_MODEL_NGM)))
+        return "ppt = 8 is compiled for the FP32 SV and NGM filters only";
     if (c->islands_per_cta < 0 || c->islands_per_cta > 4096 || (c->islands_per_cta & (c->islands_per_cta - 1)))
         return "islands_per_cta must be 0 or a power of 2";
     return nullptr;
@@ -469,6 +471,18 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     // 512 CTAs, where reading all CTA records in every CTA would cost more)
     if (ctx->launch == AIRPF_LAUNCH_AUTO)
         ctx->launch = p.P <= 512 ? AIRPF_LAUNCH_STEPS : AIRPF_LAUNCH_STEPS_SPLIT;
+    // split steps of the FP32 SV and NGM filters with islands of 256 particles: one warp an
+    // island (eight particles a thread, four islands a CTA of 128 threads; the same CTAs, so
+    // the same records and cascade) -- no island-level barriers or shared-memory carries.
+    // Measured on the m = 65536 NGM workload: 155.6 -> 118.2 ms a pass (eight islands a CTA
+    // 128.0, sixteen 147.6).  Fused steps keep four particles a thread (the m = 1024 SV
+    // workload: 4.6 against 5.8-6.0 ms).
+    if (ctx->launch == AIRPF_LAUNCH_STEPS_SPLIT && !p.fp64 && cfg->M == 256 && cfg->ppt == 0 &&
+        cfg->islands_per_cta == 0 && (cfg->model == AIRPF_MODEL_SV || cfg->model == AIRPF_MODEL_NGM) &&
+        p.G == 4) {
+        airpf::choose_mapping(cfg->m, cfg->M, p.fp64, 8, 4, &p.tpi, &p.ppt, &p.G);
+        p.lg_tpi = ilog2_exact(p.tpi);
+    }
     // (split steps keep the default 256-thread CTAs: on the m = 65536 workload they beat
     // 512-thread CTAs by 5-6% at M = 256 and 512 -- the block barriers of 16 warps cost more
     // than the cascade kernel's twice as many records -- and lose 1% at M = 64)
@@ -936,6 +950,16 @@ airpf_status airpf_moments(airpf_ctx* ctx, double* d_moments)
 }
 
 int32_t airpf_launch_mode(const airpf_ctx* ctx) { return ctx ? ctx->launch : 0; }
+
+airpf_status airpf_tiling(const airpf_ctx* ctx, int32_t* threads_per_island, int32_t* particles_per_thread,
+                          int32_t* islands_per_cta)
+{
+    if (!ctx || !threads_per_island || !particles_per_thread || !islands_per_cta) return AIRPF_ERR_ARG;
+    *threads_per_island = ctx->sp.tpi;
+    *particles_per_thread = ctx->sp.ppt;
+    *islands_per_cta = ctx->sp.G;
+    return AIRPF_OK;
+}
 
 airpf_status airpf_debug_inject(airpf_ctx* ctx, int32_t what)
 {

@@ -13,8 +13,10 @@ AIRPF_EXTERN_DISPATCH(float, AR1, 2)
 AIRPF_EXTERN_DISPATCH(float, AR1, 4)
 AIRPF_EXTERN_DISPATCH(float, SV, 2)
 AIRPF_EXTERN_DISPATCH(float, SV, 4)
+AIRPF_EXTERN_DISPATCH(float, SV, 8)
 AIRPF_EXTERN_DISPATCH(float, NGM, 2)
 AIRPF_EXTERN_DISPATCH(float, NGM, 4)
+AIRPF_EXTERN_DISPATCH(float, NGM, 8)
 AIRPF_EXTERN_DISPATCH(float, LGSSM, 2)
 AIRPF_EXTERN_DISPATCH(float, LGSSM, 4)
 AIRPF_EXTERN_DISPATCH(float, TOY, 2)
@@ -48,7 +50,7 @@ void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, 
     // (the kernels are compiled for these two); threads per island a multiple of
     // 32 covering M; islands per CTA: the requested count (up to 512 threads; a
     // whole filter when want_g >= m and it fits) or 256 threads' worth
-    int pp = (want_ppt == 2 || want_ppt == 4) ? want_ppt : (M <= 64 ? 2 : 4);
+    int pp = (want_ppt == 2 || want_ppt == 4 || want_ppt == 8) ? want_ppt : (M <= 64 ? 2 : 4);
     int t = 32;
     while (t * pp < M && t < kDefaultThreads) t *= 2;
     if (t * pp < M) {
@@ -73,6 +75,8 @@ static cudaError_t dispatch_model(const StepParams& p, int t, cudaStream_t strea
 {
     if (p.ppt == 2) return dispatch_inst<R, MODEL, 2>(p, t, stream, op, fits);
     if (p.ppt == 4) return dispatch_inst<R, MODEL, 4>(p, t, stream, op, fits);
+    if constexpr (sizeof(R) == 4 && (MODEL == SV || MODEL == NGM))
+        if (p.ppt == 8) return dispatch_inst<R, MODEL, 8>(p, t, stream, op, fits);
     return cudaErrorInvalidValue;
 }
 

@@ -265,9 +265,12 @@ __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontro
 template <typename R, int PPT>
 __device__ __forceinline__ void load_run(const R* src, R* out)
 {
-    if constexpr (sizeof(R) == 4 && PPT == 4) {
-        const float4 v = __ldcg(reinterpret_cast<const float4*>(src));
-        out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    if constexpr (sizeof(R) == 4 && PPT % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < PPT; q += 4) {
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(src) + q / 4);
+            out[q] = v.x; out[q + 1] = v.y; out[q + 2] = v.z; out[q + 3] = v.w;
+        }
     } else if constexpr (sizeof(R) == 4 && PPT == 2) {
         const float2 v = __ldcg(reinterpret_cast<const float2*>(src));
         out[0] = v.x; out[1] = v.y;
@@ -283,8 +286,10 @@ __device__ __forceinline__ void load_run(const R* src, R* out)
 template <typename R, int PPT>
 __device__ __forceinline__ void store_run(R* dst, const R* in)
 {
-    if constexpr (sizeof(R) == 4 && PPT == 4) {
-        *reinterpret_cast<float4*>(dst) = make_float4(in[0], in[1], in[2], in[3]);
+    if constexpr (sizeof(R) == 4 && PPT % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < PPT; q += 4)
+            reinterpret_cast<float4*>(dst)[q / 4] = make_float4(in[q], in[q + 1], in[q + 2], in[q + 3]);
     } else if constexpr (sizeof(R) == 4 && PPT == 2) {
         *reinterpret_cast<float2*>(dst) = make_float2(in[0], in[1]);
     } else {
@@ -2151,9 +2156,9 @@ static cudaError_t launch_dependent(K kernel, dim3 grid, dim3 block, size_t smem
 // for the fused (64-register) and split forms.  The FP64 steps are bound by the FP64
 // pipe, which the compile-time size does not relieve.
 constexpr int kFixedM = 256, kFixedPpt = 4;
-__host__ inline bool fixed_island(const StepParams& p, int M)
+__host__ inline bool fixed_island(const StepParams& p, int M, int ppt = kFixedPpt)
 {
-    return p.M == M && p.tpi == (M / kFixedPpt < 32 ? 32 : M / kFixedPpt);
+    return p.M == M && p.tpi == (M / ppt < 32 ? 32 : M / ppt);
 }
 __host__ inline bool fixed_island(const StepParams& p) { return fixed_island(p, kFixedM); }
 
@@ -2162,7 +2167,10 @@ __host__ inline bool fixed_island(const StepParams& p) { return fixed_island(p, 
 template <typename R, int MODEL, int DX, int PPT, int LV, typename F>
 __host__ bool with_fixed_kernel(const StepParams& p, F&& apply)
 {
-    if constexpr (PPT != kFixedPpt) {
+    if constexpr (PPT == 8) {        // one warp an island of 256
+        if (fixed_island(p, 256, 8)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 256>), true;
+        return false;
+    } else if constexpr (PPT != kFixedPpt) {
         return false;
     } else {
         if (fixed_island(p, 256)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 256>), true;

@@ -42,7 +42,8 @@ def test_workspace_size_and_argument_checks():
     bad = [dict(m=3), dict(m=131072), dict(M=0), dict(M=1025), dict(T=0), dict(B=0), dict(tau=0.0),
            dict(tau=1.01), dict(mode=3), dict(model=9), dict(dx=2), dict(model=3, dx=9),
            dict(precision=7), dict(record=64), dict(launch=5), dict(reserved=1),
-           dict(ppt=3), dict(ppt=8), dict(islands_per_cta=3), dict(islands_per_cta=-2),
+           dict(ppt=3), dict(ppt=16), dict(ppt=8, precision=0), dict(ppt=8, model=0),
+           dict(islands_per_cta=3), dict(islands_per_cta=-2),
            dict(tau_int=-0.1), dict(tau_int=1.5), dict(radix=3), dict(radix=1), dict(radix=8),
            dict(model=5), dict(model=5, dy=1)]
     for kw in bad:

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from parity_util import compare_filter, run_gpu
+from parity_util import compare_filter, compare_first_step, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -205,3 +205,40 @@ def test_fixed_size_fp32_kernels_match_recording_kernel(gpu_lib, M, launch):
     rec = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, record=7, **kw)
     np.testing.assert_array_equal(lean["log_z"], rec["log_z"])
     assert np.all(np.isfinite(lean["log_z"]))
+
+
+@pytest.mark.parametrize("model", [synth.MODEL_NGM, synth.MODEL_SV])
+def test_split_fp32_islands_of_256_take_one_warp(gpu_lib, model):
+    """FP32 split steps of the SV and NGM filters with islands of 256 particles run one warp an
+    island (eight particles a thread, four islands a CTA: the same CTAs and records as four
+    particles a thread).  The lean kernel (M = 256 fixed at compile time) gives the recording
+    kernel's bits; the log Z is the one of four particles a thread; the draws of step 1 agree
+    with the oracle's draw by draw; FP64 and fused steps keep four particles a thread."""
+    import torch
+    import paper_2312_06484_gb300 as gp
+    theta = synth.NGM_THETA if model == synth.MODEL_NGM else synth.SV_THETA
+    y = synth.ngm_observations(8, seed=5) if model == synth.MODEL_NGM else synth.sv_observations(8, 2)
+    m, M = 4096, 256                                 # 1024 CTAs a filter: AUTO splits the step
+    tilings = {}
+    for prec, launch in (("fp32", "auto"), ("fp64", "auto"), ("fp32", "steps")):
+        f = gp.AIRPF(model, m=m, M=M, T=len(y), B=1, mode="adaptive", tau=0.5, precision=prec, seed=3,
+                     launch=launch)
+        tilings[prec, launch] = (f.launch_mode, f.tiling)
+        f.close()
+    assert tilings["fp32", "auto"] == (4, {"threads_per_island": 32, "particles_per_thread": 8, "islands_per_cta": 4})
+    assert tilings["fp64", "auto"][1]["particles_per_thread"] == 4
+    assert tilings["fp32", "steps"][1]["particles_per_thread"] == 4
+    kw = dict(m=m, M=M, B=2, mode="adaptive", tau=0.5, seed=3, precision="fp32")
+    lean = run_gpu(model, theta, y, record=0, **kw)
+    rec = run_gpu(model, theta, y, record=7, **kw)
+    assert lean["launch_mode"] == 4 and rec["launch_mode"] == 4
+    np.testing.assert_array_equal(lean["log_z"], rec["log_z"])
+    four = run_gpu(model, theta, y, record=0, ppt=4, **kw)
+    np.testing.assert_allclose(lean["log_z"], four["log_z"], rtol=1e-12)
+    assert np.all(np.isfinite(lean["log_z"]))
+    g1 = run_gpu(model, theta, y[:1], m=m, M=M, B=2, mode="adaptive", tau=0.5, seed=3, precision="fp32")
+    for b in range(2):
+        o = oracle.airpf(model, theta, y[:1], m=m, M=M, mode=oracle.MODE_ADAPTIVE, tau=0.5, seed=3, chain=b,
+                         tie_rel=1e-5, tie_masks=True)
+        n = compare_first_step(g1, b, o, M=M, what=f"one warp an island, b={b}")
+        assert n >= 0.95 * m * M, (n, m * M)
