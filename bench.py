@@ -62,9 +62,9 @@ def ops_per_particle_step(model: str) -> float:
 # Figures from the committed ncu captures of the kernels named (set to None when the kernel
 # changes, until it is captured again): DRAM read + write per launch, issue-active fraction.
 NCU = {
-    "ngm_island_step": {"dram_bytes_per_launch": 94030080, "issue_active": 0.727,
+    "ngm_island_step": {"dram_bytes_per_launch": 95200768, "issue_active": 0.763,
                         "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, "
-                                  "airpf_step_kernel<float, NGM, 1, 4, false, 2, 256> at steps 5 and 6, caches flushed"},
+                                  "airpf_step_kernel<float, NGM, 1, 8, false, 2, 256> at steps 5 and 6, caches flushed"},
     "sv_fused_step": {"dram_bytes_per_launch": 1156352, "issue_active": 0.397,
                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum (caches flushed) and "
                                 "smsp__issue_active (warm caches, as in a pass), "
@@ -601,7 +601,7 @@ def run_gpu(args) -> None:
     step_us = 1e3 * ms_step / T_OBS           # one time step: the island kernel, the cascade kernel and gaps
     roof = alu_roofline("NGM", N, step_us, sms, peaks, peak_src)
     roof.update({
-        "kernel": "airpf_step_kernel<float, NGM, 1, 4, false, 2, 256> (split step: the island launch, then "
+        "kernel": "airpf_step_kernel<float, NGM, 1, 8, false, 2, 256> (split step: the island launch, then "
                   "airpf_group_cascade_kernel<float, 1>)" if f.launch_mode == 4 else "airpf_step_kernel (one time step)",
         "launch_avg_source": "timed region: pass time / T (a step's island and cascade kernels and the gaps, so "
                              "the island kernel's own fraction is higher by its share of the step)",
