@@ -471,16 +471,20 @@ airpf_status airpf_create(const airpf_config* cfg, void* d_workspace, size_t wor
     // 512 CTAs, where reading all CTA records in every CTA would cost more)
     if (ctx->launch == AIRPF_LAUNCH_AUTO)
         ctx->launch = p.P <= 512 ? AIRPF_LAUNCH_STEPS : AIRPF_LAUNCH_STEPS_SPLIT;
-    // split steps of the FP32 SV and NGM filters with islands of 256 particles: one warp an
-    // island (eight particles a thread, four islands a CTA of 128 threads; the same CTAs, so
-    // the same records and cascade) -- no island-level barriers or shared-memory carries.
-    // Measured on the m = 65536 NGM workload: 155.6 -> 118.2 ms a pass (eight islands a CTA
-    // 128.0, sixteen 147.6).  Fused steps keep four particles a thread (the m = 1024 SV
+    // split steps of the FP32 SV and NGM filters with islands of 256 to 1024 particles: eight
+    // particles a thread (one warp an island of 256, two of 512, four of 1024), four islands
+    // a CTA up to 512 particles -- fewer island-level barriers and shared-memory carries, and a
+    // thread's fixed costs spread over twice the particles.  Measured on the m = 65536 NGM
+    // workload: M = 256 155.6 -> 118.2 ms a pass (CTAs of 4 islands; 8 islands 128.0, 16
+    // 147.6), M = 512 290.2 -> 224.0 (4 islands; 2 islands 303.6), M = 1024 576.8 -> 438.0
+    // (the default 2 islands).  Fused steps keep four particles a thread (the m = 1024 SV
     // workload: 4.6 against 5.8-6.0 ms).
-    if (ctx->launch == AIRPF_LAUNCH_STEPS_SPLIT && !p.fp64 && cfg->M == 256 && cfg->ppt == 0 &&
-        cfg->islands_per_cta == 0 && (cfg->model == AIRPF_MODEL_SV || cfg->model == AIRPF_MODEL_NGM) &&
-        p.G == 4) {
-        airpf::choose_mapping(cfg->m, cfg->M, p.fp64, 8, 4, &p.tpi, &p.ppt, &p.G);
+    if (ctx->launch == AIRPF_LAUNCH_STEPS_SPLIT && !p.fp64 && cfg->ppt == 0 && cfg->islands_per_cta == 0 &&
+        (cfg->M == 256 || cfg->M == 512 || cfg->M == 1024) &&
+        (cfg->model == AIRPF_MODEL_SV || cfg->model == AIRPF_MODEL_NGM)) {
+        airpf::choose_mapping(cfg->m, cfg->M, p.fp64, 8, cfg->M <= 512 ? 4 : 0, &p.tpi, &p.ppt, &p.G);
+        p.P = cfg->m / p.G;
+        p.g = ilog2_exact(p.G);
         p.lg_tpi = ilog2_exact(p.tpi);
     }
     // (split steps keep the default 256-thread CTAs: on the m = 65536 workload they beat

@@ -205,7 +205,10 @@ airpf_status airpf_autotune(const airpf_config* cfg, void* d_workspace, size_t w
         seen.push_back(key);
         cands.push_back({launch, ppt, want_g});
     };
-    for (int ppt : {2, 4}) {
+    // eight particles a thread: compiled for the FP32 SV and NGM filters, islands of 256 or more
+    const bool ppt8 = !fp64 && cfg->M >= 256 && (cfg->model == AIRPF_MODEL_SV || cfg->model == AIRPF_MODEL_NGM);
+    for (int ppt : {2, 4, 8}) {
+        if (ppt == 8 && !ppt8) continue;
         add(AIRPF_LAUNCH_PERSISTENT_CTA, ppt, cfg->m);
         for (int want_g = 1; want_g <= 16 && want_g <= cfg->m; want_g *= 2) {
             add(AIRPF_LAUNCH_STEPS, ppt, want_g);

@@ -2167,8 +2167,12 @@ __host__ inline bool fixed_island(const StepParams& p) { return fixed_island(p, 
 template <typename R, int MODEL, int DX, int PPT, int LV, typename F>
 __host__ bool with_fixed_kernel(const StepParams& p, F&& apply)
 {
-    if constexpr (PPT == 8) {        // one warp an island of 256
+    if constexpr (PPT == 8) {        // one warp an island of 256 (two and four warps for 512, 1024)
         if (fixed_island(p, 256, 8)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 256>), true;
+        if constexpr (LV != 3) {
+            if (fixed_island(p, 512, 8)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 512>), true;
+            if (fixed_island(p, 1024, 8)) return apply(airpf_step_kernel<R, MODEL, DX, PPT, false, LV, 1024>), true;
+        }
         return false;
     } else if constexpr (PPT != kFixedPpt) {
         return false;

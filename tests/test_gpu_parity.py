@@ -191,20 +191,28 @@ def test_lean_passes_match_oracle(gpu_lib, launch, B):
     np.testing.assert_array_equal(f32_many["log_z"], f32_rec["log_z"])
 
 
-@pytest.mark.parametrize("M,launch", [(M, l) for M in (128, 512, 1024) for l in ("steps", "split")])
-def test_fixed_size_fp32_kernels_match_recording_kernel(gpu_lib, M, launch):
-    """FP32 islands of 128, 512 and 1024 particles run lean kernels with the island size fixed
-    at compile time (fused steps with 64 registers, split steps): the same log Z, bit for bit,
-    as the recording kernel, whose island size is read at run time."""
+@pytest.mark.parametrize("M,launch,ppt", [(M, l, 0) for M in (128, 512, 1024) for l in ("steps", "split")] +
+                         [(M, l, 8) for M in (256, 512, 1024) for l in ("steps", "split")])
+def test_fixed_size_fp32_kernels_match_recording_kernel(gpu_lib, M, launch, ppt):
+    """FP32 islands of 128, 512 and 1024 particles (and 256 to 1024 at eight particles a
+    thread) run lean kernels with the island size fixed at compile time (fused steps with 64
+    registers, split steps): the same log Z, bit for bit, as the recording kernel, whose island
+    size is read at run time; at eight particles a thread also the log Z of four."""
     y = synth.ngm_observations(8, seed=5)
     m = 64
     ctas = m * max(32, M // 4) // 256          # CTAs a filter (256-thread CTAs)
     B = 2 if launch == "split" else -(-320 // ctas)   # enough CTAs that the fused grid is not one wave
     kw = dict(m=m, M=M, B=B, mode="adaptive", tau=0.5, seed=3, launch=launch, precision="fp32")
+    if ppt:
+        kw["ppt"] = ppt
     lean = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, record=0, **kw)
     rec = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, record=7, **kw)
     np.testing.assert_array_equal(lean["log_z"], rec["log_z"])
     assert np.all(np.isfinite(lean["log_z"]))
+    if ppt:
+        kw["ppt"] = 4
+        four = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, record=0, **kw)
+        np.testing.assert_allclose(lean["log_z"], four["log_z"], rtol=1e-12)
 
 
 @pytest.mark.parametrize("model", [synth.MODEL_NGM, synth.MODEL_SV])
