@@ -250,3 +250,20 @@ def test_split_fp32_islands_of_256_take_one_warp(gpu_lib, model):
                          tie_rel=1e-5, tie_masks=True)
         n = compare_first_step(g1, b, o, M=M, what=f"one warp an island, b={b}")
         assert n >= 0.95 * m * M, (n, m * M)
+
+
+@pytest.mark.parametrize("tau_int,radix", [(0.5, 2), (0.0, 4), (0.5, 4)])
+def test_eight_particles_a_thread_with_internal_resampling_and_radix(gpu_lib, tau_int, radix):
+    """Adaptive internal resampling (carried log-weights) and radix-4 interactions on the FP32
+    split steps that take eight particles a thread (NGM, islands of 256): the same log Z as
+    four particles a thread, and the lean kernel's equal to the recording kernel's."""
+    y = synth.ngm_observations(10, seed=5)
+    kw = dict(m=4096, M=256, B=2, mode="adaptive", tau=0.5, seed=5, precision="fp32", tau_int=tau_int,
+              radix=radix)
+    eight = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, record=0, **kw)
+    rec = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, record=7, **kw)
+    four = run_gpu(synth.MODEL_NGM, synth.NGM_THETA, y, record=0, ppt=4, **kw)
+    assert eight["launch_mode"] == 4
+    np.testing.assert_array_equal(eight["log_z"], rec["log_z"])
+    np.testing.assert_allclose(eight["log_z"], four["log_z"], rtol=1e-12)
+    assert np.all(np.isfinite(eight["log_z"]))
