@@ -267,3 +267,17 @@ def test_eight_particles_a_thread_with_internal_resampling_and_radix(gpu_lib, ta
     np.testing.assert_array_equal(eight["log_z"], rec["log_z"])
     np.testing.assert_allclose(eight["log_z"], four["log_z"], rtol=1e-12)
     assert np.all(np.isfinite(eight["log_z"]))
+
+
+@pytest.mark.parametrize("launch", ["cta", "grid", "steps", "split"])
+@pytest.mark.parametrize("M", [256, 200])
+def test_eight_particles_a_thread_in_every_launch_form(gpu_lib, launch, M):
+    """Eight particles a thread (which the batch autotuner may pick for FP32 SV filters) in
+    every launch form, with islands of 256 (one warp) and of 200 (a ragged island: the last
+    lanes idle, the CDF rows swizzled): the log Z of four particles a thread."""
+    y = synth.sv_observations(12, seed=2)
+    kw = dict(m=8, M=M, B=3, mode="adaptive", tau=0.8, seed=13, precision="fp32", launch=launch)
+    eight = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, record=0, ppt=8, **kw)
+    four = run_gpu(synth.MODEL_SV, synth.SV_THETA, y, record=0, ppt=4, **kw)
+    np.testing.assert_allclose(eight["log_z"], four["log_z"], rtol=1e-12)
+    assert np.all(np.isfinite(eight["log_z"]))
