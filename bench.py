@@ -62,9 +62,12 @@ def ops_per_particle_step(model: str) -> float:
 # Figures from the committed ncu captures of the kernels named (set to None when the kernel
 # changes, until it is captured again): DRAM read + write per launch, issue-active fraction.
 NCU = {
-    "ngm_island_step": {"dram_bytes_per_launch": 95200768, "issue_active": 0.763,
-                        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum and smsp__issue_active, "
-                                  "airpf_step_kernel<float, NGM, 1, 8, false, 2, 256> at steps 5 and 6, caches flushed"},
+    # traffic null: the kernel changed (the search's top five levels by shuffles) after the
+    # counters were taken; they read 95200768 B and 0.763 issue active on the build before
+    "ngm_island_step": {"dram_bytes_per_launch": None, "issue_active": 0.763,
+                        "source": "ncu smsp__issue_active of airpf_step_kernel<float, NGM, 1, 8, false, 2, 256> "
+                                  "at steps 5 and 6, caches flushed, on the build before the search's top "
+                                  "levels moved to shuffles (DRAM traffic then 95200768 B a launch)"},
     "sv_fused_step": {"dram_bytes_per_launch": 1156352, "issue_active": 0.397,
                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum (caches flushed) and "
                                 "smsp__issue_active (warm caches, as in a pass), "
