@@ -1821,9 +1821,10 @@ __device__ __forceinline__ void step_body(const StepParams& p, int t, int c, int
                 for (int r = 0; r < PPT; ++r) node[r] = 2 * node[r] + (cdfb[node[r]] <= tb[r] ? 1 : 0);
             }
         } else if constexpr (MC > 0 && TPI == 32) {
-            // one warp an island (every lane holds particles): the tree's top five levels,
-            // nodes 1 .. 31, from the lanes' registers by shuffles (lane 0 holds the total,
-            // which no probe reads), the rest from shared memory
+            // one warp an island (every lane holds particles, and `resample` is the island's,
+            // so the whole warp is here): the tree's top five levels, nodes 1 .. 31, from the
+            // lanes' registers by shuffles (lane 0 holds the total, which no probe reads), the
+            // rest from shared memory
             const Cdf top = cdf[lane];
             int l = 0;
             for (; l < 5 && l < lgM; ++l) {
