@@ -45,11 +45,11 @@ size_t model_par_bytes() { return sizeof(ModelPar<double>); }
 void choose_mapping(int m, int M, int fp64, int want_ppt, int want_g, int* tpi, int* ppt, int* G)
 {
     (void)fp64;
-    // particles per thread: requested (2 or 4), else 2 up to M = 64 (one warp per
-    // island) and 4 above (measured fastest at M = 256: fewer threads per island)
-    // (the kernels are compiled for these two); threads per island a multiple of
-    // 32 covering M; islands per CTA: the requested count (up to 512 threads; a
-    // whole filter when want_g >= m and it fits) or 256 threads' worth
+    // particles per thread: requested (2, 4, or 8, compiled for the FP32 SV and NGM
+    // filters only; airpf_create asks for 8 on their split steps), else 2 up to M = 64
+    // (one warp per island) and 4 above (measured fastest for fused steps at M = 256);
+    // threads per island a multiple of 32 covering M; islands per CTA: the requested count
+    // (up to 512 threads; a whole filter when want_g >= m and it fits) or 256 threads' worth
     int pp = (want_ppt == 2 || want_ppt == 4 || want_ppt == 8) ? want_ppt : (M <= 64 ? 2 : 4);
     int t = 32;
     while (t * pp < M && t < kDefaultThreads) t *= 2;
